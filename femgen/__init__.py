@@ -1,0 +1,198 @@
+"""Seeded synthetic FEM inputs: stiffness matrices of jittered P1 tetrahedral
+meshes with high-contrast box inclusions, the stand-in for the paper's
+electrical-machine matrix (Section III: a 30 880-row SPD matrix with 449 798
+non-zeros, about 14.6 per row).
+
+This module produces inputs only.  It holds none of the solver's arithmetic
+(no sparse products, no conjugate-gradient steps) and is shared by the CPU
+oracle, the tests and the benchmark; it imports neither of them.
+
+The C source (``femgen.c``) is compiled on first use with ``gcc`` into
+``_femgen.so`` next to this file (``build()`` does it explicitly).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass, replace
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "femgen.c")
+_SO = os.path.join(_HERE, "_femgen.so")
+_lib = None
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+        ("n_incl", ctypes.c_int32), ("dirichlet", ctypes.c_int32), ("pad_", ctypes.c_int32),
+        ("jitter", ctypes.c_double), ("contrast", ctypes.c_double),
+        ("seed_mesh", ctypes.c_uint64), ("seed_x", ctypes.c_uint64),
+    ]
+
+
+@dataclass(frozen=True)
+class Grid:
+    """One synthetic system: node grid, inclusions, contrast and seeds."""
+    nx: int
+    ny: int
+    nz: int
+    n_incl: int = 1
+    contrast: float = 1000.0
+    jitter: float = 0.2
+    seed_mesh: int = 0
+    seed_x: int = 1
+    dirichlet: bool = True
+
+    def params(self) -> Params:
+        return Params(self.nx, self.ny, self.nz, self.n_incl, 1 if self.dirichlet else 0, 0,
+                      float(self.jitter), float(self.contrast), int(self.seed_mesh), int(self.seed_x))
+
+
+# Workloads shaped like the paper's (Section III) at the sizes the benchmark uses.
+PAPER_SIZE = Grid(31, 31, 32)                               # ~25K rows, the paper's scale
+LARGE = Grid(128, 128, 128)                                  # ~2.0M rows, ~29.6M nnz
+DIFF = Grid(64, 64, 64)                                      # ~238K rows
+LARGEST = Grid(256, 256, 256, n_incl=4)                      # ~16.4M rows, ~244M nnz
+
+
+def batched_instances(count: int = 256, seed: int = 0):
+    """Uneven batch: grid edges uniform in [12, 40] per axis, contrast
+    log-uniform in [10, 1e4], seeds derived from the instance id."""
+    lib = _load()
+    out = []
+    for i in range(count):
+        u = [lib.femgen_uniform(ctypes.c_uint64(seed + 1000003), ctypes.c_uint64(4 * i + d)) for d in range(4)]
+        nx, ny, nz = (12 + min(28, int(v * 29)) for v in u[:3])
+        contrast = float(10.0 ** (1.0 + 3.0 * u[3]))
+        out.append(Grid(nx, ny, nz, n_incl=1, contrast=contrast, seed_mesh=2 * i, seed_x=2 * i + 1))
+    return out
+
+
+def _compile(dst: str = _SO) -> str:
+    flags = ["gcc", "-O2", "-fPIC", "-shared", "-ffp-contract=off", "-std=c11"]
+    try:
+        subprocess.run(flags + ["-fopenmp", _SRC, "-o", dst, "-lm"], check=True,
+                       capture_output=True)
+    except subprocess.CalledProcessError:
+        subprocess.run(flags + [_SRC, "-o", dst, "-lm"], check=True)
+    return dst
+
+
+def build() -> str:
+    """Compile the generator (idempotent when the library is newer than the source)."""
+    if not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        _compile()
+    return _SO
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_SO)
+        P = ctypes.POINTER(Params)
+        i64p = ctypes.POINTER(ctypes.c_int64)
+        vp = ctypes.c_void_p
+        lib.femgen_size.argtypes = [P, i64p, i64p]
+        lib.femgen_build.argtypes = [P, vp, vp, vp, vp, vp]
+        lib.femgen_boxes.argtypes = [P, vp]
+        lib.femgen_min_volume.argtypes = [P]
+        lib.femgen_min_volume.restype = ctypes.c_double
+        lib.femgen_count_inclusion_tets.argtypes = [P]
+        lib.femgen_count_inclusion_tets.restype = ctypes.c_int64
+        lib.femgen_upper.argtypes = [ctypes.c_int64, vp, vp, vp, vp, vp, vp]
+        lib.femgen_uniform.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
+        lib.femgen_uniform.restype = ctypes.c_double
+        _lib = lib
+    return _lib
+
+
+def _ptr(a: np.ndarray | None):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def size(g: Grid) -> tuple[int, int]:
+    lib = _load()
+    n, nnz = ctypes.c_int64(), ctypes.c_int64()
+    if lib.femgen_size(ctypes.byref(g.params()), ctypes.byref(n), ctypes.byref(nnz)):
+        raise ValueError(f"invalid grid {g}")
+    return n.value, nnz.value
+
+
+@dataclass
+class System:
+    """A generated SPD system in full CSR (0-based, sorted columns)."""
+    grid: Grid
+    n: int
+    ptr: np.ndarray     # int32[n+1]
+    idx: np.ndarray     # int32[nnz]
+    val: np.ndarray     # float64[nnz]
+    b: np.ndarray       # float64[n], element-assembled A @ xstar
+    xstar: np.ndarray   # float64[n], U(-1, 1)
+
+    @property
+    def nnz(self) -> int:
+        return int(self.idx.shape[0])
+
+    def upper(self):
+        """(ptr, idx, val) of the stored upper triangle, diagonal included."""
+        return upper(self.n, self.ptr, self.idx, self.val)
+
+    def csc(self):
+        """(colptr, rowidx, val) of the same matrix in CSC.  The matrix is
+        exactly symmetric, so its CSC arrays are its CSR arrays."""
+        return self.ptr, self.idx, self.val
+
+
+def build_system(g: Grid) -> System:
+    lib = _load()
+    n, nnz = size(g)
+    ptr = np.empty(n + 1, dtype=np.int32)
+    idx = np.empty(nnz, dtype=np.int32)
+    val = np.empty(nnz, dtype=np.float64)
+    b = np.empty(n, dtype=np.float64)
+    xs = np.empty(n, dtype=np.float64)
+    rc = lib.femgen_build(ctypes.byref(g.params()), _ptr(ptr), _ptr(idx), _ptr(val), _ptr(b), _ptr(xs))
+    if rc:
+        raise ValueError(f"femgen_build failed ({rc}) for {g}")
+    return System(g, n, ptr, idx, val, b, xs)
+
+
+def upper(n: int, ptr: np.ndarray, idx: np.ndarray, val: np.ndarray):
+    """Upper triangle (j >= i) of a sorted-column CSR matrix: index selection only."""
+    lib = _load()
+    uptr = np.empty(n + 1, dtype=np.int32)
+    lib.femgen_upper(n, _ptr(ptr), _ptr(idx), _ptr(val), _ptr(uptr), None, None)
+    m = int(uptr[-1])
+    uidx = np.empty(m, dtype=np.int32)
+    uval = np.empty(m, dtype=np.float64)
+    lib.femgen_upper(n, _ptr(ptr), _ptr(idx), _ptr(val), _ptr(uptr), _ptr(uidx), _ptr(uval))
+    return uptr, uidx, uval
+
+
+def boxes(g: Grid) -> np.ndarray:
+    lib = _load()
+    out = np.empty((max(g.n_incl, 1), 6), dtype=np.float64)
+    lib.femgen_boxes(ctypes.byref(g.params()), _ptr(out))
+    return out[: g.n_incl]
+
+
+def min_volume(g: Grid) -> float:
+    return float(_load().femgen_min_volume(ctypes.byref(g.params())))
+
+
+def inclusion_tets(g: Grid) -> int:
+    return int(_load().femgen_count_inclusion_tets(ctypes.byref(g.params())))
+
+
+def uniform(seed: int, counter: int) -> float:
+    return float(_load().femgen_uniform(ctypes.c_uint64(seed), ctypes.c_uint64(counter)))
+
+
+def random_vector(n: int, seed: int, lo: float = -1.0, hi: float = 1.0) -> np.ndarray:
+    """Seeded U(lo, hi) vector (numpy's PCG64, seeded; inputs only)."""
+    return np.random.default_rng(seed).uniform(lo, hi, size=n)

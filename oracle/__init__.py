@@ -1,0 +1,216 @@
+"""CPU oracle for the sparse conjugate-gradient solver -- TEST INFRASTRUCTURE.
+
+Only the tests, the smoke check and the benchmark's CPU-baseline leg load this
+package; the library never does.  It wraps ``oracle.c`` (plain C, IEEE double,
+compiled with ``-ffp-contract=off``), which restates the paper's CG listing
+(Section III), its symmetric-storage product (A = L + D + U with U' = L,
+Section III) and its single-precision variant (Section IV).  It shares no code
+with the CUDA path.
+
+Parity status per function (what pins it; see ``tests/test_oracle_pins.py``):
+  spmv (CSR, symmetric upper, CSC)  -- dense brute force, format equivalence
+  cg                                  -- dense Cholesky, finite termination,
+                                         A-orthogonality, A-norm monotonicity,
+                                         closed-form diagonal/tridiagonal cases
+  cg_f32 / cg_ir                      -- true residual in double, error vs x*
+  dot_long                            -- exact rational arithmetic
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_SO = os.path.join(_HERE, "_oracle.so")
+_lib = None
+
+CSR, SYM_UPPER, CSC = 0, 1, 2
+FORMATS = {"csr": CSR, "sym": SYM_UPPER, "sym_upper": SYM_UPPER, "csc": CSC}
+STATUS = {0: "OK", 1: "INVALID", 2: "NOT_SPD", 3: "MAXIT", 4: "NONFINITE"}
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("restarts", ctypes.c_int32),
+                ("status", ctypes.c_int32), ("pad_", ctypes.c_int32),
+                ("rel_res_recursive", ctypes.c_double), ("rel_res_true", ctypes.c_double)]
+
+
+class History(ctypes.Structure):
+    _fields_ = [("cap", ctypes.c_int32), ("count", ctypes.c_int32),
+                ("p", ctypes.c_void_p), ("x", ctypes.c_void_p),
+                ("alpha", ctypes.c_void_p), ("beta", ctypes.c_void_p)]
+
+
+def compile_oracle(src: str = _SRC, dst: str = _SO) -> str:
+    subprocess.run(["gcc", "-O2", "-fPIC", "-shared", "-ffp-contract=off", "-std=c11",
+                    src, "-o", dst, "-lm"], check=True)
+    return dst
+
+
+def build() -> str:
+    if not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        compile_oracle()
+    return _SO
+
+
+def load(path: str | None = None):
+    """Load the oracle library (``path`` lets tests load a deliberately broken copy)."""
+    global _lib
+    if path is None and _lib is not None:
+        return _lib
+    so = path or build()
+    lib = ctypes.CDLL(so)
+    vp, i64, i32, d = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
+    for name in ("orc_spmv_csr", "orc_spmv_sym_upper", "orc_spmv_csc"):
+        getattr(lib, name).argtypes = [i64, vp, vp, vp, vp, vp]
+    lib.orc_spmv.argtypes = [ctypes.c_int, i64, vp, vp, vp, vp, vp]
+    lib.orc_spmv_f32.argtypes = [ctypes.c_int, i64, vp, vp, vp, vp, vp]
+    lib.orc_abs_spmv.argtypes = [ctypes.c_int, i64, vp, vp, vp, vp, vp]
+    lib.orc_dot.argtypes = [i64, vp, vp]
+    lib.orc_dot.restype = d
+    lib.orc_dot_long.argtypes = [i64, vp, vp]
+    lib.orc_dot_long.restype = d
+    lib.orc_cg.argtypes = [ctypes.c_int, i64, vp, vp, vp, vp, vp, d, i32,
+                           ctypes.POINTER(Info), ctypes.POINTER(History)]
+    lib.orc_cg_f32.argtypes = [ctypes.c_int, i64, vp, vp, vp, vp, vp, ctypes.c_float, i32,
+                               ctypes.POINTER(i32)]
+    lib.orc_cg_f32.restype = i32
+    lib.orc_cg_ir.argtypes = [ctypes.c_int, i64, vp, vp, vp, vp, vp, d, i32, d, i32,
+                              ctypes.POINTER(Info)]
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _fmt(fmt) -> int:
+    return FORMATS[fmt] if isinstance(fmt, str) else int(fmt)
+
+
+def _arrays(ptr, idx, val, vdtype=np.float64):
+    return (np.ascontiguousarray(ptr, dtype=np.int32), np.ascontiguousarray(idx, dtype=np.int32),
+            np.ascontiguousarray(val, dtype=vdtype))
+
+
+def spmv(fmt, ptr, idx, val, x, lib=None) -> np.ndarray:
+    """y = A x for A given as CSR, symmetric upper (D + U by rows) or CSC."""
+    lib = lib or load()
+    ptr, idx, val = _arrays(ptr, idx, val)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    n = ptr.shape[0] - 1
+    y = np.empty(n, dtype=np.float64)
+    lib.orc_spmv(_fmt(fmt), n, _p(ptr), _p(idx), _p(val), _p(x), _p(y))
+    return y
+
+
+def spmv_f32(fmt, ptr, idx, val32, x32, lib=None) -> np.ndarray:
+    lib = lib or load()
+    ptr, idx, val32 = _arrays(ptr, idx, val32, np.float32)
+    x32 = np.ascontiguousarray(x32, dtype=np.float32)
+    n = ptr.shape[0] - 1
+    y = np.empty(n, dtype=np.float32)
+    lib.orc_spmv_f32(_fmt(fmt), n, _p(ptr), _p(idx), _p(val32), _p(x32), _p(y))
+    return y
+
+
+def abs_spmv(fmt, ptr, idx, val, x, lib=None) -> np.ndarray:
+    """|A| |x|: the scale of the componentwise rounding bound of y = A x."""
+    lib = lib or load()
+    ptr, idx, val = _arrays(ptr, idx, val)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    n = ptr.shape[0] - 1
+    y = np.empty(n, dtype=np.float64)
+    lib.orc_abs_spmv(_fmt(fmt), n, _p(ptr), _p(idx), _p(val), _p(x), _p(y))
+    return y
+
+
+def dot(a, b, lib=None) -> float:
+    lib = lib or load()
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    return float(lib.orc_dot(a.shape[0], _p(a), _p(b)))
+
+
+def dot_long(a, b, lib=None) -> float:
+    lib = lib or load()
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    return float(lib.orc_dot_long(a.shape[0], _p(a), _p(b)))
+
+
+@dataclass
+class Result:
+    x: np.ndarray
+    iterations: int
+    restarts: int
+    status: str
+    rel_res_recursive: float
+    rel_res_true: float
+    p_hist: np.ndarray | None = None
+    x_hist: np.ndarray | None = None
+    alpha: np.ndarray | None = None
+    beta: np.ndarray | None = None
+
+
+def cg(fmt, ptr, idx, val, b, x0=None, tol=1e-10, maxit=None, history=0, lib=None) -> Result:
+    """Plain double-precision CG (Section III listing; readings in oracle.c)."""
+    lib = lib or load()
+    ptr, idx, val = _arrays(ptr, idx, val)
+    n = ptr.shape[0] - 1
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    x = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
+    maxit = n if maxit is None else int(maxit)
+    info = Info()
+    hist = None
+    ph = xh = al = be = None
+    if history:
+        ph = np.zeros((history, n))
+        xh = np.zeros((history, n))
+        al = np.zeros(history)
+        be = np.zeros(history)
+        hist = History(history, 0, ph.ctypes.data, xh.ctypes.data, al.ctypes.data, be.ctypes.data)
+    lib.orc_cg(_fmt(fmt), n, _p(ptr), _p(idx), _p(val), _p(b), _p(x), float(tol), maxit,
+               ctypes.byref(info), ctypes.byref(hist) if hist is not None else None)
+    res = Result(x, info.iterations, info.restarts, STATUS[info.status], info.rel_res_recursive,
+                 info.rel_res_true)
+    if history:
+        c = hist.count
+        res.p_hist, res.x_hist, res.alpha, res.beta = ph[:c], xh[:c], al[:c], be[:c]
+    return res
+
+
+def cg_f32(fmt, ptr, idx, val32, rhs32, tol, maxit, lib=None):
+    """Single-precision CG from d = 0; returns (d, iterations, breakdown)."""
+    lib = lib or load()
+    ptr, idx, val32 = _arrays(ptr, idx, val32, np.float32)
+    rhs32 = np.ascontiguousarray(rhs32, dtype=np.float32)
+    n = ptr.shape[0] - 1
+    d = np.zeros(n, dtype=np.float32)
+    bd = ctypes.c_int32()
+    it = lib.orc_cg_f32(_fmt(fmt), n, _p(ptr), _p(idx), _p(val32), _p(rhs32), _p(d), float(tol), int(maxit),
+                        ctypes.byref(bd))
+    return d, int(it), bool(bd.value)
+
+
+def cg_ir(fmt, ptr, idx, val, b, x0=None, tol=1e-10, maxit=None, inner_tol=1e-4, max_outer=30,
+          lib=None) -> Result:
+    """Single-precision inner CG with double-precision iterative refinement."""
+    lib = lib or load()
+    ptr, idx, val = _arrays(ptr, idx, val)
+    n = ptr.shape[0] - 1
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    x = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
+    maxit = 10 * max(n, 1) if maxit is None else int(maxit)
+    info = Info()
+    lib.orc_cg_ir(_fmt(fmt), n, _p(ptr), _p(idx), _p(val), _p(b), _p(x), float(tol), maxit,
+                  float(inner_tol), int(max_outer), ctypes.byref(info))
+    return Result(x, info.iterations, info.restarts, STATUS[info.status], info.rel_res_recursive,
+                  info.rel_res_true)

@@ -1,0 +1,333 @@
+/*
+ * oracle.c -- plain, slow, obviously correct CPU implementation of what the
+ * GPU solver computes.  TEST INFRASTRUCTURE ONLY: it is loaded by the tests,
+ * by the smoke check and by the benchmark's CPU-baseline leg, never by the
+ * library.  It shares no code with the CUDA path.
+ *
+ * Everything is IEEE double precision (single precision only where the paper's
+ * single-precision solver is restated), written as the textbook definitions:
+ * no blocking, no fusion, no reordering.  Build with -ffp-contract=off so a
+ * multiply and an add are two roundings on every host.
+ *
+ * Sections of "Parallel Sparse Matrix Solver on the GPU Applied to Simulation
+ * of Electrical Machines" (Rodrigues, Guyomarc'h, Le Menach, Dekeyser):
+ *   - Section III, the CG listing: alpha = r'r / p'Ap; x += alpha p; break on
+ *     convergence; r -= alpha Ap; beta = r_k'r_k / r_{k-1}'r_{k-1};
+ *     p = r + beta p; for 1 <= k <= N.
+ *   - Section III, after the listing: A = L + D + U with U' = L, so A can be
+ *     stored as the triangle L + D; the SCSR kernel applies L + D by rows and
+ *     the SCSC kernel applies U by reading the same arrays as columns.
+ *   - Section III: the "trivial" kernel forms y[row] += A[k] * x[col[k]] over
+ *     the row's stored entries (full CSR).
+ *   - Section IV: a double-precision CPU CG is the reference; a
+ *     single-precision GPU CG is the other variant.
+ *
+ * Readings where the paper is silent (each also listed in the design notes):
+ *   1. "init variables": x0 given (default 0), r0 = b - A x0, p0 = r0.
+ *   2. "convergence": ||r_k||_2 / ||b||_2 <= tol, tested on the updated
+ *      residual right after the r update (one step later than the listing's
+ *      position, which sits between the x and r updates and so could only
+ *      test the previous residual); a solve is declared converged only once
+ *      the true residual ||b - A x||_2 / ||b||_2 <= tol; otherwise the
+ *      recurrence restarts from r = b - A x, p = r (at most 3 restarts).
+ *   3. N (the iteration bound) is the caller's maxit; b = 0 gives x = 0.
+ *   4. Symmetric storage is the upper triangle D + U stored by rows, which
+ *      holds the same numbers as the paper's L + D stored by rows (read as
+ *      columns); entry (i, j), j > i, acts for both (i, j) and (j, i).
+ *   5. Breakdown: p'Ap not finite -> NONFINITE; p'Ap <= 0 -> NOT_SPD.
+ *   6. Single-precision variant: the same recurrence in float (values,
+ *      vectors and dots), used as the inner solver of an iterative-refinement
+ *      loop whose residual b - A x, correction x += ||r|| d and norms are in
+ *      double precision.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+enum { ORC_OK = 0, ORC_INVALID = 1, ORC_NOT_SPD = 2, ORC_MAXIT = 3, ORC_NONFINITE = 4 };
+enum { ORC_CSR = 0, ORC_SYM_UPPER = 1, ORC_CSC = 2 };
+
+typedef struct {
+  int32_t iterations;     /* CG iterations (inner iterations for refinement) */
+  int32_t restarts;       /* residual replacements (outer passes for refinement) */
+  int32_t status;
+  int32_t pad_;
+  double rel_res_recursive;
+  double rel_res_true;
+} orc_info;
+
+/* ------------------------------------------------ sparse products -------- */
+/* Full CSR (the "trivial" kernel of Section III): y_i = sum_k val[k] x[idx[k]]. */
+void orc_spmv_csr(int64_t n, const int32_t* ptr, const int32_t* idx, const double* val, const double* x,
+                  double* y) {
+  for (int64_t i = 0; i < n; ++i) {
+    double s = 0.0;
+    for (int64_t k = ptr[i]; k < ptr[i + 1]; ++k) s += val[k] * x[idx[k]];
+    y[i] = s;
+  }
+}
+
+/* Symmetric storage (Section III, A = L + D + U, U' = L): rows hold D + U.
+ * Entry (i, j) adds a_ij x_j to y_i and, when j > i, a_ij x_i to y_j. */
+void orc_spmv_sym_upper(int64_t n, const int32_t* ptr, const int32_t* idx, const double* val,
+                        const double* x, double* y) {
+  for (int64_t i = 0; i < n; ++i) y[i] = 0.0;
+  for (int64_t i = 0; i < n; ++i) {
+    for (int64_t k = ptr[i]; k < ptr[i + 1]; ++k) {
+      int64_t j = idx[k];
+      y[i] += val[k] * x[j];
+      if (j > i) y[j] += val[k] * x[i];
+    }
+  }
+}
+
+/* Column storage (the SCSC view of Section III): column j holds the entries
+ * a_ij, i = rowidx[k]; y = sum_j a_:j x_j, columns in increasing order. */
+void orc_spmv_csc(int64_t n, const int32_t* colptr, const int32_t* rowidx, const double* val,
+                  const double* x, double* y) {
+  for (int64_t i = 0; i < n; ++i) y[i] = 0.0;
+  for (int64_t j = 0; j < n; ++j)
+    for (int64_t k = colptr[j]; k < colptr[j + 1]; ++k) y[rowidx[k]] += val[k] * x[j];
+}
+
+void orc_spmv(int fmt, int64_t n, const int32_t* ptr, const int32_t* idx, const double* val, const double* x,
+              double* y) {
+  if (fmt == ORC_SYM_UPPER)
+    orc_spmv_sym_upper(n, ptr, idx, val, x, y);
+  else if (fmt == ORC_CSC)
+    orc_spmv_csc(n, ptr, idx, val, x, y);
+  else
+    orc_spmv_csr(n, ptr, idx, val, x, y);
+}
+
+/* Same products in single precision (values and vectors float). */
+void orc_spmv_f32(int fmt, int64_t n, const int32_t* ptr, const int32_t* idx, const float* val, const float* x,
+                  float* y) {
+  if (fmt == ORC_CSR) {
+    for (int64_t i = 0; i < n; ++i) {
+      float s = 0.0f;
+      for (int64_t k = ptr[i]; k < ptr[i + 1]; ++k) s += val[k] * x[idx[k]];
+      y[i] = s;
+    }
+    return;
+  }
+  for (int64_t i = 0; i < n; ++i) y[i] = 0.0f;
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t k = ptr[i]; k < ptr[i + 1]; ++k) {
+      int64_t j = idx[k];
+      if (fmt == ORC_CSC) {
+        y[j] += val[k] * x[i];
+      } else {
+        y[i] += val[k] * x[j];
+        if (j > i) y[j] += val[k] * x[i];
+      }
+    }
+}
+
+/* |A| |x| row by row: the scale of the componentwise rounding bound of a
+ * product (used by the tests as the denominator of the SpMV tolerance). */
+void orc_abs_spmv(int fmt, int64_t n, const int32_t* ptr, const int32_t* idx, const double* val, const double* x,
+                  double* y) {
+  for (int64_t i = 0; i < n; ++i) y[i] = 0.0;
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t k = ptr[i]; k < ptr[i + 1]; ++k) {
+      int64_t j = idx[k];
+      double a = fabs(val[k]);
+      if (fmt == ORC_CSC) {
+        y[j] += a * fabs(x[i]);
+      } else {
+        y[i] += a * fabs(x[j]);
+        if (fmt == ORC_SYM_UPPER && j > i) y[j] += a * fabs(x[i]);
+      }
+    }
+}
+
+/* ------------------------------------------------ vector kernels --------- */
+double orc_dot(int64_t n, const double* a, const double* b) {
+  double s = 0.0;
+  for (int64_t i = 0; i < n; ++i) s += a[i] * b[i];
+  return s;
+}
+
+/* Dot product accumulated in long double: a checker for the GPU reductions. */
+double orc_dot_long(int64_t n, const double* a, const double* b) {
+  long double s = 0.0L;
+  for (int64_t i = 0; i < n; ++i) s += (long double)a[i] * (long double)b[i];
+  return (double)s;
+}
+
+static float dot_f(int64_t n, const float* a, const float* b) {
+  float s = 0.0f;
+  for (int64_t i = 0; i < n; ++i) s += a[i] * b[i];
+  return s;
+}
+
+/* ------------------------------------------------ conjugate gradient ----- */
+/* History buffers (may be NULL): for k = 0..hist_cap-1 the search direction
+ * p_k and the iterate x_{k+1}, n values each; alpha/beta per iteration. */
+typedef struct {
+  int32_t cap;
+  int32_t count;
+  double* p;
+  double* x;
+  double* alpha;
+  double* beta;
+} orc_history;
+
+int orc_cg(int fmt, int64_t n, const int32_t* ptr, const int32_t* idx, const double* val, const double* b,
+           double* x, double tol, int32_t maxit, orc_info* info, orc_history* hist) {
+  memset(info, 0, sizeof(*info));
+  if (n < 0 || maxit < 0 || !(tol >= 0.0)) {
+    info->status = ORC_INVALID;
+    return ORC_INVALID;
+  }
+  double* r = (double*)malloc(sizeof(double) * (size_t)(n ? n : 1));
+  double* p = (double*)malloc(sizeof(double) * (size_t)(n ? n : 1));
+  double* q = (double*)malloc(sizeof(double) * (size_t)(n ? n : 1));
+  if (hist) hist->count = 0;
+  int status = ORC_OK;
+  int32_t k = 0, restarts = 0;
+  double nb = sqrt(orc_dot(n, b, b));
+  double rr = 0.0;
+  if (nb == 0.0) {
+    for (int64_t i = 0; i < n; ++i) x[i] = 0.0;
+    goto done;
+  }
+  /* reading 1: r0 = b - A x0, p0 = r0 */
+  orc_spmv(fmt, n, ptr, idx, val, x, q);
+  for (int64_t i = 0; i < n; ++i) r[i] = b[i] - q[i];
+  for (int64_t i = 0; i < n; ++i) p[i] = r[i];
+  rr = orc_dot(n, r, r);
+  for (;;) {
+    while (k < maxit && !(sqrt(rr) / nb <= tol)) {
+      orc_spmv(fmt, n, ptr, idx, val, p, q);         /* A p */
+      double pq = orc_dot(n, p, q);                  /* p' A p */
+      if (!isfinite(pq)) { status = ORC_NONFINITE; goto done; }
+      if (!(pq > 0.0)) { status = ORC_NOT_SPD; goto done; }
+      double alpha = rr / pq;                        /* alpha = r'r / p'Ap */
+      for (int64_t i = 0; i < n; ++i) x[i] += alpha * p[i];   /* x += alpha p */
+      for (int64_t i = 0; i < n; ++i) r[i] -= alpha * q[i];   /* r -= alpha A p */
+      double rr_new = orc_dot(n, r, r);
+      ++k;
+      double beta = rr_new / rr;                     /* beta = r_k'r_k / r_{k-1}'r_{k-1} */
+      if (hist && hist->count < hist->cap) {
+        int32_t h = hist->count++;
+        if (hist->p) memcpy(hist->p + (size_t)h * n, p, sizeof(double) * n);
+        if (hist->x) memcpy(hist->x + (size_t)h * n, x, sizeof(double) * n);
+        if (hist->alpha) hist->alpha[h] = alpha;
+        if (hist->beta) hist->beta[h] = beta;
+      }
+      rr = rr_new;
+      if (!isfinite(rr)) { status = ORC_NONFINITE; goto done; }
+      if (sqrt(rr) / nb <= tol) break;               /* reading 2: test after the r update */
+      for (int64_t i = 0; i < n; ++i) p[i] = r[i] + beta * p[i];  /* p = r + beta p */
+    }
+    /* reading 2: confirm with the true residual; restart from it otherwise */
+    orc_spmv(fmt, n, ptr, idx, val, x, q);
+    for (int64_t i = 0; i < n; ++i) r[i] = b[i] - q[i];
+    double rt = orc_dot(n, r, r);
+    info->rel_res_true = sqrt(rt) / nb;
+    if (info->rel_res_true <= tol) break;
+    if (k >= maxit || restarts >= 3) { status = ORC_MAXIT; break; }
+    ++restarts;
+    for (int64_t i = 0; i < n; ++i) p[i] = r[i];
+    rr = rt;
+  }
+done:
+  info->iterations = k;
+  info->restarts = restarts;
+  info->status = status;
+  info->rel_res_recursive = nb > 0.0 ? sqrt(rr) / nb : 0.0;
+  if (status != ORC_OK && status != ORC_MAXIT) info->rel_res_true = NAN;
+  if (nb == 0.0) info->rel_res_true = 0.0;
+  free(r);
+  free(p);
+  free(q);
+  return status;
+}
+
+/* Single-precision CG (Section IV's single-precision variant): solves
+ * A32 d = rhs from d = 0 until ||r|| <= tol ||rhs|| or maxit; float
+ * throughout.  Returns iterations used; *breakdown set on p'Ap <= 0. */
+int32_t orc_cg_f32(int fmt, int64_t n, const int32_t* ptr, const int32_t* idx, const float* val, const float* rhs,
+                   float* d, float tol, int32_t maxit, int32_t* breakdown) {
+  float* r = (float*)malloc(sizeof(float) * (size_t)(n ? n : 1));
+  float* p = (float*)malloc(sizeof(float) * (size_t)(n ? n : 1));
+  float* q = (float*)malloc(sizeof(float) * (size_t)(n ? n : 1));
+  *breakdown = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    d[i] = 0.0f;
+    r[i] = rhs[i];
+    p[i] = rhs[i];
+  }
+  float nr0 = sqrtf(dot_f(n, rhs, rhs));
+  float rr = nr0 * nr0;
+  int32_t k = 0;
+  while (k < maxit && nr0 > 0.0f && !(sqrtf(rr) <= tol * nr0)) {
+    orc_spmv_f32(fmt, n, ptr, idx, val, p, q);
+    float pq = dot_f(n, p, q);
+    if (!(pq > 0.0f) || !isfinite(pq)) { *breakdown = 1; break; }
+    float alpha = rr / pq;
+    for (int64_t i = 0; i < n; ++i) d[i] += alpha * p[i];
+    for (int64_t i = 0; i < n; ++i) r[i] -= alpha * q[i];
+    float rr_new = dot_f(n, r, r);
+    ++k;
+    if (sqrtf(rr_new) <= tol * nr0) break;
+    float beta = rr_new / rr;
+    rr = rr_new;
+    for (int64_t i = 0; i < n; ++i) p[i] = r[i] + beta * p[i];
+  }
+  free(r);
+  free(p);
+  free(q);
+  return k;
+}
+
+/* Mixed precision by iterative refinement: outer residual, norms and the
+ * correction in double precision; inner solve A32 d = r / ||r|| in float.
+ * maxit bounds the total inner iterations, max_outer the refinement passes. */
+int orc_cg_ir(int fmt, int64_t n, const int32_t* ptr, const int32_t* idx, const double* val, const double* b,
+              double* x, double tol, int32_t maxit, double inner_tol, int32_t max_outer, orc_info* info) {
+  memset(info, 0, sizeof(*info));
+  int64_t nnz = n > 0 ? ptr[n] : 0;
+  float* v32 = (float*)malloc(sizeof(float) * (size_t)(nnz ? nnz : 1));
+  float* rs = (float*)malloc(sizeof(float) * (size_t)(n ? n : 1));
+  float* d = (float*)malloc(sizeof(float) * (size_t)(n ? n : 1));
+  double* r = (double*)malloc(sizeof(double) * (size_t)(n ? n : 1));
+  for (int64_t k = 0; k < nnz; ++k) v32[k] = (float)val[k];
+  int status = ORC_MAXIT;
+  int32_t used = 0, outer = 0;
+  double nb = sqrt(orc_dot(n, b, b));
+  if (nb == 0.0) {
+    for (int64_t i = 0; i < n; ++i) x[i] = 0.0;
+    status = ORC_OK;
+    goto done;
+  }
+  for (;;) {
+    orc_spmv(fmt, n, ptr, idx, val, x, r);                      /* A x in double */
+    for (int64_t i = 0; i < n; ++i) r[i] = b[i] - r[i];         /* r = b - A x */
+    double nr = sqrt(orc_dot(n, r, r));
+    info->rel_res_true = nr / nb;
+    if (!isfinite(nr)) { status = ORC_NONFINITE; break; }
+    if (nr / nb <= tol) { status = ORC_OK; break; }
+    if (outer >= max_outer || used >= maxit) { status = ORC_MAXIT; break; }
+    for (int64_t i = 0; i < n; ++i) rs[i] = (float)(r[i] / nr);
+    int32_t bd = 0;
+    int32_t it = orc_cg_f32(fmt, n, ptr, idx, v32, rs, d, (float)inner_tol, maxit - used, &bd);
+    used += it;
+    ++outer;
+    if (bd && it == 0) { status = ORC_NOT_SPD; break; }
+    for (int64_t i = 0; i < n; ++i) x[i] += nr * (double)d[i];  /* x += ||r|| d */
+  }
+done:
+  info->iterations = used;
+  info->restarts = outer;
+  info->status = status;
+  info->rel_res_recursive = info->rel_res_true;
+  free(v32);
+  free(rs);
+  free(d);
+  free(r);
+  return status;
+}

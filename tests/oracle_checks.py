@@ -1,0 +1,338 @@
+"""Pins of the CPU oracle against facts that do not come from the oracle.
+
+Every ``check_*`` function takes a loaded oracle library and raises
+AssertionError when the oracle disagrees with what the paper or the
+mathematics fixes.  ``test_oracle_pins.py`` runs them on the real oracle and
+``test_oracle_mutants.py`` runs them on deliberately broken copies to show
+that a plausible mistake (a dropped term, a wrong sign or index, a transposed
+operand) is caught.
+
+Sources of truth used here: dense brute-force products (numpy), dense
+Cholesky solves (scipy), exact rational arithmetic (fractions), the
+finite-termination and A-orthogonality properties of CG in exact arithmetic,
+the monotone decrease of the A-norm of the error, and closed-form systems.
+"""
+from __future__ import annotations
+
+from fractions import Fraction
+
+import numpy as np
+import scipy.linalg as sla
+import scipy.sparse as sp
+
+import femgen
+import oracle
+
+
+# ----------------------------------------------------------------- inputs --
+def random_csr(n, m, density, seed, empty_rows=(), long_row=None, long_len=0):
+    """Random (non-symmetric) sparse matrix with sorted columns, as CSR arrays."""
+    rng = np.random.default_rng(seed)
+    dense = np.where(rng.random((n, m)) < density, rng.uniform(-1, 1, (n, m)), 0.0)
+    for r in empty_rows:
+        dense[r, :] = 0.0
+    if long_row is not None:
+        cols = rng.choice(m, size=min(long_len, m), replace=False)
+        dense[long_row, cols] = rng.uniform(-1, 1, cols.size)
+    A = sp.csr_matrix(dense)
+    A.sort_indices()
+    return A.indptr.astype(np.int32), A.indices.astype(np.int32), A.data.astype(np.float64), dense
+
+
+def spd_sparse(n, seed, density=0.2, shift=1.0):
+    """Random sparse SPD matrix M M' + shift I, returned as (csr arrays, dense)."""
+    rng = np.random.default_rng(seed)
+    M = np.where(rng.random((n, n)) < density, rng.uniform(-1, 1, (n, n)), 0.0)
+    A = M @ M.T + shift * np.eye(n)
+    A = 0.5 * (A + A.T)
+    S = sp.csr_matrix(A)
+    S.sort_indices()
+    return (S.indptr.astype(np.int32), S.indices.astype(np.int32), S.data.astype(np.float64)), A
+
+
+def fem_small(nx=8, ny=7, nz=9, **kw):
+    return femgen.build_system(femgen.Grid(nx, ny, nz, **kw))
+
+
+def dense_of(ptr, idx, val, n, m=None):
+    m = n if m is None else m
+    D = np.zeros((n, m))
+    for i in range(n):
+        for k in range(ptr[i], ptr[i + 1]):
+            D[i, idx[k]] += val[k]
+    return D
+
+
+def componentwise(y, yref, scale, bound):
+    err = np.abs(y - yref)
+    lim = bound * scale + 1e-300
+    assert np.all(err <= lim), f"max componentwise error {np.max(err / lim) * bound:.3e} > {bound}"
+
+
+# ------------------------------------------------------------- products ----
+def check_spmv_csr_bruteforce(lib):
+    for seed, (n, m) in enumerate([(1, 1), (37, 37), (64, 50), (200, 200)]):
+        ptr, idx, val, dense = random_csr(n, m, 0.1, seed, empty_rows=(0,) if n > 1 else (),
+                                          long_row=n // 2, long_len=min(m, 40))
+        x = np.random.default_rng(100 + seed).uniform(-1, 1, m)
+        y = np.empty(n)
+        lib.orc_spmv_csr(n, ptr.ctypes.data, idx.ctypes.data, val.ctypes.data, x.ctypes.data, y.ctypes.data)
+        componentwise(y, dense @ x, np.abs(dense) @ np.abs(x), 1e-14)
+
+
+def check_spmv_csc_bruteforce(lib):
+    # CSC arrays of a non-symmetric A are the CSR arrays of A'.
+    for seed, n in enumerate([1, 33, 150]):
+        ptr, idx, val, denseT = random_csr(n, n, 0.12, 50 + seed, long_row=n - 1, long_len=n)
+        dense = denseT.T
+        x = np.random.default_rng(7 + seed).uniform(-1, 1, n)
+        y = oracle.spmv("csc", ptr, idx, val, x, lib=lib)
+        componentwise(y, dense @ x, np.abs(dense) @ np.abs(x), 1e-14)
+
+
+def check_spmv_sym_bruteforce(lib):
+    # Upper-triangle storage of a symmetric A (A = L + D + U, U' = L).
+    for seed, n in enumerate([1, 2, 45, 160]):
+        (ptr, idx, val), A = spd_sparse(n, 300 + seed, density=0.08)
+        uptr, uidx, uval = femgen.upper(n, ptr, idx, val)
+        x = np.random.default_rng(seed).uniform(-1, 1, n)
+        y = oracle.spmv("sym", uptr, uidx, uval, x, lib=lib)
+        componentwise(y, A @ x, np.abs(A) @ np.abs(x), 1e-14)
+    s = fem_small(9, 8, 7)
+    D = dense_of(s.ptr, s.idx, s.val, s.n)
+    x = np.random.default_rng(3).uniform(-1, 1, s.n)
+    uptr, uidx, uval = s.upper()
+    for fmt, arrs in (("sym", (uptr, uidx, uval)), ("csr", (s.ptr, s.idx, s.val)), ("csc", s.csc())):
+        y = oracle.spmv(fmt, *arrs, x, lib=lib)
+        componentwise(y, D @ x, np.abs(D) @ np.abs(x), 1e-14)
+
+
+def check_abs_spmv(lib):
+    ptr, idx, val, dense = random_csr(40, 40, 0.2, 9)
+    x = np.random.default_rng(1).uniform(-1, 1, 40)
+    y = oracle.abs_spmv("csr", ptr, idx, val, x, lib=lib)
+    assert np.allclose(y, np.abs(dense) @ np.abs(x), rtol=1e-14, atol=0)
+    (ptr, idx, val), A = spd_sparse(30, 4)
+    u = femgen.upper(30, ptr, idx, val)
+    y = oracle.abs_spmv("sym", *u, x[:30], lib=lib)
+    assert np.allclose(y, np.abs(A) @ np.abs(x[:30]), rtol=1e-14, atol=0)
+
+
+def check_spmv_f32(lib):
+    ptr, idx, val, dense = random_csr(80, 80, 0.1, 12)
+    x = np.random.default_rng(2).uniform(-1, 1, 80).astype(np.float32)
+    v32 = val.astype(np.float32)
+    D32 = dense_of(ptr, idx, v32.astype(np.float64), 80)
+    y = oracle.spmv_f32("csr", ptr, idx, v32, x, lib=lib).astype(np.float64)
+    componentwise(y, D32 @ x.astype(np.float64), np.abs(D32) @ np.abs(x.astype(np.float64)), 1e-5)
+    (p2, i2, v2), A = spd_sparse(60, 13, density=0.1)
+    u = femgen.upper(60, p2, i2, v2)
+    u32 = u[2].astype(np.float32)
+    Au = dense_of(u[0], u[1], u32.astype(np.float64), 60)
+    As = Au + np.triu(Au, 1).T
+    xs = x[:60]
+    y = oracle.spmv_f32("sym", u[0], u[1], u32, xs, lib=lib).astype(np.float64)
+    componentwise(y, As @ xs.astype(np.float64), np.abs(As) @ np.abs(xs.astype(np.float64)), 1e-5)
+
+
+def check_dot(lib):
+    rng = np.random.default_rng(5)
+    a = rng.uniform(-1, 1, 300)
+    b = rng.uniform(-1, 1, 300)
+    exact = sum(Fraction(float(u)) * Fraction(float(v)) for u, v in zip(a, b))
+    assert abs(oracle.dot_long(a, b, lib=lib) - float(exact)) <= 1e-15 * float(np.abs(a) @ np.abs(b))
+    assert abs(oracle.dot(a, b, lib=lib) - float(exact)) <= 300 * 1.2e-16 * float(np.abs(a) @ np.abs(b))
+
+
+# ---------------------------------------------------------------- CG -------
+def check_cg_vs_cholesky(lib):
+    for seed, n in enumerate([1, 3, 10, 25, 40]):
+        (ptr, idx, val), A = spd_sparse(n, 10 + seed, density=0.3, shift=2.0)
+        b = np.random.default_rng(seed).uniform(-1, 1, n)
+        xc = sla.cho_solve(sla.cho_factor(A), b)
+        for fmt, arrs in (("csr", (ptr, idx, val)), ("sym", femgen.upper(n, ptr, idx, val)),
+                          ("csc", (ptr, idx, val))):
+            r = oracle.cg(fmt, *arrs, b, tol=1e-14, maxit=10 * n + 10, lib=lib)
+            assert r.status == "OK", r.status
+            assert np.linalg.norm(r.x - xc) <= 1e-12 * np.linalg.norm(xc), (fmt, n)
+            assert r.rel_res_true <= 1e-14
+
+
+def check_cg_fem_vs_cholesky(lib):
+    s = fem_small(7, 8, 6, contrast=1000.0)
+    D = dense_of(s.ptr, s.idx, s.val, s.n)
+    xc = sla.cho_solve(sla.cho_factor(D), s.b)
+    r = oracle.cg("sym", *s.upper(), s.b, tol=1e-13, maxit=20 * s.n, lib=lib)
+    assert r.status == "OK"
+    assert np.linalg.norm(r.x - xc) / np.linalg.norm(xc) <= 1e-9
+    # x* is the manufactured solution: b was assembled element by element from it
+    assert np.linalg.norm(r.x - s.xstar) / np.linalg.norm(s.xstar) <= 1e-9
+
+
+def check_cg_finite_termination(lib):
+    # k distinct eigenvalues -> the exact solution after at most k steps.
+    rng = np.random.default_rng(21)
+    n = 60
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    eig = np.repeat([1.0, 2.0, 5.0, 9.0], n // 4)
+    A = (Q * eig) @ Q.T
+    A = 0.5 * (A + A.T)
+    S = sp.csr_matrix(A)
+    b = rng.uniform(-1, 1, n)
+    r = oracle.cg("csr", S.indptr.astype(np.int32), S.indices.astype(np.int32), S.data, b, tol=1e-11, lib=lib)
+    assert r.status == "OK" and r.iterations <= 4, r.iterations
+    # diagonal with 3 distinct values: exactly 3 steps
+    d = np.repeat([3.0, 0.5, 7.0], 7)
+    ptr = np.arange(22, dtype=np.int32)
+    idx = np.arange(21, dtype=np.int32)
+    bb = np.random.default_rng(2).uniform(0.5, 1.0, 21)
+    r = oracle.cg("csr", ptr, idx, d, bb, tol=1e-13, lib=lib)
+    assert r.status == "OK" and r.iterations == 3, r.iterations
+    assert np.allclose(r.x, bb / d, rtol=1e-13, atol=0)
+    # well-conditioned n = 12: at most n steps
+    (p2, i2, v2), A2 = spd_sparse(12, 77, density=0.5, shift=3.0)
+    r = oracle.cg("csr", p2, i2, v2, np.ones(12), tol=1e-12, lib=lib)
+    assert r.status == "OK" and r.iterations <= 12
+
+
+def check_cg_exact_first_steps(lib):
+    # Exact rational CG on a 3x3 system: in exact arithmetic it terminates in
+    # 3 steps; the floating-point iterates must follow the rational ones.
+    A = [[Fraction(4), Fraction(1), Fraction(0)], [Fraction(1), Fraction(3), Fraction(1)],
+         [Fraction(0), Fraction(1), Fraction(2)]]
+    b = [Fraction(1), Fraction(2), Fraction(3)]
+
+    def mv(M, v):
+        return [sum(M[i][j] * v[j] for j in range(3)) for i in range(3)]
+
+    def dt(u, v):
+        return sum(a * c for a, c in zip(u, v))
+
+    x = [Fraction(0)] * 3
+    r = list(b)
+    p = list(r)
+    xs = []
+    for _ in range(3):
+        q = mv(A, p)
+        a = dt(r, r) / dt(p, q)
+        x = [xi + a * pi for xi, pi in zip(x, p)]
+        rn = [ri - a * qi for ri, qi in zip(r, q)]
+        be = dt(rn, rn) / dt(r, r)
+        p = [ri + be * pi for ri, pi in zip(rn, p)]
+        r = rn
+        xs.append([float(v) for v in x])
+    assert all(v == 0 for v in r)  # exact termination
+    Ad = np.array([[float(v) for v in row] for row in A])
+    S = sp.csr_matrix(Ad)
+    res = oracle.cg("csr", S.indptr.astype(np.int32), S.indices.astype(np.int32), S.data,
+                    np.array([1.0, 2.0, 3.0]), tol=1e-15, maxit=3, history=3, lib=lib)
+    assert res.iterations == 3
+    for k in range(3):
+        assert np.allclose(res.x_hist[k], xs[k], rtol=1e-13, atol=1e-15), k
+
+
+def check_cg_a_orthogonality(lib):
+    s = fem_small(10, 10, 10, contrast=10.0)
+    D = dense_of(s.ptr, s.idx, s.val, s.n)
+    r = oracle.cg("csr", s.ptr, s.idx, s.val, s.b, tol=1e-10, history=40, lib=lib)
+    P = r.p_hist
+    AP = P @ D
+    G = AP @ P.T
+    nrm = np.sqrt(np.diag(G))
+    for i in range(P.shape[0]):
+        for j in range(max(0, i - 2), i):
+            assert abs(G[i, j]) / (nrm[i] * nrm[j]) <= 1e-8, (i, j, G[i, j] / (nrm[i] * nrm[j]))
+
+
+def check_cg_error_a_norm_decreases(lib):
+    s = fem_small(9, 9, 9, contrast=100.0)
+    D = dense_of(s.ptr, s.idx, s.val, s.n)
+    xe = sla.cho_solve(sla.cho_factor(D), s.b)
+    r = oracle.cg("sym", *s.upper(), s.b, tol=1e-12, maxit=20 * s.n, history=2000, lib=lib)
+    E = r.x_hist - xe
+    en = np.sqrt(np.einsum("ki,ij,kj->k", E, D, E))
+    e0 = np.sqrt(xe @ D @ xe)
+    prev = e0
+    for k, e in enumerate(en):
+        assert e <= prev * (1 + 1e-9) + 1e-13 * e0, (k, e, prev)
+        prev = e
+    assert en[-1] <= 1e-9 * e0
+
+
+def check_cg_tridiagonal_closed_form(lib):
+    # -u'' = f on a uniform grid: tridiag(-1, 2, -1) x = b with x known.
+    n = 50
+    ptr = [0]
+    idx, val = [], []
+    for i in range(n):
+        for j, v in ((i - 1, -1.0), (i, 2.0), (i + 1, -1.0)):
+            if 0 <= j < n:
+                idx.append(j)
+                val.append(v)
+        ptr.append(len(idx))
+    ptr, idx, val = np.array(ptr, np.int32), np.array(idx, np.int32), np.array(val)
+    t = np.arange(1, n + 1) / (n + 1)
+    xs = np.sin(np.pi * t) + t ** 2
+    b = 2 * xs - np.r_[xs[1:], 0.0] - np.r_[0.0, xs[:-1]]
+    r = oracle.cg("csr", ptr, idx, val, b, tol=1e-13, lib=lib)
+    assert r.status == "OK" and r.iterations <= n
+    assert np.linalg.norm(r.x - xs) <= 1e-10 * np.linalg.norm(xs)
+    # the eigenvalues of tridiag(-1,2,-1) are distinct: n steps suffice and
+    # fewer than n cannot reach 1e-13 from a generic right-hand side
+    assert r.iterations >= n // 2
+
+
+def check_cg_edge_cases(lib):
+    (ptr, idx, val), A = spd_sparse(20, 5, shift=1.0)
+    b = np.random.default_rng(0).uniform(-1, 1, 20)
+    r = oracle.cg("csr", ptr, idx, val, np.zeros(20), x0=np.ones(20), lib=lib)   # b = 0 -> x = 0
+    assert r.status == "OK" and r.iterations == 0 and not np.any(r.x)
+    xe = np.linalg.solve(A, b)
+    r = oracle.cg("csr", ptr, idx, val, A @ np.ones(20), x0=np.ones(20), tol=1e-10, lib=lib)
+    assert r.status == "OK" and r.iterations == 0                                  # x0 already solves it
+    r = oracle.cg("csr", ptr, idx, val, b, tol=1e-30, maxit=3, lib=lib)
+    assert r.status == "MAXIT" and r.iterations == 3
+    neg = -val
+    r = oracle.cg("csr", ptr, idx, neg, b, lib=lib)
+    assert r.status == "NOT_SPD" and r.iterations == 0
+    bad = val.copy()
+    bad[0] = np.nan
+    r = oracle.cg("csr", ptr, idx, bad, b, lib=lib)
+    assert r.status == "NONFINITE"
+    r = oracle.cg("csr", ptr, idx, val, b, tol=1e-12, lib=lib)
+    assert np.linalg.norm(r.x - xe) <= 1e-10 * np.linalg.norm(xe)
+
+
+def check_cg_f32(lib):
+    s = fem_small(8, 8, 8, contrast=10.0)
+    u = s.upper()
+    rhs = (s.b / np.linalg.norm(s.b)).astype(np.float32)
+    d, it, bd = oracle.cg_f32("sym", u[0], u[1], u[2].astype(np.float32), rhs, 1e-4, 1000, lib=lib)
+    assert not bd and it > 0
+    D = dense_of(s.ptr, s.idx, s.val, s.n)
+    res = np.linalg.norm(rhs.astype(np.float64) - D @ d.astype(np.float64))
+    assert res <= 2e-4, res
+    xe = np.linalg.solve(D, rhs.astype(np.float64))
+    assert np.linalg.norm(d - xe) / np.linalg.norm(xe) <= 1e-2
+
+
+def check_cg_ir(lib):
+    s = fem_small(10, 9, 11, contrast=1000.0)
+    D = dense_of(s.ptr, s.idx, s.val, s.n)
+    xe = sla.cho_solve(sla.cho_factor(D), s.b)
+    for fmt, arrs in (("csr", (s.ptr, s.idx, s.val)), ("sym", s.upper())):
+        r = oracle.cg_ir(fmt, *arrs, s.b, tol=1e-10, inner_tol=1e-4, lib=lib)
+        assert r.status == "OK", r.status
+        true = np.linalg.norm(s.b - D @ r.x) / np.linalg.norm(s.b)
+        assert true <= 1e-10 and abs(true - r.rel_res_true) <= 1e-3 * true + 1e-16
+        assert np.linalg.norm(r.x - xe) / np.linalg.norm(xe) <= 1e-7
+        assert 2 <= r.restarts <= 10
+
+
+ALL_CHECKS = [
+    check_spmv_csr_bruteforce, check_spmv_csc_bruteforce, check_spmv_sym_bruteforce, check_abs_spmv,
+    check_spmv_f32, check_dot, check_cg_vs_cholesky, check_cg_fem_vs_cholesky,
+    check_cg_finite_termination, check_cg_exact_first_steps, check_cg_a_orthogonality,
+    check_cg_error_a_norm_decreases, check_cg_tridiagonal_closed_form, check_cg_edge_cases,
+    check_cg_f32, check_cg_ir,
+]

@@ -1,0 +1,56 @@
+"""Each pin set must catch plausible mistakes in the oracle.
+
+A mutant is a copy of oracle.c with one deliberate mistake (a dropped term,
+a wrong sign, a wrong index, a transposed operand), compiled on the CPU into a
+temporary directory.  Running every pin against it must fail at least once.
+"""
+import os
+import tempfile
+
+import pytest
+
+import oracle
+from oracle_checks import ALL_CHECKS
+
+MUTANTS = {
+    "csr_wrong_gather_index": ("s += val[k] * x[idx[k]];", "s += val[k] * x[i];"),
+    "csr_dropped_value": ("s += val[k] * x[idx[k]];", "s += x[idx[k]];"),
+    "sym_dropped_transpose": ("if (j > i) y[j] += val[k] * x[i];", "(void)0;"),
+    "sym_transpose_wrong_operand": ("if (j > i) y[j] += val[k] * x[i];", "if (j > i) y[j] += val[k] * x[j];"),
+    "sym_diagonal_twice": ("if (j > i) y[j] += val[k] * x[i];", "if (j >= i) y[j] += val[k] * x[i];"),
+    "csc_transposed": ("y[rowidx[k]] += val[k] * x[j];", "y[j] += val[k] * x[rowidx[k]];"),
+    "cg_x_sign": ("x[i] += alpha * p[i];   /* x += alpha p */", "x[i] -= alpha * p[i];"),
+    "cg_r_uses_p": ("r[i] -= alpha * q[i];   /* r -= alpha A p */", "r[i] -= alpha * p[i];"),
+    "cg_alpha_inverted": ("double alpha = rr / pq;", "double alpha = pq / rr;"),
+    "cg_beta_inverted": ("double beta = rr_new / rr;", "double beta = rr / rr_new;"),
+    "cg_beta_dropped": ("p[i] = r[i] + beta * p[i];  /* p = r + beta p */", "p[i] = r[i];"),
+    "cg_initial_residual_sign": ("r[i] = b[i] - q[i];\n  for", "r[i] = b[i] + q[i];\n  for"),
+    "cg_no_true_residual_confirm": ("if (info->rel_res_true <= tol) break;", "break;"),
+    "dot_long_drops_term": ("s += (long double)a[i] * (long double)b[i];",
+                            "if (i) s += (long double)a[i] * (long double)b[i];"),
+    "f32_beta_dropped": ("p[i] = r[i] + beta * p[i];\n  }\n  free(r);", "p[i] = r[i];\n  }\n  free(r);"),
+    "ir_missing_scale": ("x[i] += nr * (double)d[i];", "x[i] += (double)d[i];"),
+    "ir_residual_sign": ("r[i] = b[i] - r[i];", "r[i] = r[i] - b[i];"),
+    "abs_spmv_signed": ("double a = fabs(val[k]);", "double a = val[k];"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_mutant(name):
+    src = open(oracle._SRC).read()
+    old, new = MUTANTS[name]
+    assert src.count(old) >= 1, f"mutation anchor not found: {old!r}"
+    mutated = src.replace(old, new, 1)
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "mut.c")
+        so = os.path.join(d, "mut.so")
+        open(c, "w").write(mutated)
+        oracle.compile_oracle(c, so)
+        lib = oracle.load(so)
+        failures = []
+        for check in ALL_CHECKS:
+            try:
+                check(lib)
+            except (AssertionError, FloatingPointError, ValueError, OverflowError) as e:  # noqa: PERF203
+                failures.append((check.__name__, str(e)[:80]))
+        assert failures, f"mutant {name} survived every pin"
