@@ -1,0 +1,398 @@
+#!/usr/bin/env python3
+"""Benchmark: conjugate-gradient time to relative residual 1e-10 on the 128^3
+synthetic FEM system (2.0M rows, 29.6M non-zeros), with the SpMV HBM
+bandwidth of every storage format, mixed precision against plain FP64 CG on
+the same GPU, and the CPU oracle timed beside it.
+
+One step = one solve from x0 = 0 to a true relative residual <= 1e-10 with the
+headline method (single-precision inner CG with double-precision iterative
+refinement, symmetric upper storage), inputs resident in HBM.  The JSON line
+also carries the plain FP64 CG times of the three storage formats.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 (under torchrun): every rank solves its own replica of the system (the
+solve does not shard without a collective), timing is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import signal
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import femgen  # noqa: E402
+
+METRIC = "CG time-to-1e-10 residual (s) & SpMV HBM GB/s; mixed/batched vs FP64 CG"
+GRIDS = {"128": femgen.LARGE, "31": femgen.PAPER_SIZE, "64": femgen.DIFF, "256": femgen.LARGEST}
+TOL = 1e-10
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--grid", default="128", choices=sorted(GRIDS))
+    ap.add_argument("--format", default="sym", choices=["sym", "csr", "csc"])
+    ap.add_argument("--precision", default="fp32_ir", choices=["fp32_ir", "fp64"])
+    ap.add_argument("--inner-tol", type=float, default=1e-4)
+    ap.add_argument("--no-extras", action="store_true", help="skip the per-format and CPU-baseline legs")
+    ap.add_argument("--profile-iters", type=int, default=0,
+                    help="only run solves capped at this many iterations (small case for ncu captures)")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU-oracle sample")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ helpers
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        dist.init_process_group(backend=backend)
+        pg = dist
+    return world, rank, local, pg
+
+
+def golden(grid_key, fmt="sym"):
+    p = os.path.join(ROOT, "tests", "golden", f"oracle_{grid_key}_{fmt}.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f)
+    return None
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.send_signal(signal.SIGTERM)
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return None
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() in ("active", "1"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def flush_l2(torch, buf):
+    buf.add_(1.0)  # 256 MiB write, larger than the 129 MB L2
+
+
+def per_iteration_bytes(stats, precision):
+    """Algorithmic bytes of one CG iteration: the product (matrix arrays, ptr,
+    x read once, y written once) plus the vector passes x += a p, r -= a q,
+    r'r (read p, q, x, r; write x, r) and p = r + b p (read r, p; write p)."""
+    n = stats["n"]
+    if precision == "fp64":
+        return stats["spmv_bytes_fp64"] + 9 * 8 * n
+    return stats["spmv_bytes_fp32"] + 9 * 4 * n
+
+
+# ---------------------------------------------------------------- reference
+def run_reference(args):
+    world, rank, local, pg = dist_setup(args)
+    if rank != 0:
+        return 0
+    import oracle
+
+    g = GRIDS[args.grid]
+    s = femgen.build_system(g)
+    up = s.upper()
+    gold = golden(args.grid, "sym")
+    probe = oracle.cg("sym", *up, s.b, tol=0.0, maxit=3)  # first touch, pages in
+    t0 = time.perf_counter()
+    probe = oracle.cg("sym", *up, s.b, tol=0.0, maxit=3)
+    spi = (time.perf_counter() - t0) / 3
+    m = int(max(5, min(2000, args.cpu_seconds / max(spi, 1e-9) / 2)))
+    iters_needed = gold["iterations"] if gold else None
+    times = []
+    for step in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.cg("sym", *up, s.b, tol=0.0, maxit=m)
+        dt = time.perf_counter() - t0
+        if step >= args.warmup:
+            times.append(dt / m)
+    spi = statistics.median(times)
+    value = spi * iters_needed if iters_needed else None
+    sample = (f"{m} CG iterations of the double-precision oracle per step on the {g.nx}x{g.ny}x{g.nz} system "
+              f"(symmetric storage), scaled by the oracle's own iteration count to 1e-10 "
+              f"({iters_needed}, tests/golden/oracle_{args.grid}_sym.json)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * spi * m, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"fem {g.nx}x{g.ny}x{g.nz} P1 stiffness, {g.n_incl} inclusion(s), contrast "
+                                   f"{g.contrast:g}, tol 1e-10", "n": s.n, "nnz": s.nnz},
+            "cpu_baseline": {"value": value, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample,
+                             "seconds_per_iteration": spi},
+            "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------- ours
+def run_ours(args):
+    import torch
+
+    world, rank, local, pg = dist_setup(args)
+    torch.cuda.set_device(local)
+    import paper_1010_4639_gb300 as gb
+
+    gb.build()
+    dev = torch.device("cuda", local)
+    g = GRIDS[args.grid]
+    s = femgen.build_system(g)
+    fmt_arrays = {"sym": s.upper(), "csr": (s.ptr, s.idx, s.val), "csc": s.csc()}
+    A = gb.Matrix(args.format, *fmt_arrays[args.format])
+    st = A.stats()
+    b = torch.from_numpy(s.b).to(dev)
+    x = torch.zeros_like(b)
+    solve_kw = dict(tol=TOL, precision=args.precision, inner_tol=args.inner_tol)
+    if args.profile_iters:
+        solve_kw.update(maxit=args.profile_iters, raise_on_error=False)
+        for _ in range(max(1, args.warmup)):
+            x.zero_()
+            A.solve(b, x, **solve_kw)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_iters": args.profile_iters, "stats": st}), flush=True)
+        return 0
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        x.zero_()
+        A.solve(b, x, **solve_kw)
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    infos = []
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        for k in range(args.steps):
+            x.zero_()
+            flush_l2(torch, flush)
+            ev[k][0].record(stream)
+            _, info = A.solve(b, x, **solve_kw)
+            ev[k][1].record(stream)
+            infos.append(info)
+        torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    step_ms = [a.elapsed_time(c) for a, c in ev]
+    ms = sum(step_ms) / len(step_ms)
+    kernel_ms = sum(i.kernel_ms for i in infos) / len(infos)
+    kernel_launches = sum(i.kernel_launches for i in infos) / len(infos)
+    iters = infos[-1].iterations
+    if pg:
+        t = torch.tensor([ms, kernel_ms], dtype=torch.float64, device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms, kernel_ms = float(t[0]), float(t[1])
+    x_dev = x.clone()
+    # end to end through the public API: pinned host b and x, copies inside the call
+    bh = torch.from_numpy(s.b).pin_memory()
+    xh = torch.zeros(s.n, dtype=torch.float64).pin_memory()
+    e2e = []
+    for k in range(max(1, args.steps)):
+        xh.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, info_h = A.solve(bh, xh, **solve_kw)
+        e2e.append(time.perf_counter() - t0)
+    e2e_s = statistics.median(e2e)
+    if pg:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        e2e_s = float(t[0])
+    hbm, peak_kind = peaks()
+    per_it = per_iteration_bytes(st, args.precision)
+    achieved = per_it * iters / (kernel_ms / 1000.0) / 1e9 if kernel_ms > 0 else None
+    x_np = x_dev.cpu().numpy()
+    line = {
+        "metric": METRIC, "value": ms / 1000.0, "unit": "s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64" if args.precision == "fp32_ir" else "f64", "data": "synthetic",
+        "config": {"workload": f"fem {g.nx}x{g.ny}x{g.nz} P1 stiffness, {g.n_incl} inclusion(s), contrast "
+                               f"{g.contrast:g}, {args.format} storage, {args.precision}, tol 1e-10",
+                   "n": s.n, "nnz": s.nnz, "nnz_stored": int(fmt_arrays[args.format][1].shape[0]),
+                   "l2": "matrix larger than L2; 256 MiB L2 flush before every step",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "clocks": clk.summary(),
+        "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": 16 * s.n, "d2h_bytes_per_step": 8 * s.n},
+        "gpu_launches": int(round(sum(i.launches for i in infos) / len(infos))),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": (achieved / hbm) if achieved else None, "traffic": None,
+                     "kernel": f"k_cg<{'float' if args.precision == 'fp32_ir' else 'double'}> persistent CG",
+                     "algorithmic_bytes_per_iteration": per_it, "iterations": iters,
+                     "kernel_ms_per_step": kernel_ms, "kernel_launches_per_step": kernel_launches,
+                     "peak_kind": f"{peak_kind} HBM copy bandwidth"},
+        "solve": {"iterations": iters, "outer": infos[-1].outer, "status": infos[-1].status,
+                  "rel_res_true": infos[-1].rel_res_true,
+                  "err_vs_xstar": float(np.linalg.norm(x_np - s.xstar) / np.linalg.norm(s.xstar))},
+    }
+    gold = golden(args.grid, "sym")
+    if gold:
+        idx = np.asarray(gold["sample_index"])
+        xo = np.asarray(gold["sample_x"])
+        line["solve"]["err_vs_fp64_oracle_sampled"] = float(np.linalg.norm(x_np[idx] - xo) / np.linalg.norm(xo))
+    if not args.no_extras and rank == 0:
+        line["variants"] = extras(torch, gb, s, fmt_arrays, A, args, hbm)
+        line["cpu_baseline"] = cpu_baseline(s, args, line["variants"])
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    A.close()
+    if pg:
+        pg.barrier()
+        pg.destroy_process_group()
+    return 0
+
+
+def time_spmv(torch, M, x, y, f32, reps=20):
+    stream = torch.cuda.current_stream()
+    fn = M.spmv_f32 if f32 else M.spmv
+    for _ in range(3):
+        fn(x, y)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        fn(x, y)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def extras(torch, gb, s, fmt_arrays, A_head, args, hbm):
+    """Per-format SpMV bandwidth and FP64 / mixed-precision solve times."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    b = torch.from_numpy(s.b).to(dev)
+    xv = torch.from_numpy(femgen.random_vector(s.n, 7)).to(dev)
+    yv = torch.empty_like(xv)
+    out = {}
+    for fmt in ("sym", "csr", "csc"):
+        M = A_head if fmt == args.format else gb.Matrix(fmt, *fmt_arrays[fmt])
+        st = M.stats()
+        r = {"spmv_fp64_ms": time_spmv(torch, M, xv, yv, False),
+             "spmv_fp32_ms": time_spmv(torch, M, xv.float(), yv.float(), True)}
+        r["spmv_fp64_GBs"] = st["spmv_bytes_fp64"] / r["spmv_fp64_ms"] / 1e6
+        r["spmv_fp32_GBs"] = st["spmv_bytes_fp32"] / r["spmv_fp32_ms"] / 1e6
+        r["spmv_fp64_frac_of_measured_hbm"] = r["spmv_fp64_GBs"] / hbm
+        r["spmv_fp32_frac_of_measured_hbm"] = r["spmv_fp32_GBs"] / hbm
+        for prec in ("fp64", "fp32_ir"):
+            x = torch.zeros_like(b)
+            M.solve(b, x, tol=TOL, precision=prec, inner_tol=args.inner_tol)  # warm
+            x.zero_()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            _, info = M.solve(b, x, tol=TOL, precision=prec, inner_tol=args.inner_tol)
+            e1.record()
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1) / 1000.0
+            per_it = per_iteration_bytes(st, prec)
+            r[prec] = {"s": t, "iterations": info.iterations, "outer": info.outer, "status": info.status,
+                       "rel_res_true": info.rel_res_true, "kernel_ms": info.kernel_ms,
+                       "iter_us": 1000.0 * info.kernel_ms / max(info.iterations, 1),
+                       "kernel_GBs": per_it * info.iterations / (info.kernel_ms / 1000.0) / 1e9}
+        r["mixed_speedup_vs_fp64"] = r["fp64"]["s"] / r["fp32_ir"]["s"]
+        r["device_bytes"] = st["device_bytes"]
+        out[fmt] = r
+        if M is not A_head:
+            M.close()
+    return out
+
+
+def cpu_baseline(s, args, variants):
+    import oracle
+
+    up = s.upper()
+    gold = golden(args.grid, "sym")
+    oracle.cg("sym", *up, s.b, tol=0.0, maxit=2)
+    t0 = time.perf_counter()
+    oracle.cg("sym", *up, s.b, tol=0.0, maxit=3)
+    spi = (time.perf_counter() - t0) / 3
+    m = int(max(5, min(2000, args.cpu_seconds / max(spi, 1e-9))))
+    t0 = time.perf_counter()
+    oracle.cg("sym", *up, s.b, tol=0.0, maxit=m)
+    spi = (time.perf_counter() - t0) / m
+    iters = gold["iterations"] if gold else variants["sym"]["fp64"]["iterations"]
+    src = "the oracle's own count (tests/golden)" if gold else "the GPU FP64 solve's count (no oracle golden file)"
+    return {"value": spi * iters, "unit": "s", "cores": 1, "kind": "oracle",
+            "sample": f"{m} double-precision oracle CG iterations (symmetric storage, 1 thread) on the same system, "
+                      f"{spi * 1000:.1f} ms each, scaled by {iters} iterations to 1e-10 from {src}",
+            "seconds_per_iteration": spi}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

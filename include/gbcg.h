@@ -1,0 +1,196 @@
+/*
+ * gbcg.h -- C ABI of the GB300 sparse conjugate-gradient library.
+ *
+ * The operation is the one in Section III of "Parallel Sparse Matrix Solver
+ * on the GPU Applied to Simulation of Electrical Machines" (Rodrigues et al.):
+ * solve A x = b for a known, square, symmetric positive-definite sparse A
+ * (Section I) by the unpreconditioned conjugate-gradient iteration, with A
+ * stored in CSR, in symmetric CSR (one triangle plus the diagonal, A = L + D +
+ * U with U' = L) or in CSC, and the product y = A p computed by the library's
+ * own kernels.
+ *
+ * Conventions for every entry point:
+ *   - Return value: a gbcg_status (0 = GBCG_OK).  Nothing throws or aborts
+ *     across this boundary; on failure gbcg_last_error() gives a message for
+ *     the calling thread.
+ *   - Streams: `stream` is a cudaStream_t passed as void* (NULL = the legacy
+ *     default stream).  All device work of a call is issued on it.
+ *   - Vectors are dense, contiguous, length n, owned by the caller.  Unless a
+ *     call says otherwise they are device pointers.
+ *   - Indices are int32.  Matrices with more than 2^31 - 1 stored entries are
+ *     rejected with GBCG_ERR_INVALID.
+ *   - A gbcg_matrix_t is not thread-safe: one call at a time per handle.  Two
+ *     handles may be used concurrently from different threads and streams.
+ */
+#ifndef GBCG_H
+#define GBCG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gbcg_matrix_s* gbcg_matrix_t;
+
+/* Storage formats accepted by gbcg_create (Section III, "CSR, and Symmetric
+ * CSR and CSC formats"). */
+enum gbcg_format {
+  GBCG_CSR = 0,          /* full matrix by rows: ptr[n+1], idx = column, val */
+  GBCG_SYM_CSR_UPPER = 1,/* upper triangle and diagonal by rows (j >= i): the
+                            same numbers as the paper's L + D by rows read as
+                            columns; each off-diagonal entry stands for both
+                            (i, j) and (j, i) */
+  GBCG_CSC = 2           /* full matrix by columns: ptr[n+1], idx = row, val */
+};
+
+enum gbcg_status {
+  GBCG_OK = 0,
+  GBCG_ERR_INVALID = 1,   /* bad argument or malformed matrix */
+  GBCG_ERR_NOT_SPD = 2,   /* p'Ap <= 0 met during the iteration */
+  GBCG_ERR_MAXIT = 3,     /* iteration bound reached before the tolerance */
+  GBCG_ERR_NONFINITE = 4, /* NaN or Inf met in a reduction */
+  GBCG_ERR_TIMEOUT = 5,   /* a bounded device-side wait ran out */
+  GBCG_ERR_CUDA = 6,      /* a CUDA runtime call failed */
+  GBCG_ERR_NOMEM = 7      /* device or host allocation failed */
+};
+
+enum gbcg_precision {
+  GBCG_FP64 = 0,          /* CG in double precision throughout */
+  GBCG_FP32_IR = 1        /* single-precision inner CG (Section IV's
+                             single-precision variant) inside double-precision
+                             iterative refinement */
+};
+
+enum gbcg_memory { GBCG_HOST = 0, GBCG_DEVICE = 1 };
+
+/* Solver options.  Zero-initialised fields take the documented defaults. */
+typedef struct {
+  int32_t precision;          /* gbcg_precision; default GBCG_FP64 */
+  int32_t max_outer;          /* refinement passes for GBCG_FP32_IR; default 30 */
+  double inner_tol;           /* inner relative tolerance for GBCG_FP32_IR; default 1e-4 */
+  int32_t wait_timeout_ms;    /* bound on every device-side wait; default 1000 */
+  int32_t max_restarts;       /* true-residual restarts for GBCG_FP64; default 3 */
+} gbcg_opts;
+
+/* Report of one solve. */
+typedef struct {
+  int32_t iterations;         /* CG iterations (inner ones for GBCG_FP32_IR) */
+  int32_t outer;              /* restarts (FP64) or refinement passes (IR) */
+  int32_t status;             /* same as the return value of gbcg_solve */
+  int32_t pad_;
+  double rel_res_recursive;   /* ||r_k|| / ||b|| of the recurrence at exit */
+  double rel_res_true;        /* ||b - A x|| / ||b|| recomputed in double */
+  double ms;                  /* wall time of the call on the host, ms */
+  double kernel_ms;           /* device time of the persistent CG launches,
+                                 CUDA events on the caller's stream, ms */
+  int32_t kernel_launches;    /* persistent CG launches of the call */
+  int32_t launches;           /* kernels of this library launched by the call */
+} gbcg_info;
+
+/* Layout facts of a created matrix (for measurement and tests). */
+typedef struct {
+  int64_t n;                  /* rows */
+  int64_t nnz_input;          /* entries passed to gbcg_create */
+  int64_t nnz_full;           /* entries of the full symmetric operator */
+  int64_t stored_slots;       /* SELL slots of the row-gather layout, padding included */
+  int64_t plan_slots;         /* SELL slots of the symmetric transpose plan (0 if none) */
+  int64_t long_rows;          /* rows handled warp-per-row */
+  int64_t device_bytes;       /* device memory held by the handle */
+  int64_t spmv_bytes_fp64;    /* algorithmic bytes of one double-precision product */
+  int64_t spmv_bytes_fp32;    /* algorithmic bytes of one single-precision product */
+  int32_t format;             /* gbcg_format */
+  int32_t grid_ctas;          /* CTAs of the persistent CG launch */
+} gbcg_matrix_stats;
+
+/*
+ * gbcg_create -- build a matrix handle (Section III: the CG input is a
+ * symmetric sparse matrix in full CSR, symmetric CSR or CSC).
+ *
+ *   A          out: the new handle (NULL on failure)
+ *   format     gbcg_format
+ *   n          rows = columns, n >= 0
+ *   nnz        stored entries, = ptr[n] - index_base
+ *   ptr, idx, val
+ *              the arrays of `format`: ptr[n+1] non-decreasing, idx[nnz] in
+ *              [index_base, n + index_base), val[nnz] finite doubles.  Within
+ *              a row (column for CSC) indices are strictly increasing.  For
+ *              GBCG_SYM_CSR_UPPER every idx of row i is >= i.  Symmetry of a
+ *              full CSR/CSC input is the caller's promise (it is what CG
+ *              needs); the products themselves are exact for any matrix.
+ *   index_base 0 or 1 (the paper's kernel indexes from 1)
+ *   memory     gbcg_memory: where ptr/idx/val live
+ *   stream     used for the uploads
+ *
+ * The library deep-copies the arrays into its own device layout (a sliced
+ * row-gather layout for the product, a single-precision copy of the values,
+ * the solve workspace); the caller may free its arrays when the call returns.
+ * Errors: GBCG_ERR_INVALID for malformed input (with the first offending
+ * position in gbcg_last_error()), GBCG_ERR_NOMEM, GBCG_ERR_CUDA.
+ */
+int gbcg_create(gbcg_matrix_t* A, int32_t format, int64_t n, int64_t nnz, const int32_t* ptr,
+                const int32_t* idx, const double* val, int32_t index_base, int32_t memory, void* stream);
+
+/* gbcg_destroy -- free a handle and all device memory it holds (NULL is a no-op). */
+int gbcg_destroy(gbcg_matrix_t A);
+
+/*
+ * gbcg_spmv -- y = A x in double precision (Section III: the A p product of
+ * the CG listing), for every storage format.  x and y are device pointers to
+ * n doubles and must not overlap.  Deterministic: the same inputs give the
+ * same bits on every call (no floating-point atomics).
+ */
+int gbcg_spmv(gbcg_matrix_t A, const double* x, double* y, void* stream);
+
+/* gbcg_spmv_f32 -- y = A32 x with the single-precision copy of the values
+ * and float vectors (the product of the single-precision variant, Section IV). */
+int gbcg_spmv_f32(gbcg_matrix_t A, const float* x, float* y, void* stream);
+
+/*
+ * gbcg_solve -- conjugate gradient for A x = b (Section III listing).
+ *
+ *   b      n doubles, device or host memory
+ *   x      n doubles, device or host memory (both b and x in the same
+ *          space); on input the initial guess x0, on output the last iterate
+ *   tol    relative residual target: stop when ||b - A x||_2 <= tol ||b||_2,
+ *          checked on the recurrence residual after each r update and then
+ *          confirmed on the true residual in double precision
+ *   maxit  bound on CG iterations (inner iterations for GBCG_FP32_IR); the
+ *          paper's N; <= 0 means n
+ *   opts   may be NULL (defaults)
+ *   info   may be NULL; filled on every return that got past argument checks
+ *
+ * Host-memory b/x are staged through buffers allocated at create time; no
+ * allocation happens in this call.  The call synchronises `stream` before it
+ * returns (it reads the device status once per solve, once per refinement
+ * pass for GBCG_FP32_IR).  On GBCG_ERR_MAXIT, _NOT_SPD or _NONFINITE, x holds
+ * the last iterate.  On GBCG_ERR_TIMEOUT a device-side wait gave up after
+ * opts->wait_timeout_ms and the GPU context remains usable.
+ */
+int gbcg_solve(gbcg_matrix_t A, const double* b, double* x, double tol, int32_t maxit,
+               const gbcg_opts* opts, gbcg_info* info, void* stream);
+
+/* gbcg_stats -- layout facts of a handle. */
+int gbcg_stats(gbcg_matrix_t A, gbcg_matrix_stats* out);
+
+/* gbcg_status_string -- static text for a gbcg_status value. */
+const char* gbcg_status_string(int status);
+
+/* gbcg_last_error -- message of the last failed call on this thread ("" if none). */
+const char* gbcg_last_error(void);
+
+/*
+ * gbcg_selftest_wait_timeout -- check of the bounded device-side wait.  Runs
+ * the grid barrier used by the persistent solver on `ctas` co-resident CTAs
+ * (0 = the solver's own grid) with one CTA that never arrives, so every other
+ * CTA must give up after `timeout_ms` and record GBCG_ERR_TIMEOUT.  Returns
+ * GBCG_ERR_TIMEOUT when the wait ended as designed (the expected result),
+ * GBCG_OK if the barrier wrongly completed.  No paper counterpart: it tests
+ * the library's failure handling without faulting the GPU.
+ */
+int gbcg_selftest_wait_timeout(int32_t ctas, int32_t timeout_ms, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GBCG_H */

@@ -1,0 +1,220 @@
+"""GB300-native sparse conjugate-gradient solver (Python binding).
+
+Solves A x = b for sparse symmetric positive-definite A by the conjugate
+gradient iteration of Section III of "Parallel Sparse Matrix Solver on the GPU
+Applied to Simulation of Electrical Machines", with A given as CSR, symmetric
+CSR (upper triangle and diagonal) or CSC.  The names mirror the C ABI in
+``include/gbcg.h``: ``Matrix`` wraps ``gbcg_create``/``gbcg_destroy``,
+``Matrix.spmv`` wraps ``gbcg_spmv``, ``Matrix.solve`` wraps ``gbcg_solve``.
+
+PyTorch provides device memory and streams; every computation runs in the
+library's own sm_103a kernels.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _lib
+from ._lib import GbcgError
+
+FORMATS = {"csr": _lib.GBCG_CSR, "sym": _lib.GBCG_SYM_CSR_UPPER, "sym_upper": _lib.GBCG_SYM_CSR_UPPER,
+           "csc": _lib.GBCG_CSC}
+PRECISIONS = {"fp64": _lib.GBCG_FP64, "fp32_ir": _lib.GBCG_FP32_IR, "ir": _lib.GBCG_FP32_IR}
+
+
+def build(verbose: bool = False) -> str:
+    """Compile libgbcg.so for sm_103a in-tree."""
+    from .builder import build as _build
+    return _build(verbose=verbose)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _is_tensor(a) -> bool:
+    try:
+        torch = _torch()
+    except ImportError:  # pragma: no cover
+        return False
+    return isinstance(a, torch.Tensor)
+
+
+def _stream_handle(stream=None):
+    torch = _torch()
+    if stream is None:
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _host_stream(stream):
+    if stream is not None:
+        return _stream_handle(stream)
+    try:
+        torch = _torch()
+        if torch.cuda.is_available() and torch.cuda.is_initialized():
+            return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except ImportError:  # pragma: no cover
+        pass
+    return ctypes.c_void_p(0)
+
+
+@dataclass
+class SolveInfo:
+    iterations: int
+    outer: int
+    status: str
+    rel_res_recursive: float
+    rel_res_true: float
+    ms: float
+    kernel_ms: float = 0.0
+    kernel_launches: int = 0
+    launches: int = 0
+
+
+class Matrix:
+    """A sparse SPD matrix resident on the GPU (``gbcg_create``).
+
+    ``ptr``/``idx``/``val`` are numpy arrays (host) or CUDA tensors (device):
+    int32 offsets, int32 indices, float64 values, ``index_base`` 0 or 1.
+    """
+
+    def __init__(self, fmt, ptr, idx, val, index_base: int = 0, stream=None):
+        lib = _lib.load()
+        self._lib = lib
+        self.format = FORMATS[fmt] if isinstance(fmt, str) else int(fmt)
+        self._h = ctypes.c_void_p()
+        if _is_tensor(ptr):
+            torch = _torch()
+            ptr = ptr.to(torch.int32).contiguous()
+            idx = idx.to(torch.int32).contiguous()
+            val = val.to(torch.float64).contiguous()
+            self.n = int(ptr.numel()) - 1
+            nnz = int(idx.numel())
+            mem = _lib.GBCG_DEVICE if ptr.is_cuda else _lib.GBCG_HOST
+            args = (ptr.data_ptr(), idx.data_ptr(), val.data_ptr())
+            keep = (ptr, idx, val)
+        else:
+            ptr = np.ascontiguousarray(ptr, dtype=np.int32)
+            idx = np.ascontiguousarray(idx, dtype=np.int32)
+            val = np.ascontiguousarray(val, dtype=np.float64)
+            self.n = int(ptr.shape[0]) - 1
+            nnz = int(idx.shape[0])
+            mem = _lib.GBCG_HOST
+            args = (ptr.ctypes.data, idx.ctypes.data, val.ctypes.data)
+            keep = (ptr, idx, val)
+        rc = lib.gbcg_create(ctypes.byref(self._h), self.format, self.n, nnz, *[ctypes.c_void_p(a) for a in args],
+                             int(index_base), mem, _host_stream(stream))
+        del keep
+        _lib.check(rc, "gbcg_create")
+        self.nnz = nnz
+
+    # ------------------------------------------------------------ lifetime
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self._lib.gbcg_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # pragma: no cover
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def handle(self) -> int:
+        return int(self._h.value or 0)
+
+    def stats(self) -> dict:
+        s = _lib.Stats()
+        _lib.check(self._lib.gbcg_stats(self._h, ctypes.byref(s)), "gbcg_stats")
+        return {name: getattr(s, name) for name, _ in _lib.Stats._fields_}
+
+    # ------------------------------------------------------------ product
+    def spmv(self, x, y=None, stream=None):
+        """y = A x (float64 CUDA tensors)."""
+        torch = _torch()
+        if y is None:
+            y = torch.empty(self.n, dtype=torch.float64, device=x.device)
+        _check_vec(x, torch.float64, self.n, "x")
+        _check_vec(y, torch.float64, self.n, "y")
+        _lib.check(self._lib.gbcg_spmv(self._h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                                       _stream_handle(stream)), "gbcg_spmv")
+        return y
+
+    def spmv_f32(self, x, y=None, stream=None):
+        """y = A32 x with the single-precision copy of the values (float32 CUDA tensors)."""
+        torch = _torch()
+        if y is None:
+            y = torch.empty(self.n, dtype=torch.float32, device=x.device)
+        _check_vec(x, torch.float32, self.n, "x")
+        _check_vec(y, torch.float32, self.n, "y")
+        _lib.check(self._lib.gbcg_spmv_f32(self._h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                                           _stream_handle(stream)), "gbcg_spmv_f32")
+        return y
+
+    # ------------------------------------------------------------ solve
+    def solve(self, b, x=None, tol: float = 1e-10, maxit: int = 0, precision: str = "fp64",
+              inner_tol: float = 1e-4, max_outer: int = 30, wait_timeout_ms: int = 1000,
+              max_restarts: int = 3, stream=None, raise_on_error: bool = True):
+        """Conjugate gradient for A x = b (``gbcg_solve``).
+
+        ``b`` and ``x`` are float64 CUDA tensors, or numpy arrays (host
+        memory; the copies happen inside the call).  ``x`` holds x0 on entry
+        (zeros if None) and the solution on return.  Returns (x, SolveInfo).
+        """
+        opts = _lib.Opts(PRECISIONS[precision], int(max_outer), float(inner_tol), int(wait_timeout_ms),
+                         int(max_restarts))
+        info = _lib.Info()
+        if _is_tensor(b):
+            torch = _torch()
+            if x is None:
+                x = torch.zeros_like(b)
+            if b.is_cuda:
+                _check_vec(b, torch.float64, self.n, "b")
+                _check_vec(x, torch.float64, self.n, "x")
+                stream_h = _stream_handle(stream)
+            else:
+                b = b.contiguous()
+                stream_h = _host_stream(stream)
+            bp, xp = b.data_ptr(), x.data_ptr()
+        else:
+            b = np.ascontiguousarray(b, dtype=np.float64)
+            x = np.zeros(self.n) if x is None else x
+            if not (isinstance(x, np.ndarray) and x.dtype == np.float64 and x.flags.c_contiguous):
+                raise ValueError("x must be a contiguous float64 numpy array")
+            stream_h = _host_stream(stream)
+            bp, xp = b.ctypes.data, x.ctypes.data
+        rc = self._lib.gbcg_solve(self._h, ctypes.c_void_p(bp), ctypes.c_void_p(xp), float(tol), int(maxit),
+                                  ctypes.byref(opts), ctypes.byref(info), stream_h)
+        res = SolveInfo(info.iterations, info.outer, _lib.STATUS_NAMES[info.status] if rc == info.status else
+                        _lib.STATUS_NAMES[rc], info.rel_res_recursive, info.rel_res_true, info.ms,
+                        info.kernel_ms, info.kernel_launches, info.launches)
+        if rc != 0 and raise_on_error and rc not in (3,):
+            raise GbcgError(rc, "gbcg_solve", _lib.last_error())
+        return x, res
+
+
+def _check_vec(t, dtype, n, name):
+    if not t.is_cuda or t.dtype != dtype or t.numel() != n or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous {dtype} CUDA tensor of length {n}")
+
+
+def selftest_wait_timeout(ctas: int = 0, timeout_ms: int = 50, stream=None) -> int:
+    """Runs the bounded-wait self-test (``gbcg_selftest_wait_timeout``); returns its status code."""
+    return _lib.load().gbcg_selftest_wait_timeout(int(ctas), int(timeout_ms), _stream_handle(stream))
+
+
+__all__ = ["Matrix", "SolveInfo", "GbcgError", "build", "selftest_wait_timeout", "FORMATS", "PRECISIONS"]

@@ -1,0 +1,627 @@
+// gbcg.cu -- C ABI of the GB300 conjugate-gradient library (include/gbcg.h).
+//
+// Host driver: validates and lays out the matrix (layout.cpp), owns the
+// device copies and the solve workspace, and launches the kernels of
+// kernels.cuh.  Nothing here computes on the host: every step of a product
+// or a solve runs in the library's kernels.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/gbcg.h"
+#include "kernels.cuh"
+#include "layout.h"
+
+using namespace gbcg;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+#define CUDA_TRY(...)                                                                               \
+  do {                                                                                              \
+    cudaError_t e_ = (__VA_ARGS__);                                                                     \
+    if (e_ != cudaSuccess)                                                                          \
+      return fail(e_ == cudaErrorMemoryAllocation ? GBCG_ERR_NOMEM : GBCG_ERR_CUDA,                 \
+                  std::string(#__VA_ARGS__) + ": " + cudaGetErrorString(e_));                              \
+  } while (0)
+
+template <typename T>
+int dalloc(T** p, size_t count, int64_t& bytes) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  if (e != cudaSuccess) return fail(GBCG_ERR_NOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  bytes += (int64_t)(count * sizeof(T));
+  return 0;
+}
+
+template <typename T>
+int upload(T** p, const std::vector<T>& h, cudaStream_t s, int64_t& bytes) {
+  if (int rc = dalloc(p, h.size(), bytes)) return rc;
+  if (!h.empty()) CUDA_TRY(cudaMemcpyAsync(*p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+  return 0;
+}
+
+std::vector<float> to_f32(const std::vector<double>& v) {
+  std::vector<float> o(v.size());
+  for (size_t i = 0; i < v.size(); ++i) o[i] = (float)v[i];
+  return o;
+}
+
+int env_int(const char* name, int dflt) {
+  const char* s = getenv(name);
+  return (s && *s) ? atoi(s) : dflt;
+}
+
+}  // namespace
+
+struct gbcg_matrix_s {
+  int32_t format = 0;
+  int64_t n = 0, nnz_input = 0, nnz_full = 0, slots = 0, plan_slots = 0;
+  int64_t nslices = 0, nlong = 0, bytes = 0;
+  int sym = 0;
+  // layout (device)
+  int64_t* sl_ptr = nullptr;
+  int32_t* col = nullptr;
+  double* val64 = nullptr;
+  float* val32 = nullptr;
+  uint32_t* long_mask = nullptr;
+  int32_t* long_row = nullptr;
+  int64_t* long_ptr = nullptr;
+  int32_t* long_col = nullptr;
+  double* long_val64 = nullptr;
+  float* long_val32 = nullptr;
+  double* diag64 = nullptr;
+  float* diag32 = nullptr;
+  int64_t* pl_ptr = nullptr;
+  int32_t* pl_i = nullptr;
+  uint16_t* pl_k = nullptr;
+  // persistent-solver partition
+  int grid = 1;
+  int32_t* cta_slice = nullptr;
+  int32_t* cta_long = nullptr;
+  // workspace
+  double *r = nullptr, *p = nullptr, *q = nullptr, *bstage = nullptr, *xstage = nullptr;
+  float *r32 = nullptr, *p32 = nullptr, *q32 = nullptr, *d32 = nullptr, *rhs32 = nullptr;
+  double* part = nullptr;   // max(2 * grid, one-shot blocks)
+  double* sums = nullptr;   // small scalars
+  int64_t part_len = 0;
+  GridBar* bar = nullptr;
+  CgState* st = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // brackets of the persistent launches
+  // pinned host mirrors
+  CgState* st_h = nullptr;
+  GridBar* bar_h = nullptr;
+  double* sums_h = nullptr;
+
+  template <typename V>
+  OpDev<V> op() const;
+  int spmv_blocks() const { return (int)std::max<int64_t>(1, (nslices + nlong + 7) / 8); }
+};
+
+template <>
+OpDev<double> gbcg_matrix_s::op<double>() const {
+  OpDev<double> o;
+  o.n = n;
+  o.nslices = nslices;
+  o.nlong = nlong;
+  o.sl_ptr = sl_ptr;
+  o.col = col;
+  o.val = val64;
+  o.long_mask = long_mask;
+  o.long_row = long_row;
+  o.long_ptr = long_ptr;
+  o.long_col = long_col;
+  o.long_val = long_val64;
+  o.diag = diag64;
+  o.pl_ptr = pl_ptr;
+  o.pl_i = pl_i;
+  o.pl_k = pl_k;
+  return o;
+}
+template <>
+OpDev<float> gbcg_matrix_s::op<float>() const {
+  OpDev<float> o;
+  o.n = n;
+  o.nslices = nslices;
+  o.nlong = nlong;
+  o.sl_ptr = sl_ptr;
+  o.col = col;
+  o.val = val32;
+  o.long_mask = long_mask;
+  o.long_row = long_row;
+  o.long_ptr = long_ptr;
+  o.long_col = long_col;
+  o.long_val = long_val32;
+  o.diag = diag32;
+  o.pl_ptr = pl_ptr;
+  o.pl_i = pl_i;
+  o.pl_k = pl_k;
+  return o;
+}
+
+namespace {
+
+void free_matrix(gbcg_matrix_s* M) {
+  if (!M) return;
+  void* dev[] = {M->sl_ptr, M->col, M->val64, M->val32, M->long_mask, M->long_row, M->long_ptr, M->long_col,
+                 M->long_val64, M->long_val32, M->diag64, M->diag32, M->pl_ptr, M->pl_i, M->pl_k,
+                 M->cta_slice, M->cta_long, M->r, M->p, M->q, M->bstage, M->xstage, M->r32, M->p32, M->q32,
+                 M->d32, M->rhs32, M->part, M->sums, M->bar, M->st};
+  for (void* d : dev)
+    if (d) cudaFree(d);
+  if (M->st_h) cudaFreeHost(M->st_h);
+  if (M->bar_h) cudaFreeHost(M->bar_h);
+  if (M->sums_h) cudaFreeHost(M->sums_h);
+  if (M->ev0) cudaEventDestroy(M->ev0);
+  if (M->ev1) cudaEventDestroy(M->ev1);
+  delete M;
+}
+
+template <typename V, bool SYM, bool OUTER>
+int occupancy_of(int& per_sm) {
+  CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cg<V, SYM, OUTER>, kCgThreads, 0));
+  return 0;
+}
+
+template <bool SYM>
+int solver_occupancy(int& per_sm) {
+  int a = 0, b = 0;
+  if (int rc = occupancy_of<double, SYM, true>(a)) return rc;
+  if (int rc = occupancy_of<float, SYM, false>(b)) return rc;
+  per_sm = std::min(a, b);
+  return 0;
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+template <typename V, bool SYM, bool OUTER>
+cudaError_t launch_cg(const CgArgs<V>& args, int grid, cudaStream_t s) {
+  void* kargs[] = {(void*)&args};
+  return cudaLaunchCooperativeKernel((const void*)k_cg<V, SYM, OUTER>, dim3(grid), dim3(kCgThreads), kargs, 0, s);
+}
+
+template <typename V, bool OUTER>
+cudaError_t launch_cg_fmt(const gbcg_matrix_s* M, const CgArgs<V>& a, cudaStream_t s) {
+  return M->sym ? launch_cg<V, true, OUTER>(a, M->grid, s) : launch_cg<V, false, OUTER>(a, M->grid, s);
+}
+
+int status_from_device(const CgState& st, const GridBar& gb) {
+  if (gb.status != 0) return GBCG_ERR_TIMEOUT;
+  switch (st.status) {
+    case kOk: return GBCG_OK;
+    case kNotSpd: return GBCG_ERR_NOT_SPD;
+    case kMaxit: return GBCG_ERR_MAXIT;
+    case kNonfinite: return GBCG_ERR_NONFINITE;
+    default: return GBCG_ERR_TIMEOUT;
+  }
+}
+
+long long timeout_ns_of(const gbcg_opts* o) {
+  int ms = (o && o->wait_timeout_ms > 0) ? o->wait_timeout_ms : 1000;
+  return (long long)ms * 1000000LL;
+}
+
+template <typename V>
+CgArgs<V> make_args(const gbcg_matrix_s* M, V* x, V* r, V* p, V* q, const V* b, double tol, int maxit,
+                    int max_restarts, long long timeout_ns) {
+  CgArgs<V> a;
+  a.A = M->op<V>();
+  a.x = x;
+  a.r = r;
+  a.p = p;
+  a.q = q;
+  a.b = b;
+  a.part = M->part;
+  a.bar = M->bar;
+  a.st = M->st;
+  a.cta_slice = M->cta_slice;
+  a.cta_long = M->cta_long;
+  a.tol = tol;
+  a.maxit = maxit;
+  a.max_restarts = max_restarts;
+  a.timeout_ns = timeout_ns;
+  return a;
+}
+
+// Reads the solver state and barrier word back (one synchronisation).
+int read_state(gbcg_matrix_s* M, cudaStream_t s) {
+  CUDA_TRY(cudaMemcpyAsync(M->st_h, M->st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaMemcpyAsync(M->bar_h, M->bar, sizeof(GridBar), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  return 0;
+}
+
+int solve_fp64(gbcg_matrix_s* M, const double* b, double* x, double tol, int maxit, const gbcg_opts* o,
+               gbcg_info* info, cudaStream_t s) {
+  const int max_restarts = (o && o->max_restarts > 0) ? o->max_restarts : 3;
+  CUDA_TRY(cudaMemsetAsync(M->bar, 0, sizeof(GridBar), s));
+  CgArgs<double> a = make_args<double>(M, x, M->r, M->p, M->q, b, tol, maxit, max_restarts, timeout_ns_of(o));
+  CUDA_TRY(cudaEventRecord(M->ev0, s));
+  CUDA_TRY(launch_cg_fmt<double, true>(M, a, s));
+  CUDA_TRY(cudaEventRecord(M->ev1, s));
+  if (int rc = read_state(M, s)) return rc;
+  float kms = 0.f;
+  CUDA_TRY(cudaEventElapsedTime(&kms, M->ev0, M->ev1));
+  info->kernel_ms = kms;
+  info->kernel_launches = 1;
+  info->launches = 1;
+  const int status = status_from_device(*M->st_h, *M->bar_h);
+  info->iterations = M->st_h->k;
+  info->outer = M->st_h->restarts;
+  info->status = status;
+  info->rel_res_recursive = M->st_h->nb > 0 ? std::sqrt(M->st_h->rr) / M->st_h->nb : 0.0;
+  info->rel_res_true = M->st_h->nb > 0 ? M->st_h->rel_true : 0.0;
+  if (status == GBCG_ERR_TIMEOUT)
+    g_last_error = "device-side wait ran out (barrier " + std::to_string(M->bar_h->where) + ")";
+  return status;
+}
+
+int dot_to_host(gbcg_matrix_s* M, const double* a, const double* b, double& out, cudaStream_t s) {
+  const int blocks = (int)std::min<int64_t>(M->part_len, std::max<int64_t>(1, (M->n + 255) / 256));
+  k_dot_part<<<blocks, 256, 0, s>>>(a, b, M->n, M->part);
+  k_sum_part<<<1, 256, 0, s>>>(M->part, blocks, M->sums);
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaMemcpyAsync(M->sums_h, M->sums, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  out = M->sums_h[0];
+  return 0;
+}
+
+int residual_to_host(gbcg_matrix_s* M, const double* b, const double* x, double& rr, cudaStream_t s) {
+  const int blocks = M->spmv_blocks();
+  if (M->sym)
+    k_residual<true><<<blocks, 256, 0, s>>>(M->op<double>(), b, x, M->r, M->part);
+  else
+    k_residual<false><<<blocks, 256, 0, s>>>(M->op<double>(), b, x, M->r, M->part);
+  k_sum_part<<<1, 256, 0, s>>>(M->part, blocks, M->sums);
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaMemcpyAsync(M->sums_h, M->sums, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  rr = M->sums_h[0];
+  return 0;
+}
+
+// Single-precision inner CG with double-precision iterative refinement.
+int solve_ir(gbcg_matrix_s* M, const double* b, double* x, double tol, int maxit, const gbcg_opts* o,
+             gbcg_info* info, cudaStream_t s) {
+  const int max_outer = (o && o->max_outer > 0) ? o->max_outer : 30;
+  const double inner_tol = (o && o->inner_tol > 0) ? o->inner_tol : 1e-4;
+  const long long tns = timeout_ns_of(o);
+  const int64_t n = M->n;
+  const int gsz = (int)std::min<int64_t>(4096, std::max<int64_t>(1, (n + 255) / 256));
+  double bb = 0.0;
+  if (int rc = dot_to_host(M, b, b, bb, s)) return rc;
+  info->launches += 2;  // k_dot_part + k_sum_part
+  const double nb = std::sqrt(bb);
+  int used = 0, outer = 0, status = GBCG_ERR_MAXIT;
+  double rel = 0.0;
+  if (nb == 0.0) {
+    CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double) * n, s));
+    status = GBCG_OK;
+  } else {
+    for (;;) {
+      double rr = 0.0;
+      if (int rc = residual_to_host(M, b, x, rr, s)) return rc;
+      info->launches += 2;  // k_residual + k_sum_part
+      rel = std::sqrt(rr) / nb;
+      if (!std::isfinite(rel)) { status = GBCG_ERR_NONFINITE; break; }
+      if (rel <= tol) { status = GBCG_OK; break; }
+      if (outer >= max_outer || used >= maxit) { status = GBCG_ERR_MAXIT; break; }
+      const double nr = std::sqrt(rr);
+      k_scale_to_f32<<<gsz, 256, 0, s>>>(M->r, 1.0 / nr, n, M->rhs32);
+      CUDA_TRY(cudaGetLastError());
+      CUDA_TRY(cudaMemsetAsync(M->bar, 0, sizeof(GridBar), s));
+      CgArgs<float> a = make_args<float>(M, M->d32, M->r32, M->p32, M->q32, M->rhs32, inner_tol, maxit - used, 0, tns);
+      CUDA_TRY(cudaEventRecord(M->ev0, s));
+      CUDA_TRY(launch_cg_fmt<float, false>(M, a, s));
+      CUDA_TRY(cudaEventRecord(M->ev1, s));
+      if (int rc = read_state(M, s)) return rc;
+      float kms = 0.f;
+      CUDA_TRY(cudaEventElapsedTime(&kms, M->ev0, M->ev1));
+      info->kernel_ms += kms;
+      info->kernel_launches += 1;
+      info->launches += 2;  // k_scale_to_f32 + inner k_cg
+      if (M->bar_h->status != 0) {
+        status = GBCG_ERR_TIMEOUT;
+        g_last_error = "device-side wait ran out (inner solve)";
+        break;
+      }
+      used += M->st_h->k;
+      ++outer;
+      if ((M->st_h->status == kNotSpd || M->st_h->status == kNonfinite) && M->st_h->k == 0) {
+        status = M->st_h->status == kNotSpd ? GBCG_ERR_NOT_SPD : GBCG_ERR_NONFINITE;
+        break;
+      }
+      k_axpy_f32<<<gsz, 256, 0, s>>>(nr, M->d32, n, x);
+      CUDA_TRY(cudaGetLastError());
+      info->launches += 1;
+    }
+  }
+  info->iterations = used;
+  info->outer = outer;
+  info->status = status;
+  info->rel_res_recursive = rel;
+  info->rel_res_true = rel;
+  return status;
+}
+
+template <typename V>
+int spmv_any(gbcg_matrix_t A, const V* x, V* y, cudaStream_t s) {
+  if (!A) return fail(GBCG_ERR_INVALID, "null matrix handle");
+  if (A->n == 0) return GBCG_OK;
+  if (!x || !y) return fail(GBCG_ERR_INVALID, "null vector");
+  const int64_t warps = A->nslices + A->nlong;
+  const int blocks = (int)((warps + 7) / 8);
+  if (A->sym)
+    k_spmv<V, true><<<blocks, 256, 0, s>>>(A->op<V>(), x, y);
+  else
+    k_spmv<V, false><<<blocks, 256, 0, s>>>(A->op<V>(), x, y);
+  CUDA_TRY(cudaGetLastError());
+  return GBCG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int gbcg_create(gbcg_matrix_t* out, int32_t format, int64_t n, int64_t nnz, const int32_t* ptr, const int32_t* idx,
+                const double* val, int32_t index_base, int32_t memory, void* stream) {
+  g_last_error.clear();
+  if (!out) return fail(GBCG_ERR_INVALID, "null output handle");
+  *out = nullptr;
+  if (n < 0 || nnz < 0) return fail(GBCG_ERR_INVALID, "n and nnz must be non-negative");
+  if (memory != GBCG_HOST && memory != GBCG_DEVICE) return fail(GBCG_ERR_INVALID, "memory must be GBCG_HOST or GBCG_DEVICE");
+  if (!ptr) return fail(GBCG_ERR_INVALID, "null ptr array");
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<int32_t> hptr, hidx;
+  std::vector<double> hval;
+  if (memory == GBCG_DEVICE) {  // bring the caller's arrays to the host for the layout build
+    hptr.resize(n + 1);
+    CUDA_TRY(cudaMemcpyAsync(hptr.data(), ptr, sizeof(int32_t) * (n + 1), cudaMemcpyDeviceToHost, s));
+    if (nnz > 0) {
+      if (!idx || !val) return fail(GBCG_ERR_INVALID, "null idx/val array");
+      hidx.resize(nnz);
+      hval.resize(nnz);
+      CUDA_TRY(cudaMemcpyAsync(hidx.data(), idx, sizeof(int32_t) * nnz, cudaMemcpyDeviceToHost, s));
+      CUDA_TRY(cudaMemcpyAsync(hval.data(), val, sizeof(double) * nnz, cudaMemcpyDeviceToHost, s));
+    }
+    CUDA_TRY(cudaStreamSynchronize(s));
+    ptr = hptr.data();
+    idx = hidx.data();
+    val = hval.data();
+  }
+  LayoutHost L;
+  std::string err;
+  int rc = build_layout(format, n, nnz, ptr, idx, val, index_base, L, err);
+  if (rc) return fail(rc, err);
+
+  gbcg_matrix_s* M = new gbcg_matrix_s();
+  M->format = format;
+  M->n = n;
+  M->nnz_input = nnz;
+  M->nnz_full = L.nnz_full;
+  M->sym = format == GBCG_SYM_CSR_UPPER;
+  M->nslices = L.A.nslices;
+  M->nlong = (int64_t)L.A.long_row.size();
+  M->slots = L.A.sl_ptr.empty() ? 0 : L.A.sl_ptr.back();
+  M->plan_slots = L.plan.pl_ptr.empty() ? 0 : L.plan.pl_ptr.back();
+  auto bail = [&](int code) {
+    free_matrix(M);
+    return code;
+  };
+#define TRY(x)                  \
+  do {                          \
+    if (int rc_ = (x)) return bail(rc_); \
+  } while (0)
+  int64_t& B = M->bytes;
+  TRY(upload(&M->sl_ptr, L.A.sl_ptr, s, B));
+  TRY(upload(&M->col, L.A.col, s, B));
+  TRY(upload(&M->val64, L.A.val, s, B));
+  TRY(upload(&M->val32, to_f32(L.A.val), s, B));
+  TRY(upload(&M->long_mask, L.A.long_mask, s, B));
+  TRY(upload(&M->long_row, L.A.long_row, s, B));
+  TRY(upload(&M->long_ptr, L.A.long_ptr, s, B));
+  TRY(upload(&M->long_col, L.A.long_col, s, B));
+  TRY(upload(&M->long_val64, L.A.long_val, s, B));
+  TRY(upload(&M->long_val32, to_f32(L.A.long_val), s, B));
+  if (M->sym) {
+    TRY(upload(&M->diag64, L.diag, s, B));
+    TRY(upload(&M->diag32, to_f32(L.diag), s, B));
+    TRY(upload(&M->pl_ptr, L.plan.pl_ptr, s, B));
+    TRY(upload(&M->pl_i, L.plan.pl_i, s, B));
+    TRY(upload(&M->pl_k, L.plan.pl_k, s, B));
+  }
+  // persistent-solver grid: co-resident CTAs, at least a slice per warp
+  int dev = 0, sms = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return bail(fail(GBCG_ERR_CUDA, "cannot query the device"));
+  TRY(M->sym ? solver_occupancy<true>(per_sm) : solver_occupancy<false>(per_sm));
+  if (per_sm < 1) return bail(fail(GBCG_ERR_CUDA, "the persistent solver kernel cannot be resident"));
+  per_sm = std::min(per_sm, std::max(1, env_int("GBCG_CTAS_PER_SM", 2)));
+  int64_t want = (M->nslices + (kCgThreads / 32) - 1) / (kCgThreads / 32);
+  int env_grid = env_int("GBCG_GRID", 0);
+  M->grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * sms, want));
+  if (env_grid > 0) M->grid = std::min(env_grid, per_sm * sms);
+  std::vector<int32_t> cs = partition_slices(L, M->grid);
+  std::vector<int32_t> cl(M->grid + 1, 0);
+  for (int c = 0; c <= M->grid; ++c) {  // long rows go to the CTA that owns their row
+    const int64_t row0 = (int64_t)cs[c] * 32;
+    cl[c] = (int32_t)(std::lower_bound(L.A.long_row.begin(), L.A.long_row.end(), row0) - L.A.long_row.begin());
+  }
+  cl[M->grid] = (int32_t)M->nlong;
+  TRY(upload(&M->cta_slice, cs, s, B));
+  TRY(upload(&M->cta_long, cl, s, B));
+  // workspace
+  const size_t nn = (size_t)std::max<int64_t>(n, 1);
+  TRY(dalloc(&M->r, nn, B));
+  TRY(dalloc(&M->p, nn, B));
+  TRY(dalloc(&M->q, nn, B));
+  TRY(dalloc(&M->bstage, nn, B));
+  TRY(dalloc(&M->xstage, nn, B));
+  TRY(dalloc(&M->r32, nn, B));
+  TRY(dalloc(&M->p32, nn, B));
+  TRY(dalloc(&M->q32, nn, B));
+  TRY(dalloc(&M->d32, nn, B));
+  TRY(dalloc(&M->rhs32, nn, B));
+  M->part_len = std::max<int64_t>({2 * (int64_t)M->grid, (int64_t)M->spmv_blocks(), 4096});
+  TRY(dalloc(&M->part, (size_t)M->part_len, B));
+  TRY(dalloc(&M->sums, 8, B));
+  TRY(dalloc(&M->bar, 1, B));
+  TRY(dalloc(&M->st, 1, B));
+  if (cudaMallocHost((void**)&M->st_h, sizeof(CgState)) != cudaSuccess ||
+      cudaMallocHost((void**)&M->bar_h, sizeof(GridBar)) != cudaSuccess ||
+      cudaMallocHost((void**)&M->sums_h, 8 * sizeof(double)) != cudaSuccess)
+    return bail(fail(GBCG_ERR_NOMEM, "cudaMallocHost failed"));
+  if (cudaEventCreate(&M->ev0) != cudaSuccess || cudaEventCreate(&M->ev1) != cudaSuccess)
+    return bail(fail(GBCG_ERR_CUDA, "cudaEventCreate failed"));
+  if (cudaStreamSynchronize(s) != cudaSuccess) return bail(fail(GBCG_ERR_CUDA, "upload failed"));
+#undef TRY
+  *out = M;
+  return GBCG_OK;
+}
+
+int gbcg_destroy(gbcg_matrix_t A) {
+  free_matrix(A);
+  return GBCG_OK;
+}
+
+int gbcg_spmv(gbcg_matrix_t A, const double* x, double* y, void* stream) {
+  g_last_error.clear();
+  return spmv_any<double>(A, x, y, (cudaStream_t)stream);
+}
+
+int gbcg_spmv_f32(gbcg_matrix_t A, const float* x, float* y, void* stream) {
+  g_last_error.clear();
+  return spmv_any<float>(A, x, y, (cudaStream_t)stream);
+}
+
+int gbcg_solve(gbcg_matrix_t A, const double* b, double* x, double tol, int32_t maxit, const gbcg_opts* opts,
+               gbcg_info* info, void* stream) {
+  g_last_error.clear();
+  gbcg_info local;
+  if (!info) info = &local;
+  memset(info, 0, sizeof(*info));
+  if (!A) return fail(GBCG_ERR_INVALID, "null matrix handle");
+  if (!(tol >= 0.0) || !std::isfinite(tol)) return fail(GBCG_ERR_INVALID, "tol must be finite and >= 0");
+  if (opts && (opts->precision != GBCG_FP64 && opts->precision != GBCG_FP32_IR))
+    return fail(GBCG_ERR_INVALID, "unknown precision");
+  const auto t0 = std::chrono::steady_clock::now();
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t n = A->n;
+  if (n == 0) {
+    info->status = GBCG_OK;
+    return GBCG_OK;
+  }
+  if (!b || !x) return fail(GBCG_ERR_INVALID, "null vector");
+  if (maxit <= 0) maxit = (int32_t)std::min<int64_t>(n, 0x7fffffff);
+  const bool bdev = is_device_ptr(b), xdev = is_device_ptr(x);
+  if (bdev != xdev) return fail(GBCG_ERR_INVALID, "b and x must both be device or both be host memory");
+  const double* bd = b;
+  double* xd = x;
+  if (!bdev) {  // host vectors: stage through the buffers allocated at create time
+    CUDA_TRY(cudaMemcpyAsync(A->bstage, b, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(A->xstage, x, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+    bd = A->bstage;
+    xd = A->xstage;
+  }
+  int status;
+  if (opts && opts->precision == GBCG_FP32_IR)
+    status = solve_ir(A, bd, xd, tol, maxit, opts, info, s);
+  else
+    status = solve_fp64(A, bd, xd, tol, maxit, opts, info, s);
+  if (status == GBCG_ERR_CUDA || status == GBCG_ERR_NOMEM) return status;
+  if (!bdev) {
+    CUDA_TRY(cudaMemcpyAsync(x, A->xstage, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+  }
+  info->ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  return status;
+}
+
+int gbcg_stats(gbcg_matrix_t A, gbcg_matrix_stats* out) {
+  if (!A || !out) return fail(GBCG_ERR_INVALID, "null argument");
+  memset(out, 0, sizeof(*out));
+  out->n = A->n;
+  out->nnz_input = A->nnz_input;
+  out->nnz_full = A->nnz_full;
+  out->stored_slots = A->slots;
+  out->plan_slots = A->plan_slots;
+  out->long_rows = A->nlong;
+  out->device_bytes = A->bytes;
+  const int64_t n = A->n, m = A->nnz_input;
+  out->spmv_bytes_fp64 = 12 * m + 4 * (n + 1) + 16 * n;
+  out->spmv_bytes_fp32 = 8 * m + 4 * (n + 1) + 8 * n;
+  out->format = A->format;
+  out->grid_ctas = A->grid;
+  return GBCG_OK;
+}
+
+const char* gbcg_status_string(int status) {
+  switch (status) {
+    case GBCG_OK: return "GBCG_OK";
+    case GBCG_ERR_INVALID: return "GBCG_ERR_INVALID";
+    case GBCG_ERR_NOT_SPD: return "GBCG_ERR_NOT_SPD";
+    case GBCG_ERR_MAXIT: return "GBCG_ERR_MAXIT";
+    case GBCG_ERR_NONFINITE: return "GBCG_ERR_NONFINITE";
+    case GBCG_ERR_TIMEOUT: return "GBCG_ERR_TIMEOUT";
+    case GBCG_ERR_CUDA: return "GBCG_ERR_CUDA";
+    case GBCG_ERR_NOMEM: return "GBCG_ERR_NOMEM";
+    default: return "GBCG_UNKNOWN_STATUS";
+  }
+}
+
+const char* gbcg_last_error(void) { return g_last_error.c_str(); }
+
+int gbcg_selftest_wait_timeout(int32_t ctas, int32_t timeout_ms, void* stream) {
+  g_last_error.clear();
+  if (timeout_ms <= 0 || timeout_ms > 10000) return fail(GBCG_ERR_INVALID, "timeout_ms must be in (0, 10000]");
+  cudaStream_t s = (cudaStream_t)stream;
+  int dev = 0, sms = 0, per_sm = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_wait_selftest, 32, 0));
+  if (ctas <= 0) ctas = 2 * sms;
+  if (ctas < 2 || ctas > per_sm * sms) return fail(GBCG_ERR_INVALID, "ctas out of the co-resident range");
+  GridBar* gb = nullptr;
+  GridBar* gh = nullptr;
+  CUDA_TRY(cudaMalloc(&gb, sizeof(GridBar)));
+  if (cudaMallocHost(&gh, sizeof(GridBar)) != cudaSuccess) {
+    cudaFree(gb);
+    return fail(GBCG_ERR_NOMEM, "cudaMallocHost failed");
+  }
+  long long tns = (long long)timeout_ms * 1000000LL;
+  void* kargs[] = {(void*)&gb, (void*)&tns};
+  cudaError_t e = cudaMemsetAsync(gb, 0, sizeof(GridBar), s);
+  if (e == cudaSuccess) e = cudaLaunchCooperativeKernel((const void*)k_wait_selftest, dim3(ctas), dim3(32), kargs, 0, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(gh, gb, sizeof(GridBar), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  const int st = gh->status;
+  cudaFree(gb);
+  cudaFreeHost(gh);
+  if (e != cudaSuccess) return fail(GBCG_ERR_CUDA, cudaGetErrorString(e));
+  if (st == kTimeout) return fail(GBCG_ERR_TIMEOUT, "barrier wait ran out as designed");
+  return GBCG_OK;
+}
+
+}  // extern "C"

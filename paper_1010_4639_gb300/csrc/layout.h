@@ -1,0 +1,68 @@
+// layout.h -- host-side construction of the device layouts of a sparse matrix.
+//
+// Row-gather layout ("SELL-32"): rows are grouped in slices of 32 consecutive
+// rows; slice s stores its rows' entries slot-major, i.e. the k-th entry of
+// row 32s + l lives at sl_ptr[s] + 32k + l.  One warp computes one slice with
+// one lane per row (the paper's thread-per-row "trivial" kernel of Section
+// III), and a warp's 32 loads of one slot fall into one contiguous 256-byte
+// (double) or 128-byte (int32, float) segment.  Each slice is as long as its
+// longest row; shorter rows are padded with zero values whose column is the
+// row itself (so the padded load hits a line the row already uses).
+//
+// Rows much longer than the typical row ("long rows") are taken out of the
+// slices and computed warp-per-row from a plain CSR copy, so one long row
+// does not pad its 31 neighbours.
+//
+// Symmetric storage (Section III: A = L + D + U with U' = L) keeps the strict
+// upper triangle U in the sliced layout, the diagonal D as a vector, and a
+// transpose plan: for every row j, the list of (i, k) with U_ij being the k-th
+// stored entry of row i, in increasing i.  The plan is itself sliced, so the
+// transpose half U' x is a second row gather that reads U's values in place:
+// no entry is stored twice and no floating-point atomics are needed.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace gbcg {
+
+struct SellHost {
+  int64_t nslices = 0;
+  std::vector<int64_t> sl_ptr;     // nslices + 1, in slots, multiples of 32
+  std::vector<int32_t> col;        // slots
+  std::vector<double> val;         // slots
+  std::vector<uint32_t> long_mask; // nslices: lanes whose row is a long row
+  std::vector<int32_t> long_row;   // long rows, increasing
+  std::vector<int64_t> long_ptr;   // nlong + 1
+  std::vector<int32_t> long_col;
+  std::vector<double> long_val;
+};
+
+struct PlanHost {
+  std::vector<int64_t> pl_ptr;     // nslices + 1
+  std::vector<int32_t> pl_i;       // source row i
+  std::vector<uint16_t> pl_k;      // slot of U_ij in row i; 0xFFFF = padding
+};
+
+struct LayoutHost {
+  int32_t format = 0;
+  int64_t n = 0;
+  int64_t nnz_input = 0;
+  int64_t nnz_full = 0;            // entries of the full operator
+  SellHost A;                      // full operator (CSR/CSC) or strict upper U (symmetric)
+  std::vector<double> diag;        // symmetric only: nslices * 32, zero padded
+  PlanHost plan;                   // symmetric only
+};
+
+// Validates the input (0- or 1-based) and builds the layout.  Returns 0 or a
+// gbcg_status error code, with a message in `err`.
+int build_layout(int32_t format, int64_t n, int64_t nnz, const int32_t* ptr, const int32_t* idx,
+                 const double* val, int32_t index_base, LayoutHost& out, std::string& err);
+
+// Contiguous slice ranges for `parts` workers, balanced by stored slots
+// (plus plan slots for the symmetric layout).  Returns parts + 1 offsets.
+std::vector<int32_t> partition_slices(const LayoutHost& L, int parts);
+// Long rows split evenly over `parts` workers (parts + 1 offsets).
+std::vector<int32_t> partition_long(const LayoutHost& L, int parts);
+
+}  // namespace gbcg

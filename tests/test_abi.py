@@ -1,0 +1,103 @@
+"""The C ABI library (CPU side): it builds, loads, exports every entry point
+declared in include/gbcg.h, and rejects malformed input before any GPU work."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_1010_4639_gb300 as gb
+from paper_1010_4639_gb300 import _lib
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "gbcg.h")
+
+
+def declared_symbols():
+    src = open(HEADER).read()
+    return sorted(set(re.findall(r"^(?:int|const char\*)\s+(gbcg_\w+)\s*\(", src, flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    gb.build()
+    return _lib.load()
+
+
+def test_header_declares_the_boundary():
+    syms = declared_symbols()
+    for name in ("gbcg_create", "gbcg_spmv", "gbcg_solve", "gbcg_destroy", "gbcg_status_string", "gbcg_last_error"):
+        assert name in syms
+    assert sorted(_lib.EXPORTS) == syms
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_symbols():
+        assert hasattr(lib, name), name
+
+
+def test_status_strings(lib):
+    for code, name in enumerate(_lib.STATUS_NAMES):
+        assert lib.gbcg_status_string(code).decode() == ("GBCG_OK" if code == 0 else "GBCG_ERR_" + name)
+    assert lib.gbcg_status_string(99).decode() == "GBCG_UNKNOWN_STATUS"
+
+
+def _create(lib, fmt, ptr, idx, val, base=0, n=None, nnz=None):
+    ptr = np.asarray(ptr, np.int32)
+    idx = np.asarray(idx, np.int32)
+    val = np.asarray(val, np.float64)
+    h = ctypes.c_void_p()
+    n = len(ptr) - 1 if n is None else n
+    nnz = len(idx) if nnz is None else nnz
+    rc = lib.gbcg_create(ctypes.byref(h), fmt, n, nnz, ptr.ctypes.data_as(ctypes.c_void_p),
+                         idx.ctypes.data_as(ctypes.c_void_p), val.ctypes.data_as(ctypes.c_void_p), base,
+                         _lib.GBCG_HOST, None)
+    return rc, lib.gbcg_last_error().decode()
+
+
+@pytest.mark.parametrize("case", [
+    ("unsorted columns", 0, [0, 2, 2], [1, 0], [1.0, 2.0], 0, "strictly increasing"),
+    ("duplicate column", 0, [0, 2, 2], [0, 0], [1.0, 2.0], 0, "strictly increasing"),
+    ("column out of range", 0, [0, 1], [5], [1.0], 0, "out of range"),
+    ("negative column", 0, [0, 1], [-1], [1.0], 0, "out of range"),
+    ("lower entry in upper storage", 1, [0, 1, 2], [0, 0], [1.0, 2.0], 0, "below the diagonal"),
+    ("nan value", 0, [0, 1], [0], [float("nan")], 0, "non-finite"),
+    ("decreasing ptr", 0, [0, 2, 1], [0, 1], [1.0, 1.0], 0, "ptr"),
+    ("bad base", 0, [0, 1], [0], [1.0], 2, "index_base"),
+    ("ptr[0] != base", 0, [1, 2], [0], [1.0], 0, "ptr[0]"),
+    ("one-based index 0", 0, [1, 2], [0], [1.0], 1, "out of range"),
+    ("bad format", 7, [0, 1], [0], [1.0], 0, "format"),
+])
+def test_create_rejects_malformed_input(lib, case):
+    _, fmt, ptr, idx, val, base, needle = case
+    rc, msg = _create(lib, fmt, ptr, idx, val, base)
+    assert rc == 1, (rc, msg)
+    assert needle in msg
+
+
+def test_create_rejects_inconsistent_sizes(lib):
+    rc, msg = _create(lib, 0, [0, 1, 2], [0, 1], [1.0, 1.0], nnz=3)
+    assert rc == 1 and "nnz" in msg
+    rc, msg = _create(lib, 0, [0, 1], [0], [1.0], n=-1)
+    assert rc == 1
+    h = ctypes.c_void_p()
+    assert lib.gbcg_create(None, 0, 0, 0, None, None, None, 0, 0, None) == 1
+    assert lib.gbcg_create(ctypes.byref(h), 0, 1, 1, None, None, None, 0, 0, None) == 1
+
+
+def test_null_handle_calls(lib):
+    assert lib.gbcg_spmv(None, None, None, None) == 1
+    assert lib.gbcg_solve(None, None, None, 1e-10, 0, None, None, None) == 1
+    assert lib.gbcg_destroy(None) == 0
+    s = _lib.Stats()
+    assert lib.gbcg_stats(None, ctypes.byref(s)) == 1
+
+
+def test_python_binding_fails_loudly_without_library(tmp_path):
+    with pytest.raises(ImportError):
+        saved = _lib._lib
+        _lib._lib = None
+        try:
+            _lib.load(str(tmp_path / "missing.so"))
+        finally:
+            _lib._lib = saved
