@@ -171,9 +171,21 @@ void free_matrix(gbcg_matrix_s* M) {
   delete M;
 }
 
+template <typename V, bool SYM>
+size_t cg_smem() { return SYM ? 0 : pipe_smem_bytes<V>(); }
+
 template <typename V, bool SYM, bool OUTER>
 int occupancy_of(int& per_sm) {
-  CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cg<V, SYM, OUTER>, kCgThreads, 0));
+  const size_t sm = cg_smem<V, SYM>();
+  CUDA_TRY(cudaFuncSetAttribute(k_cg<V, SYM, OUTER>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cg<V, SYM, OUTER>, kCgThreads, sm));
+  return 0;
+}
+
+template <typename V, bool SYM, int MODE>
+int prepare_rows() {
+  CUDA_TRY(cudaFuncSetAttribute(k_rows<V, SYM, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)cg_smem<V, SYM>()));
   return 0;
 }
 
@@ -182,6 +194,9 @@ int solver_occupancy(int& per_sm) {
   int a = 0, b = 0;
   if (int rc = occupancy_of<double, SYM, true>(a)) return rc;
   if (int rc = occupancy_of<float, SYM, false>(b)) return rc;
+  if (int rc = prepare_rows<double, SYM, 0>()) return rc;
+  if (int rc = prepare_rows<float, SYM, 0>()) return rc;
+  if (int rc = prepare_rows<double, SYM, 1>()) return rc;
   per_sm = std::min(a, b);
   return 0;
 }
@@ -198,7 +213,8 @@ bool is_device_ptr(const void* p) {
 template <typename V, bool SYM, bool OUTER>
 cudaError_t launch_cg(const CgArgs<V>& args, int grid, cudaStream_t s) {
   void* kargs[] = {(void*)&args};
-  return cudaLaunchCooperativeKernel((const void*)k_cg<V, SYM, OUTER>, dim3(grid), dim3(kCgThreads), kargs, 0, s);
+  return cudaLaunchCooperativeKernel((const void*)k_cg<V, SYM, OUTER>, dim3(grid), dim3(kCgThreads), kargs,
+                                     cg_smem<V, SYM>(), s);
 }
 
 template <typename V, bool OUTER>
@@ -289,11 +305,13 @@ int dot_to_host(gbcg_matrix_s* M, const double* a, const double* b, double& out,
 }
 
 int residual_to_host(gbcg_matrix_s* M, const double* b, const double* x, double& rr, cudaStream_t s) {
-  const int blocks = M->spmv_blocks();
+  const int blocks = M->grid;
   if (M->sym)
-    k_residual<true><<<blocks, 256, 0, s>>>(M->op<double>(), b, x, M->r, M->part);
+    k_rows<double, true, 1><<<blocks, kCgThreads, cg_smem<double, true>(), s>>>(
+        M->op<double>(), M->cta_slice, M->cta_long, x, b, M->r, M->part, &M->bar->status, 1000000000LL);
   else
-    k_residual<false><<<blocks, 256, 0, s>>>(M->op<double>(), b, x, M->r, M->part);
+    k_rows<double, false, 1><<<blocks, kCgThreads, cg_smem<double, false>(), s>>>(
+        M->op<double>(), M->cta_slice, M->cta_long, x, b, M->r, M->part, &M->bar->status, 1000000000LL);
   k_sum_part<<<1, 256, 0, s>>>(M->part, blocks, M->sums);
   CUDA_TRY(cudaGetLastError());
   CUDA_TRY(cudaMemcpyAsync(M->sums_h, M->sums, sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -371,12 +389,12 @@ int spmv_any(gbcg_matrix_t A, const V* x, V* y, cudaStream_t s) {
   if (!A) return fail(GBCG_ERR_INVALID, "null matrix handle");
   if (A->n == 0) return GBCG_OK;
   if (!x || !y) return fail(GBCG_ERR_INVALID, "null vector");
-  const int64_t warps = A->nslices + A->nlong;
-  const int blocks = (int)((warps + 7) / 8);
   if (A->sym)
-    k_spmv<V, true><<<blocks, 256, 0, s>>>(A->op<V>(), x, y);
+    k_rows<V, true, 0><<<A->grid, kCgThreads, cg_smem<V, true>(), s>>>(
+        A->op<V>(), A->cta_slice, A->cta_long, x, nullptr, y, nullptr, &A->bar->status, 1000000000LL);
   else
-    k_spmv<V, false><<<blocks, 256, 0, s>>>(A->op<V>(), x, y);
+    k_rows<V, false, 0><<<A->grid, kCgThreads, cg_smem<V, false>(), s>>>(
+        A->op<V>(), A->cta_slice, A->cta_long, x, nullptr, y, nullptr, &A->bar->status, 1000000000LL);
   CUDA_TRY(cudaGetLastError());
   return GBCG_OK;
 }

@@ -3,11 +3,15 @@
 // Sparse product (Section III, "A p product on line 2"): the sliced row-gather
 // layout of layout.h, one warp per slice of 32 rows and one lane per row, as
 // in the paper's thread-per-row kernel but with the row data interleaved so
-// that each warp load is one contiguous segment.  The symmetric format adds
-// the transpose half U' x as a second gather through the transpose plan,
-// reading U's values in place (the paper used a separate scatter kernel with
-// atomics; here every output element is summed by one lane in a fixed
-// order, so results are bitwise reproducible).
+// that a slice is one contiguous block.  Each warp streams its next slice's
+// values and column indices into shared memory with a bulk asynchronous copy
+// (cp.async.bulk, completion on an mbarrier, L2 evict-first policy) while it
+// computes the current one, so the number of bytes in flight does not depend
+// on how many warps are resident.  The symmetric format adds the transpose
+// half U' x as a second gather through the transpose plan, reading U's values
+// in place (the paper used a separate scatter kernel with atomics; here every
+// output element is summed by one lane in a fixed order, so results are
+// bitwise reproducible).
 //
 // CG iteration (Section III listing): one persistent cooperative launch per
 // solve.  Each CTA owns a contiguous range of slices (and so of rows); per
@@ -16,9 +20,9 @@
 //   B: alpha = r'r / p'q; x += alpha p; r -= alpha q; partial r'r -> barrier
 //   C: beta = r_k'r_k / r_{k-1}'r_{k-1}; p = r + beta p           -> barrier
 // The partial sums of all CTAs are added by every CTA in the same fixed
-// order, so every CTA takes the same decisions.  Every grid-barrier wait is
-// bounded by a global-timer limit; on expiry the CTA records GBCG_ERR_TIMEOUT
-// and returns, so a lost CTA cannot hang the device.
+// order, so every CTA takes the same decisions.  Every wait (grid barrier,
+// mbarrier) is bounded by a global-timer limit; on expiry the CTA records
+// GBCG_ERR_TIMEOUT and leaves at the next barrier, so nothing can hang.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -26,6 +30,9 @@
 namespace gbcg {
 
 constexpr int kCgThreads = 512;
+constexpr int kWarps = kCgThreads / 32;
+constexpr int kMaxL = 16;    // slots per row one pipeline stage holds
+constexpr int kStages = 2;   // stages per warp
 constexpr uint16_t kPlanPad = 0xFFFF;
 
 enum DevStatus { kOk = 0, kNotSpd = 2, kMaxit = 3, kNonfinite = 4, kTimeout = 5 };
@@ -83,6 +90,16 @@ struct CgArgs {
   long long timeout_ns;
 };
 
+// One pipeline stage of a warp: a slice's values then its column indices,
+// both slot-major ([slot][lane]).
+template <typename V>
+struct alignas(16) Stage {
+  V val[kMaxL * 32];
+  int32_t col[kMaxL * 32];
+};
+template <typename V>
+constexpr size_t pipe_smem_bytes() { return sizeof(Stage<V>) * kStages * kWarps; }
+
 // ------------------------------------------------------------ helpers ---
 __device__ __forceinline__ long long gtime() {
   long long t;
@@ -98,6 +115,47 @@ __device__ __forceinline__ int ld_relaxed(const int32_t* p) {
   int v;
   asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
+}
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait on an mbarrier phase; false when the limit ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long limit_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = gtime();
+  while (!mbar_try_wait(bar, parity))
+    if (gtime() - t0 > limit_ns) return false;
+  return true;
+}
+__device__ __forceinline__ uint64_t policy_evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+// Global -> shared bulk copy (16-byte aligned addresses, size a multiple of 16).
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar, uint64_t pol) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::
+          "r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
+      : "memory");
 }
 
 // Matrix streams are read once per product: cache-streaming loads.
@@ -116,9 +174,13 @@ __device__ __forceinline__ T ld_vec(const T* p) {
 __device__ __forceinline__ double fma_(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ float fma_(float a, float b, float c) { return fmaf(a, b, c); }
 
-// Row product of the lane's row in slice s (layout.h).  Symmetric rows sum
-// in increasing column order: transpose half (columns < row), diagonal,
-// upper half.
+template <typename V> struct Vec;
+template <> struct Vec<double> { using T = double2; static constexpr int W = 2; };
+template <> struct Vec<float> { using T = float4; static constexpr int W = 4; };
+
+// Row product of the lane's row in slice s straight from global memory
+// (layout.h).  Symmetric rows sum in increasing column order: transpose half
+// (columns < row), diagonal, upper half.
 template <typename V, bool SYM, bool NC, int UNROLL = 8>
 __device__ __forceinline__ V sell_row(const OpDev<V>& A, int64_t s, int lane, const V* x) {
   const int64_t row = s * 32 + lane;
@@ -156,16 +218,107 @@ __device__ __forceinline__ V long_row(const OpDev<V>& A, int64_t li, int lane, c
   return acc;
 }
 
-// Visits every row of slices [s0, s1) and long rows [l0, l1) of the CTA:
-// f(row, (A x)_row) runs on the lane that computed the row.
+// Per-warp pipeline state (uniform across the warp's lanes).
+struct Pipe {
+  uint64_t* bars;      // kStages mbarriers of this warp
+  uint32_t issued;     // stage fills issued so far
+  uint32_t consumed;   // stage fills consumed so far
+  uint64_t policy;
+  long long limit_ns;
+  bool failed;
+};
+
+__device__ __forceinline__ void pipe_init(Pipe& pp, uint64_t* bars, long long limit_ns) {
+  pp.bars = bars;
+  pp.issued = pp.consumed = 0;
+  pp.policy = policy_evict_first();
+  pp.limit_ns = limit_ns;
+  pp.failed = false;
+  if ((threadIdx.x & 31) == 0)
+    for (int i = 0; i < kStages; ++i) mbar_init(&bars[i], 1);
+  fence_mbar_init();
+}
+
+template <typename V>
+__device__ __forceinline__ int slice_len(const OpDev<V>& A, int64_t s) {
+  return (int)((A.sl_ptr[s + 1] - A.sl_ptr[s]) >> 5);
+}
+
+// Issue the fill of slice s into the next stage (no-op for empty or
+// oversize slices, which are read straight from global memory).
+template <typename V>
+__device__ __forceinline__ void pipe_issue(const OpDev<V>& A, Stage<V>* stages, Pipe& pp, int64_t s) {
+  const int L = slice_len(A, s);
+  if (L == 0 || L > kMaxL || pp.failed) return;
+  const uint32_t st = pp.issued % kStages;
+  if ((threadIdx.x & 31) == 0) {
+    const uint32_t vb = (uint32_t)(L * 32 * sizeof(V)), cb = (uint32_t)(L * 32 * sizeof(int32_t));
+    mbar_arrive_expect_tx(&pp.bars[st], vb + cb);
+    bulk_g2s(stages[st].val, A.val + A.sl_ptr[s], vb, &pp.bars[st], pp.policy);
+    bulk_g2s(stages[st].col, A.col + A.sl_ptr[s], cb, &pp.bars[st], pp.policy);
+  }
+  ++pp.issued;
+}
+
+// Waits (bounded) for every fill still in flight; used before a CTA leaves
+// after a failure so no copy lands in released shared memory.
+__device__ __forceinline__ void pipe_drain(Pipe& pp) {
+  while (pp.consumed < pp.issued) {
+    const uint32_t st = pp.consumed % kStages, par = (pp.consumed / kStages) & 1u;
+    mbar_wait(&pp.bars[st], par, pp.limit_ns);
+    ++pp.consumed;
+  }
+}
+
+// Visits the rows of slices [s0, s1) and long rows [l0, l1) of the CTA:
+// f(row, (A x)_row) runs on the lane that computed the row.  Row-gather
+// formats use the per-warp bulk-copy pipeline; the symmetric format reads
+// global memory directly.
 template <typename V, bool SYM, bool NC, class F>
 __device__ __forceinline__ void spmv_rows(const OpDev<V>& A, int64_t s0, int64_t s1, int64_t l0, int64_t l1,
-                                          const V* x, F&& f) {
+                                          const V* x, Stage<V>* stages, Pipe& pp, int* err, F&& f) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int64_t s = s0 + warp; s < s1; s += nw) {
-    const V v = sell_row<V, SYM, NC, 4>(A, s, lane, x);
-    const int64_t row = s * 32 + lane;
-    if (row < A.n && !((A.long_mask[s] >> lane) & 1u)) f(row, v);
+  if constexpr (SYM) {
+    for (int64_t s = s0 + warp; s < s1; s += nw) {
+      const V v = sell_row<V, true, NC, 4>(A, s, lane, x);
+      const int64_t row = s * 32 + lane;
+      if (row < A.n) f(row, v);
+    }
+  } else {
+    int64_t s_issue = s0 + warp;
+    for (int d = 0; d < kStages - 1 && s_issue < s1; ++d, s_issue += nw) pipe_issue(A, stages, pp, s_issue);
+    for (int64_t s = s0 + warp; s < s1; s += nw) {
+      if (s_issue < s1) {
+        pipe_issue(A, stages, pp, s_issue);
+        s_issue += nw;
+      }
+      const int L = slice_len(A, s);
+      V acc = V(0);
+      if (L > kMaxL) {
+        acc = sell_row<V, false, NC, 8>(A, s, lane, x);
+      } else if (L > 0 && !pp.failed) {
+        const uint32_t st = pp.consumed % kStages, par = (pp.consumed / kStages) & 1u;
+        if (!mbar_wait(&pp.bars[st], par, pp.limit_ns)) {
+          pp.failed = true;
+          if (lane == 0) atomicCAS(err, 0, (int)kTimeout);
+        } else {
+          ++pp.consumed;
+          const V* __restrict__ sv = stages[st].val;
+          const int32_t* __restrict__ sc = stages[st].col;
+          V xv[kMaxL];
+#pragma unroll
+          for (int k = 0; k < kMaxL; ++k)
+            if (k < L) xv[k] = ld_vec<NC>(x + sc[k * 32 + lane]);
+#pragma unroll
+          for (int k = 0; k < kMaxL; ++k)
+            if (k < L) acc = fma_(sv[k * 32 + lane], xv[k], acc);
+        }
+        __syncwarp();
+      }
+      const int64_t row = s * 32 + lane;
+      if (row < A.n && !((A.long_mask[s] >> lane) & 1u)) f(row, acc);
+    }
+    if (pp.failed) pipe_drain(pp);
   }
   for (int64_t li = l0 + warp; li < l1; li += nw) {
     const V v = long_row<V, NC>(A, li, lane, x);
@@ -234,50 +387,37 @@ __device__ __forceinline__ bool grid_barrier(GridBar* gb, unsigned long long& ta
 }
 
 // -------------------------------------------------- one-shot kernels ---
-template <typename V, bool SYM>
-__global__ void __launch_bounds__(256) k_spmv(OpDev<V> A, const V* __restrict__ x, V* __restrict__ y) {
-  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (w < A.nslices) {
-    const V v = sell_row<V, SYM, true>(A, w, lane, x);
-    const int64_t row = w * 32 + lane;
-    if (row < A.n && !((A.long_mask[w] >> lane) & 1u)) y[row] = v;
-  } else if (w - A.nslices < A.nlong) {
-    const int64_t li = w - A.nslices;
-    const V v = long_row<V, true>(A, li, lane, x);
-    if (lane == 0) y[A.long_row[li]] = v;
-  }
-}
-
-// r = b - A x in double precision, with per-CTA partial sums of r'r.
-template <bool SYM>
-__global__ void __launch_bounds__(256) k_residual(OpDev<double> A, const double* __restrict__ b,
-                                                  const double* __restrict__ x, double* __restrict__ r,
-                                                  double* __restrict__ part) {
+// y = A x (MODE 0) or r = b - A x with per-CTA partial sums of r'r (MODE 1),
+// on the persistent grid's slice partition.
+template <typename V, bool SYM, int MODE>
+__global__ void __launch_bounds__(kCgThreads, 1)
+    k_rows(OpDev<V> A, const int32_t* __restrict__ cta_slice, const int32_t* __restrict__ cta_long,
+           const V* __restrict__ x, const V* __restrict__ b, V* __restrict__ y, double* __restrict__ part,
+           int* err, long long limit_ns) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ uint64_t bars[kWarps][kStages];
   __shared__ double red[33];
-  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  Stage<V>* stages = reinterpret_cast<Stage<V>*>(smem_raw) + warp * kStages;
+  Pipe pp;
+  pipe_init(pp, bars[warp], limit_ns);
+  __syncthreads();
+  const int c = blockIdx.x;
   double acc = 0.0;
-  if (w < A.nslices) {
-    const double v = sell_row<double, SYM, true>(A, w, lane, x);
-    const int64_t row = w * 32 + lane;
-    if (row < A.n && !((A.long_mask[w] >> lane) & 1u)) {
-      const double t = b[row] - v;
-      r[row] = t;
-      acc = t * t;
-    }
-  } else if (w - A.nslices < A.nlong) {
-    const int64_t li = w - A.nslices;
-    const double v = long_row<double, true>(A, li, lane, x);
-    if (lane == 0) {
-      const int64_t row = A.long_row[li];
-      const double t = b[row] - v;
-      r[row] = t;
-      acc = t * t;
-    }
+  spmv_rows<V, SYM, true>(A, cta_slice[c], cta_slice[c + 1], cta_long[c], cta_long[c + 1], x, stages, pp, err,
+                          [&](int64_t row, V v) {
+                            if constexpr (MODE == 0) {
+                              y[row] = v;
+                            } else {
+                              const V t = b[row] - v;
+                              y[row] = t;
+                              acc = fma((double)t, (double)t, acc);
+                            }
+                          });
+  if constexpr (MODE == 1) {
+    const double s = block_sum(acc, red);
+    if (threadIdx.x == 0) part[c] = s;
   }
-  const double s = block_sum(acc, red);
-  if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
 __global__ void __launch_bounds__(256) k_dot_part(const double* __restrict__ a, const double* __restrict__ b,
@@ -312,13 +452,27 @@ __global__ void k_axpy_f32(double a, const float* __restrict__ d, int64_t n, dou
 }
 
 // ------------------------------------------------- persistent solver ---
+// Vector pass over rows [r0, r1) with 16-byte accesses; f(i, w) handles the
+// w consecutive elements from i (w = the vector width, or 1 on the tail).
+template <typename V, class F>
+__device__ __forceinline__ void rows_vec(int64_t r0, int64_t r1, F&& f) {
+  constexpr int W = Vec<V>::W;
+  const int64_t g0 = r0 / W, g1 = r1 / W;  // r0 is a multiple of 32
+  for (int64_t g = g0 + threadIdx.x; g < g1; g += blockDim.x) f(g * W, W);
+  for (int64_t i = g1 * W + threadIdx.x; i < r1; i += blockDim.x) f(i, 1);
+}
+
 // OUTER = false: inner single-precision solve from x = 0 (rhs in b), no
 // true-residual confirmation.  OUTER = true: the full solve of Section III
 // from the caller's x0 with the confirm/restart step.
 template <typename V, bool SYM, bool OUTER>
 __global__ void __launch_bounds__(kCgThreads, 1) k_cg(CgArgs<V> a) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ uint64_t bars[kWarps][kStages];
   __shared__ double red[33];
   __shared__ int sflag;
+  using VT = typename Vec<V>::T;
+  constexpr int W = Vec<V>::W;
   const int G = gridDim.x, c = blockIdx.x;
   const int64_t s0 = a.cta_slice[c], s1 = a.cta_slice[c + 1];
   const int64_t l0 = a.cta_long[c], l1 = a.cta_long[c + 1];
@@ -332,6 +486,12 @@ __global__ void __launch_bounds__(kCgThreads, 1) k_cg(CgArgs<V> a) {
   const V* __restrict__ b = a.b;
   double* part0 = a.part;
   double* part1 = a.part + G;
+  const int warp = threadIdx.x >> 5;
+  Stage<V>* stages = reinterpret_cast<Stage<V>*>(smem_raw) + warp * kStages;
+  Pipe pp;
+  pipe_init(pp, bars[warp], a.timeout_ns);
+  __syncthreads();
+  int* err = &a.bar->status;
   unsigned long long target = 0;
   int nbar = 0;
   int status = kOk;
@@ -342,7 +502,7 @@ __global__ void __launch_bounds__(kCgThreads, 1) k_cg(CgArgs<V> a) {
   {
     V pr = V(0), pb = V(0);
     if constexpr (OUTER) {
-      spmv_rows<V, SYM, false>(A, s0, s1, l0, l1, x, [&](int64_t row, V v) {
+      spmv_rows<V, SYM, false>(A, s0, s1, l0, l1, x, stages, pp, err, [&](int64_t row, V v) {
         const V bi = b[row];
         const V t = bi - v;
         r[row] = t;
@@ -351,14 +511,23 @@ __global__ void __launch_bounds__(kCgThreads, 1) k_cg(CgArgs<V> a) {
         pb = fma_(bi, bi, pb);
       });
     } else {
-      for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
-        const V bi = b[i];
-        x[i] = V(0);
-        r[i] = bi;
-        p[i] = bi;
-        pr = fma_(bi, bi, pr);
-      }
-      for (int64_t li = l0; li < l1; ++li) (void)li;  // long rows lie inside [r0, r1)
+      rows_vec<V>(r0, r1, [&](int64_t i, int w) {
+        if (w > 1) {
+          const VT bv = *reinterpret_cast<const VT*>(b + i);
+          *reinterpret_cast<VT*>(x + i) = VT{};
+          *reinterpret_cast<VT*>(r + i) = bv;
+          *reinterpret_cast<VT*>(p + i) = bv;
+          const V* e = reinterpret_cast<const V*>(&bv);
+#pragma unroll
+          for (int j = 0; j < W; ++j) pr = fma_(e[j], e[j], pr);
+        } else {
+          const V bi = b[i];
+          x[i] = V(0);
+          r[i] = bi;
+          p[i] = bi;
+          pr = fma_(bi, bi, pr);
+        }
+      });
       pb = pr;
     }
     const double s_rr = block_sum((double)pr, red);
@@ -378,7 +547,7 @@ __global__ void __launch_bounds__(kCgThreads, 1) k_cg(CgArgs<V> a) {
     while (k < a.maxit && !(sqrt(rr) / nb <= a.tol)) {
       // A: q = A p, p'q
       V ppq = V(0);
-      spmv_rows<V, SYM, false>(A, s0, s1, l0, l1, p, [&](int64_t row, V v) {
+      spmv_rows<V, SYM, false>(A, s0, s1, l0, l1, p, stages, pp, err, [&](int64_t row, V v) {
         q[row] = v;
         ppq = fma_(p[row], v, ppq);
       });
@@ -395,13 +564,29 @@ __global__ void __launch_bounds__(kCgThreads, 1) k_cg(CgArgs<V> a) {
       {
         const V al = (V)alpha;
         V prr = V(0);
-        for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
-          const V pi = p[i];
-          x[i] = fma_(al, pi, x[i]);
-          const V ri = fma_(-al, q[i], r[i]);
-          r[i] = ri;
-          prr = fma_(ri, ri, prr);
-        }
+        rows_vec<V>(r0, r1, [&](int64_t i, int w) {
+          if (w > 1) {
+            VT pv = *reinterpret_cast<const VT*>(p + i), qv = *reinterpret_cast<const VT*>(q + i);
+            VT xv = *reinterpret_cast<const VT*>(x + i), rv = *reinterpret_cast<const VT*>(r + i);
+            V* pe = reinterpret_cast<V*>(&pv);
+            V* qe = reinterpret_cast<V*>(&qv);
+            V* xe = reinterpret_cast<V*>(&xv);
+            V* re = reinterpret_cast<V*>(&rv);
+#pragma unroll
+            for (int j = 0; j < W; ++j) {
+              xe[j] = fma_(al, pe[j], xe[j]);
+              re[j] = fma_(-al, qe[j], re[j]);
+              prr = fma_(re[j], re[j], prr);
+            }
+            *reinterpret_cast<VT*>(x + i) = xv;
+            *reinterpret_cast<VT*>(r + i) = rv;
+          } else {
+            x[i] = fma_(al, p[i], x[i]);
+            const V ri = fma_(-al, q[i], r[i]);
+            r[i] = ri;
+            prr = fma_(ri, ri, prr);
+          }
+        });
         const double s = block_sum((double)prr, red);
         if (threadIdx.x == 0) part1[c] = s;
       }
@@ -415,7 +600,19 @@ __global__ void __launch_bounds__(kCgThreads, 1) k_cg(CgArgs<V> a) {
       // C: p = r + beta p
       {
         const V be = (V)beta;
-        for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) p[i] = fma_(be, p[i], r[i]);
+        rows_vec<V>(r0, r1, [&](int64_t i, int w) {
+          if (w > 1) {
+            VT pv = *reinterpret_cast<const VT*>(p + i);
+            const VT rv = *reinterpret_cast<const VT*>(r + i);
+            V* pe = reinterpret_cast<V*>(&pv);
+            const V* re = reinterpret_cast<const V*>(&rv);
+#pragma unroll
+            for (int j = 0; j < W; ++j) pe[j] = fma_(be, pe[j], re[j]);
+            *reinterpret_cast<VT*>(p + i) = pv;
+          } else {
+            p[i] = fma_(be, p[i], r[i]);
+          }
+        });
       }
       if (!grid_barrier(a.bar, target, a.timeout_ns, &sflag, nbar++)) return;
     }
@@ -425,7 +622,7 @@ __global__ void __launch_bounds__(kCgThreads, 1) k_cg(CgArgs<V> a) {
     } else {
       // confirm on the true residual; restart the recurrence from it otherwise
       V ptt = V(0);
-      spmv_rows<V, SYM, false>(A, s0, s1, l0, l1, x, [&](int64_t row, V v) {
+      spmv_rows<V, SYM, false>(A, s0, s1, l0, l1, x, stages, pp, err, [&](int64_t row, V v) {
         const V t = b[row] - v;
         r[row] = t;
         ptt = fma_(t, t, ptt);
