@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--profile-iters", type=int, default=0,
                     help="only run solves capped at this many iterations (small case for ncu captures)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU-oracle sample")
+    ap.add_argument("--profile-spmv", action="store_true",
+                    help="only run a few products (double then single precision) of --format, for ncu captures")
     return ap.parse_args()
 
 
@@ -213,6 +215,15 @@ def run_ours(args):
     b = torch.from_numpy(s.b).to(dev)
     x = torch.zeros_like(b)
     solve_kw = dict(tol=TOL, precision=args.precision, inner_tol=args.inner_tol)
+    if args.profile_spmv:
+        xv = torch.from_numpy(femgen.random_vector(s.n, 7)).to(dev)
+        yv = torch.empty_like(xv)
+        for _ in range(max(1, args.warmup)):
+            A.spmv(xv, yv)
+            A.spmv_f32(xv.float(), yv.float())
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_spmv": args.format, "stats": st}), flush=True)
+        return 0
     if args.profile_iters:
         solve_kw.update(maxit=args.profile_iters, raise_on_error=False)
         for _ in range(max(1, args.warmup)):

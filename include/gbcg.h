@@ -99,8 +99,11 @@ typedef struct {
   int64_t device_bytes;       /* device memory held by the handle */
   int64_t spmv_bytes_fp64;    /* algorithmic bytes of one double-precision product */
   int64_t spmv_bytes_fp32;    /* algorithmic bytes of one single-precision product */
+  int64_t ext_slots;          /* symmetric tiles: partial sums leaving the tiles */
   int32_t format;             /* gbcg_format */
   int32_t grid_ctas;          /* CTAs of the persistent CG launch */
+  int32_t layout;             /* 0 row gather, 1 symmetric transpose plan, 2 symmetric tiles */
+  int32_t tiles;              /* symmetric tiles: number of tiles */
 } gbcg_matrix_stats;
 
 /*

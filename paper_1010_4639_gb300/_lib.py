@@ -38,7 +38,8 @@ class Stats(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("nnz_input", ctypes.c_int64), ("nnz_full", ctypes.c_int64),
                 ("stored_slots", ctypes.c_int64), ("plan_slots", ctypes.c_int64), ("long_rows", ctypes.c_int64),
                 ("device_bytes", ctypes.c_int64), ("spmv_bytes_fp64", ctypes.c_int64),
-                ("spmv_bytes_fp32", ctypes.c_int64), ("format", ctypes.c_int32), ("grid_ctas", ctypes.c_int32)]
+                ("spmv_bytes_fp32", ctypes.c_int64), ("ext_slots", ctypes.c_int64), ("format", ctypes.c_int32),
+                ("grid_ctas", ctypes.c_int32), ("layout", ctypes.c_int32), ("tiles", ctypes.c_int32)]
 
 
 class GbcgError(RuntimeError):

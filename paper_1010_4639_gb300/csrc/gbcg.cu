@@ -73,6 +73,16 @@ struct gbcg_matrix_s {
   int64_t n = 0, nnz_input = 0, nnz_full = 0, slots = 0, plan_slots = 0;
   int64_t nslices = 0, nlong = 0, bytes = 0;
   int sym = 0;
+  int mode = kGather;       // kGather (CSR/CSC), kPlan or kTiles (symmetric)
+  int64_t ntiles = 0, next = 0, tile_slots = 0;
+  // warp-tiled symmetric layout (device)
+  int32_t *t_warp_tile = nullptr, *t_tile_slice = nullptr, *t_tile_ns = nullptr, *t_ext_rows = nullptr;
+  int64_t *t_tile_ext = nullptr, *t_sl_ptr = nullptr, *t_in_src = nullptr;
+  uint16_t* t_slot = nullptr;
+  double* t_val64 = nullptr;
+  float* t_val32 = nullptr;
+  int32_t *t_in_ptr = nullptr, *t_in_row = nullptr, *t_in_len = nullptr;
+  double* t_part = nullptr;  // ext partial sums (used as float for the single-precision product)
   // layout (device)
   int64_t* sl_ptr = nullptr;
   int32_t* col = nullptr;
@@ -109,6 +119,25 @@ struct gbcg_matrix_s {
 
   template <typename V>
   OpDev<V> op() const;
+  template <typename V>
+  SymDev<V> tiles() const {
+    SymDev<V> t;
+    t.active = sym_active_warps<V>();
+    t.warp_tile = t_warp_tile;
+    t.tile_slice = t_tile_slice;
+    t.tile_ns = t_tile_ns;
+    t.tile_ext = t_tile_ext;
+    t.ext_rows = t_ext_rows;
+    t.sl_ptr = t_sl_ptr;
+    t.slot = t_slot;
+    t.val = sizeof(V) == 8 ? (const V*)(const void*)t_val64 : (const V*)(const void*)t_val32;
+    t.in_ptr = t_in_ptr;
+    t.in_row = t_in_row;
+    t.in_len = t_in_len;
+    t.in_src = t_in_src;
+    t.part = (V*)(void*)t_part;
+    return t;
+  }
   int spmv_blocks() const { return (int)std::max<int64_t>(1, (nslices + nlong + 7) / 8); }
 };
 
@@ -160,7 +189,9 @@ void free_matrix(gbcg_matrix_s* M) {
   void* dev[] = {M->sl_ptr, M->col, M->val64, M->val32, M->long_mask, M->long_row, M->long_ptr, M->long_col,
                  M->long_val64, M->long_val32, M->diag64, M->diag32, M->pl_ptr, M->pl_i, M->pl_k,
                  M->cta_slice, M->cta_long, M->r, M->p, M->q, M->bstage, M->xstage, M->r32, M->p32, M->q32,
-                 M->d32, M->rhs32, M->part, M->sums, M->bar, M->st};
+                 M->d32, M->rhs32, M->part, M->sums, M->bar, M->st, M->t_warp_tile, M->t_tile_slice,
+                 M->t_tile_ns, M->t_ext_rows, M->t_tile_ext, M->t_sl_ptr, M->t_in_src, M->t_slot, M->t_val64,
+                 M->t_val32, M->t_in_ptr, M->t_in_row, M->t_in_len, M->t_part};
   for (void* d : dev)
     if (d) cudaFree(d);
   if (M->st_h) cudaFreeHost(M->st_h);
@@ -171,34 +202,37 @@ void free_matrix(gbcg_matrix_s* M) {
   delete M;
 }
 
-template <typename V, bool SYM>
-size_t cg_smem() { return SYM ? 0 : pipe_smem_bytes<V>(); }
-
-template <typename V, bool SYM, bool OUTER>
+template <typename V, int FMT, bool OUTER>
 int occupancy_of(int& per_sm) {
-  const size_t sm = cg_smem<V, SYM>();
-  CUDA_TRY(cudaFuncSetAttribute(k_cg<V, SYM, OUTER>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-  CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cg<V, SYM, OUTER>, kCgThreads, sm));
+  const size_t sm = product_smem<V, FMT>();
+  CUDA_TRY(cudaFuncSetAttribute(k_cg<V, FMT, OUTER>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cg<V, FMT, OUTER>, kCgThreads, sm));
   return 0;
 }
 
-template <typename V, bool SYM, int MODE>
+template <typename V, int FMT>
 int prepare_rows() {
-  CUDA_TRY(cudaFuncSetAttribute(k_rows<V, SYM, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)cg_smem<V, SYM>()));
+  CUDA_TRY(cudaFuncSetAttribute(k_rows<V, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)product_smem<V, FMT>()));
   return 0;
 }
 
-template <bool SYM>
+// Co-resident CTAs per SM of the persistent solver in layout mode FMT (and
+// the shared-memory attributes of the kernels of that mode).
+template <int FMT>
 int solver_occupancy(int& per_sm) {
   int a = 0, b = 0;
-  if (int rc = occupancy_of<double, SYM, true>(a)) return rc;
-  if (int rc = occupancy_of<float, SYM, false>(b)) return rc;
-  if (int rc = prepare_rows<double, SYM, 0>()) return rc;
-  if (int rc = prepare_rows<float, SYM, 0>()) return rc;
-  if (int rc = prepare_rows<double, SYM, 1>()) return rc;
+  if (int rc = occupancy_of<double, FMT, true>(a)) return rc;
+  if (int rc = occupancy_of<float, FMT, false>(b)) return rc;
+  if (int rc = prepare_rows<double, FMT>()) return rc;
+  if (int rc = prepare_rows<float, FMT>()) return rc;
   per_sm = std::min(a, b);
   return 0;
+}
+
+int mode_occupancy(int mode, int& per_sm) {
+  return mode == kTiles ? solver_occupancy<kTiles>(per_sm)
+                        : mode == kPlan ? solver_occupancy<kPlan>(per_sm) : solver_occupancy<kGather>(per_sm);
 }
 
 bool is_device_ptr(const void* p) {
@@ -210,16 +244,40 @@ bool is_device_ptr(const void* p) {
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
-template <typename V, bool SYM, bool OUTER>
+template <typename V, int FMT, bool OUTER>
 cudaError_t launch_cg(const CgArgs<V>& args, int grid, cudaStream_t s) {
   void* kargs[] = {(void*)&args};
-  return cudaLaunchCooperativeKernel((const void*)k_cg<V, SYM, OUTER>, dim3(grid), dim3(kCgThreads), kargs,
-                                     cg_smem<V, SYM>(), s);
+  return cudaLaunchCooperativeKernel((const void*)k_cg<V, FMT, OUTER>, dim3(grid), dim3(kCgThreads), kargs,
+                                     product_smem<V, FMT>(), s);
 }
 
 template <typename V, bool OUTER>
 cudaError_t launch_cg_fmt(const gbcg_matrix_s* M, const CgArgs<V>& a, cudaStream_t s) {
-  return M->sym ? launch_cg<V, true, OUTER>(a, M->grid, s) : launch_cg<V, false, OUTER>(a, M->grid, s);
+  switch (M->mode) {
+    case kTiles: return launch_cg<V, kTiles, OUTER>(a, M->grid, s);
+    case kPlan: return launch_cg<V, kPlan, OUTER>(a, M->grid, s);
+    default: return launch_cg<V, kGather, OUTER>(a, M->grid, s);
+  }
+}
+
+// Product y = A x (MODE 0), or r = b - A x into y with per-CTA partial sums
+// of r'r in part (MODE 1, double precision), on the persistent partition.
+template <typename V, int FMT, int MODE>
+cudaError_t launch_product(const gbcg_matrix_s* M, const V* x, const V* b, V* y, cudaStream_t s) {
+  k_rows<V, FMT><<<M->grid, kCgThreads, product_smem<V, FMT>(), s>>>(
+      M->op<V>(), M->tiles<V>(), M->cta_slice, M->cta_long, x, y, &M->bar->status, 1000000000LL);
+  if (FMT == kTiles || MODE == 1)
+    k_finish<V, FMT, MODE><<<M->grid, kCgThreads, 0, s>>>(M->tiles<V>(), M->cta_slice, M->n, b, y, M->part);
+  return cudaGetLastError();
+}
+
+template <typename V, int MODE>
+cudaError_t launch_product_fmt(const gbcg_matrix_s* M, const V* x, const V* b, V* y, cudaStream_t s) {
+  switch (M->mode) {
+    case kTiles: return launch_product<V, kTiles, MODE>(M, x, b, y, s);
+    case kPlan: return launch_product<V, kPlan, MODE>(M, x, b, y, s);
+    default: return launch_product<V, kGather, MODE>(M, x, b, y, s);
+  }
 }
 
 int status_from_device(const CgState& st, const GridBar& gb) {
@@ -243,6 +301,7 @@ CgArgs<V> make_args(const gbcg_matrix_s* M, V* x, V* r, V* p, V* q, const V* b, 
                     int max_restarts, long long timeout_ns) {
   CgArgs<V> a;
   a.A = M->op<V>();
+  a.T = M->tiles<V>();
   a.x = x;
   a.r = r;
   a.p = p;
@@ -305,14 +364,8 @@ int dot_to_host(gbcg_matrix_s* M, const double* a, const double* b, double& out,
 }
 
 int residual_to_host(gbcg_matrix_s* M, const double* b, const double* x, double& rr, cudaStream_t s) {
-  const int blocks = M->grid;
-  if (M->sym)
-    k_rows<double, true, 1><<<blocks, kCgThreads, cg_smem<double, true>(), s>>>(
-        M->op<double>(), M->cta_slice, M->cta_long, x, b, M->r, M->part, &M->bar->status, 1000000000LL);
-  else
-    k_rows<double, false, 1><<<blocks, kCgThreads, cg_smem<double, false>(), s>>>(
-        M->op<double>(), M->cta_slice, M->cta_long, x, b, M->r, M->part, &M->bar->status, 1000000000LL);
-  k_sum_part<<<1, 256, 0, s>>>(M->part, blocks, M->sums);
+  CUDA_TRY(launch_product_fmt<double, 1>(M, x, b, M->r, s));
+  k_sum_part<<<1, 256, 0, s>>>(M->part, M->grid, M->sums);
   CUDA_TRY(cudaGetLastError());
   CUDA_TRY(cudaMemcpyAsync(M->sums_h, M->sums, sizeof(double), cudaMemcpyDeviceToHost, s));
   CUDA_TRY(cudaStreamSynchronize(s));
@@ -341,7 +394,7 @@ int solve_ir(gbcg_matrix_s* M, const double* b, double* x, double tol, int maxit
     for (;;) {
       double rr = 0.0;
       if (int rc = residual_to_host(M, b, x, rr, s)) return rc;
-      info->launches += 2;  // k_residual + k_sum_part
+      info->launches += 3;  // k_rows + k_finish + k_sum_part
       rel = std::sqrt(rr) / nb;
       if (!std::isfinite(rel)) { status = GBCG_ERR_NONFINITE; break; }
       if (rel <= tol) { status = GBCG_OK; break; }
@@ -389,13 +442,7 @@ int spmv_any(gbcg_matrix_t A, const V* x, V* y, cudaStream_t s) {
   if (!A) return fail(GBCG_ERR_INVALID, "null matrix handle");
   if (A->n == 0) return GBCG_OK;
   if (!x || !y) return fail(GBCG_ERR_INVALID, "null vector");
-  if (A->sym)
-    k_rows<V, true, 0><<<A->grid, kCgThreads, cg_smem<V, true>(), s>>>(
-        A->op<V>(), A->cta_slice, A->cta_long, x, nullptr, y, nullptr, &A->bar->status, 1000000000LL);
-  else
-    k_rows<V, false, 0><<<A->grid, kCgThreads, cg_smem<V, false>(), s>>>(
-        A->op<V>(), A->cta_slice, A->cta_long, x, nullptr, y, nullptr, &A->bar->status, 1000000000LL);
-  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(launch_product_fmt<V, 0>(A, x, nullptr, y, s));
   return GBCG_OK;
 }
 
@@ -453,41 +500,79 @@ int gbcg_create(gbcg_matrix_t* out, int32_t format, int64_t n, int64_t nnz, cons
     if (int rc_ = (x)) return bail(rc_); \
   } while (0)
   int64_t& B = M->bytes;
-  TRY(upload(&M->sl_ptr, L.A.sl_ptr, s, B));
-  TRY(upload(&M->col, L.A.col, s, B));
-  TRY(upload(&M->val64, L.A.val, s, B));
-  TRY(upload(&M->val32, to_f32(L.A.val), s, B));
-  TRY(upload(&M->long_mask, L.A.long_mask, s, B));
-  TRY(upload(&M->long_row, L.A.long_row, s, B));
-  TRY(upload(&M->long_ptr, L.A.long_ptr, s, B));
-  TRY(upload(&M->long_col, L.A.long_col, s, B));
-  TRY(upload(&M->long_val64, L.A.long_val, s, B));
-  TRY(upload(&M->long_val32, to_f32(L.A.long_val), s, B));
-  if (M->sym) {
-    TRY(upload(&M->diag64, L.diag, s, B));
-    TRY(upload(&M->diag32, to_f32(L.diag), s, B));
-    TRY(upload(&M->pl_ptr, L.plan.pl_ptr, s, B));
-    TRY(upload(&M->pl_i, L.plan.pl_i, s, B));
-    TRY(upload(&M->pl_k, L.plan.pl_k, s, B));
-  }
   // persistent-solver grid: co-resident CTAs, at least a slice per warp
   int dev = 0, sms = 0, per_sm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return bail(fail(GBCG_ERR_CUDA, "cannot query the device"));
-  TRY(M->sym ? solver_occupancy<true>(per_sm) : solver_occupancy<false>(per_sm));
-  if (per_sm < 1) return bail(fail(GBCG_ERR_CUDA, "the persistent solver kernel cannot be resident"));
-  per_sm = std::min(per_sm, std::max(1, env_int("GBCG_CTAS_PER_SM", 2)));
-  int64_t want = (M->nslices + (kCgThreads / 32) - 1) / (kCgThreads / 32);
-  int env_grid = env_int("GBCG_GRID", 0);
-  M->grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * sms, want));
-  if (env_grid > 0) M->grid = std::min(env_grid, per_sm * sms);
-  std::vector<int32_t> cs = partition_slices(L, M->grid);
-  std::vector<int32_t> cl(M->grid + 1, 0);
-  for (int c = 0; c <= M->grid; ++c) {  // long rows go to the CTA that owns their row
-    const int64_t row0 = (int64_t)cs[c] * 32;
-    cl[c] = (int32_t)(std::lower_bound(L.A.long_row.begin(), L.A.long_row.end(), row0) - L.A.long_row.begin());
+  const char* sym_mode = getenv("GBCG_SYM_LAYOUT");
+  M->mode = !M->sym ? kGather : (sym_mode && !strcmp(sym_mode, "plan")) ? kPlan : kTiles;
+  auto choose_grid = [&]() -> int {
+    if (int rc = mode_occupancy(M->mode, per_sm)) return rc;
+    if (per_sm < 1) return fail(GBCG_ERR_CUDA, "the persistent solver kernel cannot be resident");
+    per_sm = std::min(per_sm, std::max(1, env_int("GBCG_CTAS_PER_SM", 2)));
+    const int64_t want = (M->nslices + kWarps - 1) / kWarps;
+    const int env_grid = env_int("GBCG_GRID", 0);
+    M->grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * sms, want));
+    if (env_grid > 0) M->grid = std::min(env_grid, per_sm * sms);
+    return 0;
+  };
+  TRY(choose_grid());
+  if (M->mode == kTiles && !build_sym_tiles(L, kWarps * M->grid, kSlotCap)) {
+    M->mode = kPlan;  // a single slice needs more slots than a tile holds
+    TRY(choose_grid());
   }
-  cl[M->grid] = (int32_t)M->nlong;
+  std::vector<int32_t> cs, cl(M->grid + 1, 0);
+  if (M->mode == kTiles) {
+    const SymTilesHost& Tl = L.tiles;
+    cs.resize(M->grid + 1);
+    for (int c = 0; c <= M->grid; ++c) cs[c] = Tl.tile_slice[Tl.warp_tile[(int64_t)kWarps * c]];
+    M->ntiles = (int64_t)Tl.tile_ns.size();
+    M->next = (int64_t)Tl.ext_rows.size();
+    M->tile_slots = (int64_t)Tl.slot.size();
+    TRY(upload(&M->t_warp_tile, Tl.warp_tile, s, B));
+    TRY(upload(&M->t_tile_slice, Tl.tile_slice, s, B));
+    TRY(upload(&M->t_tile_ns, Tl.tile_ns, s, B));
+    TRY(upload(&M->t_tile_ext, Tl.tile_ext, s, B));
+    TRY(upload(&M->t_ext_rows, Tl.ext_rows, s, B));
+    TRY(upload(&M->t_sl_ptr, Tl.sl_ptr, s, B));
+    TRY(upload(&M->t_slot, Tl.slot, s, B));
+    TRY(upload(&M->t_val64, Tl.val, s, B));
+    TRY(upload(&M->t_val32, to_f32(Tl.val), s, B));
+    TRY(upload(&M->t_in_ptr, Tl.in_ptr, s, B));
+    TRY(upload(&M->t_in_row, Tl.in_row, s, B));
+    TRY(upload(&M->t_in_len, Tl.in_len, s, B));
+    TRY(upload(&M->t_in_src, Tl.in_src, s, B));
+    TRY(dalloc(&M->t_part, (size_t)std::max<int64_t>(M->next, 1), B));
+    M->slots = M->tile_slots;
+    M->plan_slots = 0;
+    TRY(upload(&M->long_mask, std::vector<uint32_t>(std::max<int64_t>(M->nslices, 1), 0u), s, B));
+  } else {
+    TRY(upload(&M->sl_ptr, L.A.sl_ptr, s, B));
+    TRY(upload(&M->col, L.A.col, s, B));
+    TRY(upload(&M->val64, L.A.val, s, B));
+    TRY(upload(&M->val32, to_f32(L.A.val), s, B));
+    TRY(upload(&M->long_mask, L.A.long_mask, s, B));
+    TRY(upload(&M->long_row, L.A.long_row, s, B));
+    TRY(upload(&M->long_ptr, L.A.long_ptr, s, B));
+    TRY(upload(&M->long_col, L.A.long_col, s, B));
+    TRY(upload(&M->long_val64, L.A.long_val, s, B));
+    TRY(upload(&M->long_val32, to_f32(L.A.long_val), s, B));
+    if (M->mode == kPlan) {
+      TRY(upload(&M->pl_ptr, L.plan.pl_ptr, s, B));
+      TRY(upload(&M->pl_i, L.plan.pl_i, s, B));
+      TRY(upload(&M->pl_k, L.plan.pl_k, s, B));
+    }
+    cs = partition_slices(L, M->grid);
+    for (int c = 0; c <= M->grid; ++c) {  // long rows go to the CTA that owns their row
+      const int64_t row0 = (int64_t)cs[c] * 32;
+      cl[c] = (int32_t)(std::lower_bound(L.A.long_row.begin(), L.A.long_row.end(), row0) - L.A.long_row.begin());
+    }
+    cl[M->grid] = (int32_t)M->nlong;
+  }
+  if (M->sym) {
+    TRY(upload(&M->diag64, L.diag, s, B));
+    TRY(upload(&M->diag32, to_f32(L.diag), s, B));
+  }
   TRY(upload(&M->cta_slice, cs, s, B));
   TRY(upload(&M->cta_long, cl, s, B));
   // workspace
@@ -592,6 +677,9 @@ int gbcg_stats(gbcg_matrix_t A, gbcg_matrix_stats* out) {
   out->spmv_bytes_fp32 = 8 * m + 4 * (n + 1) + 8 * n;
   out->format = A->format;
   out->grid_ctas = A->grid;
+  out->layout = A->mode;
+  out->tiles = (int32_t)A->ntiles;
+  out->ext_slots = A->next;
   return GBCG_OK;
 }
 

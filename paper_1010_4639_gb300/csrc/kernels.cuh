@@ -34,6 +34,12 @@ constexpr int kWarps = kCgThreads / 32;
 constexpr int kMaxL = 16;    // slots per row one pipeline stage holds
 constexpr int kStages = 2;   // stages per warp
 constexpr uint16_t kPlanPad = 0xFFFF;
+constexpr int kMaxLs = 8;       // upper-triangle slots per row one symmetric stage holds
+constexpr int kSlotCap = 1312;  // slots of a symmetric tile (own rows + ext rows)
+constexpr int kSlotArr = kSlotCap + 32;  // + one dummy slot per lane
+
+// Layout modes of the product.
+enum { kGather = 0, kPlan = 1, kTiles = 2 };
 
 enum DevStatus { kOk = 0, kNotSpd = 2, kMaxit = 3, kNonfinite = 4, kTimeout = 5 };
 
@@ -55,6 +61,25 @@ struct OpDev {
   const uint16_t* __restrict__ pl_k = nullptr;
 };
 
+// Warp-tiled symmetric layout (layout.h, SymTilesHost).
+template <typename V>
+struct SymDev {
+  int32_t active = 16;                    // warps of a CTA that run tiles
+  const int32_t* __restrict__ warp_tile = nullptr;
+  const int32_t* __restrict__ tile_slice = nullptr;
+  const int32_t* __restrict__ tile_ns = nullptr;
+  const int64_t* __restrict__ tile_ext = nullptr;
+  const int32_t* __restrict__ ext_rows = nullptr;
+  const int64_t* __restrict__ sl_ptr = nullptr;
+  const uint16_t* __restrict__ slot = nullptr;
+  const V* __restrict__ val = nullptr;
+  const int32_t* __restrict__ in_ptr = nullptr;
+  const int32_t* __restrict__ in_row = nullptr;
+  const int32_t* __restrict__ in_len = nullptr;
+  const int64_t* __restrict__ in_src = nullptr;
+  V* part = nullptr;                      // ext partial sums (scratch)
+};
+
 struct GridBar {
   unsigned long long count;  // arrivals since launch (monotone)
   int32_t status;            // first failure recorded by any CTA
@@ -74,6 +99,7 @@ struct CgState {
 template <typename V>
 struct CgArgs {
   OpDev<V> A;
+  SymDev<V> T;
   V* x;
   V* r;
   V* p;
@@ -99,6 +125,24 @@ struct alignas(16) Stage {
 };
 template <typename V>
 constexpr size_t pipe_smem_bytes() { return sizeof(Stage<V>) * kStages * kWarps; }
+
+// One symmetric stage: a slice's upper-triangle values then their slots.
+template <typename V>
+struct alignas(16) SymStage {
+  V val[kMaxLs * 32];
+  uint16_t slot[kMaxLs * 32];
+};
+// Per active warp: kStages stages, then the staged x and the accumulator.
+template <typename V>
+struct alignas(16) SymWarpSmem {
+  SymStage<V> st[kStages];
+  V xs[kSlotArr];
+  V acc[kSlotArr];
+};
+template <typename V>
+constexpr int sym_active_warps() { return sizeof(V) == 8 ? 8 : 16; }
+template <typename V>
+constexpr size_t sym_smem_bytes() { return sizeof(SymWarpSmem<V>) * sym_active_warps<V>(); }
 
 // ------------------------------------------------------------ helpers ---
 __device__ __forceinline__ long long gtime() {
@@ -278,7 +322,7 @@ template <typename V, bool SYM, bool NC, class F>
 __device__ __forceinline__ void spmv_rows(const OpDev<V>& A, int64_t s0, int64_t s1, int64_t l0, int64_t l1,
                                           const V* x, Stage<V>* stages, Pipe& pp, int* err, F&& f) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  if constexpr (SYM) {
+  if constexpr (SYM) {  // transpose-plan layout
     for (int64_t s = s0 + warp; s < s1; s += nw) {
       const V v = sell_row<V, true, NC, 4>(A, s, lane, x);
       const int64_t row = s * 32 + lane;
@@ -323,6 +367,179 @@ __device__ __forceinline__ void spmv_rows(const OpDev<V>& A, int64_t s0, int64_t
   for (int64_t li = l0 + warp; li < l1; li += nw) {
     const V v = long_row<V, NC>(A, li, lane, x);
     if (lane == 0) f((int64_t)A.long_row[li], v);
+  }
+}
+
+
+// ------------------------------------------------- symmetric tiles ---
+// for i = lane, lane + 32, ... < len: st(i, ld(i)), with B loads in flight
+// per lane before the first store (the loads are independent).
+template <int B, class LD, class ST>
+__device__ __forceinline__ void batched(int lane, int len, LD&& ld, ST&& st) {
+  for (int i0 = 0; i0 < len; i0 += 32 * B) {
+    decltype(ld(0)) v[B];
+#pragma unroll
+    for (int u = 0; u < B; ++u) {
+      const int i = i0 + u * 32 + lane;
+      if (i < len) v[u] = ld(i);
+    }
+#pragma unroll
+    for (int u = 0; u < B; ++u) {
+      const int i = i0 + u * 32 + lane;
+      if (i < len) st(i, v[u]);
+    }
+  }
+}
+
+template <typename V>
+__device__ __forceinline__ int sym_len(const SymDev<V>& T, int64_t s) {
+  return (int)((T.sl_ptr[s + 1] - T.sl_ptr[s]) >> 5);
+}
+
+template <typename V>
+__device__ __forceinline__ void sym_issue(const SymDev<V>& T, SymWarpSmem<V>* ws, Pipe& pp, int64_t s) {
+  const int L = sym_len(T, s);
+  if (L == 0 || L > kMaxLs || pp.failed) return;
+  const uint32_t st = pp.issued % kStages;
+  if ((threadIdx.x & 31) == 0) {
+    const uint32_t vb = (uint32_t)(L * 32 * sizeof(V)), cb = (uint32_t)(L * 32 * sizeof(uint16_t));
+    mbar_arrive_expect_tx(&pp.bars[st], vb + cb);
+    bulk_g2s(ws->st[st].val, T.val + T.sl_ptr[s], vb, &pp.bars[st], pp.policy);
+    bulk_g2s(ws->st[st].slot, T.slot + T.sl_ptr[s], cb, &pp.bars[st], pp.policy);
+  }
+  ++pp.issued;
+}
+
+// Slice sequence of an active warp: the warp ranges j = a, a + active, ...
+// of its CTA, each a contiguous run of slices.
+template <typename V>
+struct SymSeq {
+  const SymDev<V>* T;
+  int c, a;
+  __device__ __forceinline__ int64_t range_begin(int j) const {
+    return T->tile_slice[T->warp_tile[c * kWarps + j]];
+  }
+  __device__ __forceinline__ int64_t range_end(int j) const {
+    return T->tile_slice[T->warp_tile[c * kWarps + j + 1]];
+  }
+  // next slice after s in range j (advancing j when needed); -1 at the end
+  __device__ __forceinline__ int64_t next(int64_t s, int& j) const {
+    if (s + 1 < range_end(j)) return s + 1;
+    for (j += T->active; j < kWarps; j += T->active)
+      if (range_begin(j) < range_end(j)) return range_begin(j);
+    return -1;
+  }
+};
+
+// Phase A of the symmetric product on the tiles of this active warp:
+// f(row, (D + U) x row part + accumulated U' x from this tile, x_i, D_i x_i,
+// (U x)_i) runs on the row's lane; ext accumulators go to T.part.
+template <typename V, bool NC, class F>
+__device__ __forceinline__ void sym_tiles(const OpDev<V>& A, const SymDev<V>& T, const V* x,
+                                          SymWarpSmem<V>* ws, Pipe& pp, int* err, F&& f) {
+  const int lane = threadIdx.x & 31, a = threadIdx.x >> 5, c = blockIdx.x;
+  if (a >= T.active) return;
+  SymSeq<V> seq{&T, c, a};
+  // first slice of the sequence and its lookahead
+  int jc = a;
+  int64_t s = -1;
+  for (; jc < kWarps; jc += T.active)
+    if (seq.range_begin(jc) < seq.range_end(jc)) { s = seq.range_begin(jc); break; }
+  if (s < 0) return;
+  int ji = jc;
+  int64_t s_issue = s;
+  sym_issue(T, ws, pp, s_issue);
+  s_issue = seq.next(s_issue, ji);
+  for (int j = jc; j < kWarps; j += T.active) {
+    const int32_t t0 = T.warp_tile[c * kWarps + j], t1 = T.warp_tile[c * kWarps + j + 1];
+    for (int32_t t = t0; t < t1; ++t) {
+      const int64_t sl0 = T.tile_slice[t], sl1 = T.tile_slice[t + 1];
+      const int64_t row0 = sl0 * 32;
+      const int64_t rows = (sl1 * 32 < A.n ? sl1 * 32 : A.n) - row0;
+      const int S = T.tile_ns[t];
+      const int64_t e0 = T.tile_ext[t];
+      const int ne = S - (int)rows;
+      // stage x over the tile's slots (batches of independent loads per
+      // lane); clear the accumulator
+      batched<8>(lane, (int)rows, [&](int i) { return ld_vec<NC>(x + row0 + i); },
+                 [&](int i, V v) { ws->xs[i] = v; });
+      batched<8>(lane, ne, [&](int i) { return ld_vec<NC>(x + __ldg(T.ext_rows + e0 + i)); },
+                 [&](int i, V v) { ws->xs[rows + i] = v; });
+      ws->xs[S + lane] = V(0);
+      for (int i = lane; i < S + 32; i += 32) ws->acc[i] = V(0);
+      __syncwarp();
+      for (int64_t sl = sl0; sl < sl1; ++sl) {
+        if (s_issue >= 0) {
+          sym_issue(T, ws, pp, s_issue);
+          s_issue = seq.next(s_issue, ji);
+        }
+        const int L = sym_len(T, sl);
+        const int own = (int)((sl - sl0) * 32) + lane;
+        const int64_t row = row0 + own;
+        const V xi = row < A.n ? ws->xs[own] : V(0);
+        V direct = V(0);
+        if (L > kMaxLs) {  // long slice: straight from global memory
+          const int64_t base = T.sl_ptr[sl];
+          for (int k = 0; k < L; ++k) {
+            const int sv = T.slot[base + 32 * k + lane];
+            const V v = T.val[base + 32 * k + lane];
+            direct = fma_(v, ws->xs[sv], direct);
+            ws->acc[sv] = fma_(v, xi, ws->acc[sv]);
+            __syncwarp();
+          }
+        } else if (L > 0 && !pp.failed) {
+          const uint32_t st = pp.consumed % kStages, par = (pp.consumed / kStages) & 1u;
+          if (!mbar_wait(&pp.bars[st], par, pp.limit_ns)) {
+            pp.failed = true;
+            if (lane == 0) atomicCAS(err, 0, (int)kTimeout);
+          } else {
+            ++pp.consumed;
+            const V* __restrict__ stv = ws->st[st].val;
+            const uint16_t* __restrict__ sts = ws->st[st].slot;
+#pragma unroll
+            for (int k = 0; k < kMaxLs; ++k) {
+              if (k < L) {
+                const int sv = sts[k * 32 + lane];
+                const V v = stv[k * 32 + lane];
+                direct = fma_(v, ws->xs[sv], direct);
+                ws->acc[sv] = fma_(v, xi, ws->acc[sv]);
+              }
+              __syncwarp();
+            }
+          }
+        }
+        __syncwarp();
+        if (row < A.n) {
+          const V dxi = A.diag[row] * xi;
+          f(row, dxi + direct + ws->acc[own], xi, dxi, direct);
+        }
+      }
+      __syncwarp();
+      for (int i = lane; i < ne; i += 32) T.part[e0 + i] = ws->acc[rows + i];
+      __syncwarp();
+    }
+  }
+  if (pp.failed) pipe_drain(pp);
+}
+
+// Adds the incoming ext partial sums to y over this active warp's tiles, in
+// the fixed run order of the layout.
+template <typename V>
+__device__ __forceinline__ void sym_incoming(const SymDev<V>& T, V* y) {
+  const int lane = threadIdx.x & 31, a = threadIdx.x >> 5, c = blockIdx.x;
+  if (a >= T.active) return;
+  for (int j = a; j < kWarps; j += T.active) {
+    const int32_t t0 = T.warp_tile[c * kWarps + j], t1 = T.warp_tile[c * kWarps + j + 1];
+    for (int32_t t = t0; t < t1; ++t) {
+      const int64_t row0 = (int64_t)T.tile_slice[t] * 32;
+      for (int32_t u = T.in_ptr[t]; u < T.in_ptr[t + 1]; ++u) {
+        const int64_t rr = row0 + T.in_row[u], src = T.in_src[u];
+        const int len = T.in_len[u];
+        batched<8>(lane, len, [&](int l) { return y[rr + l] + T.part[src + l]; },
+                   [&](int l, V v) { y[rr + l] = v; });
+        __syncwarp();
+      }
+    }
   }
 }
 
@@ -387,34 +604,62 @@ __device__ __forceinline__ bool grid_barrier(GridBar* gb, unsigned long long& ta
 }
 
 // -------------------------------------------------- one-shot kernels ---
-// y = A x (MODE 0) or r = b - A x with per-CTA partial sums of r'r (MODE 1),
-// on the persistent grid's slice partition.
-template <typename V, bool SYM, int MODE>
+// Shared-memory carving of the product kernels for layout mode FMT.
+template <typename V, int FMT>
+constexpr size_t product_smem() {
+  return FMT == kGather ? pipe_smem_bytes<V>() : FMT == kTiles ? sym_smem_bytes<V>() : 0;
+}
+
+// Computes A x into y for the CTA's rows: complete for kGather / kPlan; for
+// kTiles the CTA's own part, the ext partial sums going to T.part (to be
+// added by k_incoming after every CTA is done).
+template <typename V, int FMT, bool NC>
+__device__ __forceinline__ void product_rows(const OpDev<V>& A, const SymDev<V>& T, int64_t s0, int64_t s1,
+                                             int64_t l0, int64_t l1, const V* x, V* y, unsigned char* smem,
+                                             Pipe& pp, int* err) {
+  if constexpr (FMT == kTiles) {
+    SymWarpSmem<V>* ws = reinterpret_cast<SymWarpSmem<V>*>(smem) + (threadIdx.x >> 5);
+    sym_tiles<V, NC>(A, T, x, ws, pp, err, [&](int64_t row, V qo, V, V, V) { y[row] = qo; });
+  } else {
+    Stage<V>* stages = reinterpret_cast<Stage<V>*>(smem) + (threadIdx.x >> 5) * kStages;
+    spmv_rows<V, FMT == kPlan, NC>(A, s0, s1, l0, l1, x, stages, pp, err, [&](int64_t row, V v) { y[row] = v; });
+  }
+}
+
+// y = A x on the persistent grid's partition (first pass for kTiles).
+template <typename V, int FMT>
 __global__ void __launch_bounds__(kCgThreads, 1)
-    k_rows(OpDev<V> A, const int32_t* __restrict__ cta_slice, const int32_t* __restrict__ cta_long,
-           const V* __restrict__ x, const V* __restrict__ b, V* __restrict__ y, double* __restrict__ part,
-           int* err, long long limit_ns) {
+    k_rows(OpDev<V> A, SymDev<V> T, const int32_t* __restrict__ cta_slice, const int32_t* __restrict__ cta_long,
+           const V* __restrict__ x, V* __restrict__ y, int* err, long long limit_ns) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ uint64_t bars[kWarps][kStages];
-  __shared__ double red[33];
-  const int warp = threadIdx.x >> 5;
-  Stage<V>* stages = reinterpret_cast<Stage<V>*>(smem_raw) + warp * kStages;
   Pipe pp;
-  pipe_init(pp, bars[warp], limit_ns);
+  pipe_init(pp, bars[threadIdx.x >> 5], limit_ns);
   __syncthreads();
   const int c = blockIdx.x;
-  double acc = 0.0;
-  spmv_rows<V, SYM, true>(A, cta_slice[c], cta_slice[c + 1], cta_long[c], cta_long[c + 1], x, stages, pp, err,
-                          [&](int64_t row, V v) {
-                            if constexpr (MODE == 0) {
-                              y[row] = v;
-                            } else {
-                              const V t = b[row] - v;
-                              y[row] = t;
-                              acc = fma((double)t, (double)t, acc);
-                            }
-                          });
+  product_rows<V, FMT, true>(A, T, cta_slice[c], cta_slice[c + 1], cta_long[c], cta_long[c + 1], x, y, smem_raw,
+                             pp, err);
+}
+
+// Second pass: for kTiles adds the incoming partial sums; with MODE 1 then
+// forms r = b - y in place (double precision) with per-CTA sums of r'r.
+template <typename V, int FMT, int MODE>
+__global__ void __launch_bounds__(kCgThreads, 1)
+    k_finish(SymDev<V> T, const int32_t* __restrict__ cta_slice, int64_t n, const V* __restrict__ b,
+             V* __restrict__ y, double* __restrict__ part) {
+  __shared__ double red[33];
+  if constexpr (FMT == kTiles) sym_incoming<V>(T, y);
   if constexpr (MODE == 1) {
+    __syncthreads();
+    const int c = blockIdx.x;
+    const int64_t r0 = (int64_t)cta_slice[c] * 32;
+    const int64_t r1 = (int64_t)cta_slice[c + 1] * 32 < n ? (int64_t)cta_slice[c + 1] * 32 : n;
+    double acc = 0.0;
+    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+      const V t = b[i] - y[i];
+      y[i] = t;
+      acc = fma((double)t, (double)t, acc);
+    }
     const double s = block_sum(acc, red);
     if (threadIdx.x == 0) part[c] = s;
   }
@@ -465,7 +710,7 @@ __device__ __forceinline__ void rows_vec(int64_t r0, int64_t r1, F&& f) {
 // OUTER = false: inner single-precision solve from x = 0 (rhs in b), no
 // true-residual confirmation.  OUTER = true: the full solve of Section III
 // from the caller's x0 with the confirm/restart step.
-template <typename V, bool SYM, bool OUTER>
+template <typename V, int FMT, bool OUTER>
 __global__ void __launch_bounds__(kCgThreads, 1) k_cg(CgArgs<V> a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ uint64_t bars[kWarps][kStages];
@@ -479,6 +724,7 @@ __global__ void __launch_bounds__(kCgThreads, 1) k_cg(CgArgs<V> a) {
   const int64_t r0 = s0 * 32;
   const int64_t r1 = s1 * 32 < a.A.n ? s1 * 32 : a.A.n;
   const OpDev<V>& A = a.A;
+  const SymDev<V>& T = a.T;
   V* __restrict__ x = a.x;
   V* __restrict__ r = a.r;
   V* __restrict__ p = a.p;
@@ -486,10 +732,8 @@ __global__ void __launch_bounds__(kCgThreads, 1) k_cg(CgArgs<V> a) {
   const V* __restrict__ b = a.b;
   double* part0 = a.part;
   double* part1 = a.part + G;
-  const int warp = threadIdx.x >> 5;
-  Stage<V>* stages = reinterpret_cast<Stage<V>*>(smem_raw) + warp * kStages;
   Pipe pp;
-  pipe_init(pp, bars[warp], a.timeout_ns);
+  pipe_init(pp, bars[threadIdx.x >> 5], a.timeout_ns);
   __syncthreads();
   int* err = &a.bar->status;
   unsigned long long target = 0;
@@ -498,18 +742,30 @@ __global__ void __launch_bounds__(kCgThreads, 1) k_cg(CgArgs<V> a) {
   int k = 0, restarts = 0;
   double rr = 0.0, nb = 0.0, rel_true = 0.0;
 
+  // q = A xin over the CTA's rows, complete (kTiles: across a grid barrier)
+  auto full_product = [&](const V* xin) -> bool {
+    product_rows<V, FMT, false>(A, T, s0, s1, l0, l1, xin, q, smem_raw, pp, err);
+    if constexpr (FMT == kTiles) {
+      if (!grid_barrier(a.bar, target, a.timeout_ns, &sflag, nbar++)) return false;
+      sym_incoming<V>(T, q);
+    }
+    __syncthreads();
+    return true;
+  };
+
   // init: r = b - A x0, p = r, r'r and b'b
   {
     V pr = V(0), pb = V(0);
     if constexpr (OUTER) {
-      spmv_rows<V, SYM, false>(A, s0, s1, l0, l1, x, stages, pp, err, [&](int64_t row, V v) {
-        const V bi = b[row];
-        const V t = bi - v;
-        r[row] = t;
-        p[row] = t;
+      if (!full_product(x)) return;
+      for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+        const V bi = b[i];
+        const V t = bi - q[i];
+        r[i] = t;
+        p[i] = t;
         pr = fma_(t, t, pr);
         pb = fma_(bi, bi, pb);
-      });
+      }
     } else {
       rows_vec<V>(r0, r1, [&](int64_t i, int w) {
         if (w > 1) {
@@ -547,10 +803,20 @@ __global__ void __launch_bounds__(kCgThreads, 1) k_cg(CgArgs<V> a) {
     while (k < a.maxit && !(sqrt(rr) / nb <= a.tol)) {
       // A: q = A p, p'q
       V ppq = V(0);
-      spmv_rows<V, SYM, false>(A, s0, s1, l0, l1, p, stages, pp, err, [&](int64_t row, V v) {
-        q[row] = v;
-        ppq = fma_(p[row], v, ppq);
-      });
+      if constexpr (FMT == kTiles) {
+        // p'Ap = p'Dp + 2 p'Up from the rows' own parts: no incoming sums needed
+        SymWarpSmem<V>* ws = reinterpret_cast<SymWarpSmem<V>*>(smem_raw) + (threadIdx.x >> 5);
+        sym_tiles<V, false>(A, T, p, ws, pp, err, [&](int64_t row, V qo, V xi, V dxi, V direct) {
+          q[row] = qo;
+          ppq = fma_(xi, fma_(V(2), direct, dxi), ppq);
+        });
+      } else {
+        Stage<V>* stages = reinterpret_cast<Stage<V>*>(smem_raw) + (threadIdx.x >> 5) * kStages;
+        spmv_rows<V, FMT == kPlan, false>(A, s0, s1, l0, l1, p, stages, pp, err, [&](int64_t row, V v) {
+          q[row] = v;
+          ppq = fma_(p[row], v, ppq);
+        });
+      }
       {
         const double s = block_sum((double)ppq, red);
         if (threadIdx.x == 0) part0[c] = s;
@@ -560,6 +826,10 @@ __global__ void __launch_bounds__(kCgThreads, 1) k_cg(CgArgs<V> a) {
       if (!isfinite(pq)) { status = kNonfinite; goto finish; }
       if (!(pq > 0.0)) { status = kNotSpd; goto finish; }
       const double alpha = rr / pq;
+      if constexpr (FMT == kTiles) {
+        sym_incoming<V>(T, q);
+        __syncthreads();
+      }
       // B: x += alpha p, r -= alpha q, r'r
       {
         const V al = (V)alpha;
@@ -621,12 +891,13 @@ __global__ void __launch_bounds__(kCgThreads, 1) k_cg(CgArgs<V> a) {
       break;
     } else {
       // confirm on the true residual; restart the recurrence from it otherwise
+      if (!full_product(x)) return;
       V ptt = V(0);
-      spmv_rows<V, SYM, false>(A, s0, s1, l0, l1, x, stages, pp, err, [&](int64_t row, V v) {
-        const V t = b[row] - v;
-        r[row] = t;
+      for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+        const V t = b[i] - q[i];
+        r[i] = t;
         ptt = fma_(t, t, ptt);
-      });
+      }
       {
         const double s = block_sum((double)ptt, red);
         if (threadIdx.x == 0) part0[c] = s;

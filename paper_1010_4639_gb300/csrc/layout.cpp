@@ -214,6 +214,9 @@ int build_layout(int32_t format, int64_t n, int64_t nnz, const int32_t* ptr, con
   for (int64_t r = 0; r < n; ++r) ndiag += (out.diag[r] != 0.0);
   out.nnz_full = 2 * offdiag + ndiag;
   slice_rows(n, R, false, out.A);
+  out.urp = R.rp;
+  out.urc = R.rc;
+  out.urv = R.rv;
   // transpose plan, row j lists (i, k) for U_ij = k-th entry of row i, i increasing
   std::vector<int64_t> tp(n + 1, 0);
   for (int64_t q = 0; q < offdiag; ++q) tp[R.rc[q] + 1]++;
@@ -249,6 +252,189 @@ int build_layout(int32_t format, int64_t n, int64_t nnz, const int32_t* ptr, con
       for (; P.pl_ptr[s] + 32 * k + l < P.pl_ptr[s + 1]; ++k) P.pl_i[P.pl_ptr[s] + 32 * k + l] = (int32_t)j;
     }
   return 0;
+}
+
+bool build_sym_tiles(LayoutHost& L, int warps, int slot_cap) {
+  SymTilesHost& Tl = L.tiles;
+  Tl = SymTilesHost();
+  Tl.slot_cap = slot_cap;
+  const int64_t n = L.n, ns = (n + 31) / 32;
+  const std::vector<int64_t>& rp = L.urp;
+  const std::vector<int32_t>& rc = L.urc;
+  // 1. contiguous slice ranges per warp, balanced by entries + rows
+  std::vector<int64_t> wcut(warps + 1, ns);
+  {
+    int64_t total = 0;
+    auto work = [&](int64_t s) {
+      const int64_t a = 32 * s, b = std::min<int64_t>(n, 32 * s + 32);
+      return (rp[b] - rp[a]) + 32;
+    };
+    for (int64_t s = 0; s < ns; ++s) total += work(s);
+    int64_t acc = 0, s = 0;
+    wcut[0] = 0;
+    for (int w = 1; w < warps; ++w) {
+      const long double target = (long double)total * w / warps;
+      while (s < ns && (long double)(acc + work(s)) <= target) acc += work(s++);
+      wcut[w] = s;
+    }
+    wcut[warps] = ns;
+  }
+  // 2. tiles inside each warp range under the slot cap
+  std::vector<int32_t> mark(n > 0 ? n : 1, -1);
+  Tl.warp_tile.assign(warps + 1, 0);
+  Tl.tile_slice.clear();
+  std::vector<int64_t> ext_of_tile_start;
+  int32_t tile_id = 0;
+  auto count_slots = [&](int64_t sa, int64_t sb, int32_t stamp) {  // own rows + distinct ext rows
+    const int64_t a = 32 * sa, b = std::min<int64_t>(n, 32 * sb);
+    int64_t ext = 0;
+    for (int64_t r = a; r < b; ++r)
+      for (int64_t q = rp[r]; q < rp[r + 1]; ++q) {
+        const int64_t c = rc[q];
+        if (c >= b && mark[c] != stamp) {
+          mark[c] = stamp;
+          ++ext;
+        }
+      }
+    return (b - a) + ext;
+  };
+  int32_t stamp = 0;
+  for (int w = 0; w < warps; ++w) {
+    Tl.warp_tile[w] = tile_id;
+    int64_t s = wcut[w];
+    while (s < wcut[w + 1]) {
+      int64_t e = s + 1;
+      if (count_slots(s, e, stamp++) > slot_cap) {
+        Tl = SymTilesHost();
+        return false;
+      }
+      // grow while the slot count stays under the cap
+      while (e < wcut[w + 1] && count_slots(s, e + 1, stamp++) <= slot_cap) ++e;
+      Tl.tile_slice.push_back((int32_t)s);
+      ++tile_id;
+      s = e;
+    }
+  }
+  Tl.warp_tile[warps] = tile_id;
+  Tl.tile_slice.push_back((int32_t)ns);
+  const int32_t T = tile_id;
+  // 3. per tile: ext list, slot map, conflict-free slot-major entries
+  Tl.tile_ns.assign(T, 0);
+  Tl.tile_ext.assign(T + 1, 0);
+  Tl.sl_ptr.assign(ns + 1, 0);
+  std::vector<int32_t> slot_of(n > 0 ? n : 1, -1);
+  std::vector<std::vector<int32_t>> ext_lists(T);
+  for (int32_t t = 0; t < T; ++t) {
+    const int64_t a = 32 * (int64_t)Tl.tile_slice[t], b = std::min<int64_t>(n, 32 * (int64_t)Tl.tile_slice[t + 1]);
+    std::vector<int32_t>& ext = ext_lists[t];
+    for (int64_t r = a; r < b; ++r)
+      for (int64_t q = rp[r]; q < rp[r + 1]; ++q)
+        if (rc[q] >= b) ext.push_back(rc[q]);
+    std::sort(ext.begin(), ext.end());
+    ext.erase(std::unique(ext.begin(), ext.end()), ext.end());
+    Tl.tile_ns[t] = (int32_t)((b - a) + (int64_t)ext.size());
+    Tl.tile_ext[t + 1] = Tl.tile_ext[t] + (int64_t)ext.size();
+  }
+  Tl.ext_rows.resize(Tl.tile_ext[T]);
+  for (int32_t t = 0; t < T; ++t)
+    std::copy(ext_lists[t].begin(), ext_lists[t].end(), Tl.ext_rows.begin() + Tl.tile_ext[t]);
+  // entries: greedy conflict-free placement per slice, appended in slice order
+  Tl.slot.clear();
+  Tl.val.clear();
+  std::vector<std::vector<uint16_t>> used;  // used[k] = slots taken in column k
+  std::vector<uint32_t> busy;               // busy[k]: lanes holding an entry in column k
+  std::vector<int32_t> ek, el;
+  std::vector<uint16_t> es;
+  std::vector<double> ev;
+  for (int32_t t = 0; t < T; ++t) {
+    const int64_t a = 32 * (int64_t)Tl.tile_slice[t], b = std::min<int64_t>(n, 32 * (int64_t)Tl.tile_slice[t + 1]);
+    const int32_t own = (int32_t)(b - a);
+    const int32_t S = Tl.tile_ns[t];
+    for (size_t e = 0; e < ext_lists[t].size(); ++e) slot_of[ext_lists[t][e]] = own + (int32_t)e;
+    for (int64_t s = Tl.tile_slice[t]; s < Tl.tile_slice[t + 1]; ++s) {
+      for (auto& u : used) u.clear();
+      std::fill(busy.begin(), busy.end(), 0u);
+      size_t depth = 0;
+      ek.clear();
+      el.clear();
+      es.clear();
+      ev.clear();
+      for (int l = 0; l < 32; ++l) {
+        const int64_t r = 32 * s + l;
+        if (r >= n) break;
+        for (int64_t q = rp[r]; q < rp[r + 1]; ++q) {
+          const int64_t c = rc[q];
+          const uint16_t sl = (uint16_t)(c < b ? c - a : slot_of[c]);
+          size_t k = 0;
+          for (;; ++k) {
+            if (k == used.size()) {
+              used.emplace_back();
+              busy.push_back(0u);
+            }
+            if ((busy[k] >> l) & 1u) continue;
+            if (std::find(used[k].begin(), used[k].end(), sl) != used[k].end()) continue;
+            break;
+          }
+          busy[k] |= 1u << l;
+          used[k].push_back(sl);
+          depth = std::max(depth, k + 1);
+          ek.push_back((int32_t)k);
+          el.push_back(l);
+          es.push_back(sl);
+          ev.push_back(L.urv[q]);
+        }
+      }
+      const int64_t base = (int64_t)Tl.slot.size();
+      Tl.sl_ptr[s + 1] = base + 32 * (int64_t)depth;
+      for (size_t k = 0; k < depth; ++k)
+        for (int l = 0; l < 32; ++l) {
+          Tl.slot.push_back((uint16_t)(S + l));  // dummy slot: its own lane, never read back
+          Tl.val.push_back(0.0);
+        }
+      for (size_t i = 0; i < ek.size(); ++i) {
+        Tl.slot[base + 32 * (int64_t)ek[i] + el[i]] = es[i];
+        Tl.val[base + 32 * (int64_t)ek[i] + el[i]] = ev[i];
+      }
+    }
+  }
+  // 4. incoming runs: for each target tile, (row offset, length, partial index)
+  std::vector<int32_t> tile_of_slice(ns, 0);
+  for (int32_t t = 0; t < T; ++t)
+    for (int64_t s = Tl.tile_slice[t]; s < Tl.tile_slice[t + 1]; ++s) tile_of_slice[s] = t;
+  struct Run {
+    int32_t tgt;
+    int32_t row;
+    int32_t len;
+    int64_t src;
+  };
+  std::vector<Run> runs;
+  for (int32_t t = 0; t < T; ++t) {
+    const std::vector<int32_t>& ext = ext_lists[t];
+    size_t e = 0;
+    while (e < ext.size()) {
+      const int32_t tt = tile_of_slice[ext[e] / 32];
+      const int64_t trow0 = 32 * (int64_t)Tl.tile_slice[tt];
+      const int64_t tend = std::min<int64_t>(n, 32 * (int64_t)Tl.tile_slice[tt + 1]);
+      size_t f = e + 1;
+      while (f < ext.size() && ext[f] == ext[f - 1] + 1 && ext[f] < tend) ++f;
+      runs.push_back({tt, (int32_t)(ext[e] - trow0), (int32_t)(f - e), Tl.tile_ext[t] + (int64_t)e});
+      e = f;
+    }
+  }
+  // stable sort by target tile keeps the source-tile order within a target
+  std::stable_sort(runs.begin(), runs.end(), [](const Run& x, const Run& y) { return x.tgt < y.tgt; });
+  Tl.in_ptr.assign(T + 1, 0);
+  for (const Run& r : runs) Tl.in_ptr[r.tgt + 1]++;
+  for (int32_t t = 0; t < T; ++t) Tl.in_ptr[t + 1] += Tl.in_ptr[t];
+  Tl.in_row.resize(runs.size());
+  Tl.in_len.resize(runs.size());
+  Tl.in_src.resize(runs.size());
+  for (size_t i = 0; i < runs.size(); ++i) {
+    Tl.in_row[i] = runs[i].row;
+    Tl.in_len[i] = runs[i].len;
+    Tl.in_src[i] = runs[i].src;
+  }
+  return true;
 }
 
 std::vector<int32_t> partition_slices(const LayoutHost& L, int parts) {

@@ -44,6 +44,32 @@ struct PlanHost {
   std::vector<uint16_t> pl_k;      // slot of U_ij in row i; 0xFFFF = padding
 };
 
+// Warp-tiled symmetric layout.  Rows are split into contiguous ranges, one
+// per warp of the persistent grid, and each range into tiles of whole slices.
+// A tile's column space -- its own rows, then the rows beyond it that its
+// upper entries reach ("ext" rows) -- is numbered by 16-bit slots that index
+// shared-memory copies of x and of the transpose accumulator.  Each strict
+// upper entry is stored once as (value, slot), slot-major per slice, ordered
+// so that the 32 lanes of one slot never target the same slot (conflict-free
+// shared-memory accumulation without atomics).  Ext accumulators leave the
+// tile as partial sums; "incoming runs" list, per target tile and in a fixed
+// order, which partial sums to add to which of its rows.
+struct SymTilesHost {
+  int32_t slot_cap = 0;            // max slots of a tile, dummy slots excluded
+  std::vector<int32_t> warp_tile;  // W + 1: tile range of each warp
+  std::vector<int32_t> tile_slice; // T + 1: first slice of each tile
+  std::vector<int32_t> tile_ns;    // T: slot count (own rows + ext rows)
+  std::vector<int64_t> tile_ext;   // T + 1: offset into ext_rows and the partial buffer
+  std::vector<int32_t> ext_rows;   // E: global row of each ext slot
+  std::vector<int64_t> sl_ptr;     // nslices + 1: entry offsets (multiples of 32)
+  std::vector<uint16_t> slot;      // entry slots
+  std::vector<double> val;         // entry values (0 on padding)
+  std::vector<int32_t> in_ptr;     // T + 1: incoming runs of each tile
+  std::vector<int32_t> in_row;     // run start, as a row offset inside the target tile
+  std::vector<int32_t> in_len;     // run length
+  std::vector<int64_t> in_src;     // first partial-sum index of the run
+};
+
 struct LayoutHost {
   int32_t format = 0;
   int64_t n = 0;
@@ -52,12 +78,22 @@ struct LayoutHost {
   SellHost A;                      // full operator (CSR/CSC) or strict upper U (symmetric)
   std::vector<double> diag;        // symmetric only: nslices * 32, zero padded
   PlanHost plan;                   // symmetric only
+  SymTilesHost tiles;              // symmetric only, when built
+  // strict upper rows of the symmetric input (kept for the tile builder)
+  std::vector<int64_t> urp;
+  std::vector<int32_t> urc;
+  std::vector<double> urv;
 };
 
 // Validates the input (0- or 1-based) and builds the layout.  Returns 0 or a
 // gbcg_status error code, with a message in `err`.
 int build_layout(int32_t format, int64_t n, int64_t nnz, const int32_t* ptr, const int32_t* idx,
                  const double* val, int32_t index_base, LayoutHost& out, std::string& err);
+
+// Builds the warp-tiled symmetric layout for `warps` warps with at most
+// `slot_cap` slots per tile.  Returns false (layout left empty) when a single
+// slice already needs more slots than the cap.
+bool build_sym_tiles(LayoutHost& L, int warps, int slot_cap);
 
 // Contiguous slice ranges for `parts` workers, balanced by stored slots
 // (plus plan slots for the symmetric layout).  Returns parts + 1 offsets.

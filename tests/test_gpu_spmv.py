@@ -138,3 +138,26 @@ def test_full_size_128_all_formats(torch):
         y, st = gpu_spmv(torch, fmt, arrs, x)
         check(y, oracle.spmv(fmt, *arrs, x), oracle.abs_spmv(fmt, *arrs, x), TOL64)
         assert st["n"] == 2000376
+
+
+@pytest.mark.parametrize("layout", ["tiles", "plan"])
+def test_symmetric_layouts(torch, layout, monkeypatch):
+    # both symmetric layouts (warp tiles with shared-memory accumulation, and
+    # the transpose-plan gather kept for matrices whose tiles would not fit)
+    monkeypatch.setenv("GBCG_SYM_LAYOUT", layout)
+    for grid in [(9, 10, 11), (31, 31, 32)]:
+        s = fem(*grid)
+        up = s.upper()
+        x = femgen.random_vector(s.n, 17)
+        y, st = gpu_spmv(torch, "sym", up, x)
+        assert st["layout"] == (2 if layout == "tiles" else 1)
+        check(y, oracle.spmv("sym", *up, x), oracle.abs_spmv("sym", *up, x), TOL64)
+        b = torch.from_numpy(s.b).cuda()
+        with gb.Matrix("sym", *up) as A:
+            xs, info = A.solve(b, tol=1e-10, maxit=10 * s.n)
+            assert info.status == "OK"
+            xi, info2 = A.solve(b, tol=1e-10, precision="fp32_ir", maxit=10 * s.n)
+            assert info2.status == "OK"
+        for sol in (xs, xi):
+            r = s.b - oracle.spmv("csr", s.ptr, s.idx, s.val, sol.cpu().numpy())
+            assert np.linalg.norm(r) <= 1e-10 * np.linalg.norm(s.b)
