@@ -76,7 +76,8 @@ struct gbcg_matrix_s {
   int mode = kGather;       // kGather (CSR/CSC), kPlan or kTiles (symmetric)
   int64_t ntiles = 0, next = 0, tile_slots = 0;
   // warp-tiled symmetric layout (device)
-  int32_t *t_warp_tile = nullptr, *t_tile_slice = nullptr, *t_tile_ns = nullptr, *t_ext_rows = nullptr;
+  int32_t *t_warp_tile = nullptr, *t_tile_slice = nullptr, *t_tile_ns = nullptr, *t_tile_own = nullptr;
+  int32_t *t_tile_win = nullptr, *t_win_start = nullptr, *t_win_len = nullptr;
   int64_t *t_tile_ext = nullptr, *t_sl_ptr = nullptr, *t_in_src = nullptr;
   uint16_t* t_slot = nullptr;
   double* t_val64 = nullptr;
@@ -126,8 +127,11 @@ struct gbcg_matrix_s {
     t.warp_tile = t_warp_tile;
     t.tile_slice = t_tile_slice;
     t.tile_ns = t_tile_ns;
+    t.tile_own = t_tile_own;
     t.tile_ext = t_tile_ext;
-    t.ext_rows = t_ext_rows;
+    t.tile_win = t_tile_win;
+    t.win_start = t_win_start;
+    t.win_len = t_win_len;
     t.sl_ptr = t_sl_ptr;
     t.slot = t_slot;
     t.val = sizeof(V) == 8 ? (const V*)(const void*)t_val64 : (const V*)(const void*)t_val32;
@@ -190,7 +194,7 @@ void free_matrix(gbcg_matrix_s* M) {
                  M->long_val64, M->long_val32, M->diag64, M->diag32, M->pl_ptr, M->pl_i, M->pl_k,
                  M->cta_slice, M->cta_long, M->r, M->p, M->q, M->bstage, M->xstage, M->r32, M->p32, M->q32,
                  M->d32, M->rhs32, M->part, M->sums, M->bar, M->st, M->t_warp_tile, M->t_tile_slice,
-                 M->t_tile_ns, M->t_ext_rows, M->t_tile_ext, M->t_sl_ptr, M->t_in_src, M->t_slot, M->t_val64,
+                 M->t_tile_ns, M->t_tile_own, M->t_tile_win, M->t_win_start, M->t_win_len, M->t_tile_ext, M->t_sl_ptr, M->t_in_src, M->t_slot, M->t_val64,
                  M->t_val32, M->t_in_ptr, M->t_in_row, M->t_in_len, M->t_part};
   for (void* d : dev)
     if (d) cudaFree(d);
@@ -348,7 +352,9 @@ int solve_fp64(gbcg_matrix_s* M, const double* b, double* x, double tol, int max
   info->rel_res_recursive = M->st_h->nb > 0 ? std::sqrt(M->st_h->rr) / M->st_h->nb : 0.0;
   info->rel_res_true = M->st_h->nb > 0 ? M->st_h->rel_true : 0.0;
   if (status == GBCG_ERR_TIMEOUT)
-    g_last_error = "device-side wait ran out (barrier " + std::to_string(M->bar_h->where) + ")";
+    g_last_error = "device-side wait ran out (barrier " + std::to_string(M->bar_h->where) + "; " +
+                   std::to_string(M->bar_h->detail[0]) + " " + std::to_string(M->bar_h->detail[1]) + " " +
+                   std::to_string(M->bar_h->detail[2]) + " " + std::to_string(M->bar_h->detail[3]) + ")";
   return status;
 }
 
@@ -527,13 +533,16 @@ int gbcg_create(gbcg_matrix_t* out, int32_t format, int64_t n, int64_t nnz, cons
     cs.resize(M->grid + 1);
     for (int c = 0; c <= M->grid; ++c) cs[c] = Tl.tile_slice[Tl.warp_tile[(int64_t)kWarps * c]];
     M->ntiles = (int64_t)Tl.tile_ns.size();
-    M->next = (int64_t)Tl.ext_rows.size();
+    M->next = Tl.tile_ext.back();
     M->tile_slots = (int64_t)Tl.slot.size();
     TRY(upload(&M->t_warp_tile, Tl.warp_tile, s, B));
     TRY(upload(&M->t_tile_slice, Tl.tile_slice, s, B));
     TRY(upload(&M->t_tile_ns, Tl.tile_ns, s, B));
+    TRY(upload(&M->t_tile_own, Tl.tile_own, s, B));
     TRY(upload(&M->t_tile_ext, Tl.tile_ext, s, B));
-    TRY(upload(&M->t_ext_rows, Tl.ext_rows, s, B));
+    TRY(upload(&M->t_tile_win, Tl.tile_win, s, B));
+    TRY(upload(&M->t_win_start, Tl.win_start, s, B));
+    TRY(upload(&M->t_win_len, Tl.win_len, s, B));
     TRY(upload(&M->t_sl_ptr, Tl.sl_ptr, s, B));
     TRY(upload(&M->t_slot, Tl.slot, s, B));
     TRY(upload(&M->t_val64, Tl.val, s, B));

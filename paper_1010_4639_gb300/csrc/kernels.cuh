@@ -35,6 +35,8 @@ constexpr int kMaxL = 16;    // slots per row one pipeline stage holds
 constexpr int kStages = 2;   // stages per warp
 constexpr uint16_t kPlanPad = 0xFFFF;
 constexpr int kMaxLs = 8;       // upper-triangle slots per row one symmetric stage holds
+constexpr int kSymStages = 4;   // stages per warp of the symmetric tiles
+constexpr int kMaxStages = (kSymStages > kStages ? kSymStages : kStages) + 2;  // + 2 x-staging barriers
 constexpr int kSlotCap = 1312;  // slots of a symmetric tile (own rows + ext rows)
 constexpr int kSlotArr = kSlotCap + 32;  // + one dummy slot per lane
 
@@ -68,8 +70,11 @@ struct SymDev {
   const int32_t* __restrict__ warp_tile = nullptr;
   const int32_t* __restrict__ tile_slice = nullptr;
   const int32_t* __restrict__ tile_ns = nullptr;
+  const int32_t* __restrict__ tile_own = nullptr;
   const int64_t* __restrict__ tile_ext = nullptr;
-  const int32_t* __restrict__ ext_rows = nullptr;
+  const int32_t* __restrict__ tile_win = nullptr;
+  const int32_t* __restrict__ win_start = nullptr;
+  const int32_t* __restrict__ win_len = nullptr;
   const int64_t* __restrict__ sl_ptr = nullptr;
   const uint16_t* __restrict__ slot = nullptr;
   const V* __restrict__ val = nullptr;
@@ -84,6 +89,7 @@ struct GridBar {
   unsigned long long count;  // arrivals since launch (monotone)
   int32_t status;            // first failure recorded by any CTA
   int32_t where;             // barrier index of that failure
+  long long detail[4];       // facts about that failure (addresses, sizes)
 };
 
 struct CgState {
@@ -126,21 +132,28 @@ struct alignas(16) Stage {
 template <typename V>
 constexpr size_t pipe_smem_bytes() { return sizeof(Stage<V>) * kStages * kWarps; }
 
-// One symmetric stage: a slice's upper-triangle values then their slots.
+// One symmetric stage: a slice's upper-triangle values, its rows' diagonal
+// entries, then the values' slots.
 template <typename V>
 struct alignas(16) SymStage {
   V val[kMaxLs * 32];
+  V diag[32];
   uint16_t slot[kMaxLs * 32];
 };
-// Per active warp: kStages stages, then the staged x and the accumulator.
+// Per active warp: kSymStages stages, two buffers of staged x (the current
+// tile and the next one, filled by bulk copies), and the accumulator.
 template <typename V>
 struct alignas(16) SymWarpSmem {
-  SymStage<V> st[kStages];
-  V xs[kSlotArr];
+  SymStage<V> st[kSymStages];
+  V xs[2][kSlotArr];
   V acc[kSlotArr];
 };
+// Few warps with deep prefetch: each slice is little work, so bytes in
+// flight come from the stage depth, not from the warp count.
 template <typename V>
-constexpr int sym_active_warps() { return sizeof(V) == 8 ? 8 : 16; }
+constexpr int sym_active_warps() { return sizeof(V) == 8 ? 4 : 8; }
+static_assert(sizeof(SymWarpSmem<float>) * 8 <= 220 * 1024, "symmetric tiles: shared memory (float)");
+static_assert(sizeof(SymWarpSmem<double>) * 4 <= 220 * 1024, "symmetric tiles: shared memory (double)");
 template <typename V>
 constexpr size_t sym_smem_bytes() { return sizeof(SymWarpSmem<V>) * sym_active_warps<V>(); }
 
@@ -187,6 +200,11 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long l
   while (!mbar_try_wait(bar, parity))
     if (gtime() - t0 > limit_ns) return false;
   return true;
+}
+// Orders this thread's earlier generic-proxy view of global memory before
+// its later bulk copies (data written by plain stores and read by TMA).
+__device__ __forceinline__ void fence_proxy_async_global() {
+  asm volatile("fence.proxy.async.global;" ::: "memory");
 }
 __device__ __forceinline__ uint64_t policy_evict_first() {
   uint64_t p;
@@ -264,22 +282,27 @@ __device__ __forceinline__ V long_row(const OpDev<V>& A, int64_t li, int lane, c
 
 // Per-warp pipeline state (uniform across the warp's lanes).
 struct Pipe {
-  uint64_t* bars;      // kStages mbarriers of this warp
+  uint64_t* bars;      // nst mbarriers of this warp (+ 2 for the x buffers)
+  uint32_t nst;        // stages
   uint32_t issued;     // stage fills issued so far
   uint32_t consumed;   // stage fills consumed so far
+  uint32_t xiss[2];    // x-buffer fills issued / waited for; like the stage
+  uint32_t xwait[2];   // counters they persist across calls of the kernel
   uint64_t policy;
   long long limit_ns;
   bool failed;
 };
 
-__device__ __forceinline__ void pipe_init(Pipe& pp, uint64_t* bars, long long limit_ns) {
+__device__ __forceinline__ void pipe_init(Pipe& pp, uint64_t* bars, uint32_t nst, long long limit_ns) {
   pp.bars = bars;
+  pp.nst = nst;
   pp.issued = pp.consumed = 0;
+  pp.xiss[0] = pp.xiss[1] = pp.xwait[0] = pp.xwait[1] = 0;
   pp.policy = policy_evict_first();
   pp.limit_ns = limit_ns;
   pp.failed = false;
   if ((threadIdx.x & 31) == 0)
-    for (int i = 0; i < kStages; ++i) mbar_init(&bars[i], 1);
+    for (uint32_t i = 0; i < nst + 2; ++i) mbar_init(&bars[i], 1);
   fence_mbar_init();
 }
 
@@ -294,7 +317,7 @@ template <typename V>
 __device__ __forceinline__ void pipe_issue(const OpDev<V>& A, Stage<V>* stages, Pipe& pp, int64_t s) {
   const int L = slice_len(A, s);
   if (L == 0 || L > kMaxL || pp.failed) return;
-  const uint32_t st = pp.issued % kStages;
+  const uint32_t st = pp.issued % pp.nst;
   if ((threadIdx.x & 31) == 0) {
     const uint32_t vb = (uint32_t)(L * 32 * sizeof(V)), cb = (uint32_t)(L * 32 * sizeof(int32_t));
     mbar_arrive_expect_tx(&pp.bars[st], vb + cb);
@@ -308,7 +331,7 @@ __device__ __forceinline__ void pipe_issue(const OpDev<V>& A, Stage<V>* stages, 
 // after a failure so no copy lands in released shared memory.
 __device__ __forceinline__ void pipe_drain(Pipe& pp) {
   while (pp.consumed < pp.issued) {
-    const uint32_t st = pp.consumed % kStages, par = (pp.consumed / kStages) & 1u;
+    const uint32_t st = pp.consumed % pp.nst, par = (pp.consumed / pp.nst) & 1u;
     mbar_wait(&pp.bars[st], par, pp.limit_ns);
     ++pp.consumed;
   }
@@ -341,7 +364,7 @@ __device__ __forceinline__ void spmv_rows(const OpDev<V>& A, int64_t s0, int64_t
       if (L > kMaxL) {
         acc = sell_row<V, false, NC, 8>(A, s, lane, x);
       } else if (L > 0 && !pp.failed) {
-        const uint32_t st = pp.consumed % kStages, par = (pp.consumed / kStages) & 1u;
+        const uint32_t st = pp.consumed % pp.nst, par = (pp.consumed / pp.nst) & 1u;
         if (!mbar_wait(&pp.bars[st], par, pp.limit_ns)) {
           pp.failed = true;
           if (lane == 0) atomicCAS(err, 0, (int)kTimeout);
@@ -396,16 +419,26 @@ __device__ __forceinline__ int sym_len(const SymDev<V>& T, int64_t s) {
   return (int)((T.sl_ptr[s + 1] - T.sl_ptr[s]) >> 5);
 }
 
+// Fill of slice s: its rows' diagonal, plus values and slots when the slice
+// fits a stage (longer slices read those from global memory).  Every slice
+// gets exactly one fill.
 template <typename V>
-__device__ __forceinline__ void sym_issue(const SymDev<V>& T, SymWarpSmem<V>* ws, Pipe& pp, int64_t s) {
+__device__ __forceinline__ void sym_issue(const OpDev<V>& A, const SymDev<V>& T, SymWarpSmem<V>* ws, Pipe& pp,
+                                          int64_t s) {
+  if (pp.failed) return;
   const int L = sym_len(T, s);
-  if (L == 0 || L > kMaxLs || pp.failed) return;
-  const uint32_t st = pp.issued % kStages;
+  const uint32_t st = pp.issued % pp.nst;
   if ((threadIdx.x & 31) == 0) {
-    const uint32_t vb = (uint32_t)(L * 32 * sizeof(V)), cb = (uint32_t)(L * 32 * sizeof(uint16_t));
-    mbar_arrive_expect_tx(&pp.bars[st], vb + cb);
-    bulk_g2s(ws->st[st].val, T.val + T.sl_ptr[s], vb, &pp.bars[st], pp.policy);
-    bulk_g2s(ws->st[st].slot, T.slot + T.sl_ptr[s], cb, &pp.bars[st], pp.policy);
+    const bool fits = L <= kMaxLs;
+    const uint32_t vb = fits ? (uint32_t)(L * 32 * sizeof(V)) : 0u;
+    const uint32_t cb = fits ? (uint32_t)(L * 32 * sizeof(uint16_t)) : 0u;
+    const uint32_t db = (uint32_t)(32 * sizeof(V));
+    mbar_arrive_expect_tx(&pp.bars[st], vb + cb + db);
+    bulk_g2s(ws->st[st].diag, A.diag + s * 32, db, &pp.bars[st], pp.policy);
+    if (vb) {
+      bulk_g2s(ws->st[st].val, T.val + T.sl_ptr[s], vb, &pp.bars[st], pp.policy);
+      bulk_g2s(ws->st[st].slot, T.slot + T.sl_ptr[s], cb, &pp.bars[st], pp.policy);
+    }
   }
   ++pp.issued;
 }
@@ -431,6 +464,59 @@ struct SymSeq {
   }
 };
 
+// Tile sequence of an active warp (same order as SymSeq's slices).
+template <typename V>
+__device__ __forceinline__ int32_t next_tile(const SymDev<V>& T, int c, int32_t t, int& j) {
+  if (t + 1 < T.warp_tile[c * kWarps + j + 1]) return t + 1;
+  for (j += T.active; j < kWarps; j += T.active)
+    if (T.warp_tile[c * kWarps + j] < T.warp_tile[c * kWarps + j + 1]) return T.warp_tile[c * kWarps + j];
+  return -1;
+}
+
+// Issues the bulk copies of tile t's x slots (own rows, then its windows)
+// into buffer bf; parts that are not 16-byte aligned (only at the end of the
+// matrix) are left to sym_xs_tail.
+template <typename V>
+__device__ __forceinline__ void sym_xs_issue(const OpDev<V>& A, const SymDev<V>& T, SymWarpSmem<V>* ws,
+                                             uint64_t* xbar, uint64_t policy, int32_t t, int bf, const V* x) {
+  if ((threadIdx.x & 31) != 0) return;
+  const int64_t row0 = (int64_t)T.tile_slice[t] * 32;
+  const int64_t rows = ((int64_t)T.tile_slice[t + 1] * 32 < A.n ? (int64_t)T.tile_slice[t + 1] * 32 : A.n) - row0;
+  uint32_t bytes = 0;
+  const bool own_bulk = (rows & 3) == 0;
+  if (own_bulk) bytes += (uint32_t)(rows * sizeof(V));
+  const int32_t w0 = T.tile_win[t], w1 = T.tile_win[t + 1];
+  for (int32_t w = w0; w < w1; ++w)
+    if (((T.win_start[w] | T.win_len[w]) & 3) == 0) bytes += (uint32_t)(T.win_len[w] * sizeof(V));
+  fence_proxy_async_global();
+  mbar_arrive_expect_tx(xbar, bytes);
+  if (own_bulk && rows > 0) bulk_g2s(ws->xs[bf], x + row0, (uint32_t)(rows * sizeof(V)), xbar, policy);
+  int32_t slot = T.tile_own[t];
+  for (int32_t w = w0; w < w1; ++w) {
+    const int32_t ws0 = T.win_start[w], wl = T.win_len[w];
+    if (((ws0 | wl) & 3) == 0 && wl > 0) bulk_g2s(ws->xs[bf] + slot, x + ws0, (uint32_t)(wl * sizeof(V)), xbar, policy);
+    slot += wl;
+  }
+}
+
+// Plain loads of the parts sym_xs_issue left out; then clears the dummy slots.
+template <typename V, bool NC>
+__device__ __forceinline__ void sym_xs_tail(const OpDev<V>& A, const SymDev<V>& T, V* xs, int32_t t, const V* x) {
+  const int lane = threadIdx.x & 31;
+  const int64_t row0 = (int64_t)T.tile_slice[t] * 32;
+  const int64_t rows = ((int64_t)T.tile_slice[t + 1] * 32 < A.n ? (int64_t)T.tile_slice[t + 1] * 32 : A.n) - row0;
+  if ((rows & 3) != 0)
+    for (int i = lane; i < rows; i += 32) xs[i] = ld_vec<NC>(x + row0 + i);
+  int32_t slot = T.tile_own[t];
+  for (int32_t w = T.tile_win[t]; w < T.tile_win[t + 1]; ++w) {
+    const int32_t ws0 = T.win_start[w], wl = T.win_len[w];
+    if (((ws0 | wl) & 3) != 0)
+      for (int i = lane; i < wl; i += 32) xs[slot + i] = ld_vec<NC>(x + ws0 + i);
+    slot += wl;
+  }
+  xs[T.tile_ns[t] + lane] = V(0);
+}
+
 // Phase A of the symmetric product on the tiles of this active warp:
 // f(row, (D + U) x row part + accumulated U' x from this tile, x_i, D_i x_i,
 // (U x)_i) runs on the row's lane; ext accumulators go to T.part.
@@ -448,8 +534,21 @@ __device__ __forceinline__ void sym_tiles(const OpDev<V>& A, const SymDev<V>& T,
   if (s < 0) return;
   int ji = jc;
   int64_t s_issue = s;
-  sym_issue(T, ws, pp, s_issue);
-  s_issue = seq.next(s_issue, ji);
+  for (uint32_t d = 0; d + 1 < pp.nst && s_issue >= 0; ++d) {
+    sym_issue(A, T, ws, pp, s_issue);
+    s_issue = seq.next(s_issue, ji);
+  }
+  // x staging: first tile now, then each next tile while the current one runs
+  uint64_t* xbar = pp.bars + pp.nst;  // two barriers, one per x buffer
+  uint32_t* xiss = pp.xiss;
+  uint32_t* xwait = pp.xwait;
+  int jt = jc;
+  int32_t t_next = T.warp_tile[c * kWarps + jc];
+  if (!pp.failed) {
+    sym_xs_issue(A, T, ws, xbar, pp.policy, t_next, 0, x);
+    ++xiss[0];
+  }
+  int bf = 0;
   for (int j = jc; j < kWarps; j += T.active) {
     const int32_t t0 = T.warp_tile[c * kWarps + j], t1 = T.warp_tile[c * kWarps + j + 1];
     for (int32_t t = t0; t < t1; ++t) {
@@ -457,43 +556,71 @@ __device__ __forceinline__ void sym_tiles(const OpDev<V>& A, const SymDev<V>& T,
       const int64_t row0 = sl0 * 32;
       const int64_t rows = (sl1 * 32 < A.n ? sl1 * 32 : A.n) - row0;
       const int S = T.tile_ns[t];
+      const int own0 = T.tile_own[t];
       const int64_t e0 = T.tile_ext[t];
-      const int ne = S - (int)rows;
-      // stage x over the tile's slots (batches of independent loads per
-      // lane); clear the accumulator
-      batched<8>(lane, (int)rows, [&](int i) { return ld_vec<NC>(x + row0 + i); },
-                 [&](int i, V v) { ws->xs[i] = v; });
-      batched<8>(lane, ne, [&](int i) { return ld_vec<NC>(x + __ldg(T.ext_rows + e0 + i)); },
-                 [&](int i, V v) { ws->xs[rows + i] = v; });
-      ws->xs[S + lane] = V(0);
+      const int ne = S - own0;
+      // prefetch the next tile's x into the other buffer
+      t_next = next_tile(T, c, t_next, jt);
+      if (t_next >= 0 && !pp.failed) {
+        sym_xs_issue(A, T, ws, &xbar[bf ^ 1], pp.policy, t_next, bf ^ 1, x);
+        ++xiss[bf ^ 1];
+      }
+      // wait for this tile's x; clear the accumulator
+      if (!pp.failed && xwait[bf] < xiss[bf]) {
+        if (!mbar_wait(&xbar[bf], xwait[bf] & 1u, pp.limit_ns)) {
+          pp.failed = true;
+          if (lane == 0 && atomicCAS(err, 0, (int)kTimeout) == 0) {
+            err[1] = 200000000 + 10 * (t % 1000000) + (int)(xwait[bf] & 1u) * 2 + bf;
+            long long* det = reinterpret_cast<long long*>(err + 2);
+            det[0] = (long long)smem_u32(ws->xs[bf]);
+            det[1] = (long long)(uintptr_t)(x + row0);
+            det[2] = rows;
+            det[3] = (long long)smem_u32(&xbar[bf]) * 1000 + (long long)(T.tile_win[t + 1] - T.tile_win[t]);
+          }
+        } else {
+          ++xwait[bf];
+        }
+      }
+      V* xs = ws->xs[bf];
+      sym_xs_tail<V, NC>(A, T, xs, t, x);
       for (int i = lane; i < S + 32; i += 32) ws->acc[i] = V(0);
       __syncwarp();
       for (int64_t sl = sl0; sl < sl1; ++sl) {
         if (s_issue >= 0) {
-          sym_issue(T, ws, pp, s_issue);
+          sym_issue(A, T, ws, pp, s_issue);
           s_issue = seq.next(s_issue, ji);
         }
         const int L = sym_len(T, sl);
         const int own = (int)((sl - sl0) * 32) + lane;
         const int64_t row = row0 + own;
-        const V xi = row < A.n ? ws->xs[own] : V(0);
-        V direct = V(0);
-        if (L > kMaxLs) {  // long slice: straight from global memory
-          const int64_t base = T.sl_ptr[sl];
-          for (int k = 0; k < L; ++k) {
-            const int sv = T.slot[base + 32 * k + lane];
-            const V v = T.val[base + 32 * k + lane];
-            direct = fma_(v, ws->xs[sv], direct);
-            ws->acc[sv] = fma_(v, xi, ws->acc[sv]);
-            __syncwarp();
-          }
-        } else if (L > 0 && !pp.failed) {
-          const uint32_t st = pp.consumed % kStages, par = (pp.consumed / kStages) & 1u;
+        const V xi = row < A.n ? xs[own] : V(0);
+        V direct = V(0), dg = V(0);
+        bool ok = !pp.failed;
+        uint32_t st = 0;
+        if (ok) {
+          st = pp.consumed % pp.nst;
+          const uint32_t par = (pp.consumed / pp.nst) & 1u;
           if (!mbar_wait(&pp.bars[st], par, pp.limit_ns)) {
             pp.failed = true;
-            if (lane == 0) atomicCAS(err, 0, (int)kTimeout);
+            ok = false;
+            if (lane == 0 && atomicCAS(err, 0, (int)kTimeout) == 0)
+              err[1] = 100000000 + 100 * (int)(sl % 1000000) + 10 * (int)st + (int)par;
           } else {
             ++pp.consumed;
+          }
+        }
+        if (ok) {
+          dg = ws->st[st].diag[lane];
+          if (L > kMaxLs) {  // long slice: values and slots from global memory
+            const int64_t base = T.sl_ptr[sl];
+            for (int k = 0; k < L; ++k) {
+              const int sv = T.slot[base + 32 * k + lane];
+              const V v = T.val[base + 32 * k + lane];
+              direct = fma_(v, xs[sv], direct);
+              ws->acc[sv] = fma_(v, xi, ws->acc[sv]);
+              __syncwarp();
+            }
+          } else {
             const V* __restrict__ stv = ws->st[st].val;
             const uint16_t* __restrict__ sts = ws->st[st].slot;
 #pragma unroll
@@ -501,7 +628,7 @@ __device__ __forceinline__ void sym_tiles(const OpDev<V>& A, const SymDev<V>& T,
               if (k < L) {
                 const int sv = sts[k * 32 + lane];
                 const V v = stv[k * 32 + lane];
-                direct = fma_(v, ws->xs[sv], direct);
+                direct = fma_(v, xs[sv], direct);
                 ws->acc[sv] = fma_(v, xi, ws->acc[sv]);
               }
               __syncwarp();
@@ -510,15 +637,21 @@ __device__ __forceinline__ void sym_tiles(const OpDev<V>& A, const SymDev<V>& T,
         }
         __syncwarp();
         if (row < A.n) {
-          const V dxi = A.diag[row] * xi;
+          const V dxi = dg * xi;
           f(row, dxi + direct + ws->acc[own], xi, dxi, direct);
         }
       }
       __syncwarp();
-      for (int i = lane; i < ne; i += 32) T.part[e0 + i] = ws->acc[rows + i];
+      for (int i = lane; i < ne; i += 32) T.part[e0 + i] = ws->acc[own0 + i];
       __syncwarp();
+      bf ^= 1;
     }
   }
+  // a failed warp may still have x fills in flight: wait (bounded) for the
+  // last one of each buffer, which completes after the earlier ones
+  if (pp.failed)
+    for (int b2 = 0; b2 < 2; ++b2)
+      if (xwait[b2] < xiss[b2]) mbar_wait(&xbar[b2], (xiss[b2] - 1u) & 1u, pp.limit_ns);
   if (pp.failed) pipe_drain(pp);
 }
 
@@ -574,6 +707,9 @@ __device__ __forceinline__ double grid_sum(const double* part, int G, double* re
   __syncthreads();
   return r;
 }
+
+// (err points at GridBar::status; err[1] is GridBar::where, a code naming
+// the wait that ran out.)
 
 // Bounded grid barrier.  Returns false (uniformly within the CTA) when the
 // wait ran out or another CTA already failed.
@@ -632,9 +768,9 @@ __global__ void __launch_bounds__(kCgThreads, 1)
     k_rows(OpDev<V> A, SymDev<V> T, const int32_t* __restrict__ cta_slice, const int32_t* __restrict__ cta_long,
            const V* __restrict__ x, V* __restrict__ y, int* err, long long limit_ns) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  __shared__ uint64_t bars[kWarps][kStages];
+  __shared__ uint64_t bars[kWarps][kMaxStages];
   Pipe pp;
-  pipe_init(pp, bars[threadIdx.x >> 5], limit_ns);
+  pipe_init(pp, bars[threadIdx.x >> 5], FMT == kTiles ? kSymStages : kStages, limit_ns);
   __syncthreads();
   const int c = blockIdx.x;
   product_rows<V, FMT, true>(A, T, cta_slice[c], cta_slice[c + 1], cta_long[c], cta_long[c + 1], x, y, smem_raw,
@@ -713,7 +849,7 @@ __device__ __forceinline__ void rows_vec(int64_t r0, int64_t r1, F&& f) {
 template <typename V, int FMT, bool OUTER>
 __global__ void __launch_bounds__(kCgThreads, 1) k_cg(CgArgs<V> a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  __shared__ uint64_t bars[kWarps][kStages];
+  __shared__ uint64_t bars[kWarps][kMaxStages];
   __shared__ double red[33];
   __shared__ int sflag;
   using VT = typename Vec<V>::T;
@@ -733,7 +869,7 @@ __global__ void __launch_bounds__(kCgThreads, 1) k_cg(CgArgs<V> a) {
   double* part0 = a.part;
   double* part1 = a.part + G;
   Pipe pp;
-  pipe_init(pp, bars[threadIdx.x >> 5], a.timeout_ns);
+  pipe_init(pp, bars[threadIdx.x >> 5], FMT == kTiles ? kSymStages : kStages, a.timeout_ns);
   __syncthreads();
   int* err = &a.bar->status;
   unsigned long long target = 0;

@@ -254,6 +254,31 @@ int build_layout(int32_t format, int64_t n, int64_t nnz, const int32_t* ptr, con
   return 0;
 }
 
+namespace {
+
+struct Window {
+  int64_t start, len;
+};
+
+// Aligned windows covering the sorted targets: each starts on a multiple of
+// 4 rows and ends on one (clamped to n); overlapping or adjacent windows merge.
+void make_windows(const std::vector<int32_t>& tg, int64_t n, std::vector<Window>& out) {
+  out.clear();
+  size_t i = 0;
+  while (i < tg.size()) {
+    int64_t a = tg[i] & ~int64_t(3), b = ((int64_t)tg[i] + 4) & ~int64_t(3);
+    size_t j = i + 1;
+    while (j < tg.size() && (tg[j] & ~int64_t(3)) <= b) {
+      b = std::max<int64_t>(b, ((int64_t)tg[j] + 4) & ~int64_t(3));
+      ++j;
+    }
+    out.push_back({a, std::min<int64_t>(b, n) - a});
+    i = j;
+  }
+}
+
+}  // namespace
+
 bool build_sym_tiles(LayoutHost& L, int warps, int slot_cap) {
   SymTilesHost& Tl = L.tiles;
   Tl = SymTilesHost();
@@ -279,66 +304,55 @@ bool build_sym_tiles(LayoutHost& L, int warps, int slot_cap) {
     }
     wcut[warps] = ns;
   }
-  // 2. tiles inside each warp range under the slot cap
-  std::vector<int32_t> mark(n > 0 ? n : 1, -1);
-  Tl.warp_tile.assign(warps + 1, 0);
-  Tl.tile_slice.clear();
-  std::vector<int64_t> ext_of_tile_start;
-  int32_t tile_id = 0;
-  auto count_slots = [&](int64_t sa, int64_t sb, int32_t stamp) {  // own rows + distinct ext rows
+  // targets beyond a candidate tile and the resulting slot count
+  std::vector<int32_t> tg;
+  std::vector<Window> wins;
+  auto targets = [&](int64_t sa, int64_t sb) {
     const int64_t a = 32 * sa, b = std::min<int64_t>(n, 32 * sb);
-    int64_t ext = 0;
+    tg.clear();
     for (int64_t r = a; r < b; ++r)
-      for (int64_t q = rp[r]; q < rp[r + 1]; ++q) {
-        const int64_t c = rc[q];
-        if (c >= b && mark[c] != stamp) {
-          mark[c] = stamp;
-          ++ext;
-        }
-      }
-    return (b - a) + ext;
+      for (int64_t q = rp[r]; q < rp[r + 1]; ++q)
+        if (rc[q] >= b) tg.push_back(rc[q]);
+    std::sort(tg.begin(), tg.end());
+    tg.erase(std::unique(tg.begin(), tg.end()), tg.end());
+    make_windows(tg, n, wins);
+    int64_t slots = ((b - a) + 3) & ~int64_t(3);
+    for (const Window& w : wins) slots += w.len;
+    return slots;
   };
-  int32_t stamp = 0;
+  // 2. tiles inside each warp range: the longest prefix under the slot cap
+  //    (the slot count grows with the tile, so a binary search finds it)
+  Tl.warp_tile.assign(warps + 1, 0);
+  int32_t tile_id = 0;
   for (int w = 0; w < warps; ++w) {
     Tl.warp_tile[w] = tile_id;
     int64_t s = wcut[w];
     while (s < wcut[w + 1]) {
-      int64_t e = s + 1;
-      if (count_slots(s, e, stamp++) > slot_cap) {
+      if (targets(s, s + 1) > slot_cap) {
         Tl = SymTilesHost();
         return false;
       }
-      // grow while the slot count stays under the cap
-      while (e < wcut[w + 1] && count_slots(s, e + 1, stamp++) <= slot_cap) ++e;
+      int64_t lo = s + 1, hi = wcut[w + 1];  // lo fits; find the largest e in [lo, hi] that fits
+      while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) / 2;
+        if (targets(s, mid) <= slot_cap) lo = mid;
+        else hi = mid - 1;
+      }
       Tl.tile_slice.push_back((int32_t)s);
       ++tile_id;
-      s = e;
+      s = lo;
     }
   }
   Tl.warp_tile[warps] = tile_id;
   Tl.tile_slice.push_back((int32_t)ns);
   const int32_t T = tile_id;
-  // 3. per tile: ext list, slot map, conflict-free slot-major entries
+  // 3. per tile: windows, slot map, conflict-free slot-major entries
   Tl.tile_ns.assign(T, 0);
+  Tl.tile_own.assign(T, 0);
   Tl.tile_ext.assign(T + 1, 0);
+  Tl.tile_win.assign(T + 1, 0);
   Tl.sl_ptr.assign(ns + 1, 0);
   std::vector<int32_t> slot_of(n > 0 ? n : 1, -1);
-  std::vector<std::vector<int32_t>> ext_lists(T);
-  for (int32_t t = 0; t < T; ++t) {
-    const int64_t a = 32 * (int64_t)Tl.tile_slice[t], b = std::min<int64_t>(n, 32 * (int64_t)Tl.tile_slice[t + 1]);
-    std::vector<int32_t>& ext = ext_lists[t];
-    for (int64_t r = a; r < b; ++r)
-      for (int64_t q = rp[r]; q < rp[r + 1]; ++q)
-        if (rc[q] >= b) ext.push_back(rc[q]);
-    std::sort(ext.begin(), ext.end());
-    ext.erase(std::unique(ext.begin(), ext.end()), ext.end());
-    Tl.tile_ns[t] = (int32_t)((b - a) + (int64_t)ext.size());
-    Tl.tile_ext[t + 1] = Tl.tile_ext[t] + (int64_t)ext.size();
-  }
-  Tl.ext_rows.resize(Tl.tile_ext[T]);
-  for (int32_t t = 0; t < T; ++t)
-    std::copy(ext_lists[t].begin(), ext_lists[t].end(), Tl.ext_rows.begin() + Tl.tile_ext[t]);
-  // entries: greedy conflict-free placement per slice, appended in slice order
   Tl.slot.clear();
   Tl.val.clear();
   std::vector<std::vector<uint16_t>> used;  // used[k] = slots taken in column k
@@ -348,9 +362,19 @@ bool build_sym_tiles(LayoutHost& L, int warps, int slot_cap) {
   std::vector<double> ev;
   for (int32_t t = 0; t < T; ++t) {
     const int64_t a = 32 * (int64_t)Tl.tile_slice[t], b = std::min<int64_t>(n, 32 * (int64_t)Tl.tile_slice[t + 1]);
-    const int32_t own = (int32_t)(b - a);
-    const int32_t S = Tl.tile_ns[t];
-    for (size_t e = 0; e < ext_lists[t].size(); ++e) slot_of[ext_lists[t][e]] = own + (int32_t)e;
+    const int64_t S = targets(Tl.tile_slice[t], Tl.tile_slice[t + 1]);
+    const int32_t own = (int32_t)(((b - a) + 3) & ~int64_t(3));
+    Tl.tile_ns[t] = (int32_t)S;
+    Tl.tile_own[t] = own;
+    Tl.tile_ext[t + 1] = Tl.tile_ext[t] + (S - own);
+    Tl.tile_win[t + 1] = Tl.tile_win[t] + (int32_t)wins.size();
+    int32_t slot0 = own;
+    for (const Window& w : wins) {
+      Tl.win_start.push_back((int32_t)w.start);
+      Tl.win_len.push_back((int32_t)w.len);
+      for (int64_t r = w.start; r < w.start + w.len; ++r) slot_of[r] = slot0 + (int32_t)(r - w.start);
+      slot0 += (int32_t)w.len;
+    }
     for (int64_t s = Tl.tile_slice[t]; s < Tl.tile_slice[t + 1]; ++s) {
       for (auto& u : used) u.clear();
       std::fill(busy.begin(), busy.end(), 0u);
@@ -397,7 +421,7 @@ bool build_sym_tiles(LayoutHost& L, int warps, int slot_cap) {
       }
     }
   }
-  // 4. incoming runs: for each target tile, (row offset, length, partial index)
+  // 4. incoming runs: each window's rows, split by the tile that owns them
   std::vector<int32_t> tile_of_slice(ns, 0);
   for (int32_t t = 0; t < T; ++t)
     for (int64_t s = Tl.tile_slice[t]; s < Tl.tile_slice[t + 1]; ++s) tile_of_slice[s] = t;
@@ -409,16 +433,19 @@ bool build_sym_tiles(LayoutHost& L, int warps, int slot_cap) {
   };
   std::vector<Run> runs;
   for (int32_t t = 0; t < T; ++t) {
-    const std::vector<int32_t>& ext = ext_lists[t];
-    size_t e = 0;
-    while (e < ext.size()) {
-      const int32_t tt = tile_of_slice[ext[e] / 32];
-      const int64_t trow0 = 32 * (int64_t)Tl.tile_slice[tt];
-      const int64_t tend = std::min<int64_t>(n, 32 * (int64_t)Tl.tile_slice[tt + 1]);
-      size_t f = e + 1;
-      while (f < ext.size() && ext[f] == ext[f - 1] + 1 && ext[f] < tend) ++f;
-      runs.push_back({tt, (int32_t)(ext[e] - trow0), (int32_t)(f - e), Tl.tile_ext[t] + (int64_t)e});
-      e = f;
+    int64_t src = Tl.tile_ext[t];
+    for (int32_t w = Tl.tile_win[t]; w < Tl.tile_win[t + 1]; ++w) {
+      int64_t r = Tl.win_start[w];
+      const int64_t e = r + Tl.win_len[w];
+      while (r < e) {
+        const int32_t tt = tile_of_slice[r / 32];
+        const int64_t trow0 = 32 * (int64_t)Tl.tile_slice[tt];
+        const int64_t tend = std::min<int64_t>(n, 32 * (int64_t)Tl.tile_slice[tt + 1]);
+        const int64_t f = std::min(e, tend);
+        runs.push_back({tt, (int32_t)(r - trow0), (int32_t)(f - r), src});
+        src += f - r;
+        r = f;
+      }
     }
   }
   // stable sort by target tile keeps the source-tile order within a target

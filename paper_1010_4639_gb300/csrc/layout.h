@@ -46,21 +46,27 @@ struct PlanHost {
 
 // Warp-tiled symmetric layout.  Rows are split into contiguous ranges, one
 // per warp of the persistent grid, and each range into tiles of whole slices.
-// A tile's column space -- its own rows, then the rows beyond it that its
-// upper entries reach ("ext" rows) -- is numbered by 16-bit slots that index
-// shared-memory copies of x and of the transpose accumulator.  Each strict
-// upper entry is stored once as (value, slot), slot-major per slice, ordered
-// so that the 32 lanes of one slot never target the same slot (conflict-free
-// shared-memory accumulation without atomics).  Ext accumulators leave the
-// tile as partial sums; "incoming runs" list, per target tile and in a fixed
-// order, which partial sums to add to which of its rows.
+// A tile's column space -- its own rows, then windows of rows beyond it that
+// its upper entries reach ("ext" rows) -- is numbered by 16-bit slots that
+// index shared-memory copies of x and of the transpose accumulator.  Own rows
+// and every window start on a multiple of 4 rows and span a multiple of 4
+// rows (16-byte aligned), so a tile's x arrives by a few bulk copies; padding
+// rows inside a window are simply never targeted.  Each strict upper entry is
+// stored once as (value, slot), slot-major per slice, ordered so that the 32
+// lanes of one slot never target the same slot (conflict-free shared-memory
+// accumulation without atomics).  Window accumulators leave the tile as
+// partial sums; "incoming runs" list, per target tile and in a fixed order,
+// which partial sums to add to which of its rows.
 struct SymTilesHost {
   int32_t slot_cap = 0;            // max slots of a tile, dummy slots excluded
   std::vector<int32_t> warp_tile;  // W + 1: tile range of each warp
   std::vector<int32_t> tile_slice; // T + 1: first slice of each tile
-  std::vector<int32_t> tile_ns;    // T: slot count (own rows + ext rows)
-  std::vector<int64_t> tile_ext;   // T + 1: offset into ext_rows and the partial buffer
-  std::vector<int32_t> ext_rows;   // E: global row of each ext slot
+  std::vector<int32_t> tile_ns;    // T: slot count (padded own rows + windows)
+  std::vector<int32_t> tile_own;   // T: own rows padded to a multiple of 4
+  std::vector<int64_t> tile_ext;   // T + 1: first partial sum of each tile
+  std::vector<int32_t> tile_win;   // T + 1: window range of each tile
+  std::vector<int32_t> win_start;  // global first row of each window
+  std::vector<int32_t> win_len;    // rows of each window
   std::vector<int64_t> sl_ptr;     // nslices + 1: entry offsets (multiples of 32)
   std::vector<uint16_t> slot;      // entry slots
   std::vector<double> val;         // entry values (0 on padding)
