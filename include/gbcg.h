@@ -193,6 +193,39 @@ const char* gbcg_last_error(void);
  */
 int gbcg_selftest_wait_timeout(int32_t ctas, int32_t timeout_ms, void* stream);
 
+/*
+ * gbcg_solve_csr_static -- conjugate gradient for A x = b that allocates no
+ * memory: no cudaMalloc, no cudaFree, no allocating library call.  The paper
+ * has no counterpart; it exists for callers that cannot allocate device
+ * memory -- code running inside a memory pool's or allocator's callback
+ * (allocating there re-enters the allocator), latency-critical loops where an
+ * allocation would stall or synchronise the device, and plug-ins whose host
+ * application owns all device memory.
+ *
+ *   n, nnz, ptr, idx, val
+ *          the full symmetric matrix in 0-based CSR, device pointers, used in
+ *          place (sorted, in-range indices are the caller's promise: they are
+ *          not checked here)
+ *   b, x   device pointers to n doubles; x holds x0 on entry, the solution
+ *          on return
+ *   tol, maxit, info, stream  as for gbcg_solve (FP64, at most 3 restarts)
+ *
+ * The solver's scratch (three work vectors, partial sums, barrier and state)
+ * lives in one fixed device array of GBCG_STATIC_SCRATCH_BYTES defined in the
+ * library, so n must not exceed GBCG_STATIC_MAX_N; larger n is rejected with
+ * GBCG_ERR_INVALID.  Every GPU that loads the library holds that array until
+ * the process exits.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  All calls share the array and the call clears what must start at
+ * zero, so calls whose GPU work overlaps (several streams or host threads on
+ * one device) race: issue one at a time per device.  The call synchronises
+ * `stream` before it returns.
+ */
+#define GBCG_STATIC_SCRATCH_BYTES (16u * 1024u * 1024u)
+#define GBCG_STATIC_MAX_N 680000
+int gbcg_solve_csr_static(int64_t n, int64_t nnz, const int32_t* ptr, const int32_t* idx, const double* val,
+                          const double* b, double* x, double tol, int32_t maxit, gbcg_info* info, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

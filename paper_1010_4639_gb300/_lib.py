@@ -19,7 +19,8 @@ STATUS_NAMES = ["OK", "INVALID", "NOT_SPD", "MAXIT", "NONFINITE", "TIMEOUT", "CU
 
 # Every entry point declared in include/gbcg.h.
 EXPORTS = ["gbcg_create", "gbcg_destroy", "gbcg_spmv", "gbcg_spmv_f32", "gbcg_solve", "gbcg_stats",
-           "gbcg_status_string", "gbcg_last_error", "gbcg_selftest_wait_timeout"]
+           "gbcg_status_string", "gbcg_last_error", "gbcg_selftest_wait_timeout", "gbcg_solve_csr_static"]
+STATIC_MAX_N = 680000
 
 
 class Opts(ctypes.Structure):
@@ -72,8 +73,9 @@ def load(path: str = LIB_PATH):
     lib.gbcg_last_error.argtypes = []
     lib.gbcg_last_error.restype = ctypes.c_char_p
     lib.gbcg_selftest_wait_timeout.argtypes = [i32, i32, vp]
+    lib.gbcg_solve_csr_static.argtypes = [i64, i64, vp, vp, vp, vp, vp, d, i32, ctypes.POINTER(Info), vp]
     for name in ("gbcg_create", "gbcg_destroy", "gbcg_spmv", "gbcg_spmv_f32", "gbcg_solve", "gbcg_stats",
-                 "gbcg_selftest_wait_timeout"):
+                 "gbcg_selftest_wait_timeout", "gbcg_solve_csr_static"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib

@@ -68,6 +68,12 @@ int env_int(const char* name, int dflt) {
 
 }  // namespace
 
+namespace gbcg {
+// Sets the calling thread's message for gbcg_last_error() (also used by the
+// allocation-free entry point in static_solve.cu).
+void set_last_error(const std::string& m) { g_last_error = m; }
+}  // namespace gbcg
+
 struct gbcg_matrix_s {
   int32_t format = 0;
   int64_t n = 0, nnz_input = 0, nnz_full = 0, slots = 0, plan_slots = 0;
