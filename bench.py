@@ -6,8 +6,9 @@ the same GPU, and the CPU oracle timed beside it.
 
 One step = one solve from x0 = 0 to a true relative residual <= 1e-10 with the
 headline method (single-precision inner CG with double-precision iterative
-refinement, symmetric upper storage), inputs resident in HBM.  The JSON line
-also carries the plain FP64 CG times of the three storage formats.
+refinement, full CSR storage -- the fastest storage of the library on this
+system), inputs resident in HBM.  The JSON line also carries the plain FP64 CG
+and mixed-precision times and the SpMV bandwidth of the three storage formats.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -44,7 +45,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--grid", default="128", choices=sorted(GRIDS))
-    ap.add_argument("--format", default="sym", choices=["sym", "csr", "csc"])
+    ap.add_argument("--format", default="csr", choices=["sym", "csr", "csc"])
     ap.add_argument("--precision", default="fp32_ir", choices=["fp32_ir", "fp64"])
     ap.add_argument("--inner-tol", type=float, default=1e-4)
     ap.add_argument("--no-extras", action="store_true", help="skip the per-format and CPU-baseline legs")
