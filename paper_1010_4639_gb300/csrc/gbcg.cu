@@ -81,15 +81,16 @@ struct gbcg_matrix_s {
   int sym = 0;
   int mode = kGather;       // kGather (CSR/CSC), kPlan or kTiles (symmetric)
   int64_t ntiles = 0, next = 0, tile_slots = 0;
-  // warp-tiled symmetric layout (device)
-  int32_t *t_warp_tile = nullptr, *t_tile_slice = nullptr, *t_tile_ns = nullptr, *t_tile_own = nullptr;
-  int32_t *t_tile_win = nullptr, *t_win_start = nullptr, *t_win_len = nullptr;
-  int64_t *t_tile_ext = nullptr, *t_sl_ptr = nullptr, *t_in_src = nullptr;
-  uint16_t* t_slot = nullptr;
+  // tiled symmetric layout (device)
+  int32_t *t_cta_tile = nullptr, *t_tile_slice = nullptr, *t_tile_ns = nullptr, *t_tile_own = nullptr;
+  int32_t *t_tile_len = nullptr, *t_tile_rlog = nullptr, *t_tile_win = nullptr, *t_win_start = nullptr,
+          *t_win_len = nullptr;
+  int64_t *t_tile_ent = nullptr, *t_tile_meta = nullptr, *t_tile_ext = nullptr, *t_in_src = nullptr;
+  uint16_t* t_meta = nullptr;
   double* t_val64 = nullptr;
   float* t_val32 = nullptr;
   int32_t *t_in_ptr = nullptr, *t_in_row = nullptr, *t_in_len = nullptr;
-  double* t_part = nullptr;  // ext partial sums (used as float for the single-precision product)
+  double* t_part = nullptr;  // window partial sums (used as float for the single-precision product)
   // layout (device)
   int64_t* sl_ptr = nullptr;
   int32_t* col = nullptr;
@@ -129,18 +130,20 @@ struct gbcg_matrix_s {
   template <typename V>
   SymDev<V> tiles() const {
     SymDev<V> t;
-    t.active = sym_active_warps<V>();
-    t.warp_tile = t_warp_tile;
+    t.cta_tile = t_cta_tile;
     t.tile_slice = t_tile_slice;
     t.tile_ns = t_tile_ns;
     t.tile_own = t_tile_own;
+    t.tile_len = t_tile_len;
+    t.tile_rlog = t_tile_rlog;
+    t.tile_ent = t_tile_ent;
+    t.tile_meta = t_tile_meta;
     t.tile_ext = t_tile_ext;
     t.tile_win = t_tile_win;
     t.win_start = t_win_start;
     t.win_len = t_win_len;
-    t.sl_ptr = t_sl_ptr;
-    t.slot = t_slot;
     t.val = sizeof(V) == 8 ? (const V*)(const void*)t_val64 : (const V*)(const void*)t_val32;
+    t.meta = t_meta;
     t.in_ptr = t_in_ptr;
     t.in_row = t_in_row;
     t.in_len = t_in_len;
@@ -199,9 +202,10 @@ void free_matrix(gbcg_matrix_s* M) {
   void* dev[] = {M->sl_ptr, M->col, M->val64, M->val32, M->long_mask, M->long_row, M->long_ptr, M->long_col,
                  M->long_val64, M->long_val32, M->diag64, M->diag32, M->pl_ptr, M->pl_i, M->pl_k,
                  M->cta_slice, M->cta_long, M->r, M->p, M->q, M->bstage, M->xstage, M->r32, M->p32, M->q32,
-                 M->d32, M->rhs32, M->part, M->sums, M->bar, M->st, M->t_warp_tile, M->t_tile_slice,
-                 M->t_tile_ns, M->t_tile_own, M->t_tile_win, M->t_win_start, M->t_win_len, M->t_tile_ext, M->t_sl_ptr, M->t_in_src, M->t_slot, M->t_val64,
-                 M->t_val32, M->t_in_ptr, M->t_in_row, M->t_in_len, M->t_part};
+                 M->d32, M->rhs32, M->part, M->sums, M->bar, M->st, M->t_cta_tile, M->t_tile_slice,
+                 M->t_tile_ns, M->t_tile_own, M->t_tile_len, M->t_tile_rlog, M->t_tile_win, M->t_win_start, M->t_win_len,
+                 M->t_tile_ent, M->t_tile_meta, M->t_tile_ext, M->t_in_src, M->t_meta, M->t_val64, M->t_val32,
+                 M->t_in_ptr, M->t_in_row, M->t_in_len, M->t_part};
   for (void* d : dev)
     if (d) cudaFree(d);
   if (M->st_h) cudaFreeHost(M->st_h);
@@ -212,11 +216,14 @@ void free_matrix(gbcg_matrix_s* M) {
   delete M;
 }
 
+// Threads per CTA: the tiled symmetric kernels add a producer warp.
+constexpr int block_of(int fmt) { return fmt == kTiles ? kTileThreads : kCgThreads; }
+
 template <typename V, int FMT, bool OUTER>
 int occupancy_of(int& per_sm) {
   const size_t sm = product_smem<V, FMT>();
   CUDA_TRY(cudaFuncSetAttribute(k_cg<V, FMT, OUTER>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-  CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cg<V, FMT, OUTER>, kCgThreads, sm));
+  CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cg<V, FMT, OUTER>, block_of(FMT), sm));
   return 0;
 }
 
@@ -257,7 +264,7 @@ bool is_device_ptr(const void* p) {
 template <typename V, int FMT, bool OUTER>
 cudaError_t launch_cg(const CgArgs<V>& args, int grid, cudaStream_t s) {
   void* kargs[] = {(void*)&args};
-  return cudaLaunchCooperativeKernel((const void*)k_cg<V, FMT, OUTER>, dim3(grid), dim3(kCgThreads), kargs,
+  return cudaLaunchCooperativeKernel((const void*)k_cg<V, FMT, OUTER>, dim3(grid), dim3(block_of(FMT)), kargs,
                                      product_smem<V, FMT>(), s);
 }
 
@@ -274,7 +281,7 @@ cudaError_t launch_cg_fmt(const gbcg_matrix_s* M, const CgArgs<V>& a, cudaStream
 // of r'r in part (MODE 1, double precision), on the persistent partition.
 template <typename V, int FMT, int MODE>
 cudaError_t launch_product(const gbcg_matrix_s* M, const V* x, const V* b, V* y, cudaStream_t s) {
-  k_rows<V, FMT><<<M->grid, kCgThreads, product_smem<V, FMT>(), s>>>(
+  k_rows<V, FMT><<<M->grid, block_of(FMT), product_smem<V, FMT>(), s>>>(
       M->op<V>(), M->tiles<V>(), M->cta_slice, M->cta_long, x, y, &M->bar->status, 1000000000LL);
   if (FMT == kTiles || MODE == 1)
     k_finish<V, FMT, MODE><<<M->grid, kCgThreads, 0, s>>>(M->tiles<V>(), M->cta_slice, M->n, b, y, M->part);
@@ -529,28 +536,31 @@ int gbcg_create(gbcg_matrix_t* out, int32_t format, int64_t n, int64_t nnz, cons
     return 0;
   };
   TRY(choose_grid());
-  if (M->mode == kTiles && !build_sym_tiles(L, kWarps * M->grid, kSlotCap)) {
-    M->mode = kPlan;  // a single slice needs more slots than a tile holds
+  if (M->mode == kTiles && !build_sym_tiles(L, M->grid, kTileSlot, kTileEnt)) {
+    M->mode = kPlan;  // a single slice exceeds what a tile holds
     TRY(choose_grid());
   }
   std::vector<int32_t> cs, cl(M->grid + 1, 0);
   if (M->mode == kTiles) {
     const SymTilesHost& Tl = L.tiles;
     cs.resize(M->grid + 1);
-    for (int c = 0; c <= M->grid; ++c) cs[c] = Tl.tile_slice[Tl.warp_tile[(int64_t)kWarps * c]];
+    for (int c = 0; c <= M->grid; ++c) cs[c] = Tl.tile_slice[Tl.cta_tile[c]];
     M->ntiles = (int64_t)Tl.tile_ns.size();
     M->next = Tl.tile_ext.back();
-    M->tile_slots = (int64_t)Tl.slot.size();
-    TRY(upload(&M->t_warp_tile, Tl.warp_tile, s, B));
+    M->tile_slots = (int64_t)Tl.val.size();
+    TRY(upload(&M->t_cta_tile, Tl.cta_tile, s, B));
     TRY(upload(&M->t_tile_slice, Tl.tile_slice, s, B));
     TRY(upload(&M->t_tile_ns, Tl.tile_ns, s, B));
     TRY(upload(&M->t_tile_own, Tl.tile_own, s, B));
+    TRY(upload(&M->t_tile_len, Tl.tile_len, s, B));
+    TRY(upload(&M->t_tile_rlog, Tl.tile_rlog, s, B));
+    TRY(upload(&M->t_tile_ent, Tl.tile_ent, s, B));
+    TRY(upload(&M->t_tile_meta, Tl.tile_meta, s, B));
     TRY(upload(&M->t_tile_ext, Tl.tile_ext, s, B));
     TRY(upload(&M->t_tile_win, Tl.tile_win, s, B));
     TRY(upload(&M->t_win_start, Tl.win_start, s, B));
     TRY(upload(&M->t_win_len, Tl.win_len, s, B));
-    TRY(upload(&M->t_sl_ptr, Tl.sl_ptr, s, B));
-    TRY(upload(&M->t_slot, Tl.slot, s, B));
+    TRY(upload(&M->t_meta, Tl.meta, s, B));
     TRY(upload(&M->t_val64, Tl.val, s, B));
     TRY(upload(&M->t_val32, to_f32(Tl.val), s, B));
     TRY(upload(&M->t_in_ptr, Tl.in_ptr, s, B));

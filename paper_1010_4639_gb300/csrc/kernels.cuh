@@ -31,14 +31,12 @@ namespace gbcg {
 
 constexpr int kCgThreads = 512;
 constexpr int kWarps = kCgThreads / 32;
+constexpr int kTileThreads = kCgThreads + 32;  // tiled symmetric kernels: + one producer warp
+constexpr int kMaxThreads = kTileThreads;
 constexpr int kMaxL = 16;    // slots per row one pipeline stage holds
 constexpr int kStages = 2;   // stages per warp
 constexpr uint16_t kPlanPad = 0xFFFF;
-constexpr int kMaxLs = 8;       // upper-triangle slots per row one symmetric stage holds
-constexpr int kSymStages = 4;   // stages per warp of the symmetric tiles
-constexpr int kMaxStages = (kSymStages > kStages ? kSymStages : kStages) + 2;  // + 2 x-staging barriers
-constexpr int kSlotCap = 1312;  // slots of a symmetric tile (own rows + ext rows)
-constexpr int kSlotArr = kSlotCap + 32;  // + one dummy slot per lane
+constexpr int kMaxStages = 3 + 2;  // gather-pipeline stages (<= 3) + 2 spare
 
 // Layout modes of the product.
 enum { kGather = 0, kPlan = 1, kTiles = 2 };
@@ -63,26 +61,28 @@ struct OpDev {
   const uint16_t* __restrict__ pl_k = nullptr;
 };
 
-// Warp-tiled symmetric layout (layout.h, SymTilesHost).
+// Tiled symmetric layout (layout.h, SymTilesHost).
 template <typename V>
 struct SymDev {
-  int32_t active = 16;                    // warps of a CTA that run tiles
-  const int32_t* __restrict__ warp_tile = nullptr;
+  const int32_t* __restrict__ cta_tile = nullptr;
   const int32_t* __restrict__ tile_slice = nullptr;
   const int32_t* __restrict__ tile_ns = nullptr;
   const int32_t* __restrict__ tile_own = nullptr;
+  const int32_t* __restrict__ tile_len = nullptr;
+  const int32_t* __restrict__ tile_rlog = nullptr;
+  const int64_t* __restrict__ tile_ent = nullptr;
+  const int64_t* __restrict__ tile_meta = nullptr;
   const int64_t* __restrict__ tile_ext = nullptr;
   const int32_t* __restrict__ tile_win = nullptr;
   const int32_t* __restrict__ win_start = nullptr;
   const int32_t* __restrict__ win_len = nullptr;
-  const int64_t* __restrict__ sl_ptr = nullptr;
-  const uint16_t* __restrict__ slot = nullptr;
   const V* __restrict__ val = nullptr;
+  const uint16_t* __restrict__ meta = nullptr;
   const int32_t* __restrict__ in_ptr = nullptr;
   const int32_t* __restrict__ in_row = nullptr;
   const int32_t* __restrict__ in_len = nullptr;
   const int64_t* __restrict__ in_src = nullptr;
-  V* part = nullptr;                      // ext partial sums (scratch)
+  V* part = nullptr;                      // window partial sums (scratch)
 };
 
 struct GridBar {
@@ -129,33 +129,62 @@ struct alignas(16) Stage {
   V val[kMaxL * 32];
   int32_t col[kMaxL * 32];
 };
+// Stages per warp of the row-gather pipeline: three for single precision
+// (more bytes in flight for a bandwidth-bound product), two for double
+// precision (FP64-FMA-bound; a third would not fit shared memory).
 template <typename V>
-constexpr size_t pipe_smem_bytes() { return sizeof(Stage<V>) * kStages * kWarps; }
+__host__ __device__ constexpr int gather_stages() { return sizeof(V) == 4 ? 3 : kStages; }
+template <typename V>
+constexpr size_t pipe_smem_bytes() { return sizeof(Stage<V>) * gather_stages<V>() * kWarps; }
 
-// One symmetric stage: a slice's upper-triangle values, its rows' diagonal
-// entries, then the values' slots.
-template <typename V>
-struct alignas(16) SymStage {
-  V val[kMaxLs * 32];
-  V diag[32];
-  uint16_t slot[kMaxLs * 32];
+// Shared memory of the tiled symmetric product: two stages (the current tile
+// and the next one, filled by bulk copies), the entries' transpose products
+// and the tile rows' transpose sums.
+constexpr int kTileEnt = 4096;   // padded entries of a tile
+constexpr int kTileSlot = 2048;  // slots of a tile
+constexpr int kTileRows = 512;   // 16 slices
+// Geometry of the tile a stage holds, written by the producer with the
+// stage's copies (published to the consumers by the same mbarrier phase).
+struct TileInfo {
+  int64_t row0, ext0, e8;
+  int32_t rows, nsl, L, S, own, tail;  // tail: some x slots need plain loads
+  int32_t rmask;                       // R - 1: entry e belongs to local row e & rmask
+  int32_t pad_[3];
 };
-// Per active warp: kSymStages stages, two buffers of staged x (the current
-// tile and the next one, filled by bulk copies), and the accumulator.
 template <typename V>
-struct alignas(16) SymWarpSmem {
-  SymStage<V> st[kSymStages];
-  V xs[2][kSlotArr];
-  V acc[kSlotArr];
+struct alignas(16) TileStage {
+  TileInfo info;
+  V val[kTileEnt];
+  uint16_t meta[2 * kTileEnt + kTileSlot + 8];  // slots, transpose index, index offsets
+  V diag[kTileRows];
+  V xs[kTileSlot];
 };
-// Few warps with deep prefetch: each slice is little work, so bytes in
-// flight come from the stage depth, not from the warp count.
+// Tiles in flight per CTA: three in single precision (bandwidth-bound), two
+// in double precision (FP64-FMA-bound; a third stage would not fit).
 template <typename V>
-constexpr int sym_active_warps() { return sizeof(V) == 8 ? 4 : 8; }
-static_assert(sizeof(SymWarpSmem<float>) * 8 <= 220 * 1024, "symmetric tiles: shared memory (float)");
-static_assert(sizeof(SymWarpSmem<double>) * 4 <= 220 * 1024, "symmetric tiles: shared memory (double)");
+__host__ __device__ constexpr int tile_stages() { return sizeof(V) == 4 ? 3 : 2; }
 template <typename V>
-constexpr size_t sym_smem_bytes() { return sizeof(SymWarpSmem<V>) * sym_active_warps<V>(); }
+struct alignas(16) TileSmem {
+  TileStage<V> st[tile_stages<V>()];
+  V acc[kTileRows];
+};
+static_assert(sizeof(TileInfo) % 16 == 0, "stage payload alignment");
+template <typename V>
+constexpr size_t sym_smem_bytes() { return sizeof(TileSmem<V>); }
+static_assert(sizeof(TileSmem<float>) <= 220 * 1024, "symmetric tiles: shared memory (float)");
+static_assert(sizeof(TileSmem<double>) <= 220 * 1024, "symmetric tiles: shared memory (double)");
+
+// Fill counters of the tile stages; like the gather pipeline's they persist
+// across calls within one launch.
+struct TilePipe {
+  uint64_t* bar;      // "full" mbarrier per stage (shared memory): the stage's copies landed
+  uint64_t* empty;    // "empty" mbarrier per stage: the consumers are done with it
+  uint32_t iss[3];    // fills issued per stage (producer) / waited for (consumers)
+  uint32_t wait[3];
+  uint64_t policy;
+  long long limit_ns;
+  bool failed;
+};
 
 // ------------------------------------------------------------ helpers ---
 __device__ __forceinline__ long long gtime() {
@@ -201,6 +230,24 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long l
     if (gtime() - t0 > limit_ns) return false;
   return true;
 }
+// Named barrier 1 over the `count` consumer threads (warps 0..count/32-1).
+__device__ __forceinline__ void consumers_sync(int count) {
+  asm volatile("bar.sync 1, %0;" ::"r"(count) : "memory");
+}
+// Same, returning whether `pred` holds on every consumer thread.
+__device__ __forceinline__ bool consumers_and(int count, bool pred) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.and.pred q, 1, %2, p;\n selp.u32 %0, 1, 0, q;\n}"
+      : "=r"(r)
+      : "r"((uint32_t)pred), "r"(count)
+      : "memory");
+  return r != 0;
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 // Orders this thread's earlier generic-proxy view of global memory before
 // its later bulk copies (data written by plain stores and read by TMA).
 __device__ __forceinline__ void fence_proxy_async_global() {
@@ -353,7 +400,7 @@ __device__ __forceinline__ void spmv_rows(const OpDev<V>& A, int64_t s0, int64_t
     }
   } else {
     int64_t s_issue = s0 + warp;
-    for (int d = 0; d < kStages - 1 && s_issue < s1; ++d, s_issue += nw) pipe_issue(A, stages, pp, s_issue);
+    for (uint32_t d = 0; d + 1 < pp.nst && s_issue < s1; ++d, s_issue += nw) pipe_issue(A, stages, pp, s_issue);
     for (int64_t s = s0 + warp; s < s1; s += nw) {
       if (s_issue < s1) {
         pipe_issue(A, stages, pp, s_issue);
@@ -415,265 +462,205 @@ __device__ __forceinline__ void batched(int lane, int len, LD&& ld, ST&& st) {
 }
 
 template <typename V>
-__device__ __forceinline__ int sym_len(const SymDev<V>& T, int64_t s) {
-  return (int)((T.sl_ptr[s + 1] - T.sl_ptr[s]) >> 5);
-}
-
-// Fill of slice s: its rows' diagonal, plus values and slots when the slice
-// fits a stage (longer slices read those from global memory).  Every slice
-// gets exactly one fill.
-template <typename V>
-__device__ __forceinline__ void sym_issue(const OpDev<V>& A, const SymDev<V>& T, SymWarpSmem<V>* ws, Pipe& pp,
-                                          int64_t s) {
-  if (pp.failed) return;
-  const int L = sym_len(T, s);
-  const uint32_t st = pp.issued % pp.nst;
-  if ((threadIdx.x & 31) == 0) {
-    const bool fits = L <= kMaxLs;
-    const uint32_t vb = fits ? (uint32_t)(L * 32 * sizeof(V)) : 0u;
-    const uint32_t cb = fits ? (uint32_t)(L * 32 * sizeof(uint16_t)) : 0u;
-    const uint32_t db = (uint32_t)(32 * sizeof(V));
-    mbar_arrive_expect_tx(&pp.bars[st], vb + cb + db);
-    bulk_g2s(ws->st[st].diag, A.diag + s * 32, db, &pp.bars[st], pp.policy);
-    if (vb) {
-      bulk_g2s(ws->st[st].val, T.val + T.sl_ptr[s], vb, &pp.bars[st], pp.policy);
-      bulk_g2s(ws->st[st].slot, T.slot + T.sl_ptr[s], cb, &pp.bars[st], pp.policy);
-    }
-  }
-  ++pp.issued;
-}
-
-// Slice sequence of an active warp: the warp ranges j = a, a + active, ...
-// of its CTA, each a contiguous run of slices.
-template <typename V>
-struct SymSeq {
-  const SymDev<V>* T;
-  int c, a;
-  __device__ __forceinline__ int64_t range_begin(int j) const {
-    return T->tile_slice[T->warp_tile[c * kWarps + j]];
-  }
-  __device__ __forceinline__ int64_t range_end(int j) const {
-    return T->tile_slice[T->warp_tile[c * kWarps + j + 1]];
-  }
-  // next slice after s in range j (advancing j when needed); -1 at the end
-  __device__ __forceinline__ int64_t next(int64_t s, int& j) const {
-    if (s + 1 < range_end(j)) return s + 1;
-    for (j += T->active; j < kWarps; j += T->active)
-      if (range_begin(j) < range_end(j)) return range_begin(j);
-    return -1;
-  }
+struct TileGeom {
+  int64_t row0, rows;
+  int nsl, L, S, own;
 };
 
-// Tile sequence of an active warp (same order as SymSeq's slices).
 template <typename V>
-__device__ __forceinline__ int32_t next_tile(const SymDev<V>& T, int c, int32_t t, int& j) {
-  if (t + 1 < T.warp_tile[c * kWarps + j + 1]) return t + 1;
-  for (j += T.active; j < kWarps; j += T.active)
-    if (T.warp_tile[c * kWarps + j] < T.warp_tile[c * kWarps + j + 1]) return T.warp_tile[c * kWarps + j];
-  return -1;
+__device__ __forceinline__ TileGeom<V> tile_geom(const OpDev<V>& A, const SymDev<V>& T, int32_t t) {
+  TileGeom<V> g;
+  const int64_t s0 = T.tile_slice[t], s1 = T.tile_slice[t + 1];
+  g.row0 = s0 * 32;
+  g.rows = (s1 * 32 < A.n ? s1 * 32 : A.n) - g.row0;
+  g.nsl = (int)(s1 - s0);
+  g.L = T.tile_len[t];
+  g.S = T.tile_ns[t];
+  g.own = T.tile_own[t];
+  return g;
 }
 
-// Issues the bulk copies of tile t's x slots (own rows, then its windows)
-// into buffer bf; parts that are not 16-byte aligned (only at the end of the
-// matrix) are left to sym_xs_tail.
+// Issues (thread 0) the bulk copies of tile t into stage bf: values, index
+// blob, diagonal, and the x slots (own rows and windows) that are 16-byte
+// aligned; the rest is loaded by tile_tail.
 template <typename V>
-__device__ __forceinline__ void sym_xs_issue(const OpDev<V>& A, const SymDev<V>& T, SymWarpSmem<V>* ws,
-                                             uint64_t* xbar, uint64_t policy, int32_t t, int bf, const V* x) {
-  if ((threadIdx.x & 31) != 0) return;
-  const int64_t row0 = (int64_t)T.tile_slice[t] * 32;
-  const int64_t rows = ((int64_t)T.tile_slice[t + 1] * 32 < A.n ? (int64_t)T.tile_slice[t + 1] * 32 : A.n) - row0;
-  uint32_t bytes = 0;
-  const bool own_bulk = (rows & 3) == 0;
-  if (own_bulk) bytes += (uint32_t)(rows * sizeof(V));
+__device__ __forceinline__ void tile_issue(const OpDev<V>& A, const SymDev<V>& T, TileSmem<V>* sm, TilePipe& tp,
+                                           int32_t t, int bf, const V* x) {
+  const TileGeom<V> g = tile_geom(A, T, t);
+  TileStage<V>& st = sm->st[bf];
+  uint64_t* bar = &tp.bar[bf];
+  const int64_t e0 = T.tile_ent[t], e1 = T.tile_ent[t + 1];
+  const int64_t m0 = T.tile_meta[t], m1 = T.tile_meta[t + 1];
+  const uint32_t vb = (uint32_t)((e1 - e0) * sizeof(V)), mb = (uint32_t)((m1 - m0) * sizeof(uint16_t));
+  const uint32_t db = (uint32_t)(g.nsl * 32 * sizeof(V));
+  const bool own_bulk = (g.rows & 3) == 0;
+  uint32_t bytes = vb + mb + db + (own_bulk ? (uint32_t)(g.rows * sizeof(V)) : 0u);
   const int32_t w0 = T.tile_win[t], w1 = T.tile_win[t + 1];
   for (int32_t w = w0; w < w1; ++w)
     if (((T.win_start[w] | T.win_len[w]) & 3) == 0) bytes += (uint32_t)(T.win_len[w] * sizeof(V));
+  int tail = own_bulk ? 0 : 1;
+  for (int32_t w = w0; w < w1; ++w)
+    if (((T.win_start[w] | T.win_len[w]) & 3) != 0) tail = 1;
+  st.info.row0 = g.row0;
+  st.info.ext0 = T.tile_ext[t];
+  st.info.e8 = e1 - e0;
+  st.info.rows = (int32_t)g.rows;
+  st.info.nsl = g.nsl;
+  st.info.L = g.L;
+  st.info.S = g.S;
+  st.info.own = g.own;
+  st.info.tail = tail;
+  st.info.rmask = (1 << T.tile_rlog[t]) - 1;
   fence_proxy_async_global();
-  mbar_arrive_expect_tx(xbar, bytes);
-  if (own_bulk && rows > 0) bulk_g2s(ws->xs[bf], x + row0, (uint32_t)(rows * sizeof(V)), xbar, policy);
-  int32_t slot = T.tile_own[t];
+  mbar_arrive_expect_tx(bar, bytes);
+  if (vb) bulk_g2s(st.val, T.val + e0, vb, bar, tp.policy);
+  if (mb) bulk_g2s(st.meta, T.meta + m0, mb, bar, tp.policy);
+  bulk_g2s(st.diag, A.diag + g.row0, db, bar, tp.policy);
+  if (own_bulk && g.rows > 0) bulk_g2s(st.xs, x + g.row0, (uint32_t)(g.rows * sizeof(V)), bar, tp.policy);
+  int32_t slot = g.own;
   for (int32_t w = w0; w < w1; ++w) {
     const int32_t ws0 = T.win_start[w], wl = T.win_len[w];
-    if (((ws0 | wl) & 3) == 0 && wl > 0) bulk_g2s(ws->xs[bf] + slot, x + ws0, (uint32_t)(wl * sizeof(V)), xbar, policy);
+    if (((ws0 | wl) & 3) == 0 && wl > 0) bulk_g2s(st.xs + slot, x + ws0, (uint32_t)(wl * sizeof(V)), bar, tp.policy);
     slot += wl;
   }
+  ++tp.iss[bf];
 }
 
-// Plain loads of the parts sym_xs_issue left out; then clears the dummy slots.
+// Plain loads of the x slots tile_issue left out (only at the end of the matrix).
 template <typename V, bool NC>
-__device__ __forceinline__ void sym_xs_tail(const OpDev<V>& A, const SymDev<V>& T, V* xs, int32_t t, const V* x) {
-  const int lane = threadIdx.x & 31;
-  const int64_t row0 = (int64_t)T.tile_slice[t] * 32;
-  const int64_t rows = ((int64_t)T.tile_slice[t + 1] * 32 < A.n ? (int64_t)T.tile_slice[t + 1] * 32 : A.n) - row0;
-  if ((rows & 3) != 0)
-    for (int i = lane; i < rows; i += 32) xs[i] = ld_vec<NC>(x + row0 + i);
-  int32_t slot = T.tile_own[t];
+__device__ __forceinline__ void tile_tail(const OpDev<V>& A, const SymDev<V>& T, V* xs, int32_t t, const V* x) {
+  const TileGeom<V> g = tile_geom(A, T, t);
+  if ((g.rows & 3) != 0)
+    for (int64_t i = threadIdx.x; i < g.rows; i += blockDim.x) xs[i] = ld_vec<NC>(x + g.row0 + i);
+  int32_t slot = g.own;
   for (int32_t w = T.tile_win[t]; w < T.tile_win[t + 1]; ++w) {
     const int32_t ws0 = T.win_start[w], wl = T.win_len[w];
     if (((ws0 | wl) & 3) != 0)
-      for (int i = lane; i < wl; i += 32) xs[slot + i] = ld_vec<NC>(x + ws0 + i);
+      for (int i = threadIdx.x; i < wl; i += blockDim.x) xs[slot + i] = ld_vec<NC>(x + ws0 + i);
     slot += wl;
   }
-  xs[T.tile_ns[t] + lane] = V(0);
 }
 
-// Phase A of the symmetric product on the tiles of this active warp:
-// f(row, (D + U) x row part + accumulated U' x from this tile, x_i, D_i x_i,
-// (U x)_i) runs on the row's lane; ext accumulators go to T.part.
+// Symmetric product over the CTA's tiles (a producer warp streams tiles into
+// the stages; 16 consumer warps cooperate on each tile):
+//   pass 1, one warp per slice, one lane per row: the direct sum (U x)_i
+//           from the staged x;
+//   pass 2, one thread per slot s: sum over the entries e that target s of
+//           val[e] * x[row(e)], in the layout's fixed order -- the tile's own
+//           rows keep theirs, the window slots leave as partial sums;
+//   then f(row, own part of (A x)_row, x_i, D_i x_i, (U x)_i) on the row's lane.
+// Uniform control flow: every thread takes every __syncthreads.
 template <typename V, bool NC, class F>
-__device__ __forceinline__ void sym_tiles(const OpDev<V>& A, const SymDev<V>& T, const V* x,
-                                          SymWarpSmem<V>* ws, Pipe& pp, int* err, F&& f) {
-  const int lane = threadIdx.x & 31, a = threadIdx.x >> 5, c = blockIdx.x;
-  if (a >= T.active) return;
-  SymSeq<V> seq{&T, c, a};
-  // first slice of the sequence and its lookahead
-  int jc = a;
-  int64_t s = -1;
-  for (; jc < kWarps; jc += T.active)
-    if (seq.range_begin(jc) < seq.range_end(jc)) { s = seq.range_begin(jc); break; }
-  if (s < 0) return;
-  int ji = jc;
-  int64_t s_issue = s;
-  for (uint32_t d = 0; d + 1 < pp.nst && s_issue >= 0; ++d) {
-    sym_issue(A, T, ws, pp, s_issue);
-    s_issue = seq.next(s_issue, ji);
+__device__ __forceinline__ void sym_tiles(const OpDev<V>& A, const SymDev<V>& T, const V* x, TileSmem<V>* sm,
+                                          TilePipe& tp, int* err, F&& f) {
+  constexpr int NST = tile_stages<V>();
+  constexpr int NC_THREADS = kCgThreads;  // consumers: warps 0..15; warp 16 produces
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, c = blockIdx.x;
+  const int32_t t0 = T.cta_tile[c], t1 = T.cta_tile[c + 1];
+  if (t0 >= t1) return;
+  if (warp == kWarps) {
+    // producer: lane 0 fills stages as the consumers release them
+    if (lane == 0) {
+      for (int32_t t = t0; t < t1 && !tp.failed; ++t) {
+        const int b = (int)((t - t0) % NST);
+        if (tp.iss[b] > 0 && !mbar_wait(&tp.empty[b], (tp.iss[b] - 1u) & 1u, tp.limit_ns)) {
+          tp.failed = true;
+          if (atomicCAS(err, 0, (int)kTimeout) == 0) err[1] = 400000000 + (int)(t % 1000000) * 10 + b;
+          break;
+        }
+        tile_issue(A, T, sm, tp, t, b, x);
+      }
+      // the CTA must not move on while its copies are in flight: wait
+      // (bounded) for the last fill of every stage to land
+      for (int b = 0; b < NST; ++b)
+        if (tp.iss[b] > 0) mbar_wait(&tp.bar[b], (tp.iss[b] - 1u) & 1u, tp.limit_ns);
+    }
+    __syncwarp();
+    return;
   }
-  // x staging: first tile now, then each next tile while the current one runs
-  uint64_t* xbar = pp.bars + pp.nst;  // two barriers, one per x buffer
-  uint32_t* xiss = pp.xiss;
-  uint32_t* xwait = pp.xwait;
-  int jt = jc;
-  int32_t t_next = T.warp_tile[c * kWarps + jc];
-  if (!pp.failed) {
-    sym_xs_issue(A, T, ws, xbar, pp.policy, t_next, 0, x);
-    ++xiss[0];
-  }
-  int bf = 0;
-  for (int j = jc; j < kWarps; j += T.active) {
-    const int32_t t0 = T.warp_tile[c * kWarps + j], t1 = T.warp_tile[c * kWarps + j + 1];
-    for (int32_t t = t0; t < t1; ++t) {
-      const int64_t sl0 = T.tile_slice[t], sl1 = T.tile_slice[t + 1];
-      const int64_t row0 = sl0 * 32;
-      const int64_t rows = (sl1 * 32 < A.n ? sl1 * 32 : A.n) - row0;
-      const int S = T.tile_ns[t];
-      const int own0 = T.tile_own[t];
-      const int64_t e0 = T.tile_ext[t];
-      const int ne = S - own0;
-      // prefetch the next tile's x into the other buffer
-      t_next = next_tile(T, c, t_next, jt);
-      if (t_next >= 0 && !pp.failed) {
-        sym_xs_issue(A, T, ws, &xbar[bf ^ 1], pp.policy, t_next, bf ^ 1, x);
-        ++xiss[bf ^ 1];
+  for (int32_t t = t0; t < t1; ++t) {
+    const int bf = (int)((t - t0) % NST);
+    TileStage<V>& st = sm->st[bf];
+    bool ok = !tp.failed;
+    if (ok) {
+      ok = mbar_wait(&tp.bar[bf], tp.wait[bf] & 1u, tp.limit_ns);
+      if (!ok && atomicCAS(err, 0, (int)kTimeout) == 0) err[1] = 300000000 + (int)(t % 1000000) * 10 + bf;
+    }
+    if (ok && st.info.tail) tile_tail<V, NC>(A, T, st.xs, t, x);
+    ok = consumers_and(NC_THREADS, ok);
+    if (!ok) {
+      tp.failed = true;
+      continue;
+    }
+    ++tp.wait[bf];
+    const TileInfo g = st.info;
+    const uint16_t* slot = st.meta;
+    const uint16_t* tidx = st.meta + g.e8;
+    const uint16_t* tptr = st.meta + 2 * g.e8;
+    // pass 1 (row gather of D + U) and pass 2 (transpose gather of U') read
+    // only the stage, so they run back to back without a barrier
+    V xi = V(0), dg = V(0), direct = V(0);
+    const bool mine = warp < g.nsl;
+    const int own_row = warp * 32 + lane;
+    if (mine) {
+      if (own_row < g.rows) {
+        xi = st.xs[own_row];
+        dg = st.diag[own_row];
       }
-      // wait for this tile's x; clear the accumulator
-      if (!pp.failed && xwait[bf] < xiss[bf]) {
-        if (!mbar_wait(&xbar[bf], xwait[bf] & 1u, pp.limit_ns)) {
-          pp.failed = true;
-          if (lane == 0 && atomicCAS(err, 0, (int)kTimeout) == 0) {
-            err[1] = 200000000 + 10 * (t % 1000000) + (int)(xwait[bf] & 1u) * 2 + bf;
-            long long* det = reinterpret_cast<long long*>(err + 2);
-            det[0] = (long long)smem_u32(ws->xs[bf]);
-            det[1] = (long long)(uintptr_t)(x + row0);
-            det[2] = rows;
-            det[3] = (long long)smem_u32(&xbar[bf]) * 1000 + (long long)(T.tile_win[t + 1] - T.tile_win[t]);
-          }
-        } else {
-          ++xwait[bf];
-        }
+      const int R = g.rmask + 1;
+      for (int k = 0; k < g.L; ++k) {
+        const int e = k * R + own_row;
+        direct = fma_(st.val[e], st.xs[slot[e]], direct);
       }
-      V* xs = ws->xs[bf];
-      sym_xs_tail<V, NC>(A, T, xs, t, x);
-      for (int i = lane; i < S + 32; i += 32) ws->acc[i] = V(0);
-      __syncwarp();
-      for (int64_t sl = sl0; sl < sl1; ++sl) {
-        if (s_issue >= 0) {
-          sym_issue(A, T, ws, pp, s_issue);
-          s_issue = seq.next(s_issue, ji);
-        }
-        const int L = sym_len(T, sl);
-        const int own = (int)((sl - sl0) * 32) + lane;
-        const int64_t row = row0 + own;
-        const V xi = row < A.n ? xs[own] : V(0);
-        V direct = V(0), dg = V(0);
-        bool ok = !pp.failed;
-        uint32_t st = 0;
-        if (ok) {
-          st = pp.consumed % pp.nst;
-          const uint32_t par = (pp.consumed / pp.nst) & 1u;
-          if (!mbar_wait(&pp.bars[st], par, pp.limit_ns)) {
-            pp.failed = true;
-            ok = false;
-            if (lane == 0 && atomicCAS(err, 0, (int)kTimeout) == 0)
-              err[1] = 100000000 + 100 * (int)(sl % 1000000) + 10 * (int)st + (int)par;
-          } else {
-            ++pp.consumed;
-          }
-        }
-        if (ok) {
-          dg = ws->st[st].diag[lane];
-          if (L > kMaxLs) {  // long slice: values and slots from global memory
-            const int64_t base = T.sl_ptr[sl];
-            for (int k = 0; k < L; ++k) {
-              const int sv = T.slot[base + 32 * k + lane];
-              const V v = T.val[base + 32 * k + lane];
-              direct = fma_(v, xs[sv], direct);
-              ws->acc[sv] = fma_(v, xi, ws->acc[sv]);
-              __syncwarp();
-            }
-          } else {
-            const V* __restrict__ stv = ws->st[st].val;
-            const uint16_t* __restrict__ sts = ws->st[st].slot;
-#pragma unroll
-            for (int k = 0; k < kMaxLs; ++k) {
-              if (k < L) {
-                const int sv = sts[k * 32 + lane];
-                const V v = stv[k * 32 + lane];
-                direct = fma_(v, xs[sv], direct);
-                ws->acc[sv] = fma_(v, xi, ws->acc[sv]);
-              }
-              __syncwarp();
-            }
-          }
-        }
-        __syncwarp();
-        if (row < A.n) {
-          const V dxi = dg * xi;
-          f(row, dxi + direct + ws->acc[own], xi, dxi, direct);
-        }
+    }
+    V* __restrict__ part = T.part + g.ext0;
+    for (int sl = threadIdx.x; sl < g.S; sl += NC_THREADS) {
+      if (sl >= g.rows && sl < g.own) continue;  // padding of the own rows
+      V sum = V(0);
+      const int j1 = tptr[sl + 1];
+      for (int j = tptr[sl]; j < j1; ++j) {
+        const int e = tidx[j];
+        sum = fma_(st.val[e], st.xs[e & g.rmask], sum);
       }
-      __syncwarp();
-      for (int i = lane; i < ne; i += 32) T.part[e0 + i] = ws->acc[own0 + i];
-      __syncwarp();
-      bf ^= 1;
+      if (sl < g.rows) sm->acc[sl] = sum;
+      else part[sl - g.own] = sum;
+    }
+    consumers_sync(NC_THREADS);
+    // the stage is free: release it to the producer
+    if (threadIdx.x == 0) mbar_arrive(&tp.empty[bf]);
+    if (mine && own_row < g.rows) {
+      const V dxi = dg * xi;
+      f(g.row0 + own_row, dxi + direct + sm->acc[own_row], xi, dxi, direct);
     }
   }
-  // a failed warp may still have x fills in flight: wait (bounded) for the
-  // last one of each buffer, which completes after the earlier ones
-  if (pp.failed)
-    for (int b2 = 0; b2 < 2; ++b2)
-      if (xwait[b2] < xiss[b2]) mbar_wait(&xbar[b2], (xiss[b2] - 1u) & 1u, pp.limit_ns);
-  if (pp.failed) pipe_drain(pp);
 }
 
-// Adds the incoming ext partial sums to y over this active warp's tiles, in
-// the fixed run order of the layout.
+// Adds the incoming window partial sums to y over the CTA's tiles (warp w
+// takes tiles t0 + w, t0 + w + 16, ...), runs in the layout's fixed order.
 template <typename V>
 __device__ __forceinline__ void sym_incoming(const SymDev<V>& T, V* y) {
-  const int lane = threadIdx.x & 31, a = threadIdx.x >> 5, c = blockIdx.x;
-  if (a >= T.active) return;
-  for (int j = a; j < kWarps; j += T.active) {
-    const int32_t t0 = T.warp_tile[c * kWarps + j], t1 = T.warp_tile[c * kWarps + j + 1];
-    for (int32_t t = t0; t < t1; ++t) {
-      const int64_t row0 = (int64_t)T.tile_slice[t] * 32;
-      for (int32_t u = T.in_ptr[t]; u < T.in_ptr[t + 1]; ++u) {
-        const int64_t rr = row0 + T.in_row[u], src = T.in_src[u];
-        const int len = T.in_len[u];
-        batched<8>(lane, len, [&](int l) { return y[rr + l] + T.part[src + l]; },
-                   [&](int l, V v) { y[rr + l] = v; });
-        __syncwarp();
-      }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5, c = blockIdx.x;
+  for (int32_t t = T.cta_tile[c] + warp; t < T.cta_tile[c + 1]; t += nw) {
+    const int64_t row0 = (int64_t)T.tile_slice[t] * 32;
+    for (int32_t u = T.in_ptr[t]; u < T.in_ptr[t + 1]; ++u) {
+      const int64_t rr = row0 + T.in_row[u], src = T.in_src[u];
+      const int len = T.in_len[u];
+      batched<8>(lane, len, [&](int l) { return y[rr + l] + T.part[src + l]; }, [&](int l, V v) { y[rr + l] = v; });
+      __syncwarp();
     }
   }
+}
+
+__device__ __forceinline__ void tile_pipe_init(TilePipe& tp, uint64_t* bar6, long long limit_ns) {
+  tp.bar = bar6;
+  tp.empty = bar6 + 3;
+  for (int b = 0; b < 3; ++b) tp.iss[b] = tp.wait[b] = 0;
+  tp.policy = policy_evict_first();
+  tp.limit_ns = limit_ns;
+  tp.failed = false;
+  if (threadIdx.x == 0)
+    for (int b = 0; b < 6; ++b) mbar_init(&bar6[b], 1);
+  fence_mbar_init();
 }
 
 // Deterministic CTA sum (fixed trees); the result is valid on thread 0.
@@ -752,29 +739,32 @@ constexpr size_t product_smem() {
 template <typename V, int FMT, bool NC>
 __device__ __forceinline__ void product_rows(const OpDev<V>& A, const SymDev<V>& T, int64_t s0, int64_t s1,
                                              int64_t l0, int64_t l1, const V* x, V* y, unsigned char* smem,
-                                             Pipe& pp, int* err) {
+                                             Pipe& pp, TilePipe& tp, int* err) {
   if constexpr (FMT == kTiles) {
-    SymWarpSmem<V>* ws = reinterpret_cast<SymWarpSmem<V>*>(smem) + (threadIdx.x >> 5);
-    sym_tiles<V, NC>(A, T, x, ws, pp, err, [&](int64_t row, V qo, V, V, V) { y[row] = qo; });
+    TileSmem<V>* sm = reinterpret_cast<TileSmem<V>*>(smem);
+    sym_tiles<V, NC>(A, T, x, sm, tp, err, [&](int64_t row, V qo, V, V, V) { y[row] = qo; });
   } else {
-    Stage<V>* stages = reinterpret_cast<Stage<V>*>(smem) + (threadIdx.x >> 5) * kStages;
+    Stage<V>* stages = reinterpret_cast<Stage<V>*>(smem) + (threadIdx.x >> 5) * gather_stages<V>();
     spmv_rows<V, FMT == kPlan, NC>(A, s0, s1, l0, l1, x, stages, pp, err, [&](int64_t row, V v) { y[row] = v; });
   }
 }
 
 // y = A x on the persistent grid's partition (first pass for kTiles).
 template <typename V, int FMT>
-__global__ void __launch_bounds__(kCgThreads, 1)
+__global__ void __launch_bounds__(FMT == kTiles ? kTileThreads : kCgThreads, 1)
     k_rows(OpDev<V> A, SymDev<V> T, const int32_t* __restrict__ cta_slice, const int32_t* __restrict__ cta_long,
            const V* __restrict__ x, V* __restrict__ y, int* err, long long limit_ns) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  __shared__ uint64_t bars[kWarps][kMaxStages];
+  __shared__ uint64_t bars[kMaxThreads / 32][kMaxStages];
+  __shared__ uint64_t tbar[6];
   Pipe pp;
-  pipe_init(pp, bars[threadIdx.x >> 5], FMT == kTiles ? kSymStages : kStages, limit_ns);
+  pipe_init(pp, bars[threadIdx.x >> 5], gather_stages<V>(), limit_ns);
+  TilePipe tp;
+  tile_pipe_init(tp, tbar, limit_ns);
   __syncthreads();
   const int c = blockIdx.x;
   product_rows<V, FMT, true>(A, T, cta_slice[c], cta_slice[c + 1], cta_long[c], cta_long[c + 1], x, y, smem_raw,
-                             pp, err);
+                             pp, tp, err);
 }
 
 // Second pass: for kTiles adds the incoming partial sums; with MODE 1 then
@@ -833,23 +823,38 @@ __global__ void k_axpy_f32(double a, const float* __restrict__ d, int64_t n, dou
 }
 
 // ------------------------------------------------- persistent solver ---
-// Vector pass over rows [r0, r1) with 16-byte accesses; f(i, w) handles the
-// w consecutive elements from i (w = the vector width, or 1 on the tail).
-template <typename V, class F>
-__device__ __forceinline__ void rows_vec(int64_t r0, int64_t r1, F&& f) {
+// Vector pass over rows [r0, r1) with 16-byte accesses.  ld(i) loads the
+// group of W elements from i into a register tuple and st(i, tuple) finishes
+// it; each thread keeps two groups in flight (both loaded before either is
+// finished).  The tail runs element-wise through f1(i).
+template <typename V, class LD, class ST, class F1>
+__device__ __forceinline__ void rows_vec(int64_t r0, int64_t r1, LD&& ld, ST&& st, F1&& f1) {
   constexpr int W = Vec<V>::W;
   const int64_t g0 = r0 / W, g1 = r1 / W;  // r0 is a multiple of 32
-  for (int64_t g = g0 + threadIdx.x; g < g1; g += blockDim.x) f(g * W, W);
-  for (int64_t i = g1 * W + threadIdx.x; i < r1; i += blockDim.x) f(i, 1);
+  const int64_t bd = blockDim.x;
+  for (int64_t g = g0 + threadIdx.x; g < g1; g += 2 * bd) {
+    const bool two = g + bd < g1;
+    auto t0 = ld(g * W);
+    decltype(t0) t1;
+    if (two) t1 = ld((g + bd) * W);
+    st(g * W, t0);
+    if (two) st((g + bd) * W, t1);
+  }
+  for (int64_t i = g1 * W + threadIdx.x; i < r1; i += blockDim.x) f1(i);
 }
+
+template <typename VT>
+struct Quad {
+  VT a, b, c, d;
+};
 
 // OUTER = false: inner single-precision solve from x = 0 (rhs in b), no
 // true-residual confirmation.  OUTER = true: the full solve of Section III
 // from the caller's x0 with the confirm/restart step.
 template <typename V, int FMT, bool OUTER>
-__global__ void __launch_bounds__(kCgThreads, 1) k_cg(CgArgs<V> a) {
+__global__ void __launch_bounds__(FMT == kTiles ? kTileThreads : kCgThreads, 1) k_cg(CgArgs<V> a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  __shared__ uint64_t bars[kWarps][kMaxStages];
+  __shared__ uint64_t bars[kMaxThreads / 32][kMaxStages];
   __shared__ double red[33];
   __shared__ int sflag;
   using VT = typename Vec<V>::T;
@@ -868,8 +873,11 @@ __global__ void __launch_bounds__(kCgThreads, 1) k_cg(CgArgs<V> a) {
   const V* __restrict__ b = a.b;
   double* part0 = a.part;
   double* part1 = a.part + G;
+  __shared__ uint64_t tbar[6];
   Pipe pp;
-  pipe_init(pp, bars[threadIdx.x >> 5], FMT == kTiles ? kSymStages : kStages, a.timeout_ns);
+  pipe_init(pp, bars[threadIdx.x >> 5], gather_stages<V>(), a.timeout_ns);
+  TilePipe tp;
+  tile_pipe_init(tp, tbar, a.timeout_ns);
   __syncthreads();
   int* err = &a.bar->status;
   unsigned long long target = 0;
@@ -880,7 +888,7 @@ __global__ void __launch_bounds__(kCgThreads, 1) k_cg(CgArgs<V> a) {
 
   // q = A xin over the CTA's rows, complete (kTiles: across a grid barrier)
   auto full_product = [&](const V* xin) -> bool {
-    product_rows<V, FMT, false>(A, T, s0, s1, l0, l1, xin, q, smem_raw, pp, err);
+    product_rows<V, FMT, false>(A, T, s0, s1, l0, l1, xin, q, smem_raw, pp, tp, err);
     if constexpr (FMT == kTiles) {
       if (!grid_barrier(a.bar, target, a.timeout_ns, &sflag, nbar++)) return false;
       sym_incoming<V>(T, q);
@@ -903,23 +911,23 @@ __global__ void __launch_bounds__(kCgThreads, 1) k_cg(CgArgs<V> a) {
         pb = fma_(bi, bi, pb);
       }
     } else {
-      rows_vec<V>(r0, r1, [&](int64_t i, int w) {
-        if (w > 1) {
-          const VT bv = *reinterpret_cast<const VT*>(b + i);
-          *reinterpret_cast<VT*>(x + i) = VT{};
-          *reinterpret_cast<VT*>(r + i) = bv;
-          *reinterpret_cast<VT*>(p + i) = bv;
-          const V* e = reinterpret_cast<const V*>(&bv);
+      rows_vec<V>(
+          r0, r1, [&](int64_t i) { return *reinterpret_cast<const VT*>(b + i); },
+          [&](int64_t i, VT bv) {
+            *reinterpret_cast<VT*>(x + i) = VT{};
+            *reinterpret_cast<VT*>(r + i) = bv;
+            *reinterpret_cast<VT*>(p + i) = bv;
+            const V* e = reinterpret_cast<const V*>(&bv);
 #pragma unroll
-          for (int j = 0; j < W; ++j) pr = fma_(e[j], e[j], pr);
-        } else {
-          const V bi = b[i];
-          x[i] = V(0);
-          r[i] = bi;
-          p[i] = bi;
-          pr = fma_(bi, bi, pr);
-        }
-      });
+            for (int j = 0; j < W; ++j) pr = fma_(e[j], e[j], pr);
+          },
+          [&](int64_t i) {
+            const V bi = b[i];
+            x[i] = V(0);
+            r[i] = bi;
+            p[i] = bi;
+            pr = fma_(bi, bi, pr);
+          });
       pb = pr;
     }
     const double s_rr = block_sum((double)pr, red);
@@ -941,13 +949,13 @@ __global__ void __launch_bounds__(kCgThreads, 1) k_cg(CgArgs<V> a) {
       V ppq = V(0);
       if constexpr (FMT == kTiles) {
         // p'Ap = p'Dp + 2 p'Up from the rows' own parts: no incoming sums needed
-        SymWarpSmem<V>* ws = reinterpret_cast<SymWarpSmem<V>*>(smem_raw) + (threadIdx.x >> 5);
-        sym_tiles<V, false>(A, T, p, ws, pp, err, [&](int64_t row, V qo, V xi, V dxi, V direct) {
+        TileSmem<V>* sm = reinterpret_cast<TileSmem<V>*>(smem_raw);
+        sym_tiles<V, false>(A, T, p, sm, tp, err, [&](int64_t row, V qo, V xi, V dxi, V direct) {
           q[row] = qo;
           ppq = fma_(xi, fma_(V(2), direct, dxi), ppq);
         });
       } else {
-        Stage<V>* stages = reinterpret_cast<Stage<V>*>(smem_raw) + (threadIdx.x >> 5) * kStages;
+        Stage<V>* stages = reinterpret_cast<Stage<V>*>(smem_raw) + (threadIdx.x >> 5) * gather_stages<V>();
         spmv_rows<V, FMT == kPlan, false>(A, s0, s1, l0, l1, p, stages, pp, err, [&](int64_t row, V v) {
           q[row] = v;
           ppq = fma_(p[row], v, ppq);
@@ -970,29 +978,32 @@ __global__ void __launch_bounds__(kCgThreads, 1) k_cg(CgArgs<V> a) {
       {
         const V al = (V)alpha;
         V prr = V(0);
-        rows_vec<V>(r0, r1, [&](int64_t i, int w) {
-          if (w > 1) {
-            VT pv = *reinterpret_cast<const VT*>(p + i), qv = *reinterpret_cast<const VT*>(q + i);
-            VT xv = *reinterpret_cast<const VT*>(x + i), rv = *reinterpret_cast<const VT*>(r + i);
-            V* pe = reinterpret_cast<V*>(&pv);
-            V* qe = reinterpret_cast<V*>(&qv);
-            V* xe = reinterpret_cast<V*>(&xv);
-            V* re = reinterpret_cast<V*>(&rv);
+        rows_vec<V>(
+            r0, r1,
+            [&](int64_t i) {
+              return Quad<VT>{*reinterpret_cast<const VT*>(p + i), *reinterpret_cast<const VT*>(q + i),
+                              *reinterpret_cast<const VT*>(x + i), *reinterpret_cast<const VT*>(r + i)};
+            },
+            [&](int64_t i, Quad<VT> t) {
+              const V* pe = reinterpret_cast<const V*>(&t.a);
+              const V* qe = reinterpret_cast<const V*>(&t.b);
+              V* xe = reinterpret_cast<V*>(&t.c);
+              V* re = reinterpret_cast<V*>(&t.d);
 #pragma unroll
-            for (int j = 0; j < W; ++j) {
-              xe[j] = fma_(al, pe[j], xe[j]);
-              re[j] = fma_(-al, qe[j], re[j]);
-              prr = fma_(re[j], re[j], prr);
-            }
-            *reinterpret_cast<VT*>(x + i) = xv;
-            *reinterpret_cast<VT*>(r + i) = rv;
-          } else {
-            x[i] = fma_(al, p[i], x[i]);
-            const V ri = fma_(-al, q[i], r[i]);
-            r[i] = ri;
-            prr = fma_(ri, ri, prr);
-          }
-        });
+              for (int j = 0; j < W; ++j) {
+                xe[j] = fma_(al, pe[j], xe[j]);
+                re[j] = fma_(-al, qe[j], re[j]);
+                prr = fma_(re[j], re[j], prr);
+              }
+              *reinterpret_cast<VT*>(x + i) = t.c;
+              *reinterpret_cast<VT*>(r + i) = t.d;
+            },
+            [&](int64_t i) {
+              x[i] = fma_(al, p[i], x[i]);
+              const V ri = fma_(-al, q[i], r[i]);
+              r[i] = ri;
+              prr = fma_(ri, ri, prr);
+            });
         const double s = block_sum((double)prr, red);
         if (threadIdx.x == 0) part1[c] = s;
       }
@@ -1006,19 +1017,19 @@ __global__ void __launch_bounds__(kCgThreads, 1) k_cg(CgArgs<V> a) {
       // C: p = r + beta p
       {
         const V be = (V)beta;
-        rows_vec<V>(r0, r1, [&](int64_t i, int w) {
-          if (w > 1) {
-            VT pv = *reinterpret_cast<const VT*>(p + i);
-            const VT rv = *reinterpret_cast<const VT*>(r + i);
-            V* pe = reinterpret_cast<V*>(&pv);
-            const V* re = reinterpret_cast<const V*>(&rv);
+        rows_vec<V>(
+            r0, r1,
+            [&](int64_t i) {
+              return Quad<VT>{*reinterpret_cast<const VT*>(p + i), *reinterpret_cast<const VT*>(r + i), VT{}, VT{}};
+            },
+            [&](int64_t i, Quad<VT> t) {
+              V* pe = reinterpret_cast<V*>(&t.a);
+              const V* re = reinterpret_cast<const V*>(&t.b);
 #pragma unroll
-            for (int j = 0; j < W; ++j) pe[j] = fma_(be, pe[j], re[j]);
-            *reinterpret_cast<VT*>(p + i) = pv;
-          } else {
-            p[i] = fma_(be, p[i], r[i]);
-          }
-        });
+              for (int j = 0; j < W; ++j) pe[j] = fma_(be, pe[j], re[j]);
+              *reinterpret_cast<VT*>(p + i) = t.a;
+            },
+            [&](int64_t i) { p[i] = fma_(be, p[i], r[i]); });
       }
       if (!grid_barrier(a.bar, target, a.timeout_ns, &sflag, nbar++)) return;
     }

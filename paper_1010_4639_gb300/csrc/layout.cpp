@@ -279,15 +279,21 @@ void make_windows(const std::vector<int32_t>& tg, int64_t n, std::vector<Window>
 
 }  // namespace
 
-bool build_sym_tiles(LayoutHost& L, int warps, int slot_cap) {
+bool build_sym_tiles(LayoutHost& L, int ctas, int slot_cap, int ent_cap) {
   SymTilesHost& Tl = L.tiles;
   Tl = SymTilesHost();
   Tl.slot_cap = slot_cap;
+  Tl.ent_cap = ent_cap;
   const int64_t n = L.n, ns = (n + 31) / 32;
   const std::vector<int64_t>& rp = L.urp;
   const std::vector<int32_t>& rc = L.urc;
-  // 1. contiguous slice ranges per warp, balanced by entries + rows
-  std::vector<int64_t> wcut(warps + 1, ns);
+  auto slice_len = [&](int64_t s) {
+    int64_t m = 0;
+    for (int64_t r = 32 * s; r < std::min<int64_t>(n, 32 * s + 32); ++r) m = std::max(m, rp[r + 1] - rp[r]);
+    return m;
+  };
+  // 1. contiguous slice ranges per CTA, balanced by entries + rows
+  std::vector<int64_t> ccut(ctas + 1, ns);
   {
     int64_t total = 0;
     auto work = [&](int64_t s) {
@@ -296,15 +302,15 @@ bool build_sym_tiles(LayoutHost& L, int warps, int slot_cap) {
     };
     for (int64_t s = 0; s < ns; ++s) total += work(s);
     int64_t acc = 0, s = 0;
-    wcut[0] = 0;
-    for (int w = 1; w < warps; ++w) {
-      const long double target = (long double)total * w / warps;
+    ccut[0] = 0;
+    for (int c = 1; c < ctas; ++c) {
+      const long double target = (long double)total * c / ctas;
       while (s < ns && (long double)(acc + work(s)) <= target) acc += work(s++);
-      wcut[w] = s;
+      ccut[c] = s;
     }
-    wcut[warps] = ns;
+    ccut[ctas] = ns;
   }
-  // targets beyond a candidate tile and the resulting slot count
+  // targets beyond a candidate tile, its windows and slot count
   std::vector<int32_t> tg;
   std::vector<Window> wins;
   auto targets = [&](int64_t sa, int64_t sb) {
@@ -320,52 +326,65 @@ bool build_sym_tiles(LayoutHost& L, int warps, int slot_cap) {
     for (const Window& w : wins) slots += w.len;
     return slots;
   };
-  // 2. tiles inside each warp range: the longest prefix under the slot cap
-  //    (the slot count grows with the tile, so a binary search finds it)
-  Tl.warp_tile.assign(warps + 1, 0);
+  auto pow2 = [](int64_t v) {
+    int64_t p = 1;
+    while (p < v) p <<= 1;
+    return p;
+  };
+  auto fits = [&](int64_t sa, int64_t sb) {
+    if (sb - sa > 16) return false;
+    int64_t lmax = 0;
+    for (int64_t s = sa; s < sb; ++s) lmax = std::max(lmax, slice_len(s));
+    if (32 * pow2(sb - sa) * lmax > ent_cap) return false;
+    return targets(sa, sb) <= slot_cap;
+  };
+  // 2. tiles inside each CTA range: the longest prefix that fits
+  Tl.cta_tile.assign(ctas + 1, 0);
   int32_t tile_id = 0;
-  for (int w = 0; w < warps; ++w) {
-    Tl.warp_tile[w] = tile_id;
-    int64_t s = wcut[w];
-    while (s < wcut[w + 1]) {
-      if (targets(s, s + 1) > slot_cap) {
+  for (int c = 0; c < ctas; ++c) {
+    Tl.cta_tile[c] = tile_id;
+    int64_t s = ccut[c];
+    while (s < ccut[c + 1]) {
+      if (!fits(s, s + 1)) {
         Tl = SymTilesHost();
         return false;
       }
-      int64_t lo = s + 1, hi = wcut[w + 1];  // lo fits; find the largest e in [lo, hi] that fits
-      while (lo < hi) {
-        const int64_t mid = (lo + hi + 1) / 2;
-        if (targets(s, mid) <= slot_cap) lo = mid;
-        else hi = mid - 1;
-      }
+      int64_t e = s + 1;
+      while (e < ccut[c + 1] && fits(s, e + 1)) ++e;
       Tl.tile_slice.push_back((int32_t)s);
       ++tile_id;
-      s = lo;
+      s = e;
     }
   }
-  Tl.warp_tile[warps] = tile_id;
+  Tl.cta_tile[ctas] = tile_id;
   Tl.tile_slice.push_back((int32_t)ns);
   const int32_t T = tile_id;
-  // 3. per tile: windows, slot map, conflict-free slot-major entries
+  // 3. per tile: windows, slot map, entries, transpose index
   Tl.tile_ns.assign(T, 0);
   Tl.tile_own.assign(T, 0);
+  Tl.tile_len.assign(T, 0);
+  Tl.tile_rlog.assign(T, 0);
+  Tl.tile_ent.assign(T + 1, 0);
+  Tl.tile_meta.assign(T + 1, 0);
   Tl.tile_ext.assign(T + 1, 0);
   Tl.tile_win.assign(T + 1, 0);
-  Tl.sl_ptr.assign(ns + 1, 0);
   std::vector<int32_t> slot_of(n > 0 ? n : 1, -1);
-  Tl.slot.clear();
-  Tl.val.clear();
-  std::vector<std::vector<uint16_t>> used;  // used[k] = slots taken in column k
-  std::vector<uint32_t> busy;               // busy[k]: lanes holding an entry in column k
-  std::vector<int32_t> ek, el;
-  std::vector<uint16_t> es;
-  std::vector<double> ev;
+  auto up8 = [](int64_t v) { return (v + 7) & ~int64_t(7); };
+  std::vector<std::vector<uint16_t>> lists;
   for (int32_t t = 0; t < T; ++t) {
-    const int64_t a = 32 * (int64_t)Tl.tile_slice[t], b = std::min<int64_t>(n, 32 * (int64_t)Tl.tile_slice[t + 1]);
-    const int64_t S = targets(Tl.tile_slice[t], Tl.tile_slice[t + 1]);
+    const int64_t s0 = Tl.tile_slice[t], s1 = Tl.tile_slice[t + 1];
+    const int64_t a = 32 * s0, b = std::min<int64_t>(n, 32 * s1);
+    const int64_t S = targets(s0, s1);
     const int32_t own = (int32_t)(((b - a) + 3) & ~int64_t(3));
+    int64_t lmax = 0;
+    for (int64_t s = s0; s < s1; ++s) lmax = std::max(lmax, slice_len(s));
     Tl.tile_ns[t] = (int32_t)S;
     Tl.tile_own[t] = own;
+    Tl.tile_len[t] = (int32_t)lmax;
+    const int64_t R = 32 * pow2(s1 - s0);
+    int32_t rlog = 0;
+    while ((int64_t(1) << rlog) < R) ++rlog;
+    Tl.tile_rlog[t] = rlog;
     Tl.tile_ext[t + 1] = Tl.tile_ext[t] + (S - own);
     Tl.tile_win[t + 1] = Tl.tile_win[t] + (int32_t)wins.size();
     int32_t slot0 = own;
@@ -375,51 +394,37 @@ bool build_sym_tiles(LayoutHost& L, int warps, int slot_cap) {
       for (int64_t r = w.start; r < w.start + w.len; ++r) slot_of[r] = slot0 + (int32_t)(r - w.start);
       slot0 += (int32_t)w.len;
     }
-    for (int64_t s = Tl.tile_slice[t]; s < Tl.tile_slice[t + 1]; ++s) {
-      for (auto& u : used) u.clear();
-      std::fill(busy.begin(), busy.end(), 0u);
-      size_t depth = 0;
-      ek.clear();
-      el.clear();
-      es.clear();
-      ev.clear();
-      for (int l = 0; l < 32; ++l) {
-        const int64_t r = 32 * s + l;
-        if (r >= n) break;
-        for (int64_t q = rp[r]; q < rp[r + 1]; ++q) {
-          const int64_t c = rc[q];
-          const uint16_t sl = (uint16_t)(c < b ? c - a : slot_of[c]);
-          size_t k = 0;
-          for (;; ++k) {
-            if (k == used.size()) {
-              used.emplace_back();
-              busy.push_back(0u);
-            }
-            if ((busy[k] >> l) & 1u) continue;
-            if (std::find(used[k].begin(), used[k].end(), sl) != used[k].end()) continue;
-            break;
-          }
-          busy[k] |= 1u << l;
-          used[k].push_back(sl);
-          depth = std::max(depth, k + 1);
-          ek.push_back((int32_t)k);
-          el.push_back(l);
-          es.push_back(sl);
-          ev.push_back(L.urv[q]);
-        }
-      }
-      const int64_t base = (int64_t)Tl.slot.size();
-      Tl.sl_ptr[s + 1] = base + 32 * (int64_t)depth;
-      for (size_t k = 0; k < depth; ++k)
-        for (int l = 0; l < 32; ++l) {
-          Tl.slot.push_back((uint16_t)(S + l));  // dummy slot: its own lane, never read back
-          Tl.val.push_back(0.0);
-        }
-      for (size_t i = 0; i < ek.size(); ++i) {
-        Tl.slot[base + 32 * (int64_t)ek[i] + el[i]] = es[i];
-        Tl.val[base + 32 * (int64_t)ek[i] + el[i]] = ev[i];
+    const int64_t E = R * lmax, E8 = up8(E);
+    const int64_t e0 = Tl.tile_ent[t];
+    Tl.tile_ent[t + 1] = e0 + E8;
+    Tl.val.resize(e0 + E8, 0.0);
+    std::vector<uint16_t> slot(E8, 0);
+    lists.assign(S, {});
+    // entry e = k * R + l for the k-th stored entry of local row l = r - a; rows
+    // are visited in increasing order, so each slot's list is in increasing source row
+    for (int64_t r = a; r < b; ++r) {
+      int64_t k = 0;
+      for (int64_t q = rp[r]; q < rp[r + 1]; ++q, ++k) {
+        const int64_t c = rc[q];
+        const int32_t sl = (int32_t)(c < b ? c - a : slot_of[c]);
+        const int64_t e = k * R + (r - a);
+        slot[e] = (uint16_t)sl;
+        Tl.val[e0 + e] = L.urv[q];
+        lists[sl].push_back((uint16_t)e);
       }
     }
+    // blob: slots[E8], transpose index[E8], index offsets[S + 1 rounded up to 8]
+    const int64_t m0 = Tl.tile_meta[t];
+    const int64_t P8 = up8(S + 1);
+    Tl.tile_meta[t + 1] = m0 + 2 * E8 + P8;
+    Tl.meta.resize(m0 + 2 * E8 + P8, 0);
+    std::copy(slot.begin(), slot.end(), Tl.meta.begin() + m0);
+    int64_t pos = 0;
+    for (int64_t sl = 0; sl < S; ++sl) {
+      Tl.meta[m0 + 2 * E8 + sl] = (uint16_t)pos;
+      for (uint16_t e : lists[sl]) Tl.meta[m0 + E8 + pos++] = e;
+    }
+    Tl.meta[m0 + 2 * E8 + S] = (uint16_t)pos;
   }
   // 4. incoming runs: each window's rows, split by the tile that owns them
   std::vector<int32_t> tile_of_slice(ns, 0);
@@ -448,7 +453,6 @@ bool build_sym_tiles(LayoutHost& L, int warps, int slot_cap) {
       }
     }
   }
-  // stable sort by target tile keeps the source-tile order within a target
   std::stable_sort(runs.begin(), runs.end(), [](const Run& x, const Run& y) { return x.tgt < y.tgt; });
   Tl.in_ptr.assign(T + 1, 0);
   for (const Run& r : runs) Tl.in_ptr[r.tgt + 1]++;

@@ -44,32 +44,36 @@ struct PlanHost {
   std::vector<uint16_t> pl_k;      // slot of U_ij in row i; 0xFFFF = padding
 };
 
-// Warp-tiled symmetric layout.  Rows are split into contiguous ranges, one
-// per warp of the persistent grid, and each range into tiles of whole slices.
-// A tile's column space -- its own rows, then windows of rows beyond it that
-// its upper entries reach ("ext" rows) -- is numbered by 16-bit slots that
-// index shared-memory copies of x and of the transpose accumulator.  Own rows
-// and every window start on a multiple of 4 rows and span a multiple of 4
-// rows (16-byte aligned), so a tile's x arrives by a few bulk copies; padding
-// rows inside a window are simply never targeted.  Each strict upper entry is
-// stored once as (value, slot), slot-major per slice, ordered so that the 32
-// lanes of one slot never target the same slot (conflict-free shared-memory
-// accumulation without atomics).  Window accumulators leave the tile as
-// partial sums; "incoming runs" list, per target tile and in a fixed order,
-// which partial sums to add to which of its rows.
+// Tiled symmetric layout.  Rows are split into contiguous ranges, one per CTA
+// of the persistent grid, and each range into tiles of at most 16 whole
+// slices (one per warp).  A tile's column space -- its own rows (padded to a
+// multiple of 4), then 16-byte-aligned windows of the rows beyond it that its
+// upper entries reach -- is numbered by 16-bit slots indexing a shared-memory
+// copy of x.  Each strict upper entry is stored once (value and slot); entry
+// k of the tile's local row l sits at position k * R + l, R a power of two, so
+// the row of any position is position & (R - 1) (rows padded to the tile's
+// longest row L).  A transpose index lists, for every slot, the positions of
+// the entries that target it, in increasing source row: the transpose half
+// U'x of a tile is then a gather sum_e val[e] * x[row(e)] over shared memory,
+// in a fixed order, without atomics.  Window sums leave the
+// tile as partial sums; "incoming runs" list, per target tile and in a fixed
+// order, which partial sums to add to which of its rows.
 struct SymTilesHost {
-  int32_t slot_cap = 0;            // max slots of a tile, dummy slots excluded
-  std::vector<int32_t> warp_tile;  // W + 1: tile range of each warp
+  int32_t slot_cap = 0, ent_cap = 0;
+  std::vector<int32_t> cta_tile;   // G + 1: tile range of each CTA
   std::vector<int32_t> tile_slice; // T + 1: first slice of each tile
   std::vector<int32_t> tile_ns;    // T: slot count (padded own rows + windows)
   std::vector<int32_t> tile_own;   // T: own rows padded to a multiple of 4
+  std::vector<int32_t> tile_len;   // T: padded row length L (entry k of local row l at k * R + l)
+  std::vector<int32_t> tile_rlog;  // T: log2 of R = 32 * (slices rounded up to a power of 2)
+  std::vector<int64_t> tile_ent;   // T + 1: first entry of each tile (multiples of 8)
+  std::vector<int64_t> tile_meta;  // T + 1: first u16 of each tile's index blob (multiples of 8)
   std::vector<int64_t> tile_ext;   // T + 1: first partial sum of each tile
   std::vector<int32_t> tile_win;   // T + 1: window range of each tile
   std::vector<int32_t> win_start;  // global first row of each window
   std::vector<int32_t> win_len;    // rows of each window
-  std::vector<int64_t> sl_ptr;     // nslices + 1: entry offsets (multiples of 32)
-  std::vector<uint16_t> slot;      // entry slots
   std::vector<double> val;         // entry values (0 on padding)
+  std::vector<uint16_t> meta;      // per tile: slots[E8], transpose index[E8], index offsets[S+1 rounded to 8]
   std::vector<int32_t> in_ptr;     // T + 1: incoming runs of each tile
   std::vector<int32_t> in_row;     // run start, as a row offset inside the target tile
   std::vector<int32_t> in_len;     // run length
@@ -96,10 +100,10 @@ struct LayoutHost {
 int build_layout(int32_t format, int64_t n, int64_t nnz, const int32_t* ptr, const int32_t* idx,
                  const double* val, int32_t index_base, LayoutHost& out, std::string& err);
 
-// Builds the warp-tiled symmetric layout for `warps` warps with at most
-// `slot_cap` slots per tile.  Returns false (layout left empty) when a single
-// slice already needs more slots than the cap.
-bool build_sym_tiles(LayoutHost& L, int warps, int slot_cap);
+// Builds the tiled symmetric layout for `ctas` CTAs, with at most
+// `slot_cap` slots and `ent_cap` padded entries per tile.  Returns false
+// (layout left empty) when a single slice already exceeds a cap.
+bool build_sym_tiles(LayoutHost& L, int ctas, int slot_cap, int ent_cap);
 
 // Contiguous slice ranges for `parts` workers, balanced by stored slots
 // (plus plan slots for the symmetric layout).  Returns parts + 1 offsets.
