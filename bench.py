@@ -71,6 +71,17 @@ def dist_setup(args):
     return world, rank, local, pg
 
 
+def max_over_ranks(values, pg, device):
+    """Element-wise max of a list of floats over all ranks (replica timing:
+    the job is as slow as its slowest GPU).  Identity without a process group."""
+    if not pg:
+        return [float(v) for v in values]
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
 def golden(grid_key, fmt="sym"):
     p = os.path.join(ROOT, "tests", "golden", f"oracle_{grid_key}_{fmt}.json")
     if os.path.exists(p):
@@ -260,10 +271,7 @@ def run_ours(args):
     kernel_ms = sum(i.kernel_ms for i in infos) / len(infos)
     kernel_launches = sum(i.kernel_launches for i in infos) / len(infos)
     iters = infos[-1].iterations
-    if pg:
-        t = torch.tensor([ms, kernel_ms], dtype=torch.float64, device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms, kernel_ms = float(t[0]), float(t[1])
+    ms, kernel_ms = max_over_ranks([ms, kernel_ms], pg, dev)
     x_dev = x.clone()
     # end to end through the public API: pinned host b and x, copies inside the call
     bh = torch.from_numpy(s.b).pin_memory()
@@ -275,11 +283,7 @@ def run_ours(args):
         t0 = time.perf_counter()
         _, info_h = A.solve(bh, xh, **solve_kw)
         e2e.append(time.perf_counter() - t0)
-    e2e_s = statistics.median(e2e)
-    if pg:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        e2e_s = float(t[0])
+    e2e_s = max_over_ranks([statistics.median(e2e)], pg, dev)[0]
     hbm, peak_kind = peaks()
     per_it = per_iteration_bytes(st, args.precision)
     achieved = per_it * iters / (kernel_ms / 1000.0) / 1e9 if kernel_ms > 0 else None
