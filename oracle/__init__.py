@@ -14,6 +14,7 @@ Parity status per function (what pins it; see ``tests/test_oracle_pins.py``):
                                          closed-form diagonal/tridiagonal cases
   cg_f32 / cg_ir                      -- true residual in double, error vs x*
   dot_long                            -- exact rational arithmetic
+  dot_f32                             -- exact sum within the pairwise bound
 """
 from __future__ import annotations
 
@@ -75,6 +76,8 @@ def load(path: str | None = None):
     lib.orc_dot.restype = d
     lib.orc_dot_long.argtypes = [i64, vp, vp]
     lib.orc_dot_long.restype = d
+    lib.orc_dot_f32.argtypes = [i64, vp, vp]
+    lib.orc_dot_f32.restype = ctypes.c_float
     lib.orc_cg.argtypes = [ctypes.c_int, i64, vp, vp, vp, vp, vp, d, i32,
                            ctypes.POINTER(Info), ctypes.POINTER(History)]
     lib.orc_cg_f32.argtypes = [ctypes.c_int, i64, vp, vp, vp, vp, vp, ctypes.c_float, i32,
@@ -146,6 +149,14 @@ def dot_long(a, b, lib=None) -> float:
     return float(lib.orc_dot_long(a.shape[0], _p(a), _p(b)))
 
 
+def dot_f32(a, b, lib=None) -> float:
+    """Single-precision dot product of the single-precision CG (tree order)."""
+    lib = lib or load()
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    b = np.ascontiguousarray(b, dtype=np.float32)
+    return float(lib.orc_dot_f32(a.shape[0], _p(a), _p(b)))
+
+
 @dataclass
 class Result:
     x: np.ndarray
@@ -214,3 +225,34 @@ def cg_ir(fmt, ptr, idx, val, b, x0=None, tol=1e-10, maxit=None, inner_tol=1e-4,
                   float(inner_tol), int(max_outer), ctypes.byref(info))
     return Result(x, info.iterations, info.restarts, STATUS[info.status], info.rel_res_recursive,
                   info.rel_res_true)
+
+
+def batch_solve(row_off, ptr, idx, val, B, X0=None, tol=1e-10, maxit=None, precision="fp32_ir", inner_tol=1e-4,
+                max_outer=30, lib=None):
+    """Independent systems of a block-diagonal CSR (instance i: rows
+    row_off[i]..row_off[i+1], global columns), each right-hand side solved on
+    its own by ``cg_ir`` (precision "fp32_ir") or ``cg`` ("fp64").  Returns
+    (X, results) with results[i][k] the Result of instance i, column k."""
+    lib = lib or load()
+    row_off = np.asarray(row_off, dtype=np.int64)
+    B = np.asarray(B, dtype=np.float64)
+    X = np.zeros_like(B) if X0 is None else np.array(X0, dtype=np.float64, copy=True)
+    results = []
+    for i in range(row_off.shape[0] - 1):
+        r0, r1 = int(row_off[i]), int(row_off[i + 1])
+        k0, k1 = int(ptr[r0]), int(ptr[r1])
+        p_i = np.asarray(ptr[r0:r1 + 1], dtype=np.int64) - k0
+        i_i = np.asarray(idx[k0:k1], dtype=np.int64) - r0
+        v_i = val[k0:k1]
+        row = []
+        for k in range(B.shape[1]):
+            m = maxit if maxit is not None else max(r1 - r0, 1)
+            if precision == "fp64":
+                res = cg("csr", p_i, i_i, v_i, B[r0:r1, k], X[r0:r1, k], tol=tol, maxit=m, lib=lib)
+            else:
+                res = cg_ir("csr", p_i, i_i, v_i, B[r0:r1, k], X[r0:r1, k], tol=tol, maxit=m, inner_tol=inner_tol,
+                            max_outer=max_outer, lib=lib)
+            X[r0:r1, k] = res.x
+            row.append(res)
+        results.append(row)
+    return X, results

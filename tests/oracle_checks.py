@@ -144,6 +144,25 @@ def check_dot(lib):
     assert abs(oracle.dot(a, b, lib=lib) - float(exact)) <= 300 * 1.2e-16 * float(np.abs(a) @ np.abs(b))
 
 
+def check_dot_f32(lib):
+    # the exact sum (rational arithmetic on the float inputs) within the
+    # pairwise-summation bound (log2(n) + 8) u sum |a_i b_i|, u = 2^-24
+    rng = np.random.default_rng(6)
+    for n in (1, 7, 9, 300, 3001):
+        a = rng.uniform(-1, 1, n).astype(np.float32)
+        b = rng.uniform(-1, 1, n).astype(np.float32)
+        exact = sum(Fraction(float(u)) * Fraction(float(v)) for u, v in zip(a, b))
+        bound = (np.log2(n) + 8) * 2.0 ** -24 * float(np.abs(a.astype(np.float64)) @ np.abs(b.astype(np.float64)))
+        assert abs(oracle.dot_f32(a, b, lib=lib) - float(exact)) <= bound, n
+    # 2^20 copies of 0.1f: a left-to-right float sum drifts by about 1e-2
+    # relative, the tree order stays within its log2(n) bound
+    n = 1 << 20
+    a = np.full(n, 0.1, dtype=np.float32)
+    ones = np.ones(n, dtype=np.float32)
+    exact = n * float(np.float32(0.1))
+    assert abs(oracle.dot_f32(a, ones, lib=lib) - exact) <= (20 + 8) * 2.0 ** -24 * exact
+
+
 # ---------------------------------------------------------------- CG -------
 def check_cg_vs_cholesky(lib):
     for seed, n in enumerate([1, 3, 10, 25, 40]):
@@ -331,7 +350,7 @@ def check_cg_ir(lib):
 
 ALL_CHECKS = [
     check_spmv_csr_bruteforce, check_spmv_csc_bruteforce, check_spmv_sym_bruteforce, check_abs_spmv,
-    check_spmv_f32, check_dot, check_cg_vs_cholesky, check_cg_fem_vs_cholesky,
+    check_spmv_f32, check_dot, check_dot_f32, check_cg_vs_cholesky, check_cg_fem_vs_cholesky,
     check_cg_finite_termination, check_cg_exact_first_steps, check_cg_a_orthogonality,
     check_cg_error_a_norm_decreases, check_cg_tridiagonal_closed_form, check_cg_edge_cases,
     check_cg_f32, check_cg_ir,

@@ -32,6 +32,8 @@ MUTANTS = {
     "ir_missing_scale": ("x[i] += nr * (double)d[i];", "x[i] += (double)d[i];"),
     "ir_residual_sign": ("r[i] = b[i] - r[i];", "r[i] = r[i] - b[i];"),
     "abs_spmv_signed": ("double a = fabs(val[k]);", "double a = val[k];"),
+    "f32_dot_left_to_right": ("  if (n <= 8) {\n    float s", "  if (1) {\n    float s"),
+    "f32_dot_wrong_half": ("dot_f(n - h, a + h, b + h)", "dot_f(n - h, a + h, b)"),
 }
 
 
