@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--profile-iters", type=int, default=0,
                     help="only run solves capped at this many iterations (small case for ncu captures)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU-oracle sample")
+    ap.add_argument("--only-batched", action="store_true", help="only run the batched leg (for ncu captures)")
     ap.add_argument("--profile-spmv", action="store_true",
                     help="only run a few products (double then single precision) of --format, for ncu captures")
     return ap.parse_args()
@@ -219,6 +220,9 @@ def run_ours(args):
 
     gb.build()
     dev = torch.device("cuda", local)
+    if args.only_batched:
+        print(json.dumps({"batched": batched(torch, gb, args)}), flush=True)
+        return 0
     g = GRIDS[args.grid]
     s = femgen.build_system(g)
     fmt_arrays = {"sym": s.upper(), "csr": (s.ptr, s.idx, s.val), "csc": s.csc()}
@@ -317,6 +321,8 @@ def run_ours(args):
         line["solve"]["err_vs_fp64_oracle_sampled"] = float(np.linalg.norm(x_np[idx] - xo) / np.linalg.norm(xo))
     if not args.no_extras and rank == 0:
         line["variants"] = extras(torch, gb, s, fmt_arrays, A, args, hbm)
+        line["paper_size"] = paper_size(torch, gb, args)
+        line["batched"] = batched(torch, gb, args)
         line["cpu_baseline"] = cpu_baseline(s, args, line["variants"])
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -379,6 +385,102 @@ def extras(torch, gb, s, fmt_arrays, A_head, args, hbm):
         out[fmt] = r
         if M is not A_head:
             M.close()
+    return out
+
+
+def paper_size(torch, gb, args):
+    """The paper's problem size (31x31x32 nodes, 25 230 rows, L2-resident):
+    time to 1e-10 and microseconds per iteration, per storage and precision."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    s = femgen.build_system(femgen.PAPER_SIZE)
+    arrays = {"sym": s.upper(), "csr": (s.ptr, s.idx, s.val), "csc": s.csc()}
+    b = torch.from_numpy(s.b).to(dev)
+    out = {"workload": "fem 31x31x32, 1 inclusion, contrast 1000", "n": s.n, "nnz": s.nnz}
+    for fmt in ("sym", "csr"):
+        with gb.Matrix(fmt, *arrays[fmt]) as M:
+            out[fmt] = {"grid_ctas": M.stats()["grid_ctas"]}
+            for prec in ("fp64", "fp32_ir"):
+                x = torch.zeros_like(b)
+                ts = []
+                for k in range(4):
+                    x.zero_()
+                    torch.cuda.synchronize()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    _, info = M.solve(b, x, tol=TOL, precision=prec, inner_tol=args.inner_tol)
+                    e1.record()
+                    torch.cuda.synchronize()
+                    if k:
+                        ts.append(e0.elapsed_time(e1) / 1000.0)
+                t = statistics.median(ts)
+                out[fmt][prec] = {"s": t, "iterations": info.iterations, "outer": info.outer,
+                                  "status": info.status, "rel_res_true": info.rel_res_true,
+                                  "iter_us": 1000.0 * info.kernel_ms / max(info.iterations, 1)}
+    return out
+
+
+def batched(torch, gb, args):
+    """256 uneven FEM systems (grid edges 12..40, contrast 10..1e4), eight
+    right-hand sides each, one persistent cluster launch per solve under a
+    CUDA graph: mixed precision and double precision, against plain FP64 CG
+    solving one system and right-hand side at a time on the same GPU."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    t0 = time.perf_counter()
+    bs = femgen.build_batch(femgen.batched_instances(256), nrhs=8)
+    gen_s = time.perf_counter() - t0
+    out = {"workload": "256 fem instances, edges U{12..40}, contrast log-U[10, 1e4], 8 rhs, tol 1e-10",
+           "n": bs.n, "nnz": bs.nnz, "generate_s": gen_s}
+    b = torch.from_numpy(bs.B).to(dev)
+    sizes = np.diff(bs.row_off)
+    nnz_i = np.diff(bs.ptr[bs.row_off])
+    with gb.Batch(bs.row_off, bs.ptr, bs.idx, bs.val, nrhs=8, tune=False) as Bt:
+        t0 = time.perf_counter()
+        tune = Bt.autotune("fp32_ir")
+        tune["seconds"] = time.perf_counter() - t0
+        out["tuning_fp32"] = tune
+        for prec, reps in (("fp32_ir", 3), ("fp64", 1)):
+            x = torch.zeros_like(b)
+            Bt.solve(b, x, tol=TOL, maxit=100000, precision=prec)  # warm (captures the graph)
+            ts, reps_out = [], []
+            for _ in range(reps):
+                x.zero_()
+                torch.cuda.synchronize()
+                x, infos, rep = Bt.solve(b, x, tol=TOL, maxit=100000, precision=prec)
+                ts.append(rep["kernel_ms"] / 1000.0)
+                reps_out.append(rep)
+            rep = reps_out[-1]
+            _, prods, outers = Bt.instance_times()
+            per_it = 8 * nnz_i + 4 * (sizes + 1) + 11 * 4 * 8 * sizes if prec == "fp32_ir" else \
+                12 * nnz_i + 4 * (sizes + 1) + 11 * 8 * 8 * sizes
+            moved = float(np.sum(prods.astype(np.float64) * per_it))
+            t = statistics.median(ts)
+            out[prec] = {"s": t, "status": rep["status"], "products": int(rep["products"]),
+                         "iterations_total": int(rep["iterations"]), "max_iterations": int(rep["max_iterations"]),
+                         "max_rel_res_true": float(infos["rel_res_true"].max()),
+                         "systems_ok": int(np.sum(infos["status"] == 0)), "systems": int(infos.size),
+                         "threads": rep["threads"], "cluster": rep["cluster"], "clusters": rep["clusters"],
+                         "busy_fraction": rep["busy_fraction"], "span_ms": rep["span_ms"],
+                         "graph": rep["graph"], "launches_per_solve": rep["launches"],
+                         "algorithmic_GBs": moved / t / 1e9}
+        out["mixed_speedup_vs_batched_fp64"] = out["fp64"]["s"] / out["fp32_ir"]["s"]
+    # plain double-precision CG, one system and right-hand side at a time (all
+    # 256 systems, first right-hand side; eight right-hand sides = 8x)
+    seq = 0.0
+    for i in range(bs.count):
+        p, j, v = bs.instance(i)
+        with gb.Matrix("csr", p, j, v) as M:
+            bi = torch.from_numpy(np.ascontiguousarray(bs.B[bs.row_off[i]:bs.row_off[i + 1], 0])).to(dev)
+            xi = torch.zeros_like(bi)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            M.solve(bi, xi, tol=TOL, maxit=100000, precision="fp64")
+            e1.record()
+            torch.cuda.synchronize()
+            seq += e0.elapsed_time(e1) / 1000.0
+    out["sequential_fp64_one_rhs_s"] = seq
+    out["sequential_fp64_8rhs_s"] = 8 * seq
+    out["batched_speedup_vs_sequential_fp64"] = 8 * seq / out["fp32_ir"]["s"]
     return out
 
 

@@ -61,14 +61,26 @@ LARGEST = Grid(256, 256, 256, n_incl=4)                      # ~16.4M rows, ~244
 
 def batched_instances(count: int = 256, seed: int = 0):
     """Uneven batch: grid edges uniform in [12, 40] per axis, contrast
-    log-uniform in [10, 1e4], seeds derived from the instance id."""
+    log-uniform in [10, 1e4], seeds derived from the instance id.
+
+    Independent +-0.2h jitter of every coordinate can invert a Kuhn
+    tetrahedron (rarely: one instance in the first 256), which makes the
+    stiffness matrix indefinite; such an instance is redrawn with the next
+    mesh seed (2 i + 512 a for attempt a) until every element is positively
+    oriented."""
     lib = _load()
     out = []
     for i in range(count):
         u = [lib.femgen_uniform(ctypes.c_uint64(seed + 1000003), ctypes.c_uint64(4 * i + d)) for d in range(4)]
         nx, ny, nz = (12 + min(28, int(v * 29)) for v in u[:3])
         contrast = float(10.0 ** (1.0 + 3.0 * u[3]))
-        out.append(Grid(nx, ny, nz, n_incl=1, contrast=contrast, seed_mesh=2 * i, seed_x=2 * i + 1))
+        for a in range(64):
+            g = Grid(nx, ny, nz, n_incl=1, contrast=contrast, seed_mesh=2 * i + 512 * a, seed_x=2 * i + 1)
+            if min_volume(g) > 0.0:
+                break
+        else:  # pragma: no cover
+            raise RuntimeError(f"no positively oriented mesh for batch instance {i}")
+        out.append(g)
     return out
 
 
@@ -191,6 +203,70 @@ def inclusion_tets(g: Grid) -> int:
 
 def uniform(seed: int, counter: int) -> float:
     return float(_load().femgen_uniform(ctypes.c_uint64(seed), ctypes.c_uint64(counter)))
+
+
+@dataclass
+class BatchSystem:
+    """Independent systems as one block-diagonal CSR with global columns:
+    instance i owns rows row_off[i]..row_off[i+1]; B = A X* column by column,
+    (n, nrhs) row-major."""
+    grids: list
+    row_off: np.ndarray   # int64[count+1]
+    ptr: np.ndarray       # int32[n+1]
+    idx: np.ndarray       # int32[nnz], global columns
+    val: np.ndarray       # float64[nnz]
+    B: np.ndarray         # float64[n, nrhs]
+    Xstar: np.ndarray     # float64[n, nrhs]
+
+    @property
+    def count(self) -> int:
+        return int(self.row_off.shape[0]) - 1
+
+    @property
+    def n(self) -> int:
+        return int(self.row_off[-1])
+
+    @property
+    def nnz(self) -> int:
+        return int(self.idx.shape[0])
+
+    def instance(self, i: int):
+        """(ptr, idx, val) of instance i alone, 0-based local columns."""
+        r0, r1 = int(self.row_off[i]), int(self.row_off[i + 1])
+        k0, k1 = int(self.ptr[r0]), int(self.ptr[r1])
+        return ((self.ptr[r0:r1 + 1] - k0).astype(np.int32), (self.idx[k0:k1] - r0).astype(np.int32),
+                self.val[k0:k1])
+
+
+def build_batch(grids, nrhs: int = 8) -> BatchSystem:
+    """Block-diagonal batch of the generator's systems with nrhs manufactured
+    solutions per instance: x*_k ~ U(-1, 1) seeded by the instance's seed_x and
+    k, b_k = A x*_k (sparse product of the generated matrix, input generation)."""
+    import scipy.sparse as sp
+
+    ptrs, idxs, vals, Bs, Xs = [], [], [], [], []
+    row_off = [0]
+    nnz_off = 0
+    for g in grids:
+        s = build_system(g)
+        r0 = row_off[-1]
+        ptrs.append(s.ptr[:-1].astype(np.int64) + nnz_off)
+        idxs.append(s.idx.astype(np.int64) + r0)
+        vals.append(s.val)
+        X = np.stack([random_vector(s.n, 1_000_000 + 8 * g.seed_x + k) for k in range(nrhs)], axis=1) \
+            if s.n else np.zeros((0, nrhs))
+        A = sp.csr_matrix((s.val, s.idx, s.ptr), shape=(s.n, s.n))
+        Bs.append(np.asarray(A @ X).reshape(s.n, nrhs))
+        Xs.append(X.reshape(s.n, nrhs))
+        nnz_off += s.nnz
+        row_off.append(r0 + s.n)
+    ptr = np.concatenate(ptrs + [np.array([nnz_off], dtype=np.int64)])
+    if nnz_off >= 2 ** 31:
+        raise ValueError("batch has more than 2^31 - 1 entries")
+    return BatchSystem(list(grids), np.array(row_off, dtype=np.int64), ptr.astype(np.int32),
+                       np.concatenate(idxs).astype(np.int32), np.concatenate(vals),
+                       np.ascontiguousarray(np.concatenate(Bs, axis=0)),
+                       np.ascontiguousarray(np.concatenate(Xs, axis=0)))
 
 
 def random_vector(n: int, seed: int, lo: float = -1.0, hi: float = 1.0) -> np.ndarray:

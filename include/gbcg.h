@@ -226,6 +226,159 @@ int gbcg_selftest_wait_timeout(int32_t ctas, int32_t timeout_ms, void* stream);
 int gbcg_solve_csr_static(int64_t n, int64_t nnz, const int32_t* ptr, const int32_t* idx, const double* val,
                           const double* b, double* x, double tol, int32_t maxit, gbcg_info* info, void* stream);
 
+
+/* ------------------------------------------------------------ batches ---
+ * Many independent SPD systems of uneven size, each with up to eight
+ * right-hand sides, solved by one persistent launch of thread-block clusters
+ * replayed as a CUDA graph.  Per system and right-hand side the method is
+ * the CG iteration of Section III, either in double precision or in the
+ * single-precision form of Section IV inside double-precision iterative
+ * refinement; the systems share nothing but the launch.
+ *
+ * Layout ("block-diagonal CSR"): instance i owns rows [row_off[i],
+ * row_off[i+1]); ptr[n_tot+1] and idx/val are one 0-based CSR of the whole
+ * block-diagonal matrix with global column numbers, and every column of a
+ * row of instance i lies in instance i's row range.  Right-hand sides and
+ * solutions are n_tot x nrhs row-major (the nrhs values of a row are
+ * adjacent).
+ */
+typedef struct gbcg_batch_s* gbcg_batch_t;
+
+/* Result of one system and right-hand side. */
+typedef struct {
+  int32_t iterations;     /* inner CG iterations */
+  int32_t outer;          /* refinement passes (GBCG_FP64: first run + restarts) */
+  int32_t status;         /* gbcg_status */
+  int32_t pad_;
+  double rel_res_true;    /* ||b - A x|| / ||b|| in double precision at the last check */
+} gbcg_batch_info;
+
+/* Options of gbcg_batch_solve; zero fields take the defaults. */
+typedef struct {
+  int32_t precision;      /* gbcg_precision; default GBCG_FP64 */
+  int32_t max_outer;      /* passes: default 30 for GBCG_FP32_IR, 4 (one run and up to
+                             three true-residual restarts) for GBCG_FP64 */
+  double inner_tol;       /* GBCG_FP32_IR inner relative tolerance; default 1e-4 */
+  int32_t fixed_order;    /* 1: keep the work-queue order (by default every solve
+                             reorders the queue by the measured time per instance,
+                             longest first, for the next solve) */
+  int32_t pad_;
+} gbcg_batch_opts;
+
+/* Report of one gbcg_batch_solve. */
+typedef struct {
+  double ms;              /* host wall time of the call */
+  double kernel_ms;       /* device time of the graph launch (CUDA events) */
+  double span_ms;         /* first instance start to last instance end, global timer */
+  double busy_fraction;   /* instance time summed / (span x clusters): queue balance */
+  int64_t products;       /* inner matrix products summed over instances (eight
+                             right-hand sides each) */
+  int64_t iterations;     /* inner iterations summed over systems and right-hand sides */
+  int32_t max_iterations; /* largest inner iteration count of one right-hand side */
+  int32_t launches;       /* kernels launched: the one persistent kernel */
+  int32_t graph;          /* 1: the launch was a CUDA graph replay */
+  int32_t threads;        /* CTA size of the launch */
+  int32_t cluster;        /* CTAs per cluster */
+  int32_t clusters;       /* co-resident clusters (the grid) */
+} gbcg_batch_report;
+
+/* Launch configuration of a batch: chosen by the autotuner or set by hand. */
+typedef struct {
+  int32_t threads;           /* CTA size: 256 or 512 */
+  int32_t cluster;           /* CTAs per cluster: 1, 2, 4, 8 or 16 */
+  int32_t rows_per_warp[8];  /* per nnz-per-row bucket b (2^b <= nnz/row < 2^(b+1)):
+                                rows a warp works on at once, 1, 2, 4, 8 or 16
+                                (16 only for the single-precision inner solve) */
+  int32_t clusters;          /* out: co-resident clusters of that configuration */
+  int32_t from_cache;        /* out: 1 if taken from the process's tuning cache */
+  int32_t candidates;        /* out: probe launches timed */
+  int32_t pad_;
+  double probe_ms;           /* out: time of the winning probe launch */
+} gbcg_batch_tuning;
+
+typedef struct {
+  int64_t n;                 /* rows of all instances */
+  int64_t nnz;               /* stored entries of all instances */
+  int64_t device_bytes;      /* device memory held by the handle */
+  int64_t iter_bytes_fp32;   /* algorithmic bytes of one single-precision inner
+                                iteration of every instance (matrix once, eight
+                                right-hand sides of vectors) */
+  int64_t iter_bytes_fp64;   /* the same in double precision */
+  int32_t count;             /* instances */
+  int32_t nrhs;              /* right-hand sides */
+  int32_t threads[2];        /* [0] double, [1] single-precision inner solve */
+  int32_t cluster[2];
+  int32_t rows_per_warp[2][8];
+} gbcg_batch_stats_t;
+
+/*
+ * gbcg_batch_create -- build a batch handle.
+ *
+ *   count      instances, >= 1
+ *   row_off    host array of count + 1 row offsets, row_off[0] = 0, non-decreasing
+ *   ptr, idx, val
+ *              the block-diagonal CSR described above (memory: gbcg_memory);
+ *              within a row columns strictly increase; values finite.  Each
+ *              instance must be symmetric positive-definite (the caller's promise)
+ *   nrhs       right-hand sides per instance, 1..8 (the kernels always carry
+ *              eight; fewer leave lanes idle)
+ *   tune       1: run the autotuner for the single-precision inner solve now
+ *              (or take its cached result for an identical batch shape)
+ *
+ * Deep-copies the matrix (double and single-precision values), allocates the
+ * solve workspace (five vectors of n_tot x 8 values) and the pinned host
+ * blocks the graph reads and writes.  Errors: GBCG_ERR_INVALID with the first
+ * offending position, GBCG_ERR_NOMEM, GBCG_ERR_CUDA.
+ */
+int gbcg_batch_create(gbcg_batch_t* B, int32_t count, const int64_t* row_off, const int32_t* ptr, const int32_t* idx,
+                      const double* val, int32_t nrhs, int32_t memory, int32_t tune, void* stream);
+
+/* gbcg_batch_destroy -- free a batch handle (NULL is a no-op). */
+int gbcg_batch_destroy(gbcg_batch_t B);
+
+/*
+ * gbcg_batch_autotune -- choose the CTA size, the cluster size and, per
+ * nnz-per-row bucket, the rows per warp of the inner product for `precision`
+ * by timing probe launches (every instance runs 16 inner iterations of one
+ * refinement pass; each candidate's per-instance times come from the device's
+ * global timer).  The result is cached per process by device and batch shape.
+ * `rep` may be NULL.  Allocates two temporary n_tot x nrhs vectors.
+ */
+int gbcg_batch_autotune(gbcg_batch_t B, int32_t precision, gbcg_batch_tuning* rep, void* stream);
+
+/* gbcg_batch_set_tuning -- set the launch configuration of `precision` by hand. */
+int gbcg_batch_set_tuning(gbcg_batch_t B, int32_t precision, const gbcg_batch_tuning* t);
+
+/*
+ * gbcg_batch_solve -- solve every instance for every right-hand side.
+ *
+ *   b, x     n_tot x nrhs doubles, both device or both host memory; x holds
+ *            x0 on entry and the solutions on return
+ *   tol      relative residual target per system and right-hand side, checked
+ *            on the true residual in double precision
+ *   maxit    bound on inner iterations per system and right-hand side; <= 0
+ *            means the instance's row count
+ *   opts     may be NULL (double precision)
+ *   infos    host array of count x nrhs results (instance-major), may be NULL
+ *   rep      may be NULL
+ *
+ * The first call per precision (and the first after a tuning change)
+ * captures the solve graph: upload of the argument block, queue reset, the
+ * persistent launch and the result downloads; later calls replay it.  No
+ * device allocation.  Returns GBCG_OK when every system converged, else the
+ * status of the first failing one in instance order; synchronises `stream`.
+ */
+int gbcg_batch_solve(gbcg_batch_t B, const double* b, double* x, double tol, int32_t maxit,
+                     const gbcg_batch_opts* opts, gbcg_batch_info* infos, gbcg_batch_report* rep, void* stream);
+
+/* gbcg_batch_instance_times -- of the last solve, per instance: global-timer
+ * start and end (2 x count, ns), inner products and double-precision residual
+ * products.  Any output may be NULL. */
+int gbcg_batch_instance_times(gbcg_batch_t B, int64_t* t_ns, int32_t* products, int32_t* outer_products);
+
+/* gbcg_batch_stats -- shape, memory and launch configuration of a batch. */
+int gbcg_batch_stats(gbcg_batch_t B, gbcg_batch_stats_t* out);
+
 #ifdef __cplusplus
 }
 #endif

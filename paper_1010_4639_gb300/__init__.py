@@ -207,6 +207,141 @@ class Matrix:
         return x, res
 
 
+BATCH_INFO_DTYPE = np.dtype([("iterations", np.int32), ("outer", np.int32), ("status", np.int32),
+                             ("pad_", np.int32), ("rel_res_true", np.float64)])
+
+
+def _tuning_dict(t) -> dict:
+    return {"threads": t.threads, "cluster": t.cluster, "rows_per_warp": list(t.rows_per_warp),
+            "clusters": t.clusters, "from_cache": bool(t.from_cache), "candidates": t.candidates,
+            "probe_ms": t.probe_ms}
+
+
+class Batch:
+    """Independent SPD systems of uneven size with up to eight right-hand
+    sides each, solved in one persistent launch (``gbcg_batch_create``).
+
+    ``row_off`` (count + 1 int64 row offsets) is a host array; ``ptr``/``idx``/
+    ``val`` form one 0-based CSR of the block-diagonal matrix with global
+    column numbers (numpy arrays or CUDA tensors).
+    """
+
+    def __init__(self, row_off, ptr, idx, val, nrhs: int = 8, tune: bool = True, stream=None):
+        lib = _lib.load()
+        self._lib = lib
+        self._h = ctypes.c_void_p()
+        row_off = np.ascontiguousarray(row_off, dtype=np.int64)
+        self.count = int(row_off.shape[0]) - 1
+        self.n = int(row_off[-1])
+        self.nrhs = int(nrhs)
+        self.row_off = row_off
+        if _is_tensor(ptr):
+            torch = _torch()
+            ptr = ptr.to(torch.int32).contiguous()
+            idx = idx.to(torch.int32).contiguous()
+            val = val.to(torch.float64).contiguous()
+            mem = _lib.GBCG_DEVICE if ptr.is_cuda else _lib.GBCG_HOST
+            args = (ptr.data_ptr(), idx.data_ptr(), val.data_ptr())
+        else:
+            ptr = np.ascontiguousarray(ptr, dtype=np.int32)
+            idx = np.ascontiguousarray(idx, dtype=np.int32)
+            val = np.ascontiguousarray(val, dtype=np.float64)
+            mem = _lib.GBCG_HOST
+            args = (ptr.ctypes.data, idx.ctypes.data, val.ctypes.data)
+        keep = (row_off, ptr, idx, val)
+        rc = lib.gbcg_batch_create(ctypes.byref(self._h), self.count, ctypes.c_void_p(row_off.ctypes.data),
+                                   *[ctypes.c_void_p(a) for a in args], self.nrhs, mem, int(bool(tune)),
+                                   _host_stream(stream))
+        del keep
+        _lib.check(rc, "gbcg_batch_create")
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self._lib.gbcg_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # pragma: no cover
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def stats(self) -> dict:
+        s = _lib.BatchStats()
+        _lib.check(self._lib.gbcg_batch_stats(self._h, ctypes.byref(s)), "gbcg_batch_stats")
+        return {"n": s.n, "nnz": s.nnz, "device_bytes": s.device_bytes, "iter_bytes_fp32": s.iter_bytes_fp32,
+                "iter_bytes_fp64": s.iter_bytes_fp64, "count": s.count, "nrhs": s.nrhs,
+                "threads": list(s.threads), "cluster": list(s.cluster),
+                "rows_per_warp": [list(r) for r in s.rows_per_warp]}
+
+    def autotune(self, precision: str = "fp32_ir", stream=None) -> dict:
+        t = _lib.BatchTuning()
+        _lib.check(self._lib.gbcg_batch_autotune(self._h, PRECISIONS[precision], ctypes.byref(t),
+                                                 _host_stream(stream)), "gbcg_batch_autotune")
+        return _tuning_dict(t)
+
+    def set_tuning(self, precision: str, threads: int, cluster: int, rows_per_warp):
+        rpw = list(rows_per_warp) if not isinstance(rows_per_warp, int) else [rows_per_warp] * 8
+        t = _lib.BatchTuning(int(threads), int(cluster), (ctypes.c_int32 * 8)(*rpw))
+        _lib.check(self._lib.gbcg_batch_set_tuning(self._h, PRECISIONS[precision], ctypes.byref(t)),
+                   "gbcg_batch_set_tuning")
+
+    def instance_times(self):
+        """(start/end ns [count, 2], inner products [count], residual products [count]) of the last solve."""
+        t = np.zeros((self.count, 2), dtype=np.int64)
+        p = np.zeros(self.count, dtype=np.int32)
+        o = np.zeros(self.count, dtype=np.int32)
+        _lib.check(self._lib.gbcg_batch_instance_times(self._h, ctypes.c_void_p(t.ctypes.data),
+                                                       ctypes.c_void_p(p.ctypes.data),
+                                                       ctypes.c_void_p(o.ctypes.data)), "gbcg_batch_instance_times")
+        return t, p, o
+
+    def solve(self, b, x=None, tol: float = 1e-10, maxit: int = 0, precision: str = "fp32_ir",
+              inner_tol: float = 1e-4, max_outer: int = 0, fixed_order: bool = False, stream=None,
+              raise_on_error: bool = True):
+        """Solve every instance for every right-hand side (``gbcg_batch_solve``).
+
+        ``b``, ``x``: (n, nrhs) float64, both CUDA tensors or both numpy
+        arrays; ``x`` holds x0 (zeros if None) and receives the solutions.
+        Returns (x, infos, report): infos a (count, nrhs) structured array
+        (iterations, outer, status, rel_res_true), report a dict.
+        """
+        opts = _lib.BatchOpts(PRECISIONS[precision], int(max_outer), float(inner_tol), int(bool(fixed_order)), 0)
+        infos = np.zeros((self.count, self.nrhs), dtype=BATCH_INFO_DTYPE)
+        rep = _lib.BatchReport()
+        shape = (self.n, self.nrhs)
+        if _is_tensor(b):
+            torch = _torch()
+            if x is None:
+                x = torch.zeros(shape, dtype=torch.float64, device=b.device)
+            for t, name in ((b, "b"), (x, "x")):
+                if t.dtype != torch.float64 or tuple(t.shape) != shape or not t.is_contiguous():
+                    raise ValueError(f"{name} must be a contiguous float64 tensor of shape {shape}")
+            stream_h = _stream_handle(stream) if b.is_cuda else _host_stream(stream)
+            bp, xp = b.data_ptr(), x.data_ptr()
+        else:
+            b = np.ascontiguousarray(b, dtype=np.float64).reshape(shape)
+            x = np.zeros(shape) if x is None else x
+            if not (isinstance(x, np.ndarray) and x.dtype == np.float64 and x.flags.c_contiguous and x.shape == shape):
+                raise ValueError(f"x must be a contiguous float64 numpy array of shape {shape}")
+            stream_h = _host_stream(stream)
+            bp, xp = b.ctypes.data, x.ctypes.data
+        rc = self._lib.gbcg_batch_solve(self._h, ctypes.c_void_p(bp), ctypes.c_void_p(xp), float(tol), int(maxit),
+                                        ctypes.byref(opts), ctypes.c_void_p(infos.ctypes.data), ctypes.byref(rep),
+                                        stream_h)
+        if rc != 0 and raise_on_error and rc not in (2, 3, 4):
+            raise GbcgError(rc, "gbcg_batch_solve", _lib.last_error())
+        report = {name: getattr(rep, name) for name, _ in _lib.BatchReport._fields_}
+        report["status"] = _lib.STATUS_NAMES[rc] if 0 <= rc < len(_lib.STATUS_NAMES) else str(rc)
+        return x, infos, report
+
+
 def _check_vec(t, dtype, n, name):
     if not t.is_cuda or t.dtype != dtype or t.numel() != n or not t.is_contiguous():
         raise ValueError(f"{name} must be a contiguous {dtype} CUDA tensor of length {n}")
@@ -217,4 +352,4 @@ def selftest_wait_timeout(ctas: int = 0, timeout_ms: int = 50, stream=None) -> i
     return _lib.load().gbcg_selftest_wait_timeout(int(ctas), int(timeout_ms), _stream_handle(stream))
 
 
-__all__ = ["Matrix", "SolveInfo", "GbcgError", "build", "selftest_wait_timeout", "FORMATS", "PRECISIONS"]
+__all__ = ["Matrix", "Batch", "SolveInfo", "GbcgError", "build", "selftest_wait_timeout", "FORMATS", "PRECISIONS"]

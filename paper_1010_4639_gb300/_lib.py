@@ -19,7 +19,9 @@ STATUS_NAMES = ["OK", "INVALID", "NOT_SPD", "MAXIT", "NONFINITE", "TIMEOUT", "CU
 
 # Every entry point declared in include/gbcg.h.
 EXPORTS = ["gbcg_create", "gbcg_destroy", "gbcg_spmv", "gbcg_spmv_f32", "gbcg_solve", "gbcg_stats",
-           "gbcg_status_string", "gbcg_last_error", "gbcg_selftest_wait_timeout", "gbcg_solve_csr_static"]
+           "gbcg_status_string", "gbcg_last_error", "gbcg_selftest_wait_timeout", "gbcg_solve_csr_static",
+           "gbcg_batch_create", "gbcg_batch_destroy", "gbcg_batch_autotune", "gbcg_batch_set_tuning",
+           "gbcg_batch_solve", "gbcg_batch_instance_times", "gbcg_batch_stats"]
 STATIC_MAX_N = 680000
 
 
@@ -41,6 +43,36 @@ class Stats(ctypes.Structure):
                 ("device_bytes", ctypes.c_int64), ("spmv_bytes_fp64", ctypes.c_int64),
                 ("spmv_bytes_fp32", ctypes.c_int64), ("ext_slots", ctypes.c_int64), ("format", ctypes.c_int32),
                 ("grid_ctas", ctypes.c_int32), ("layout", ctypes.c_int32), ("tiles", ctypes.c_int32)]
+
+
+class BatchInfo(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("outer", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("pad_", ctypes.c_int32), ("rel_res_true", ctypes.c_double)]
+
+
+class BatchOpts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("max_outer", ctypes.c_int32), ("inner_tol", ctypes.c_double),
+                ("fixed_order", ctypes.c_int32), ("pad_", ctypes.c_int32)]
+
+
+class BatchReport(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double), ("kernel_ms", ctypes.c_double), ("span_ms", ctypes.c_double),
+                ("busy_fraction", ctypes.c_double), ("products", ctypes.c_int64), ("iterations", ctypes.c_int64),
+                ("max_iterations", ctypes.c_int32), ("launches", ctypes.c_int32), ("graph", ctypes.c_int32),
+                ("threads", ctypes.c_int32), ("cluster", ctypes.c_int32), ("clusters", ctypes.c_int32)]
+
+
+class BatchTuning(ctypes.Structure):
+    _fields_ = [("threads", ctypes.c_int32), ("cluster", ctypes.c_int32), ("rows_per_warp", ctypes.c_int32 * 8),
+                ("clusters", ctypes.c_int32), ("from_cache", ctypes.c_int32), ("candidates", ctypes.c_int32),
+                ("pad_", ctypes.c_int32), ("probe_ms", ctypes.c_double)]
+
+
+class BatchStats(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
+                ("iter_bytes_fp32", ctypes.c_int64), ("iter_bytes_fp64", ctypes.c_int64), ("count", ctypes.c_int32),
+                ("nrhs", ctypes.c_int32), ("threads", ctypes.c_int32 * 2), ("cluster", ctypes.c_int32 * 2),
+                ("rows_per_warp", (ctypes.c_int32 * 8) * 2)]
 
 
 class GbcgError(RuntimeError):
@@ -74,8 +106,18 @@ def load(path: str = LIB_PATH):
     lib.gbcg_last_error.restype = ctypes.c_char_p
     lib.gbcg_selftest_wait_timeout.argtypes = [i32, i32, vp]
     lib.gbcg_solve_csr_static.argtypes = [i64, i64, vp, vp, vp, vp, vp, d, i32, ctypes.POINTER(Info), vp]
+    lib.gbcg_batch_create.argtypes = [ctypes.POINTER(vp), i32, vp, vp, vp, vp, i32, i32, i32, vp]
+    lib.gbcg_batch_destroy.argtypes = [vp]
+    lib.gbcg_batch_autotune.argtypes = [vp, i32, ctypes.POINTER(BatchTuning), vp]
+    lib.gbcg_batch_set_tuning.argtypes = [vp, i32, ctypes.POINTER(BatchTuning)]
+    lib.gbcg_batch_solve.argtypes = [vp, vp, vp, d, i32, ctypes.POINTER(BatchOpts), vp,
+                                     ctypes.POINTER(BatchReport), vp]
+    lib.gbcg_batch_instance_times.argtypes = [vp, vp, vp, vp]
+    lib.gbcg_batch_stats.argtypes = [vp, ctypes.POINTER(BatchStats)]
     for name in ("gbcg_create", "gbcg_destroy", "gbcg_spmv", "gbcg_spmv_f32", "gbcg_solve", "gbcg_stats",
-                 "gbcg_selftest_wait_timeout", "gbcg_solve_csr_static"):
+                 "gbcg_selftest_wait_timeout", "gbcg_solve_csr_static", "gbcg_batch_create", "gbcg_batch_destroy",
+                 "gbcg_batch_autotune", "gbcg_batch_set_tuning", "gbcg_batch_solve", "gbcg_batch_instance_times",
+                 "gbcg_batch_stats"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib

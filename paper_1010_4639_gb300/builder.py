@@ -1,9 +1,10 @@
 """Builds ``libgbcg.so`` in-tree for sm_103a (GB300).
 
-Three translation units compiled in parallel: ``csrc/gbcg.cu`` (kernels and
-the C ABI, nvcc), ``csrc/static_solve.cu`` (the allocation-free solve, nvcc)
-and ``csrc/layout.cpp`` (host-side layout construction, g++), linked by nvcc
-into a shared library next to this file.
+Four translation units compiled in parallel: ``csrc/gbcg.cu`` (kernels and
+the C ABI, nvcc), ``csrc/static_solve.cu`` (the allocation-free solve, nvcc),
+``csrc/batch.cu`` (the batched multi-right-hand-side solver, nvcc) and
+``csrc/layout.cpp`` (host-side layout construction, g++), linked by nvcc into
+a shared library next to this file.
 """
 from __future__ import annotations
 
@@ -17,7 +18,8 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgbcg.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = [os.path.join(CSRC, f) for f in ("gbcg.cu", "static_solve.cu", "layout.cpp", "kernels.cuh", "layout.h")]
+SOURCES = [os.path.join(CSRC, f) for f in ("gbcg.cu", "static_solve.cu", "batch.cu", "layout.cpp",
+                                              "kernels.cuh", "layout.h")]
 HEADERS = [os.path.join(INCLUDE, "gbcg.h")]
 
 
@@ -40,12 +42,15 @@ def build(verbose: bool = False, force: bool = False) -> str:
     nvcc = _nvcc()
     cu_obj = os.path.join(BUILD, "gbcg.o")
     st_obj = os.path.join(BUILD, "static_solve.o")
+    bt_obj = os.path.join(BUILD, "batch.o")
     cpp_obj = os.path.join(BUILD, "layout.o")
     cmds = [
         [nvcc, "-c", "-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC",
          "-I", INCLUDE, os.path.join(CSRC, "gbcg.cu"), "-o", cu_obj],
         [nvcc, "-c", "-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC",
          "-I", INCLUDE, os.path.join(CSRC, "static_solve.cu"), "-o", st_obj],
+        [nvcc, "-c", "-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC",
+         "-I", INCLUDE, os.path.join(CSRC, "batch.cu"), "-o", bt_obj],
         ["g++", "-c", "-O2", "-std=c++17", "-fPIC", "-I", INCLUDE,
          os.path.join(CSRC, "layout.cpp"), "-o", cpp_obj],
     ]
@@ -60,7 +65,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
     if errors:
         raise RuntimeError("building libgbcg.so failed:\n" + "\n".join(errors))
     tmp = LIB + ".tmp"
-    subprocess.run([nvcc, "-shared", *ARCH, cu_obj, st_obj, cpp_obj, "-o", tmp], check=True)
+    subprocess.run([nvcc, "-shared", *ARCH, cu_obj, st_obj, bt_obj, cpp_obj, "-o", tmp], check=True)
     os.replace(tmp, LIB)
     return LIB
 

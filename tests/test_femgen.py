@@ -111,3 +111,17 @@ def test_batched_instances_ranges():
     c = np.array([g.contrast for g in inst])
     assert c.min() >= 10 and c.max() <= 1e4
     assert len({(g.seed_mesh, g.seed_x) for g in inst}) == 256
+
+
+def test_batched_instances_are_positively_oriented():
+    # +-0.2h jitter per coordinate can invert a Kuhn tetrahedron: the
+    # original draw of instance 159 (mesh seed 318) does, and its stiffness
+    # matrix then has a negative diagonal entry; the batch redraws that mesh
+    inst = femgen.batched_instances(256)
+    bad = femgen.Grid(34, 21, 27, contrast=inst[159].contrast, seed_mesh=318, seed_x=319)
+    assert femgen.min_volume(bad) < 0.0
+    s = femgen.build_system(bad)
+    diag = np.array([s.val[s.ptr[i] + np.searchsorted(s.idx[s.ptr[i]:s.ptr[i + 1]], i)] for i in range(s.n)])
+    assert diag.min() < 0.0
+    assert inst[159].seed_mesh == 318 + 512
+    assert all(femgen.min_volume(g) > 0.0 for g in inst)
