@@ -459,6 +459,7 @@ def batched(torch, gb, args):
                          "max_rel_res_true": float(infos["rel_res_true"].max()),
                          "systems_ok": int(np.sum(infos["status"] == 0)), "systems": int(infos.size),
                          "threads": rep["threads"], "cluster": rep["cluster"], "clusters": rep["clusters"],
+                         "groups": rep["groups"], "max_group": rep["max_group"],
                          "busy_fraction": rep["busy_fraction"], "span_ms": rep["span_ms"],
                          "graph": rep["graph"], "launches_per_solve": rep["launches"],
                          "algorithmic_GBs": moved / t / 1e9}

@@ -259,13 +259,18 @@ typedef struct {
   int32_t max_outer;      /* passes: default 30 for GBCG_FP32_IR, 4 (one run and up to
                              three true-residual restarts) for GBCG_FP64 */
   double inner_tol;       /* GBCG_FP32_IR inner relative tolerance; default 1e-4 */
-  int32_t fixed_order;    /* 1: keep the work-queue order (by default every solve
-                             reorders the queue by the measured time per instance,
-                             longest first, for the next solve) */
-  int32_t pad_;
+  int32_t fixed_order;    /* 1: keep the schedule (by default every solve replans the
+                             queue and the group sizes from the measured time per
+                             instance, for the next solve) */
+  int32_t max_group;      /* clusters one instance may span, 1..8; default 8 (1: none) */
+  int32_t force_group;    /* > 0: every instance spans this many clusters (testing) */
+  int32_t wait_timeout_ms;/* bound on each wait between the clusters of one instance;
+                             default 1000; a wait that runs out ends the launch with
+                             GBCG_ERR_TIMEOUT */
 } gbcg_batch_opts;
 
-/* Report of one gbcg_batch_solve. */
+/* Report of one gbcg_batch_solve.  busy_fraction counts an instance's time
+ * once per cluster of its group. */
 typedef struct {
   double ms;              /* host wall time of the call */
   double kernel_ms;       /* device time of the graph launch (CUDA events) */
@@ -280,6 +285,8 @@ typedef struct {
   int32_t threads;        /* CTA size of the launch */
   int32_t cluster;        /* CTAs per cluster */
   int32_t clusters;       /* co-resident clusters (the grid) */
+  int32_t groups;         /* instances that spanned more than one cluster */
+  int32_t max_group;      /* largest number of clusters on one instance */
 } gbcg_batch_report;
 
 /* Launch configuration of a batch: chosen by the autotuner or set by hand. */
@@ -370,6 +377,18 @@ int gbcg_batch_set_tuning(gbcg_batch_t B, int32_t precision, const gbcg_batch_tu
  */
 int gbcg_batch_solve(gbcg_batch_t B, const double* b, double* x, double tol, int32_t maxit,
                      const gbcg_batch_opts* opts, gbcg_batch_info* infos, gbcg_batch_report* rep, void* stream);
+
+/*
+ * gbcg_batch_selftest_group_timeout -- check of the bounded wait between the
+ * clusters of one instance.  Runs the batch kernel with the last instance of
+ * the queue made a group of two clusters whose second part is left out of
+ * the queue, so its first part must give up after `timeout_ms` and end the
+ * launch.  Returns GBCG_ERR_TIMEOUT when the wait ended as designed (the
+ * expected result), GBCG_OK if it wrongly completed.  Needs two co-resident
+ * clusters.  No paper counterpart: it tests failure handling without
+ * faulting the GPU.
+ */
+int gbcg_batch_selftest_group_timeout(gbcg_batch_t B, int32_t timeout_ms, void* stream);
 
 /* gbcg_batch_instance_times -- of the last solve, per instance: global-timer
  * start and end (2 x count, ns), inner products and double-precision residual

@@ -302,9 +302,13 @@ class Batch:
                                                        ctypes.c_void_p(o.ctypes.data)), "gbcg_batch_instance_times")
         return t, p, o
 
+    def selftest_group_timeout(self, timeout_ms: int = 50, stream=None) -> int:
+        """Bounded-wait self-test of the multi-cluster groups; returns the status code (5 expected)."""
+        return self._lib.gbcg_batch_selftest_group_timeout(self._h, int(timeout_ms), _host_stream(stream))
+
     def solve(self, b, x=None, tol: float = 1e-10, maxit: int = 0, precision: str = "fp32_ir",
-              inner_tol: float = 1e-4, max_outer: int = 0, fixed_order: bool = False, stream=None,
-              raise_on_error: bool = True):
+              inner_tol: float = 1e-4, max_outer: int = 0, fixed_order: bool = False, max_group: int = 0,
+              force_group: int = 0, wait_timeout_ms: int = 0, stream=None, raise_on_error: bool = True):
         """Solve every instance for every right-hand side (``gbcg_batch_solve``).
 
         ``b``, ``x``: (n, nrhs) float64, both CUDA tensors or both numpy
@@ -312,7 +316,8 @@ class Batch:
         Returns (x, infos, report): infos a (count, nrhs) structured array
         (iterations, outer, status, rel_res_true), report a dict.
         """
-        opts = _lib.BatchOpts(PRECISIONS[precision], int(max_outer), float(inner_tol), int(bool(fixed_order)), 0)
+        opts = _lib.BatchOpts(PRECISIONS[precision], int(max_outer), float(inner_tol), int(bool(fixed_order)),
+                              int(max_group), int(force_group), int(wait_timeout_ms))
         infos = np.zeros((self.count, self.nrhs), dtype=BATCH_INFO_DTYPE)
         rep = _lib.BatchReport()
         shape = (self.n, self.nrhs)

@@ -21,7 +21,8 @@ STATUS_NAMES = ["OK", "INVALID", "NOT_SPD", "MAXIT", "NONFINITE", "TIMEOUT", "CU
 EXPORTS = ["gbcg_create", "gbcg_destroy", "gbcg_spmv", "gbcg_spmv_f32", "gbcg_solve", "gbcg_stats",
            "gbcg_status_string", "gbcg_last_error", "gbcg_selftest_wait_timeout", "gbcg_solve_csr_static",
            "gbcg_batch_create", "gbcg_batch_destroy", "gbcg_batch_autotune", "gbcg_batch_set_tuning",
-           "gbcg_batch_solve", "gbcg_batch_instance_times", "gbcg_batch_stats"]
+           "gbcg_batch_solve", "gbcg_batch_instance_times", "gbcg_batch_stats",
+           "gbcg_batch_selftest_group_timeout"]
 STATIC_MAX_N = 680000
 
 
@@ -52,14 +53,16 @@ class BatchInfo(ctypes.Structure):
 
 class BatchOpts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("max_outer", ctypes.c_int32), ("inner_tol", ctypes.c_double),
-                ("fixed_order", ctypes.c_int32), ("pad_", ctypes.c_int32)]
+                ("fixed_order", ctypes.c_int32), ("max_group", ctypes.c_int32), ("force_group", ctypes.c_int32),
+                ("wait_timeout_ms", ctypes.c_int32)]
 
 
 class BatchReport(ctypes.Structure):
     _fields_ = [("ms", ctypes.c_double), ("kernel_ms", ctypes.c_double), ("span_ms", ctypes.c_double),
                 ("busy_fraction", ctypes.c_double), ("products", ctypes.c_int64), ("iterations", ctypes.c_int64),
                 ("max_iterations", ctypes.c_int32), ("launches", ctypes.c_int32), ("graph", ctypes.c_int32),
-                ("threads", ctypes.c_int32), ("cluster", ctypes.c_int32), ("clusters", ctypes.c_int32)]
+                ("threads", ctypes.c_int32), ("cluster", ctypes.c_int32), ("clusters", ctypes.c_int32),
+                ("groups", ctypes.c_int32), ("max_group", ctypes.c_int32)]
 
 
 class BatchTuning(ctypes.Structure):
@@ -114,10 +117,11 @@ def load(path: str = LIB_PATH):
                                      ctypes.POINTER(BatchReport), vp]
     lib.gbcg_batch_instance_times.argtypes = [vp, vp, vp, vp]
     lib.gbcg_batch_stats.argtypes = [vp, ctypes.POINTER(BatchStats)]
+    lib.gbcg_batch_selftest_group_timeout.argtypes = [vp, i32, vp]
     for name in ("gbcg_create", "gbcg_destroy", "gbcg_spmv", "gbcg_spmv_f32", "gbcg_solve", "gbcg_stats",
                  "gbcg_selftest_wait_timeout", "gbcg_solve_csr_static", "gbcg_batch_create", "gbcg_batch_destroy",
                  "gbcg_batch_autotune", "gbcg_batch_set_tuning", "gbcg_batch_solve", "gbcg_batch_instance_times",
-                 "gbcg_batch_stats"):
+                 "gbcg_batch_stats", "gbcg_batch_selftest_group_timeout"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib

@@ -43,8 +43,9 @@ namespace {
 constexpr int kRhs = 8;          // right-hand sides held per row
 constexpr int kBuckets = 8;      // nnz-per-row buckets [2^b, 2^(b+1))
 constexpr int kMaxWarps = 16;
+constexpr int kMaxGroup = 8;     // clusters one instance may span
 
-enum { kOk = 0, kNotSpd = 2, kMaxit = 3, kNonfinite = 4 };
+enum { kOk = 0, kNotSpd = 2, kMaxit = 3, kNonfinite = 4, kTimeout = 5 };
 
 int fail(int code, const std::string& msg) {
   gbcg::set_last_error(msg);
@@ -81,8 +82,13 @@ struct BArgs {
   const int32_t* idx;       // global column of every entry
   const double* val64;
   const float* val32;
-  const int32_t* order;     // queue position -> instance
+  const int32_t* slot_inst; // queue slot -> instance
+  const int32_t* slot_part; // queue slot -> part of a multi-cluster group (0 .. G-1)
+  const int8_t* grp;        // clusters per instance (G)
   const int8_t* rpw;        // rows per warp of the inner product, per instance
+  unsigned* gbar;           // per instance: group barrier arrivals
+  double* gpart;            // per instance: [2][kMaxGroup][16] cluster partial sums
+  int* err;                 // launch-wide failure (a group wait ran out)
   const double* B;          // n_tot x nrhs, caller layout
   double* X;                // n_tot x nrhs, caller layout
   double* R64;              // n_tot x 8: outer residual
@@ -96,7 +102,8 @@ struct BArgs {
   int32_t* inst_outer;      // count: double-precision residual products
   long long* t_inst;        // 2 x count: start and end, global timer ns
   double tol, inner_tol;
-  int count, nrhs, maxit, max_outer, force_rpw;
+  long long timeout_ns;
+  int count, nslots, nrhs, maxit, max_outer, force_rpw;
 };
 
 __device__ __forceinline__ int64_t min64(int64_t a, int64_t b) { return a < b ? a : b; }
@@ -297,323 +304,437 @@ __device__ __forceinline__ void outer_residual(const BArgs& a, int64_t r0, int64
   }
 }
 
-// The persistent batched solver.  V is the precision of the inner CG (float:
-// Section IV's single-precision iteration inside double-precision
-// refinement; double: double precision throughout, where each refinement
-// pass is a restart of the Section III iteration from the current x).
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ int ld_relaxed_s32(const int* p) {
+  int v;
+  asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// The clusters working on one instance: G clusters of C CTAs, this cluster
+// being part p.  With G = 1 every synchronisation is a cluster barrier;
+// with G > 1 cluster rank 0 of each part meets the others on a global
+// counter (bounded wait).
+struct Group {
+  int G, p;
+  unsigned C, cr;
+  unsigned* bar;
+  double* part;     // [2][kMaxGroup][16]
+  unsigned target;  // arrivals awaited by the next wait (cluster rank 0, thread 0 only)
+  int gpar;         // slot of the next group sum; changed by thread 0 between barriers
+};
+
+// Barrier of the whole group; false (uniformly within the cluster) when the
+// wait ran out or another group failed.  Writes before it, by any CTA of the
+// group, are visible after it.
+__device__ __forceinline__ bool group_sync(const BArgs& a, Group& g, int* s_flag) {
+  cluster_sync();
+  if (g.G == 1) return true;
+  if (g.cr == 0 && threadIdx.x == 0) {
+    g.target += (unsigned)g.G;
+    int ok = 1;
+    __threadfence();
+    atomicAdd(g.bar, 1u);
+    const long long t0 = now_ns();
+    for (unsigned spins = 0;; ++spins) {
+      if (ld_acquire_u32(g.bar) >= g.target) break;
+      if (ld_relaxed_s32(a.err) != 0) {
+        ok = 0;
+        break;
+      }
+      if ((spins & 63u) == 63u && now_ns() - t0 > a.timeout_ns) {
+        atomicCAS(a.err, 0, (int)kTimeout);
+        ok = 0;
+        break;
+      }
+    }
+    __threadfence();
+    *s_flag = ok;
+  }
+  cluster_sync();
+  const int ok = ld_dsmem_s32(s_flag, 0);
+  if (!ok) {
+    cluster_sync();  // no CTA leaves while another still reads its shared memory
+    return false;
+  }
+  if (threadIdx.x == 0) __threadfence();  // acquire for this SM before reading the other clusters' data
+  __syncthreads();
+  return true;
+}
+
+// Sums over the whole group (see cluster_reduce): the cluster's sums, then
+// for G > 1 the parts' sums in part order, read from global memory.
+template <int VW, int NS>
+__device__ __forceinline__ double group_reduce(const BArgs& a, double (&v)[NS][VW], Red& red, int& par, Group& g,
+                                               int* s_flag, bool& ok) {
+  double s = cluster_reduce<VW, NS>(v, red, par, g.C);
+  if (g.G == 1) return s;
+  double* slot = g.part + g.gpar * (kMaxGroup * 2 * kRhs);
+  if (g.cr == 0 && threadIdx.x < NS * kRhs) slot[g.p * 2 * kRhs + threadIdx.x] = s;
+  ok = group_sync(a, g, s_flag);  // every thread has read g.gpar before it returns
+  if (threadIdx.x == 0) g.gpar ^= 1;  // read again only after the caller's next __syncthreads
+  s = 0.0;
+  if (threadIdx.x < NS * kRhs)
+    for (int q = 0; q < g.G; ++q) s += __ldcg(slot + q * 2 * kRhs + threadIdx.x);
+  return s;
+}
+
+// One instance, all right-hand sides, on this cluster's share of its rows.
+// Returns false when a group wait failed (the instance is abandoned).
 template <typename V, int NT>
-__global__ void __launch_bounds__(NT, 1024 / NT) k_bcg(const BArgs* __restrict__ args) {
+__device__ bool solve_instance(const BArgs& a, int inst, Group& g, Red& red, St& st, int& par, int* s_flag) {
   using VT = typename V16<V>::T;
   constexpr int VW = V16<V>::W, CH = kRhs / VW;
-  __shared__ BArgs a;
-  __shared__ Red red;
-  __shared__ St st;
-  __shared__ int s_next;
-  if (threadIdx.x == 0) a = *args;
-  __syncthreads();
-  const unsigned C = cluster_ctas(), cr = cluster_rank();
-  const int t = threadIdx.x, lane = t & 31;
+  const int t = threadIdx.x;
   const int ch = t % CH;  // this thread's group of right-hand sides in the vector passes
   V* __restrict__ R = reinterpret_cast<V*>(a.R);
   V* __restrict__ P = reinterpret_cast<V*>(a.P);
   V* __restrict__ Q = reinterpret_cast<V*>(a.Q);
   V* __restrict__ D = reinterpret_cast<V*>(a.D);
   const V* __restrict__ AV = sizeof(V) == 4 ? reinterpret_cast<const V*>(a.val32) : reinterpret_cast<const V*>(a.val64);
-  int par = 0;
-  cluster_sync();  // every CTA of the cluster is running before any shared-memory access across CTAs
-  for (;;) {
-    if (cr == 0 && t == 0) s_next = atomicAdd(a.queue, 1);
-    cluster_sync();
-    const int qpos = ld_dsmem_s32(&s_next, 0);
-    cluster_sync();
-    if (qpos >= a.count) break;
-    const int inst = a.order[qpos];
-    const int64_t row0 = a.inst_row[inst];
-    const int64_t nI = a.inst_row[inst + 1] - row0;
-    const int64_t per = (nI + C - 1) / C;
-    const int64_t r0 = row0 + min64(nI, per * cr);
-    const int64_t r1 = row0 + min64(nI, per * (cr + 1));
-    const int rp = a.force_rpw > 0 ? a.force_rpw : (int)a.rpw[inst];
-    const int64_t e0 = r0 * CH, e1 = r1 * CH;  // 16-byte groups of the CTA's rows
-    if (t < 32) {
-      if (t < kRhs) {
-        st.used[t] = 0;
-        st.outer[t] = 0;
-        st.status[t] = kMaxit;
-        st.rel[t] = 0.0;
-        st.nb[t] = 0.0;
-      }
-      const unsigned pad = __ballot_sync(~0u, t < kRhs && t >= a.nrhs);
-      if (t == 0) {
-        st.fin = pad;
-        st.zero = 0;
-        st.maxit = a.maxit > 0 ? a.maxit : (int)min64(nI, 0x7fffffff);
-        st.products = 0;
-        st.outers = 0;
-        if (cr == 0) a.t_inst[2 * inst] = now_ns();
-      }
+  const int64_t row0 = a.inst_row[inst];
+  const int64_t nI = a.inst_row[inst + 1] - row0;
+  const int64_t GC = (int64_t)g.G * g.C, gc = (int64_t)g.p * g.C + g.cr;
+  const int64_t per = (nI + GC - 1) / GC;
+  const int64_t r0 = row0 + min64(nI, per * gc);
+  const int64_t r1 = row0 + min64(nI, per * (gc + 1));
+  const int rp = a.force_rpw > 0 ? a.force_rpw : (int)a.rpw[inst];
+  const int64_t e0 = r0 * CH, e1 = r1 * CH;  // 16-byte groups of the CTA's rows
+  bool ok = true;
+  if (t < 32) {
+    if (t < kRhs) {
+      st.used[t] = 0;
+      st.outer[t] = 0;
+      st.status[t] = kMaxit;
+      st.rel[t] = 0.0;
+      st.nb[t] = 0.0;
     }
-    __syncthreads();
-    for (bool first = true;; first = false) {
-      // outer step: R64 = B - A64 X and the norms, in double precision
-      {
-        double v[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
-        outer_residual(a, r0, r1, v);
-        const double s = cluster_reduce<2, 2>(v, red, par, C);
-        if (t >= kRhs && t < 2 * kRhs) red.sum[t] = s;
-        __syncthreads();
-        if (t < 32) {
-          bool act = false, zero = false, done = false;
-          if (t < kRhs && !((st.fin >> t) & 1u)) {
-            if (first) st.nb[t] = sqrt(red.sum[kRhs + t]);
-            const double nb = st.nb[t];
-            if (nb == 0.0) {
-              zero = true;
+    const unsigned pad = __ballot_sync(~0u, t < kRhs && t >= a.nrhs);
+    if (t == 0) {
+      st.fin = pad;
+      st.zero = 0;
+      st.maxit = a.maxit > 0 ? a.maxit : (int)min64(nI, 0x7fffffff);
+      st.products = 0;
+      st.outers = 0;
+    }
+  }
+  __syncthreads();
+  for (bool first = true;; first = false) {
+    // outer step: R64 = B - A64 X and the norms, in double precision
+    {
+      double v[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+      outer_residual(a, r0, r1, v);
+      const double s = group_reduce<2, 2>(a, v, red, par, g, s_flag, ok);
+      if (!ok) return false;
+      if (t >= kRhs && t < 2 * kRhs) red.sum[t] = s;
+      __syncthreads();
+      if (t < 32) {
+        bool act = false, zero = false, done = false;
+        if (t < kRhs && !((st.fin >> t) & 1u)) {
+          if (first) st.nb[t] = sqrt(red.sum[kRhs + t]);
+          const double nb = st.nb[t];
+          if (nb == 0.0) {
+            zero = true;
+            done = true;
+            st.status[t] = kOk;
+            st.rel[t] = 0.0;
+          } else {
+            const double nr = sqrt(s);
+            const double rel = nr / nb;
+            st.rel[t] = rel;
+            if (!isfinite(rel)) {
+              st.status[t] = kNonfinite;
               done = true;
+            } else if (rel <= a.tol) {
               st.status[t] = kOk;
-              st.rel[t] = 0.0;
+              done = true;
+            } else if (st.outer[t] >= a.max_outer || st.used[t] >= st.maxit) {
+              st.status[t] = kMaxit;
+              done = true;
             } else {
-              const double nr = sqrt(s);
-              const double rel = nr / nb;
-              st.rel[t] = rel;
-              if (!isfinite(rel)) {
-                st.status[t] = kNonfinite;
-                done = true;
-              } else if (rel <= a.tol) {
-                st.status[t] = kOk;
-                done = true;
-              } else if (st.outer[t] >= a.max_outer || st.used[t] >= st.maxit) {
-                st.status[t] = kMaxit;
-                done = true;
-              } else {
-                act = true;
-                st.nr[t] = nr;
-                // inner target relative to the pass's own starting residual:
-                // fixed for the refinement; for double precision the one that
-                // brings ||b - A x|| to tol ||b||, so that later passes are the
-                // true-residual restarts of the Section III solve
-                st.itol[t] = sizeof(V) == 4 ? a.inner_tol : a.tol * nb / nr;
-              }
+              act = true;
+              st.nr[t] = nr;
+              // inner target relative to the pass's own starting residual:
+              // fixed for the refinement; for double precision the one that
+              // brings ||b - A x|| to tol ||b||, so that later passes are the
+              // true-residual restarts of the Section III solve
+              st.itol[t] = sizeof(V) == 4 ? a.inner_tol : a.tol * nb / nr;
             }
           }
-          const unsigned am = __ballot_sync(~0u, act), zm = __ballot_sync(~0u, zero), dm = __ballot_sync(~0u, done);
-          if (t == 0) {
-            st.oact = am;
-            st.zero = zm;
-            st.fin |= dm;
-            st.outers += 1;
+        }
+        const unsigned am = __ballot_sync(~0u, act), zm = __ballot_sync(~0u, zero), dm = __ballot_sync(~0u, done);
+        if (t == 0) {
+          st.oact = am;
+          st.zero = zm;
+          st.fin |= dm;
+          st.outers += 1;
+        }
+      }
+      __syncthreads();
+    }
+    if (st.zero) {  // b = 0: x = 0
+      const unsigned zm = st.zero;
+      for (int64_t row = r0 + t; row < r1; row += NT)
+        for (int k = 0; k < a.nrhs; ++k)
+          if ((zm >> k) & 1u) a.X[row * a.nrhs + k] = 0.0;
+    }
+    const unsigned oact = st.oact;
+    if (oact == 0) break;
+    // inner setup: R = P = r / ||r|| in V, D = 0, r'r
+    {
+      V pr[VW];
+      double nrv[VW];
+      bool on[VW];
+#pragma unroll
+      for (int j = 0; j < VW; ++j) {
+        pr[j] = V(0);
+        on[j] = (oact >> (ch * VW + j)) & 1u;
+        nrv[j] = on[j] ? st.nr[ch * VW + j] : 1.0;
+      }
+      for (int64_t e = e0 + t; e < e1; e += NT) {
+        VT rv;
+        V* re = reinterpret_cast<V*>(&rv);
+#pragma unroll
+        for (int j = 0; j < VW; ++j) {
+          re[j] = on[j] ? (V)(a.R64[e * VW + j] / nrv[j]) : V(0);
+          pr[j] = re[j] * re[j] + pr[j];
+        }
+        reinterpret_cast<VT*>(R)[e] = rv;
+        reinterpret_cast<VT*>(P)[e] = rv;
+        reinterpret_cast<VT*>(D)[e] = VT{};
+      }
+      double v[1][VW];
+#pragma unroll
+      for (int j = 0; j < VW; ++j) v[0][j] = (double)pr[j];
+      const double s = group_reduce<VW, 1>(a, v, red, par, g, s_flag, ok);  // also publishes P
+      if (!ok) return false;
+      if (t < 32) {
+        bool go = false;
+        if (t < kRhs && ((oact >> t) & 1u)) {
+          st.rr[t] = s;
+          st.nr0[t] = sqrt(s);
+          st.kin[t] = 0;
+          st.bd[t] = 0;
+          go = st.nr0[t] > 0.0 && !(sqrt(s) <= st.itol[t] * st.nr0[t]) && st.used[t] < st.maxit;
+        }
+        const unsigned m = __ballot_sync(~0u, go);
+        if (t == 0) st.iact = m;
+      }
+      __syncthreads();
+    }
+    // inner CG, one right-hand side per bit of st.iact
+    while (st.iact) {
+      // q = A p, p'q
+      {
+        double v[1][VW];
+        V pq[VW];
+#pragma unroll
+        for (int j = 0; j < VW; ++j) pq[j] = V(0);
+        product_rpw<V>(rp, a.ptr, a.idx, AV, P, r0, r1, [&](int64_t row, int c, VT acc) {
+          const int64_t e = row * CH + c;
+          reinterpret_cast<VT*>(Q)[e] = acc;
+          const VT pv = reinterpret_cast<const VT*>(P)[e];
+          const V* pe = reinterpret_cast<const V*>(&pv);
+          const V* qe = reinterpret_cast<const V*>(&acc);
+#pragma unroll
+          for (int j = 0; j < VW; ++j) pq[j] = pe[j] * qe[j] + pq[j];
+        });
+#pragma unroll
+        for (int j = 0; j < VW; ++j) v[0][j] = (double)pq[j];
+        const double s = group_reduce<VW, 1>(a, v, red, par, g, s_flag, ok);
+        if (!ok) return false;
+        if (t < kRhs) {
+          double al = 0.0;
+          if ((st.iact >> t) & 1u) {
+            if (!isfinite(s) || !(s > 0.0))
+              st.bd[t] = 1;
+            else
+              al = st.rr[t] / s;
           }
+          st.alpha[t] = al;
         }
         __syncthreads();
       }
-      if (st.zero) {  // b = 0: x = 0
-        const unsigned zm = st.zero;
-        for (int64_t row = r0 + t; row < r1; row += NT)
-          for (int k = 0; k < a.nrhs; ++k)
-            if ((zm >> k) & 1u) a.X[row * a.nrhs + k] = 0.0;
-      }
-      const unsigned oact = st.oact;
-      if (oact == 0) break;
-      // inner setup: R = P = r / ||r|| in V, D = 0, r'r
+      // x_inner += alpha p, r -= alpha q, r'r   (alpha = 0 leaves a stopped column unchanged)
       {
-        double v[1][VW];
-#pragma unroll
-        for (int j = 0; j < VW; ++j) v[0][j] = 0.0;
-        V pr[VW];
-#pragma unroll
-        for (int j = 0; j < VW; ++j) pr[j] = V(0);
-        double nrv[VW];
-        bool on[VW];
+        V al[VW], pr[VW];
 #pragma unroll
         for (int j = 0; j < VW; ++j) {
-          on[j] = (oact >> (ch * VW + j)) & 1u;
-          nrv[j] = on[j] ? st.nr[ch * VW + j] : 1.0;
+          al[j] = (V)st.alpha[ch * VW + j];
+          pr[j] = V(0);
         }
         for (int64_t e = e0 + t; e < e1; e += NT) {
-          VT rv;
+          const VT pv = reinterpret_cast<const VT*>(P)[e];
+          const VT qv = reinterpret_cast<const VT*>(Q)[e];
+          VT dv = reinterpret_cast<const VT*>(D)[e];
+          VT rv = reinterpret_cast<const VT*>(R)[e];
+          const V* pe = reinterpret_cast<const V*>(&pv);
+          const V* qe = reinterpret_cast<const V*>(&qv);
+          V* de = reinterpret_cast<V*>(&dv);
           V* re = reinterpret_cast<V*>(&rv);
 #pragma unroll
           for (int j = 0; j < VW; ++j) {
-            re[j] = on[j] ? (V)(a.R64[e * VW + j] / nrv[j]) : V(0);
+            de[j] = al[j] * pe[j] + de[j];
+            re[j] = -al[j] * qe[j] + re[j];
             pr[j] = re[j] * re[j] + pr[j];
           }
+          reinterpret_cast<VT*>(D)[e] = dv;
           reinterpret_cast<VT*>(R)[e] = rv;
-          reinterpret_cast<VT*>(P)[e] = rv;
-          reinterpret_cast<VT*>(D)[e] = VT{};
         }
+        double v[1][VW];
 #pragma unroll
         for (int j = 0; j < VW; ++j) v[0][j] = (double)pr[j];
-        const double s = cluster_reduce<VW, 1>(v, red, par, C);
+        const double s = group_reduce<VW, 1>(a, v, red, par, g, s_flag, ok);
+        if (!ok) return false;
         if (t < 32) {
           bool go = false;
-          if (t < kRhs && ((oact >> t) & 1u)) {
-            st.rr[t] = s;
-            st.nr0[t] = sqrt(s);
-            st.kin[t] = 0;
-            st.bd[t] = 0;
-            go = st.nr0[t] > 0.0 && !(sqrt(s) <= st.itol[t] * st.nr0[t]) && st.used[t] < st.maxit;
-          }
-          const unsigned m = __ballot_sync(~0u, go);
-          if (t == 0) st.iact = m;
-        }
-        __syncthreads();  // P, R of every CTA written before the first product (cluster_reduce synced them)
-      }
-      // inner CG, one right-hand side per bit of st.iact
-      while (st.iact) {
-        // q = A p, p'q
-        {
-          double v[1][VW];
-          V pq[VW];
-#pragma unroll
-          for (int j = 0; j < VW; ++j) pq[j] = V(0);
-          product_rpw<V>(rp, a.ptr, a.idx, AV, P, r0, r1, [&](int64_t row, int c, VT acc) {
-            const int64_t e = row * CH + c;
-            reinterpret_cast<VT*>(Q)[e] = acc;
-            const VT pv = reinterpret_cast<const VT*>(P)[e];
-            const V* pe = reinterpret_cast<const V*>(&pv);
-            const V* qe = reinterpret_cast<const V*>(&acc);
-#pragma unroll
-            for (int j = 0; j < VW; ++j) pq[j] = pe[j] * qe[j] + pq[j];
-          });
-#pragma unroll
-          for (int j = 0; j < VW; ++j) v[0][j] = (double)pq[j];
-          const double s = cluster_reduce<VW, 1>(v, red, par, C);
-          if (t < kRhs) {
-            double al = 0.0;
-            if ((st.iact >> t) & 1u) {
-              if (!isfinite(s) || !(s > 0.0))
-                st.bd[t] = 1;
-              else
-                al = st.rr[t] / s;
-            }
-            st.alpha[t] = al;
-          }
-          __syncthreads();
-        }
-        // x_inner += alpha p, r -= alpha q, r'r   (alpha = 0 leaves a stopped column unchanged)
-        {
-          V al[VW];
-#pragma unroll
-          for (int j = 0; j < VW; ++j) al[j] = (V)st.alpha[ch * VW + j];
-          V pr[VW];
-#pragma unroll
-          for (int j = 0; j < VW; ++j) pr[j] = V(0);
-          for (int64_t e = e0 + t; e < e1; e += NT) {
-            const VT pv = reinterpret_cast<const VT*>(P)[e];
-            const VT qv = reinterpret_cast<const VT*>(Q)[e];
-            VT dv = reinterpret_cast<const VT*>(D)[e];
-            VT rv = reinterpret_cast<const VT*>(R)[e];
-            const V* pe = reinterpret_cast<const V*>(&pv);
-            const V* qe = reinterpret_cast<const V*>(&qv);
-            V* de = reinterpret_cast<V*>(&dv);
-            V* re = reinterpret_cast<V*>(&rv);
-#pragma unroll
-            for (int j = 0; j < VW; ++j) {
-              de[j] = al[j] * pe[j] + de[j];
-              re[j] = -al[j] * qe[j] + re[j];
-              pr[j] = re[j] * re[j] + pr[j];
-            }
-            reinterpret_cast<VT*>(D)[e] = dv;
-            reinterpret_cast<VT*>(R)[e] = rv;
-          }
-          double v[1][VW];
-#pragma unroll
-          for (int j = 0; j < VW; ++j) v[0][j] = (double)pr[j];
-          const double s = cluster_reduce<VW, 1>(v, red, par, C);
-          if (t < 32) {
-            bool go = false;
-            if (t < kRhs && ((st.iact >> t) & 1u)) {
-              if (st.bd[t]) {
+          if (t < kRhs && ((st.iact >> t) & 1u)) {
+            if (st.bd[t]) {
+              st.beta[t] = 0.0;
+            } else {
+              st.kin[t] += 1;
+              st.used[t] += 1;
+              if (sqrt(s) <= st.itol[t] * st.nr0[t]) {
                 st.beta[t] = 0.0;
               } else {
-                st.kin[t] += 1;
-                st.used[t] += 1;
-                if (sqrt(s) <= st.itol[t] * st.nr0[t]) {
-                  st.beta[t] = 0.0;
-                } else {
-                  st.beta[t] = s / st.rr[t];
-                  st.rr[t] = s;
-                  go = st.used[t] < st.maxit;
-                }
+                st.beta[t] = s / st.rr[t];
+                st.rr[t] = s;
+                go = st.used[t] < st.maxit;
               }
-            } else if (t < kRhs) {
-              st.beta[t] = 0.0;
             }
-            const unsigned m = __ballot_sync(~0u, go);
-            if (t == 0) {
-              st.iact = m;
-              st.products += 1;
-            }
+          } else if (t < kRhs) {
+            st.beta[t] = 0.0;
           }
-          __syncthreads();
-        }
-        if (!st.iact) break;
-        // p = r + beta p
-        {
-          V be[VW];
-#pragma unroll
-          for (int j = 0; j < VW; ++j) be[j] = (V)st.beta[ch * VW + j];
-          for (int64_t e = e0 + t; e < e1; e += NT) {
-            const VT rv = reinterpret_cast<const VT*>(R)[e];
-            VT pv = reinterpret_cast<const VT*>(P)[e];
-            const V* re = reinterpret_cast<const V*>(&rv);
-            V* pe = reinterpret_cast<V*>(&pv);
-#pragma unroll
-            for (int j = 0; j < VW; ++j) pe[j] = be[j] * pe[j] + re[j];
-            reinterpret_cast<VT*>(P)[e] = pv;
+          const unsigned m = __ballot_sync(~0u, go);
+          if (t == 0) {
+            st.iact = m;
+            st.products += 1;
           }
-          cluster_sync();  // the new p of every CTA is visible to the next product
         }
+        __syncthreads();
       }
-      // x += ||r|| x_inner in double precision; a breakdown before any
-      // inner iteration ends that right-hand side
+      if (!st.iact) break;
+      // p = r + beta p
       {
-        double nrv[VW];
-        bool on[VW];
+        V be[VW];
 #pragma unroll
-        for (int j = 0; j < VW; ++j) {
-          const int k = ch * VW + j;
-          on[j] = ((oact >> k) & 1u) && k < a.nrhs;
-          nrv[j] = on[j] ? st.nr[k] : 0.0;
-        }
+        for (int j = 0; j < VW; ++j) be[j] = (V)st.beta[ch * VW + j];
         for (int64_t e = e0 + t; e < e1; e += NT) {
-          const VT dv = reinterpret_cast<const VT*>(D)[e];
-          const V* de = reinterpret_cast<const V*>(&dv);
-          const int64_t row = e / CH;
+          const VT rv = reinterpret_cast<const VT*>(R)[e];
+          VT pv = reinterpret_cast<const VT*>(P)[e];
+          const V* re = reinterpret_cast<const V*>(&rv);
+          V* pe = reinterpret_cast<V*>(&pv);
 #pragma unroll
-          for (int j = 0; j < VW; ++j)
-            if (on[j]) {
-              double* xp = a.X + row * a.nrhs + ch * VW + j;
-              *xp = fma(nrv[j], (double)de[j], *xp);
-            }
+          for (int j = 0; j < VW; ++j) pe[j] = be[j] * pe[j] + re[j];
+          reinterpret_cast<VT*>(P)[e] = pv;
         }
-        if (t < 32) {
-          bool stop = false;
-          if (t < kRhs && ((oact >> t) & 1u)) {
-            st.outer[t] += 1;
-            // p'Ap <= 0: in double precision the Section III iteration stops
-            // there; the refinement stops only when no inner step was taken
-            if (st.bd[t] && (sizeof(V) == 8 || st.kin[t] == 0)) {
-              st.status[t] = kNotSpd;
-              stop = true;
-            }
-          }
-          const unsigned m = __ballot_sync(~0u, stop);
-          if (t == 0) st.fin |= m;
-        }
-        cluster_sync();  // x of every CTA is visible to the next residual product
+        if (!group_sync(a, g, s_flag)) return false;  // the new p of every CTA is visible to the next product
       }
     }
-    if (t < a.nrhs) {
+    // x += ||r|| x_inner in double precision; a breakdown before any
+    // inner iteration ends that right-hand side
+    {
+      double nrv[VW];
+      bool on[VW];
+#pragma unroll
+      for (int j = 0; j < VW; ++j) {
+        const int k = ch * VW + j;
+        on[j] = ((oact >> k) & 1u) && k < a.nrhs;
+        nrv[j] = on[j] ? st.nr[k] : 0.0;
+      }
+      for (int64_t e = e0 + t; e < e1; e += NT) {
+        const VT dv = reinterpret_cast<const VT*>(D)[e];
+        const V* de = reinterpret_cast<const V*>(&dv);
+        const int64_t row = e / CH;
+#pragma unroll
+        for (int j = 0; j < VW; ++j)
+          if (on[j]) {
+            double* xp = a.X + row * a.nrhs + ch * VW + j;
+            *xp = fma(nrv[j], (double)de[j], *xp);
+          }
+      }
+      if (t < 32) {
+        bool stop = false;
+        if (t < kRhs && ((oact >> t) & 1u)) {
+          st.outer[t] += 1;
+          // p'Ap <= 0: in double precision the Section III iteration stops
+          // there; the refinement stops only when no inner step was taken
+          if (st.bd[t] && (sizeof(V) == 8 || st.kin[t] == 0)) {
+            st.status[t] = kNotSpd;
+            stop = true;
+          }
+        }
+        const unsigned m = __ballot_sync(~0u, stop);
+        if (t == 0) st.fin |= m;
+      }
+      if (!group_sync(a, g, s_flag)) return false;  // x of every CTA is visible to the next residual product
+    }
+  }
+  return true;
+}
+
+// The persistent batched solver.  V is the precision of the inner CG (float:
+// Section IV's single-precision iteration inside double-precision
+// refinement; double: double precision throughout, where each refinement
+// pass is a restart of the Section III iteration from the current x).  Each
+// cluster takes queue slots in order; a slot is (instance, part) and an
+// instance of G parts is solved by the G clusters that take its G slots.
+template <typename V, int NT>
+__global__ void __launch_bounds__(NT, 1024 / NT) k_bcg(const BArgs* __restrict__ args) {
+  __shared__ BArgs a;
+  __shared__ Red red;
+  __shared__ St st;
+  __shared__ int s_next, s_flag;
+  __shared__ Group g;
+  if (threadIdx.x == 0) {
+    a = *args;
+    g.C = cluster_ctas();
+    g.cr = cluster_rank();
+  }
+  __syncthreads();
+  const int t = threadIdx.x;
+  int par = 0;
+  cluster_sync();  // every CTA of the cluster is running before any shared-memory access across CTAs
+  for (;;) {
+    if (g.cr == 0 && t == 0) s_next = ld_relaxed_s32(a.err) != 0 ? a.nslots : atomicAdd(a.queue, 1);
+    cluster_sync();
+    const int qpos = ld_dsmem_s32(&s_next, 0);
+    cluster_sync();
+    if (qpos >= a.nslots) break;
+    const int inst = a.slot_inst[qpos];
+    if (t == 0) {
+      g.p = a.slot_part[qpos];
+      g.G = a.grp[inst];
+      g.bar = a.gbar + inst;
+      g.part = a.gpart + (int64_t)inst * (2 * kMaxGroup * 2 * kRhs);
+      g.target = 0;
+      g.gpar = 0;
+    }
+    __syncthreads();
+    const bool lead = g.p == 0 && g.cr == 0;
+    if (lead && t == 0) a.t_inst[2 * inst] = now_ns();
+    const bool ok = solve_instance<V, NT>(a, inst, g, red, st, par, &s_flag);
+    if (!ok) {
+      if (lead && t < a.nrhs) {
+        gbcg_batch_info o = {st.used[t], st.outer[t], (int)kTimeout, 0, st.rel[t]};
+        a.out[(int64_t)inst * a.nrhs + t] = o;
+      }
+      break;
+    }
+    if (lead && t < a.nrhs) {
       gbcg_batch_info o;
       o.iterations = st.used[t];
       o.outer = st.outer[t];
       o.status = st.status[t];
       o.pad_ = 0;
       o.rel_res_true = st.rel[t];
-      if (cr == 0) a.out[(int64_t)inst * a.nrhs + t] = o;
+      a.out[(int64_t)inst * a.nrhs + t] = o;
     }
-    if (cr == 0 && t == 0) {
+    if (lead && t == 0) {
       a.inst_iters[inst] = st.products;
       a.inst_outer[inst] = st.outers;
       a.t_inst[2 * inst + 1] = now_ns();
@@ -690,7 +811,12 @@ struct gbcg_batch_s {
   std::vector<int64_t> row_off, nnz_of;
   std::vector<int> bucket;
   int64_t* d_inst_row = nullptr;
-  int32_t *d_ptr = nullptr, *d_idx = nullptr, *d_order = nullptr;
+  int32_t *d_ptr = nullptr, *d_idx = nullptr, *d_slot_inst = nullptr, *d_slot_part = nullptr;
+  int8_t* d_grp = nullptr;
+  unsigned* d_gbar = nullptr;
+  double* d_gpart = nullptr;
+  int* d_err = nullptr;
+  int* h_err = nullptr;  // pinned
   double* d_val64 = nullptr;
   float* d_val32 = nullptr;
   int8_t* d_rpw = nullptr;
@@ -706,8 +832,10 @@ struct gbcg_batch_s {
   gbcg_batch_info* h_out = nullptr; // pinned
   int32_t *h_iters = nullptr, *h_outer = nullptr;
   long long* h_t = nullptr;
-  std::vector<int32_t> order;
+  std::vector<double> weight;      // per instance: expected cluster time (a priori, then measured)
   std::vector<int8_t> rpw_loaded;  // per-instance rows per warp now in d_rpw
+  std::vector<int8_t> grp_loaded;  // schedule now on the device
+  std::vector<int32_t> sinst_loaded, spart_loaded;
   Tuning tune[2];        // [0] double inner, [1] float inner
   bool tuned[2] = {false, false};
   int clusters[2] = {0, 0};
@@ -736,12 +864,13 @@ void free_batch(gbcg_batch_s* B) {
     if (B->exec[i]) cudaGraphExecDestroy(B->exec[i]);
     if (B->graph[i]) cudaGraphDestroy(B->graph[i]);
   }
-  void* dev[] = {B->d_inst_row, B->d_ptr, B->d_idx, B->d_order, B->d_val64, B->d_val32, B->d_rpw, B->d_R64,
-                 B->d_R,        B->d_P,   B->d_Q,   B->d_D,     B->d_Bst,   B->d_Xst,   B->d_queue, B->d_out,
-                 B->d_iters,    B->d_outer, B->d_t, B->d_args};
+  void* dev[] = {B->d_inst_row, B->d_ptr,  B->d_idx,  B->d_slot_inst, B->d_slot_part, B->d_grp,  B->d_gbar,
+                 B->d_gpart,    B->d_err,  B->d_val64, B->d_val32,  B->d_rpw,       B->d_R64,  B->d_R,
+                 B->d_P,        B->d_Q,    B->d_D,     B->d_Bst,    B->d_Xst,       B->d_queue, B->d_out,
+                 B->d_iters,    B->d_outer, B->d_t,    B->d_args};
   for (void* p : dev)
     if (p) cudaFree(p);
-  void* host[] = {B->h_args, B->h_out, B->h_iters, B->h_outer, B->h_t};
+  void* host[] = {B->h_args, B->h_out, B->h_iters, B->h_outer, B->h_t, B->h_err};
   for (void* p : host)
     if (p) cudaFreeHost(p);
   if (B->cap) cudaStreamDestroy(B->cap);
@@ -797,6 +926,71 @@ int apply_rpw(gbcg_batch_s* B, const Tuning& T, bool f32, cudaStream_t s) {
   return 0;
 }
 
+// Queue of (instance, part) slots.  Instances whose expected cluster time
+// exceeds the average load per cluster span G clusters (a power of two, at
+// most max_group, the groups together holding at most half the clusters),
+// so that no single instance outlasts the rest of the batch.  Groups come
+// first in the queue, then single-cluster instances, each longest first.
+void make_schedule(const gbcg_batch_s* B, int clusters, int max_group, int force_group, std::vector<int8_t>& grp,
+                   std::vector<int32_t>& sinst, std::vector<int32_t>& spart) {
+  const int n = B->count;
+  const std::vector<double>& w = B->weight;
+  grp.assign(n, 1);
+  const int gmax = std::max(1, std::min(std::min(max_group, kMaxGroup), clusters));
+  std::vector<int32_t> ord(n);
+  std::iota(ord.begin(), ord.end(), 0);
+  std::stable_sort(ord.begin(), ord.end(), [&](int p, int q) { return w[p] > w[q]; });
+  if (force_group > 0) {
+    const int G = std::min(force_group, gmax);
+    for (int i = 0; i < n; ++i) grp[i] = (int8_t)G;
+  } else if (gmax > 1 && clusters > 1) {
+    const double W = std::accumulate(w.begin(), w.end(), 0.0) / clusters;
+    int budget = clusters / 2;
+    for (int i : ord) {
+      if (!(w[i] > W)) break;
+      int G = 1;
+      while (G < gmax && w[i] / G > W) G *= 2;
+      if (G > 1 && G <= budget) {
+        grp[i] = (int8_t)G;
+        budget -= G;
+      }
+    }
+  }
+  std::stable_sort(ord.begin(), ord.end(), [&](int p, int q) {
+    const bool gp = grp[p] > 1, gq = grp[q] > 1;
+    if (gp != gq) return gp;
+    return w[p] / grp[p] > w[q] / grp[q];
+  });
+  sinst.clear();
+  spart.clear();
+  for (int i : ord)
+    for (int part = 0; part < grp[i]; ++part) {
+      sinst.push_back(i);
+      spart.push_back(part);
+    }
+}
+
+int upload_schedule(gbcg_batch_s* B, const std::vector<int8_t>& grp, const std::vector<int32_t>& sinst,
+                    const std::vector<int32_t>& spart, cudaStream_t s) {
+  if (grp == B->grp_loaded && sinst == B->sinst_loaded && spart == B->spart_loaded) return 0;
+  BCUDA(cudaMemcpyAsync(B->d_grp, grp.data(), grp.size(), cudaMemcpyHostToDevice, s));
+  BCUDA(cudaMemcpyAsync(B->d_slot_inst, sinst.data(), sizeof(int32_t) * sinst.size(), cudaMemcpyHostToDevice, s));
+  BCUDA(cudaMemcpyAsync(B->d_slot_part, spart.data(), sizeof(int32_t) * spart.size(), cudaMemcpyHostToDevice, s));
+  BCUDA(cudaStreamSynchronize(s));
+  B->grp_loaded = grp;
+  B->sinst_loaded = sinst;
+  B->spart_loaded = spart;
+  return 0;
+}
+
+// The single-cluster schedule (every G = 1), longest first.
+int single_schedule(gbcg_batch_s* B, cudaStream_t s) {
+  std::vector<int8_t> grp;
+  std::vector<int32_t> si, sp;
+  make_schedule(B, 1, 1, 0, grp, si, sp);
+  return upload_schedule(B, grp, si, sp, s);
+}
+
 BArgs base_args(gbcg_batch_s* B) {
   BArgs a = {};
   a.inst_row = B->d_inst_row;
@@ -804,7 +998,14 @@ BArgs base_args(gbcg_batch_s* B) {
   a.idx = B->d_idx;
   a.val64 = B->d_val64;
   a.val32 = B->d_val32;
-  a.order = B->d_order;
+  a.slot_inst = B->d_slot_inst;
+  a.slot_part = B->d_slot_part;
+  a.grp = B->d_grp;
+  a.gbar = B->d_gbar;
+  a.gpart = B->d_gpart;
+  a.err = B->d_err;
+  a.nslots = (int)B->sinst_loaded.size();
+  a.timeout_ns = 1000000000LL;
   a.rpw = B->d_rpw;
   a.R64 = B->d_R64;
   a.R = B->d_R;
@@ -826,6 +1027,7 @@ BArgs base_args(gbcg_batch_s* B) {
 // per-instance table).  Returns the launch time and fills h_t.
 int probe(gbcg_batch_s* B, bool f32, int threads, int cluster, int clusters, int rpw, int iters, const double* Bp,
           double* Xp, cudaStream_t s, float* ms) {
+  if (int rc = single_schedule(B, s)) return rc;
   BArgs a = base_args(B);
   a.B = Bp;
   a.X = Xp;
@@ -838,6 +1040,8 @@ int probe(gbcg_batch_s* B, bool f32, int threads, int cluster, int clusters, int
   BCUDA(cudaMemcpyAsync(B->d_args, B->h_args, sizeof(BArgs), cudaMemcpyHostToDevice, s));
   BCUDA(cudaMemsetAsync(Xp, 0, sizeof(double) * (size_t)std::max<int64_t>(1, B->n_tot) * B->nrhs, s));
   BCUDA(cudaMemsetAsync(B->d_queue, 0, sizeof(int), s));
+  BCUDA(cudaMemsetAsync(B->d_err, 0, sizeof(int), s));
+  BCUDA(cudaMemsetAsync(B->d_gbar, 0, sizeof(unsigned) * B->count, s));
   BCUDA(cudaEventRecord(B->ev0, s));
   if (int rc = launch(kernel_for(f32, threads), threads, cluster, clusters, B->d_args, s)) return rc;
   BCUDA(cudaEventRecord(B->ev1, s));
@@ -957,6 +1161,9 @@ int capture(gbcg_batch_s* B, bool f32) {
   };
   step(cudaMemcpyAsync(B->d_args, B->h_args, sizeof(BArgs), cudaMemcpyHostToDevice, s), "capture args");
   step(cudaMemsetAsync(B->d_queue, 0, sizeof(int), s), "capture queue reset");
+  step(cudaMemsetAsync(B->d_err, 0, sizeof(int), s), "capture error reset");
+  step(cudaMemsetAsync(B->d_out, 0, sizeof(gbcg_batch_info) * (size_t)B->count * B->nrhs, s), "capture info reset");
+  step(cudaMemsetAsync(B->d_gbar, 0, sizeof(unsigned) * B->count, s), "capture group barrier reset");
   if (!rc) rc = launch(kernel_for(f32, T.threads), T.threads, T.cluster, nc, B->d_args, s);
   step(cudaMemcpyAsync(B->h_out, B->d_out, sizeof(gbcg_batch_info) * (size_t)B->count * B->nrhs,
                        cudaMemcpyDeviceToHost, s),
@@ -964,6 +1171,7 @@ int capture(gbcg_batch_s* B, bool f32) {
   step(cudaMemcpyAsync(B->h_iters, B->d_iters, sizeof(int32_t) * B->count, cudaMemcpyDeviceToHost, s), "capture iters");
   step(cudaMemcpyAsync(B->h_outer, B->d_outer, sizeof(int32_t) * B->count, cudaMemcpyDeviceToHost, s), "capture outer");
   step(cudaMemcpyAsync(B->h_t, B->d_t, sizeof(long long) * 2 * B->count, cudaMemcpyDeviceToHost, s), "capture times");
+  step(cudaMemcpyAsync(B->h_err, B->d_err, sizeof(int), cudaMemcpyDeviceToHost, s), "capture error flag");
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamEndCapture(s, &g);
   if (rc) {
@@ -1074,15 +1282,11 @@ int gbcg_batch_create(gbcg_batch_t* out, int32_t count, const int64_t* row_off, 
     B->nnz_of[i] = (int64_t)ptr[row_off[i + 1]] - ptr[row_off[i]];
     B->bucket[i] = bucket_of(row_off[i + 1] - row_off[i], B->nnz_of[i]);
   }
-  // longest first by an a-priori estimate (entries x rows^(1/3): CG
-  // iterations of these systems grow with the mesh diameter)
-  B->order.resize(count);
-  std::iota(B->order.begin(), B->order.end(), 0);
-  std::stable_sort(B->order.begin(), B->order.end(), [&](int a, int b) {
-    const double wa = (double)B->nnz_of[a] * std::cbrt((double)(row_off[a + 1] - row_off[a]));
-    const double wb = (double)B->nnz_of[b] * std::cbrt((double)(row_off[b + 1] - row_off[b]));
-    return wa > wb;
-  });
+  // a-priori cluster time: entries x rows^(1/3) (CG iterations of these
+  // systems grow with the mesh diameter); replaced by measured times
+  B->weight.resize(count);
+  for (int i = 0; i < count; ++i)
+    B->weight[i] = (double)B->nnz_of[i] * std::cbrt((double)(row_off[i + 1] - row_off[i]));
   auto bail = [&](int code) {
     free_batch(B);
     return code;
@@ -1092,7 +1296,10 @@ int gbcg_batch_create(gbcg_batch_t* out, int32_t count, const int64_t* row_off, 
   int rc = 0;
   if ((rc = balloc(B, &B->d_inst_row, count + 1)) || (rc = balloc(B, &B->d_ptr, n + 1)) ||
       (rc = balloc(B, &B->d_idx, nnz)) || (rc = balloc(B, &B->d_val64, nnz)) || (rc = balloc(B, &B->d_val32, nnz)) ||
-      (rc = balloc(B, &B->d_order, count)) || (rc = balloc(B, &B->d_rpw, count)) ||
+      (rc = balloc(B, &B->d_slot_inst, (size_t)count * kMaxGroup)) ||
+      (rc = balloc(B, &B->d_slot_part, (size_t)count * kMaxGroup)) || (rc = balloc(B, &B->d_grp, count)) ||
+      (rc = balloc(B, &B->d_gbar, count)) || (rc = balloc(B, &B->d_gpart, (size_t)count * 2 * kMaxGroup * 2 * kRhs)) ||
+      (rc = balloc(B, &B->d_err, 1)) || (rc = balloc(B, &B->d_rpw, count)) ||
       (rc = balloc(B, &B->d_R64, nv)) || (rc = balloc(B, (double**)&B->d_R, nv)) ||
       (rc = balloc(B, (double**)&B->d_P, nv)) || (rc = balloc(B, (double**)&B->d_Q, nv)) ||
       (rc = balloc(B, (double**)&B->d_D, nv)) || (rc = balloc(B, &B->d_Bst, (size_t)std::max<int64_t>(1, n) * nrhs)) ||
@@ -1110,7 +1317,8 @@ int gbcg_batch_create(gbcg_batch_t* out, int32_t count, const int64_t* row_off, 
       (rc = hostalloc((void**)&B->h_out, sizeof(gbcg_batch_info) * (size_t)count * nrhs)) ||
       (rc = hostalloc((void**)&B->h_iters, sizeof(int32_t) * count)) ||
       (rc = hostalloc((void**)&B->h_outer, sizeof(int32_t) * count)) ||
-      (rc = hostalloc((void**)&B->h_t, sizeof(long long) * 2 * count)))
+      (rc = hostalloc((void**)&B->h_t, sizeof(long long) * 2 * count)) ||
+      (rc = hostalloc((void**)&B->h_err, sizeof(int))))
     return bail(rc);
   if (cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreate(&B->ev0) != cudaSuccess || cudaEventCreate(&B->ev1) != cudaSuccess)
@@ -1127,13 +1335,13 @@ int gbcg_batch_create(gbcg_batch_t* out, int32_t count, const int64_t* row_off, 
     up(B->d_idx, idx, sizeof(int32_t) * nnz);
     up(B->d_val64, val, sizeof(double) * nnz);
     up(B->d_val32, v32.data(), sizeof(float) * nnz);
-    up(B->d_order, B->order.data(), sizeof(int32_t) * count);
     if (e == cudaSuccess) e = cudaMemsetAsync(B->d_out, 0, sizeof(gbcg_batch_info) * (size_t)count * nrhs, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return bail(fail(GBCG_ERR_CUDA, std::string("batch upload: ") + cudaGetErrorString(e)));
   }
   for (int f = 0; f < 2; ++f)
     if ((rc = apply_rpw(B, B->tune[f], f == 1, s))) return bail(rc);
+  if ((rc = single_schedule(B, s))) return bail(rc);
   if (tune) {
     if ((rc = autotune(B, true, nullptr, s))) return bail(rc);
     if ((rc = apply_rpw(B, B->tune[1], true, s))) return bail(rc);
@@ -1224,6 +1432,15 @@ int gbcg_batch_solve(gbcg_batch_t B, const double* b, double* x, double tol, int
   } else if ((rc = apply_rpw(B, B->tune[f32], f32, s))) {
     return rc;
   }
+  // schedule of this solve: group sizes from the expected cluster times
+  const int max_group = (opts && opts->max_group > 0) ? opts->max_group : kMaxGroup;
+  const int force_group = opts ? opts->force_group : 0;
+  {
+    std::vector<int8_t> grp;
+    std::vector<int32_t> si, sp;
+    make_schedule(B, B->clusters[f32], max_group, force_group, grp, si, sp);
+    if ((rc = upload_schedule(B, grp, si, sp, s))) return rc;
+  }
   const size_t nvb = sizeof(double) * (size_t)B->n_tot * B->nrhs;
   const double* bd = b;
   double* xd = x;
@@ -1243,6 +1460,7 @@ int gbcg_batch_solve(gbcg_batch_t B, const double* b, double* x, double tol, int
   a.maxit = maxit;
   a.max_outer = (opts && opts->max_outer > 0) ? opts->max_outer : (f32 ? 30 : 4);
   a.force_rpw = 0;
+  a.timeout_ns = (long long)((opts && opts->wait_timeout_ms > 0) ? opts->wait_timeout_ms : 1000) * 1000000LL;
   BCUDA(cudaStreamSynchronize(s));  // the previous solve's graph has read h_args
   *B->h_args = a;
   BCUDA(cudaEventRecord(B->ev0, s));
@@ -1264,18 +1482,16 @@ int gbcg_batch_solve(gbcg_batch_t B, const double* b, double* x, double tol, int
       if (status == GBCG_OK && o.status != GBCG_OK) status = o.status;
     }
   }
+  if (*B->h_err) {
+    status = GBCG_ERR_TIMEOUT;
+    gbcg::set_last_error("a multi-cluster group wait ran out; instances not reached report zeros");
+  }
   if (infos) memcpy(infos, B->h_out, sizeof(gbcg_batch_info) * (size_t)B->count * B->nrhs);
-  if (B->reorder && !(opts && opts->fixed_order)) {
-    // next solve: longest measured instance first
-    std::vector<long long> dur(B->count);
-    for (int i = 0; i < B->count; ++i) dur[i] = B->h_t[2 * i + 1] - B->h_t[2 * i];
-    std::vector<int32_t> ord(B->count);
-    std::iota(ord.begin(), ord.end(), 0);
-    std::stable_sort(ord.begin(), ord.end(), [&](int p, int q) { return dur[p] > dur[q]; });
-    if (ord != B->order) {
-      B->order = ord;
-      BCUDA(cudaMemcpyAsync(B->d_order, B->order.data(), sizeof(int32_t) * B->count, cudaMemcpyHostToDevice, s));
-      BCUDA(cudaStreamSynchronize(s));
+  if (B->reorder && !(opts && opts->fixed_order) && !*B->h_err) {
+    // next solve: measured cluster time (duration x clusters of the group)
+    for (int i = 0; i < B->count; ++i) {
+      const long long d = B->h_t[2 * i + 1] - B->h_t[2 * i];
+      if (d > 0) B->weight[i] = (double)d * B->grp_loaded[i];
     }
   }
   if (rep) {
@@ -1290,17 +1506,76 @@ int gbcg_batch_solve(gbcg_batch_t B, const double* b, double* x, double tol, int
     rep->threads = T.threads;
     rep->cluster = T.cluster;
     rep->clusters = B->clusters[f32];
+    for (int i = 0; i < B->count; ++i) {
+      if (B->grp_loaded[i] > 1) rep->groups += 1;
+      rep->max_group = std::max<int32_t>(rep->max_group, B->grp_loaded[i]);
+    }
     long long lo = 0, hi = 0, busy = 0;
     for (int i = 0; i < B->count; ++i) {
       const long long a0 = B->h_t[2 * i], a1 = B->h_t[2 * i + 1];
       if (i == 0 || a0 < lo) lo = a0;
       if (i == 0 || a1 > hi) hi = a1;
-      busy += a1 - a0;
+      busy += (a1 - a0) * B->grp_loaded[i];
     }
     rep->span_ms = (double)(hi - lo) * 1e-6;
     rep->busy_fraction = (hi > lo && B->clusters[f32] > 0) ? (double)busy / ((double)(hi - lo) * B->clusters[f32]) : 0.0;
   }
   return status;
+}
+
+int gbcg_batch_selftest_group_timeout(gbcg_batch_t B, int32_t timeout_ms, void* stream) {
+  gbcg::set_last_error("");
+  if (!B) return fail(GBCG_ERR_INVALID, "null batch handle");
+  if (timeout_ms <= 0) return fail(GBCG_ERR_INVALID, "timeout_ms must be > 0");
+  cudaStream_t s = (cudaStream_t)stream;
+  const Tuning& T = B->tune[1];
+  int nc = 0;
+  if (int rc = max_clusters(kernel_for(true, T.threads), T.threads, T.cluster, &nc)) return rc;
+  if (nc < 2) return fail(GBCG_ERR_CUDA, "the self-test needs two co-resident clusters");
+  // every instance on one cluster, except the last, a group of two whose
+  // second slot is left out of the queue: its first part waits for a
+  // partner that never comes
+  std::vector<int8_t> grp;
+  std::vector<int32_t> si, sp;
+  make_schedule(B, 1, 1, 0, grp, si, sp);
+  const int last = si.back();
+  grp[last] = 2;
+  if (int rc = upload_schedule(B, grp, si, sp, s)) return rc;
+  if (int rc = apply_rpw(B, T, true, s)) return rc;
+  const size_t nv = (size_t)std::max<int64_t>(1, B->n_tot) * B->nrhs;
+  double *Bp = nullptr, *Xp = nullptr;
+  BCUDA(cudaMalloc(&Bp, sizeof(double) * nv));
+  cudaError_t e = cudaMalloc(&Xp, sizeof(double) * nv);
+  if (e != cudaSuccess) {
+    cudaFree(Bp);
+    return fail(GBCG_ERR_NOMEM, "self-test buffers");
+  }
+  BArgs a = base_args(B);
+  a.B = Bp;
+  a.X = Xp;
+  a.tol = 0.0;
+  a.inner_tol = 0.0;
+  a.maxit = 2;
+  a.max_outer = 1;
+  a.timeout_ns = (long long)timeout_ms * 1000000LL;
+  *B->h_args = a;
+  int rc = 0;
+  auto step = [&](cudaError_t c, const char* what) {
+    if (!rc && c != cudaSuccess) rc = fail(GBCG_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(c));
+  };
+  step(cudaMemsetAsync(Bp, 0, sizeof(double) * nv, s), "self-test b");
+  step(cudaMemsetAsync(Xp, 0, sizeof(double) * nv, s), "self-test x");
+  step(cudaMemcpyAsync(B->d_args, B->h_args, sizeof(BArgs), cudaMemcpyHostToDevice, s), "self-test args");
+  step(cudaMemsetAsync(B->d_queue, 0, sizeof(int), s), "self-test queue");
+  step(cudaMemsetAsync(B->d_err, 0, sizeof(int), s), "self-test error flag");
+  step(cudaMemsetAsync(B->d_gbar, 0, sizeof(unsigned) * B->count, s), "self-test group barriers");
+  if (!rc) rc = launch(kernel_for(true, T.threads), T.threads, T.cluster, nc, B->d_args, s);
+  step(cudaMemcpyAsync(B->h_err, B->d_err, sizeof(int), cudaMemcpyDeviceToHost, s), "self-test error read");
+  step(cudaStreamSynchronize(s), "self-test sync");
+  cudaFree(Bp);
+  cudaFree(Xp);
+  if (rc) return rc;
+  return *B->h_err == kTimeout ? GBCG_ERR_TIMEOUT : GBCG_OK;
 }
 
 int gbcg_batch_instance_times(gbcg_batch_t B, int64_t* t_ns, int32_t* products, int32_t* outer_products) {

@@ -164,14 +164,51 @@ def test_every_launch_configuration(torch, small):
     assert ran >= 60
 
 
-def test_result_is_independent_of_the_schedule(torch, small):
-    """The second solve runs with the queue reordered by the first one's
-    measured times; every instance's result is bit-identical."""
+@pytest.mark.parametrize("G", [2, 4, 8])
+def test_instances_spanning_several_clusters(torch, small, G):
+    """Every instance split over G clusters (global-memory sums and bounded
+    group barriers): same gates against the oracle, and the same bits on a
+    repeated solve with the same schedule."""
+    maxit = 50 * int(np.diff(small.row_off).max())
+    Xo, res = oracle.batch_solve(small.row_off, small.ptr, small.idx, small.val, small.B, tol=TOL, maxit=maxit,
+                                 precision="fp32_ir")
     with gb.Batch(small.row_off, small.ptr, small.idx, small.val, nrhs=8, tune=False) as Bt:
         b = torch.from_numpy(small.B).cuda()
-        x1, i1, r1 = Bt.solve(b, tol=TOL, maxit=100000)
+        x1, infos, rep = Bt.solve(b, tol=TOL, maxit=maxit, force_group=G, fixed_order=True)
+        x2, infos2, rep2 = Bt.solve(b, tol=TOL, maxit=maxit, force_group=G, fixed_order=True)
+    assert rep["status"] == "OK", rep
+    assert rep["max_group"] == min(G, rep["clusters"]) and rep["groups"] == small.count
+    assert torch.equal(x1, x2) and np.array_equal(infos, infos2)
+    assert true_rel_res(small, x1.cpu().numpy()).max() <= TOL
+    for i in range(small.count):
+        for k in range(8):
+            o = res[i][k]
+            assert abs(int(infos[i, k]["iterations"]) - o.iterations) <= 0.10 * o.iterations + 10, (i, k)
+
+
+def test_group_wait_times_out_cleanly(torch, small):
+    """A group member that never arrives: the waiting cluster gives up after
+    the bound, the launch ends with GBCG_ERR_TIMEOUT and the context stays
+    usable for the next solve."""
+    maxit = 50 * int(np.diff(small.row_off).max())
+    with gb.Batch(small.row_off, small.ptr, small.idx, small.val, nrhs=8, tune=False) as Bt:
+        assert Bt.selftest_group_timeout(50) == 5
+        b = torch.from_numpy(small.B).cuda()
+        x, infos, rep = Bt.solve(b, tol=TOL, maxit=maxit)
+    assert rep["status"] == "OK"
+    assert true_rel_res(small, x.cpu().numpy()).max() <= TOL
+
+
+def test_result_is_independent_of_the_schedule(torch, small):
+    """The second solve runs with the queue reordered by the first one's
+    measured times; with single-cluster instances every result is
+    bit-identical (which cluster runs an instance, and when, does not enter
+    its arithmetic)."""
+    with gb.Batch(small.row_off, small.ptr, small.idx, small.val, nrhs=8, tune=False) as Bt:
+        b = torch.from_numpy(small.B).cuda()
+        x1, i1, r1 = Bt.solve(b, tol=TOL, maxit=100000, max_group=1)
         t1, p1, _ = Bt.instance_times()
-        x2, i2, r2 = Bt.solve(b, tol=TOL, maxit=100000)
+        x2, i2, r2 = Bt.solve(b, tol=TOL, maxit=100000, max_group=1)
         t2, p2, _ = Bt.instance_times()
     assert torch.equal(x1, x2)
     assert np.array_equal(i1, i2) and np.array_equal(p1, p2)
