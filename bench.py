@@ -52,7 +52,9 @@ def parse():
     ap.add_argument("--profile-iters", type=int, default=0,
                     help="only run solves capped at this many iterations (small case for ncu captures)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU-oracle sample")
-    ap.add_argument("--only-batched", action="store_true", help="only run the batched leg (for ncu captures)")
+    ap.add_argument("--only-batched", action="store_true", help="only run the batched leg")
+    ap.add_argument("--profile-batched", type=int, default=0,
+                    help="only one mixed-precision solve of the first N batch instances (small case for ncu)")
     ap.add_argument("--profile-spmv", action="store_true",
                     help="only run a few products (double then single precision) of --format, for ncu captures")
     return ap.parse_args()
@@ -222,6 +224,15 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     if args.only_batched:
         print(json.dumps({"batched": batched(torch, gb, args)}), flush=True)
+        return 0
+    if args.profile_batched:
+        bs = femgen.build_batch(femgen.batched_instances(256)[:args.profile_batched], nrhs=8)
+        with gb.Batch(bs.row_off, bs.ptr, bs.idx, bs.val, nrhs=8, tune=False) as Bt:
+            Bt.set_tuning("fp32_ir", 512, 4, [1, 1, 1, 16, 1, 1, 1, 1])
+            _, _, rep = Bt.solve(torch.from_numpy(bs.B).to(dev), tol=TOL, maxit=100000, precision="fp32_ir")
+            st = Bt.stats()
+        print(json.dumps({"profile_batched": args.profile_batched, "n": bs.n, "nnz": bs.nnz, "report": rep,
+                          "iter_bytes_fp32": st["iter_bytes_fp32"]}), flush=True)
         return 0
     g = GRIDS[args.grid]
     s = femgen.build_system(g)
