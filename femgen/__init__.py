@@ -111,6 +111,7 @@ def _load():
         vp = ctypes.c_void_p
         lib.femgen_size.argtypes = [P, i64p, i64p]
         lib.femgen_build.argtypes = [P, vp, vp, vp, vp, vp]
+        lib.femgen_elements.argtypes = [P, vp, vp, vp]
         lib.femgen_boxes.argtypes = [P, vp]
         lib.femgen_min_volume.argtypes = [P]
         lib.femgen_min_volume.restype = ctypes.c_double
@@ -267,6 +268,92 @@ def build_batch(grids, nrhs: int = 8) -> BatchSystem:
                        np.concatenate(idxs).astype(np.int32), np.concatenate(vals),
                        np.ascontiguousarray(np.concatenate(Bs, axis=0)),
                        np.ascontiguousarray(np.concatenate(Xs, axis=0)))
+
+
+@dataclass
+class Elements:
+    """Tetrahedra of a generated system: unknown index of each vertex (-1 for
+    an eliminated Dirichlet node), unit-coefficient element matrix
+    Kh = |V| G G' (4 x 4) and coefficient; A = sum_e coef_e Kh_e restricted to
+    the unknowns."""
+    nodes: np.ndarray   # int32[E, 4]
+    kh: np.ndarray      # float64[E, 4, 4]
+    coef: np.ndarray    # float64[E]
+
+    @property
+    def count(self) -> int:
+        return int(self.coef.shape[0])
+
+
+def elements(g: Grid) -> Elements:
+    lib = _load()
+    ne = 6 * (g.nx - 1) * (g.ny - 1) * (g.nz - 1)
+    nodes = np.empty((ne, 4), dtype=np.int32)
+    kh = np.empty((ne, 4, 4), dtype=np.float64)
+    coef = np.empty(ne, dtype=np.float64)
+    if lib.femgen_elements(ctypes.byref(g.params()), _ptr(nodes), _ptr(kh), _ptr(coef)):
+        raise ValueError(f"invalid grid {g}")
+    return Elements(nodes, kh, coef)
+
+
+def element_map(el: Elements, ptr: np.ndarray, idx: np.ndarray, storage: str = "csr"):
+    """Positions of the element matrices in a stored matrix.
+
+    Returns (pos int32[E, m], w float64[E, m]): entry k of element e adds
+    coef_e * w[e, k] to the stored value at pos[e, k] (-1: none).  "csr" (full
+    storage, or CSC of the symmetric matrix): m = 16, every vertex pair (a, b).
+    "sym" (upper triangle and diagonal): m = 10, the pairs a <= b, placed at
+    the stored entry (min(i, j), max(i, j)).  The assembly A = sum_e coef_e Kh_e
+    is then val[p] = sum over (e, k) with pos[e, k] = p of coef_e w[e, k].
+    """
+    E = el.count
+    pairs = [(a, b) for a in range(4) for b in range(4)] if storage == "csr" else \
+        [(a, b) for a in range(4) for b in range(a, 4)]
+    m = len(pairs)
+    pos = np.full((E, m), -1, dtype=np.int64)
+    w = np.zeros((E, m))
+    ptr = np.asarray(ptr, dtype=np.int64)
+    idx = np.asarray(idx, dtype=np.int64)
+    for k, (a, b) in enumerate(pairs):
+        i = el.nodes[:, a].astype(np.int64)
+        j = el.nodes[:, b].astype(np.int64)
+        ok = (i >= 0) & (j >= 0)
+        r = np.where(ok, np.minimum(i, j) if storage == "sym" else i, 0)
+        c = np.where(ok, np.maximum(i, j) if storage == "sym" else j, 0)
+        # position of column c in row r: rows hold sorted columns
+        lo = ptr[r]
+        hi = ptr[r + 1]
+        p = lo.copy()
+        step = hi - lo
+        while np.any(step > 0):  # vectorised lower bound
+            half = step // 2
+            mid = p + half
+            go = (step > 0) & (idx[np.minimum(mid, len(idx) - 1)] < c)
+            p = np.where(go, mid + 1, p)
+            step = np.where(go, step - half - 1, half)
+        found = ok & (p < hi) & (idx[np.minimum(p, len(idx) - 1)] == c)
+        if np.any(ok & ~found):
+            raise ValueError("an element pair is missing from the stored pattern")
+        pos[:, k] = np.where(found, p, -1)
+        w[:, k] = np.where(found, el.kh[:, a, b], 0.0)
+    return pos.astype(np.int32), w
+
+
+def assembly_map(pos: np.ndarray, w: np.ndarray, nnz: int):
+    """The element map by stored position: (tptr int64[nnz+1], telem int32,
+    tw float64) with the contributions (element, weight) of position p at
+    tptr[p]..tptr[p+1], elements increasing."""
+    E, m = pos.shape
+    p = pos.reshape(-1).astype(np.int64)
+    e = np.repeat(np.arange(E, dtype=np.int64), m)
+    ww = w.reshape(-1)
+    keep = p >= 0
+    p, e, ww = p[keep], e[keep], ww[keep]
+    order = np.lexsort((e, p))
+    p, e, ww = p[order], e[order], ww[order]
+    tptr = np.zeros(nnz + 1, dtype=np.int64)
+    np.add.at(tptr, p + 1, 1)
+    return np.cumsum(tptr), e.astype(np.int32), np.ascontiguousarray(ww)
 
 
 def random_vector(n: int, seed: int, lo: float = -1.0, hi: float = 1.0) -> np.ndarray:

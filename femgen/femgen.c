@@ -289,6 +289,32 @@ int femgen_build(const femgen_params* p, int32_t* ptr, int32_t* idx, double* val
   return 0;
 }
 
+/* Element data: for tetrahedron e = 6 * (ci + (nx-1) * (cj + (ny-1) * ck)) + t,
+ * the unknown index of each of its 4 vertices (-1 for an eliminated node),
+ * its unit-coefficient element matrix Kh = |V| G G' (4 x 4, row-major) and its
+ * coefficient, so that A = sum_e coef_e Kh_e over the unknown vertices. */
+int femgen_elements(const femgen_params* p, int32_t* nodes, double* kh, double* coef) {
+  fg_ctx c;
+  if (fg_init(&c, p)) return -1;
+  const int nx = p->nx, ny = p->ny, nz = p->nz;
+#pragma omp parallel for schedule(static)
+  for (int ck = 0; ck < nz - 1; ++ck)
+    for (int cj = 0; cj < ny - 1; ++cj)
+      for (int ci = 0; ci < nx - 1; ++ci)
+        for (int t = 0; t < 6; ++t) {
+          const int64_t e = 6 * ((int64_t)ci + (int64_t)(nx - 1) * ((int64_t)cj + (int64_t)(ny - 1) * ck)) + t;
+          double G[4][3], cc;
+          const double vol = tet_element(&c, ci, cj, ck, t, G, &cc);
+          for (int v = 0; v < 4; ++v) {
+            const int m = TET[t][v];
+            nodes[4 * e + v] = (int32_t)unk(&c, ci + (m & 1), cj + ((m >> 1) & 1), ck + ((m >> 2) & 1));
+            for (int w = 0; w < 4; ++w) kh[16 * e + 4 * v + w] = kab(G, v, w, vol);
+          }
+          coef[e] = cc;
+        }
+  return 0;
+}
+
 /* Smallest signed tetrahedron volume divided by h^3 (positive means every
  * element is positively oriented after jitter). */
 double femgen_min_volume(const femgen_params* p) {

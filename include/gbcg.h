@@ -173,6 +173,54 @@ int gbcg_spmv_f32(gbcg_matrix_t A, const float* x, float* y, void* stream);
 int gbcg_solve(gbcg_matrix_t A, const double* b, double* x, double tol, int32_t maxit,
                const gbcg_opts* opts, gbcg_info* info, void* stream);
 
+/*
+ * gbcg_update_values -- replace the values of a handle, same pattern.  `val`
+ * holds nnz doubles in the order of the arrays given to gbcg_create (memory:
+ * gbcg_memory).  The first call builds and keeps a map from every device
+ * value slot to its input entry (host work of the order of gbcg_create's
+ * layout build, and 4 bytes per stored slot of device memory); later calls
+ * are one gather kernel per value array, writing both precisions.  Used by
+ * the differentiable solve, whose values change between calls.  Values are
+ * not checked: non-finite values show up as GBCG_ERR_NONFINITE in a solve.
+ */
+int gbcg_update_values(gbcg_matrix_t A, const double* val, int32_t memory, void* stream);
+
+/*
+ * Gradients of a loss L(x) with respect to what the caller stores, for the
+ * solution x of A x = b (A symmetric positive-definite).  With lambda the
+ * solution of the adjoint system A lambda = dL/dx (same matrix, same
+ * solver), dL/db = lambda and dL/dA_ij = -lambda_i x_j.  The configured
+ * differentiable form of the Section III solve; no paper counterpart.
+ *
+ * gbcg_grad_values -- grad[k] = dL/d(stored value k) on the pattern
+ * (format, n, nnz, ptr, idx, index_base as for gbcg_create; device arrays):
+ * CSR entry k of row i, column j: -lambda_i x_j; CSC entry k of column j,
+ * row i: -lambda_i x_j; symmetric upper entry of row i, column j > i (which
+ * stands for A_ij and A_ji): -(lambda_i x_j + lambda_j x_i), diagonal:
+ * -lambda_i x_i.  lambda, x, grad: device arrays (n, n, nnz).
+ */
+int gbcg_grad_values(int32_t format, int64_t n, int64_t nnz, const int32_t* ptr, const int32_t* idx,
+                     int32_t index_base, const double* lambda, const double* x, double* grad, void* stream);
+
+/*
+ * gbcg_element_grad -- chain rule through a finite-element assembly
+ * A = sum_e coef_e Kh_e: element e adds coef_e * w[e*m + k] to stored value
+ * pos[e*m + k] (pos < 0: nothing), k < m; then
+ * grad_coef[e] = sum_k w[e*m + k] * grad[pos[e*m + k]].  Device arrays;
+ * ne elements, m <= 64 pairs each.  For symmetric upper storage list only
+ * the vertex pairs a <= b (the stored gradient already holds both halves).
+ */
+int gbcg_element_grad(int64_t ne, int32_t m, const int32_t* pos, const double* w, const double* grad,
+                      double* grad_coef, void* stream);
+
+/*
+ * gbcg_assemble -- the same assembly by stored position: val[p] =
+ * sum over k in [tptr[p], tptr[p+1]) of tw[k] * coef[telem[k]], summed in
+ * that order (no atomics; bitwise reproducible).  Device arrays.
+ */
+int gbcg_assemble(int64_t nnz, const int64_t* tptr, const int32_t* telem, const double* tw, const double* coef,
+                  double* val, void* stream);
+
 /* gbcg_stats -- layout facts of a handle. */
 int gbcg_stats(gbcg_matrix_t A, gbcg_matrix_stats* out);
 

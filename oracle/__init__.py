@@ -15,6 +15,10 @@ Parity status per function (what pins it; see ``tests/test_oracle_pins.py``):
   cg_f32 / cg_ir                      -- true residual in double, error vs x*
   dot_long                            -- exact rational arithmetic
   dot_f32                             -- exact sum within the pairwise bound
+  grad_values / element_grad /        -- central finite differences of the
+  assemble                               loss through oracle solves, dense
+                                         reference gradients, the generator's
+                                         assembled matrix
 """
 from __future__ import annotations
 
@@ -85,6 +89,9 @@ def load(path: str | None = None):
     lib.orc_cg_f32.restype = i32
     lib.orc_cg_ir.argtypes = [ctypes.c_int, i64, vp, vp, vp, vp, vp, d, i32, d, i32,
                               ctypes.POINTER(Info)]
+    lib.orc_grad_values.argtypes = [ctypes.c_int, i64, vp, vp, vp, vp, vp]
+    lib.orc_element_grad.argtypes = [i64, i32, vp, vp, vp, vp]
+    lib.orc_assemble.argtypes = [i64, vp, vp, vp, vp, vp]
     if path is None:
         _lib = lib
     return lib
@@ -256,3 +263,53 @@ def batch_solve(row_off, ptr, idx, val, B, X0=None, tol=1e-10, maxit=None, preci
             row.append(res)
         results.append(row)
     return X, results
+
+
+# ------------------------------------------------------------ differentiation
+def grad_values(fmt, ptr, idx, lam, x, lib=None) -> np.ndarray:
+    """dL/d(stored values) from the adjoint lambda = A^-1 dL/dx and x."""
+    lib = lib or load()
+    ptr = np.ascontiguousarray(ptr, dtype=np.int32)
+    idx = np.ascontiguousarray(idx, dtype=np.int32)
+    lam = np.ascontiguousarray(lam, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    g = np.empty(idx.shape[0])
+    lib.orc_grad_values(_fmt(fmt), ptr.shape[0] - 1, _p(ptr), _p(idx), _p(lam), _p(x), _p(g))
+    return g
+
+
+def element_grad(pos, w, g, lib=None) -> np.ndarray:
+    """dL/dcoef per element from the stored-value gradient g (chain rule
+    through the assembly map)."""
+    lib = lib or load()
+    pos = np.ascontiguousarray(pos, dtype=np.int32)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    out = np.empty(pos.shape[0])
+    lib.orc_element_grad(pos.shape[0], pos.shape[1], _p(pos), _p(w), _p(g), _p(out))
+    return out
+
+
+def assemble(tptr, telem, tw, coef, lib=None) -> np.ndarray:
+    """Stored values sum_e coef_e w from the assembly map by position."""
+    lib = lib or load()
+    tptr = np.ascontiguousarray(tptr, dtype=np.int64)
+    telem = np.ascontiguousarray(telem, dtype=np.int32)
+    tw = np.ascontiguousarray(tw, dtype=np.float64)
+    coef = np.ascontiguousarray(coef, dtype=np.float64)
+    out = np.empty(tptr.shape[0] - 1)
+    lib.orc_assemble(out.shape[0], _p(tptr), _p(telem), _p(tw), _p(coef), _p(out))
+    return out
+
+
+def loss_gradients(fmt, ptr, idx, val, b, xt, tol=1e-13, maxit=None, lib=None):
+    """L = ||x - xt||^2 with A x = b (double-precision CG): returns
+    (L, x, lambda, dL/db, dL/dval) through the adjoint solve A lambda = 2 (x - xt)."""
+    lib = lib or load()
+    n = np.asarray(ptr).shape[0] - 1
+    m = maxit if maxit is not None else 20 * max(n, 1)
+    fw = cg(fmt, ptr, idx, val, b, tol=tol, maxit=m, lib=lib)
+    gx = 2.0 * (fw.x - xt)
+    adj = cg(fmt, ptr, idx, val, gx, tol=tol, maxit=m, lib=lib)
+    L = float(np.dot(fw.x - xt, fw.x - xt))
+    return L, fw.x, adj.x, adj.x.copy(), grad_values(fmt, ptr, idx, adj.x, fw.x, lib=lib)

@@ -342,3 +342,52 @@ done:
   free(r);
   return status;
 }
+
+/* ------------------------------------------------ differentiation -------- */
+/* Gradient of a loss L(x) through x = A^-1 b (the configured differentiable
+ * form of the Section III solve).  With lambda = A^-T dL/dx (the adjoint
+ * solve; A is symmetric, so A lambda = dL/dx) the derivative with respect to
+ * matrix entry A_ij is -lambda_i x_j.  For each STORED value:
+ *   CSR:  value k of row i, column j = idx[k]        -> -lambda_i x_j
+ *   CSC:  value k of column j, row i = idx[k]        -> -lambda_i x_j
+ *   symmetric upper: value k of row i, column j >= i stands for A_ij and A_ji:
+ *         j > i -> -(lambda_i x_j + lambda_j x_i),   j = i -> -lambda_i x_i. */
+void orc_grad_values(int fmt, int64_t n, const int32_t* ptr, const int32_t* idx, const double* lambda,
+                     const double* x, double* g) {
+  for (int64_t r = 0; r < n; ++r)
+    for (int64_t k = ptr[r]; k < ptr[r + 1]; ++k) {
+      const int64_t c = idx[k];
+      if (fmt == ORC_CSC) {                      /* r is the column, c the row */
+        g[k] = -(lambda[c] * x[r]);
+      } else if (fmt == ORC_SYM_UPPER && c != r) {
+        g[k] = -(lambda[r] * x[c] + lambda[c] * x[r]);
+      } else {
+        g[k] = -(lambda[r] * x[c]);
+      }
+    }
+}
+
+/* Chain rule through the assembly A = sum_e coef_e Kh_e: with the stored
+ * positions pos[e*m + k] (-1: none) and weights w[e*m + k] of element e,
+ * dL/dcoef_e = sum_k w[e*m+k] * g[pos[e*m+k]]. */
+void orc_element_grad(int64_t ne, int32_t m, const int32_t* pos, const double* w, const double* g, double* gc) {
+  for (int64_t e = 0; e < ne; ++e) {
+    double s = 0.0;
+    for (int32_t k = 0; k < m; ++k) {
+      const int32_t p = pos[e * m + k];
+      if (p >= 0) s += w[e * m + k] * g[p];
+    }
+    gc[e] = s;
+  }
+}
+
+/* The assembly itself, by stored position: val[p] = sum over the
+ * contributions (elem, weight) at tptr[p]..tptr[p+1] of weight * coef_elem. */
+void orc_assemble(int64_t nnz, const int64_t* tptr, const int32_t* telem, const double* tw, const double* coef,
+                  double* val) {
+  for (int64_t p = 0; p < nnz; ++p) {
+    double s = 0.0;
+    for (int64_t k = tptr[p]; k < tptr[p + 1]; ++k) s += tw[k] * coef[telem[k]];
+    val[p] = s;
+  }
+}

@@ -142,6 +142,26 @@ class Matrix:
         _lib.check(self._lib.gbcg_stats(self._h, ctypes.byref(s)), "gbcg_stats")
         return {name: getattr(s, name) for name, _ in _lib.Stats._fields_}
 
+    def update_values(self, val, stream=None):
+        """Replace the stored values (same pattern, same order as at creation):
+        a float64 CUDA tensor or a numpy array (``gbcg_update_values``)."""
+        if _is_tensor(val):
+            torch = _torch()
+            val = val.to(torch.float64).contiguous()
+            if val.numel() != self.nnz:
+                raise ValueError(f"expected {self.nnz} values")
+            mem = _lib.GBCG_DEVICE if val.is_cuda else _lib.GBCG_HOST
+            stream_h = _stream_handle(stream) if val.is_cuda else _host_stream(stream)
+            ptr = val.data_ptr()
+        else:
+            val = np.ascontiguousarray(val, dtype=np.float64)
+            if val.shape[0] != self.nnz:
+                raise ValueError(f"expected {self.nnz} values")
+            mem, stream_h, ptr = _lib.GBCG_HOST, _host_stream(stream), val.ctypes.data
+        _lib.check(self._lib.gbcg_update_values(self._h, ctypes.c_void_p(ptr), mem, stream_h), "gbcg_update_values")
+        if mem == _lib.GBCG_HOST:
+            _torch().cuda.synchronize()
+
     # ------------------------------------------------------------ product
     def spmv(self, x, y=None, stream=None):
         """y = A x (float64 CUDA tensors)."""
@@ -352,9 +372,60 @@ def _check_vec(t, dtype, n, name):
         raise ValueError(f"{name} must be a contiguous {dtype} CUDA tensor of length {n}")
 
 
+def _cuda_arg(t, dtype, name):
+    torch = _torch()
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dtype and t.is_contiguous()):
+        raise ValueError(f"{name} must be a contiguous {dtype} CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def grad_values(fmt, ptr, idx, lam, x, index_base: int = 0, out=None, stream=None):
+    """dL/d(stored values) = the sampled outer product of the adjoint lambda and
+    x on the pattern (``gbcg_grad_values``); CUDA tensors."""
+    torch = _torch()
+    f = FORMATS[fmt] if isinstance(fmt, str) else int(fmt)
+    n, nnz = ptr.numel() - 1, idx.numel()
+    if out is None:
+        out = torch.empty(nnz, dtype=torch.float64, device=lam.device)
+    args = [_cuda_arg(ptr, torch.int32, "ptr"), _cuda_arg(idx, torch.int32, "idx"), int(index_base),
+            _cuda_arg(lam, torch.float64, "lambda"), _cuda_arg(x, torch.float64, "x"),
+            _cuda_arg(out, torch.float64, "out")]
+    _lib.check(_lib.load().gbcg_grad_values(f, n, nnz, *args, _stream_handle(stream)), "gbcg_grad_values")
+    return out
+
+
+def element_grad(pos, w, grad, out=None, stream=None):
+    """dL/dcoef per element through the assembly map (``gbcg_element_grad``);
+    pos int32 [E, m], w float64 [E, m], grad float64 [nnz]."""
+    torch = _torch()
+    ne, m = pos.shape
+    if out is None:
+        out = torch.empty(ne, dtype=torch.float64, device=grad.device)
+    _lib.check(_lib.load().gbcg_element_grad(ne, m, _cuda_arg(pos, torch.int32, "pos"),
+                                             _cuda_arg(w, torch.float64, "w"), _cuda_arg(grad, torch.float64, "grad"),
+                                             _cuda_arg(out, torch.float64, "out"), _stream_handle(stream)),
+               "gbcg_element_grad")
+    return out
+
+
+def assemble(tptr, telem, tw, coef, out=None, stream=None):
+    """Stored values from element coefficients (``gbcg_assemble``)."""
+    torch = _torch()
+    nnz = tptr.numel() - 1
+    if out is None:
+        out = torch.empty(nnz, dtype=torch.float64, device=coef.device)
+    _lib.check(_lib.load().gbcg_assemble(nnz, _cuda_arg(tptr, torch.int64, "tptr"),
+                                         _cuda_arg(telem, torch.int32, "telem"), _cuda_arg(tw, torch.float64, "tw"),
+                                         _cuda_arg(coef, torch.float64, "coef"), _cuda_arg(out, torch.float64, "out"),
+                                         _stream_handle(stream)), "gbcg_assemble")
+    return out
+
+
 def selftest_wait_timeout(ctas: int = 0, timeout_ms: int = 50, stream=None) -> int:
     """Runs the bounded-wait self-test (``gbcg_selftest_wait_timeout``); returns its status code."""
     return _lib.load().gbcg_selftest_wait_timeout(int(ctas), int(timeout_ms), _stream_handle(stream))
 
 
-__all__ = ["Matrix", "Batch", "SolveInfo", "GbcgError", "build", "selftest_wait_timeout", "FORMATS", "PRECISIONS"]
+from .autograd import Assembly, SparseSolve  # noqa: E402
+
+__all__ = ["Matrix", "Batch", "SparseSolve", "Assembly", "grad_values", "element_grad", "assemble", "SolveInfo", "GbcgError", "build", "selftest_wait_timeout", "FORMATS", "PRECISIONS"]

@@ -22,7 +22,8 @@ EXPORTS = ["gbcg_create", "gbcg_destroy", "gbcg_spmv", "gbcg_spmv_f32", "gbcg_so
            "gbcg_status_string", "gbcg_last_error", "gbcg_selftest_wait_timeout", "gbcg_solve_csr_static",
            "gbcg_batch_create", "gbcg_batch_destroy", "gbcg_batch_autotune", "gbcg_batch_set_tuning",
            "gbcg_batch_solve", "gbcg_batch_instance_times", "gbcg_batch_stats",
-           "gbcg_batch_selftest_group_timeout"]
+           "gbcg_batch_selftest_group_timeout", "gbcg_update_values", "gbcg_grad_values", "gbcg_element_grad",
+           "gbcg_assemble"]
 STATIC_MAX_N = 680000
 
 
@@ -118,10 +119,15 @@ def load(path: str = LIB_PATH):
     lib.gbcg_batch_instance_times.argtypes = [vp, vp, vp, vp]
     lib.gbcg_batch_stats.argtypes = [vp, ctypes.POINTER(BatchStats)]
     lib.gbcg_batch_selftest_group_timeout.argtypes = [vp, i32, vp]
+    lib.gbcg_update_values.argtypes = [vp, vp, i32, vp]
+    lib.gbcg_grad_values.argtypes = [i32, i64, i64, vp, vp, i32, vp, vp, vp, vp]
+    lib.gbcg_element_grad.argtypes = [i64, i32, vp, vp, vp, vp, vp]
+    lib.gbcg_assemble.argtypes = [i64, vp, vp, vp, vp, vp, vp]
     for name in ("gbcg_create", "gbcg_destroy", "gbcg_spmv", "gbcg_spmv_f32", "gbcg_solve", "gbcg_stats",
                  "gbcg_selftest_wait_timeout", "gbcg_solve_csr_static", "gbcg_batch_create", "gbcg_batch_destroy",
                  "gbcg_batch_autotune", "gbcg_batch_set_tuning", "gbcg_batch_solve", "gbcg_batch_instance_times",
-                 "gbcg_batch_stats", "gbcg_batch_selftest_group_timeout"):
+                 "gbcg_batch_stats", "gbcg_batch_selftest_group_timeout", "gbcg_update_values",
+                 "gbcg_grad_values", "gbcg_element_grad", "gbcg_assemble"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib

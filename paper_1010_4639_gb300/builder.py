@@ -1,8 +1,9 @@
 """Builds ``libgbcg.so`` in-tree for sm_103a (GB300).
 
-Four translation units compiled in parallel: ``csrc/gbcg.cu`` (kernels and
+Five translation units compiled in parallel: ``csrc/gbcg.cu`` (kernels and
 the C ABI, nvcc), ``csrc/static_solve.cu`` (the allocation-free solve, nvcc),
-``csrc/batch.cu`` (the batched multi-right-hand-side solver, nvcc) and
+``csrc/batch.cu`` (the batched multi-right-hand-side solver, nvcc),
+``csrc/grad.cu`` (gradient kernels of the differentiable solve, nvcc) and
 ``csrc/layout.cpp`` (host-side layout construction, g++), linked by nvcc into
 a shared library next to this file.
 """
@@ -18,7 +19,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgbcg.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = [os.path.join(CSRC, f) for f in ("gbcg.cu", "static_solve.cu", "batch.cu", "layout.cpp",
+SOURCES = [os.path.join(CSRC, f) for f in ("gbcg.cu", "static_solve.cu", "batch.cu", "grad.cu", "layout.cpp",
                                               "kernels.cuh", "layout.h")]
 HEADERS = [os.path.join(INCLUDE, "gbcg.h")]
 
@@ -43,6 +44,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
     cu_obj = os.path.join(BUILD, "gbcg.o")
     st_obj = os.path.join(BUILD, "static_solve.o")
     bt_obj = os.path.join(BUILD, "batch.o")
+    gr_obj = os.path.join(BUILD, "grad.o")
     cpp_obj = os.path.join(BUILD, "layout.o")
     cmds = [
         [nvcc, "-c", "-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC",
@@ -51,6 +53,8 @@ def build(verbose: bool = False, force: bool = False) -> str:
          "-I", INCLUDE, os.path.join(CSRC, "static_solve.cu"), "-o", st_obj],
         [nvcc, "-c", "-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC",
          "-I", INCLUDE, os.path.join(CSRC, "batch.cu"), "-o", bt_obj],
+        [nvcc, "-c", "-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC",
+         "-I", INCLUDE, os.path.join(CSRC, "grad.cu"), "-o", gr_obj],
         ["g++", "-c", "-O2", "-std=c++17", "-fPIC", "-I", INCLUDE,
          os.path.join(CSRC, "layout.cpp"), "-o", cpp_obj],
     ]
@@ -65,7 +69,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
     if errors:
         raise RuntimeError("building libgbcg.so failed:\n" + "\n".join(errors))
     tmp = LIB + ".tmp"
-    subprocess.run([nvcc, "-shared", *ARCH, cu_obj, st_obj, bt_obj, cpp_obj, "-o", tmp], check=True)
+    subprocess.run([nvcc, "-shared", *ARCH, cu_obj, st_obj, bt_obj, gr_obj, cpp_obj, "-o", tmp], check=True)
     os.replace(tmp, LIB)
     return LIB
 

@@ -75,8 +75,14 @@ void set_last_error(const std::string& m) { g_last_error = m; }
 }  // namespace gbcg
 
 struct gbcg_matrix_s {
-  int32_t format = 0;
+  int32_t format = 0, index_base = 0;
   int64_t n = 0, nnz_input = 0, nnz_full = 0, slots = 0, plan_slots = 0;
+  // the caller's pattern, kept for value updates; device value slot -> input
+  // entry maps (-1 on padding), built at the first update
+  std::vector<int32_t> h_ptr, h_idx;
+  int32_t *u_map_main = nullptr, *u_map_long = nullptr, *u_map_diag = nullptr;
+  int64_t u_len_main = 0, u_len_long = 0, u_len_diag = 0;
+  double* u_stage = nullptr;
   int64_t nslices = 0, nlong = 0, bytes = 0;
   int sym = 0;
   int mode = kGather;       // kGather (CSR/CSC), kPlan or kTiles (symmetric)
@@ -205,7 +211,8 @@ void free_matrix(gbcg_matrix_s* M) {
                  M->d32, M->rhs32, M->part, M->sums, M->bar, M->st, M->t_cta_tile, M->t_tile_slice,
                  M->t_tile_ns, M->t_tile_own, M->t_tile_len, M->t_tile_rlog, M->t_tile_win, M->t_win_start, M->t_win_len,
                  M->t_tile_ent, M->t_tile_meta, M->t_tile_ext, M->t_in_src, M->t_meta, M->t_val64, M->t_val32,
-                 M->t_in_ptr, M->t_in_row, M->t_in_len, M->t_part};
+                 M->t_in_ptr, M->t_in_row, M->t_in_len, M->t_part, M->u_map_main, M->u_map_long, M->u_map_diag,
+                 M->u_stage};
   for (void* d : dev)
     if (d) cudaFree(d);
   if (M->st_h) cudaFreeHost(M->st_h);
@@ -510,6 +517,9 @@ int gbcg_create(gbcg_matrix_t* out, int32_t format, int64_t n, int64_t nnz, cons
   M->nlong = (int64_t)L.A.long_row.size();
   M->slots = L.A.sl_ptr.empty() ? 0 : L.A.sl_ptr.back();
   M->plan_slots = L.plan.pl_ptr.empty() ? 0 : L.plan.pl_ptr.back();
+  M->index_base = index_base;
+  M->h_ptr.assign(ptr, ptr + n + 1);
+  M->h_idx.assign(idx, idx + nnz);
   auto bail = [&](int code) {
     free_matrix(M);
     return code;
@@ -705,6 +715,72 @@ int gbcg_stats(gbcg_matrix_t A, gbcg_matrix_stats* out) {
   out->layout = A->mode;
   out->tiles = (int32_t)A->ntiles;
   out->ext_slots = A->next;
+  return GBCG_OK;
+}
+
+int gbcg_update_values(gbcg_matrix_t A, const double* val, int32_t memory, void* stream) {
+  g_last_error.clear();
+  if (!A) return fail(GBCG_ERR_INVALID, "null matrix handle");
+  if (memory != GBCG_HOST && memory != GBCG_DEVICE) return fail(GBCG_ERR_INVALID, "memory must be GBCG_HOST or GBCG_DEVICE");
+  const int64_t nnz = A->nnz_input;
+  if (nnz == 0) return GBCG_OK;
+  if (!val) return fail(GBCG_ERR_INVALID, "null value array");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!A->u_map_main && !A->u_map_long && !A->u_map_diag) {
+    // the layout of the same pattern with value k + 1 at input entry k: every
+    // device value slot then names the input entry it holds (0: padding)
+    std::vector<double> iv(nnz);
+    for (int64_t k = 0; k < nnz; ++k) iv[k] = (double)(k + 1);
+    LayoutHost L;
+    std::string err;
+    if (int rc = build_layout(A->format, A->n, nnz, A->h_ptr.data(), A->h_idx.data(), iv.data(), A->index_base, L, err))
+      return fail(rc, "rebuilding the value map: " + err);
+    if (A->mode == kTiles && !build_sym_tiles(L, A->grid, kTileSlot, kTileEnt))
+      return fail(GBCG_ERR_INVALID, "rebuilding the value map: tiles differ from the handle's");
+    auto to_map = [](const std::vector<double>& v) {
+      std::vector<int32_t> m(v.size());
+      for (size_t i = 0; i < v.size(); ++i) m[i] = (int32_t)v[i] - 1;
+      return m;
+    };
+    int64_t& B = A->bytes;
+    if (A->mode == kTiles) {
+      if ((int64_t)L.tiles.val.size() != A->tile_slots) return fail(GBCG_ERR_INVALID, "value map: tile size mismatch");
+      if (int rc = upload(&A->u_map_main, to_map(L.tiles.val), s, B)) return rc;
+      A->u_len_main = (int64_t)L.tiles.val.size();
+    } else {
+      if (int rc = upload(&A->u_map_main, to_map(L.A.val), s, B)) return rc;
+      A->u_len_main = (int64_t)L.A.val.size();
+      if (!L.A.long_val.empty()) {
+        if (int rc = upload(&A->u_map_long, to_map(L.A.long_val), s, B)) return rc;
+        A->u_len_long = (int64_t)L.A.long_val.size();
+      }
+    }
+    if (A->sym) {
+      if (int rc = upload(&A->u_map_diag, to_map(L.diag), s, B)) return rc;
+      A->u_len_diag = (int64_t)L.diag.size();
+    }
+    if (int rc = dalloc(&A->u_stage, (size_t)nnz, B)) return rc;
+  }
+  const double* src = val;
+  if (memory == GBCG_HOST) {
+    CUDA_TRY(cudaMemcpyAsync(A->u_stage, val, sizeof(double) * nnz, cudaMemcpyHostToDevice, s));
+    src = A->u_stage;
+  }
+  auto run = [&](const int32_t* map, int64_t len, double* d64, float* d32) -> int {
+    if (!map || len == 0) return 0;
+    const int blocks = (int)std::min<int64_t>(4096, (len + 255) / 256);
+    k_place_values<<<blocks, 256, 0, s>>>(map, len, src, d64, d32);
+    CUDA_TRY(cudaGetLastError());
+    return 0;
+  };
+  if (A->mode == kTiles) {
+    if (int rc = run(A->u_map_main, A->u_len_main, A->t_val64, A->t_val32)) return rc;
+  } else {
+    if (int rc = run(A->u_map_main, A->u_len_main, A->val64, A->val32)) return rc;
+    if (int rc = run(A->u_map_long, A->u_len_long, A->long_val64, A->long_val32)) return rc;
+  }
+  if (A->sym)
+    if (int rc = run(A->u_map_diag, A->u_len_diag, A->diag64, A->diag32)) return rc;
   return GBCG_OK;
 }
 

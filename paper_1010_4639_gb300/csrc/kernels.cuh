@@ -816,6 +816,18 @@ __global__ void k_scale_to_f32(const double* __restrict__ r, double scale, int64
     out[i] = (float)(r[i] * scale);
 }
 
+// Value update of a handle: slot i of a device value array takes input
+// value map[i] (0 where map[i] < 0: padding), in both precisions.
+__global__ void k_place_values(const int32_t* __restrict__ map, int64_t len, const double* __restrict__ src,
+                               double* __restrict__ d64, float* __restrict__ d32) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t k = map[i];
+    const double v = k >= 0 ? src[k] : 0.0;
+    d64[i] = v;
+    d32[i] = (float)v;
+  }
+}
+
 // x += a * double(d)
 __global__ void k_axpy_f32(double a, const float* __restrict__ d, int64_t n, double* __restrict__ x) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)

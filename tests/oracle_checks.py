@@ -348,10 +348,103 @@ def check_cg_ir(lib):
         assert 2 <= r.restarts <= 10
 
 
+# ------------------------------------------------------- differentiation ---
+def _diff_case(g):
+    s = femgen.build_system(g)
+    el = femgen.elements(g)
+    xt = femgen.random_vector(s.n, 77)
+    return s, el, xt
+
+
+def _dense(ptr, idx, val, n):
+    A = np.zeros((n, n))
+    for i in range(n):
+        A[i, idx[ptr[i]:ptr[i + 1]]] = val[ptr[i]:ptr[i + 1]]
+    return A
+
+
+def check_grad_dense_reference(lib):
+    # L = ||x - xt||^2, A x = b: dense solves give lambda = A^-1 2(x - xt) and
+    # the full dL/dA = -lambda x'; every stored form must be that matrix (or its
+    # symmetric fold) at the stored positions, dL/db = lambda, and the element
+    # gradient the sum of Kh_e against dL/dA over the element's unknowns
+    g = femgen.Grid(6, 6, 6, contrast=30.0, seed_mesh=5, seed_x=6)
+    s, el, xt = _diff_case(g)
+    A = _dense(s.ptr, s.idx, s.val, s.n)
+    x = np.linalg.solve(A, s.b)
+    lam = np.linalg.solve(A, 2.0 * (x - xt))
+    GA = -np.outer(lam, x)
+    rows = np.repeat(np.arange(s.n), np.diff(s.ptr))
+    g_csr = oracle.grad_values("csr", s.ptr, s.idx, lam, x, lib=lib)
+    np.testing.assert_allclose(g_csr, GA[rows, s.idx], rtol=1e-13, atol=1e-13 * np.abs(GA).max())
+    g_csc = oracle.grad_values("csc", s.ptr, s.idx, lam, x, lib=lib)  # columns of A (= rows: symmetric)
+    np.testing.assert_allclose(g_csc, GA[s.idx, rows], rtol=1e-13, atol=1e-13 * np.abs(GA).max())
+    up, ui, uv = s.upper()
+    urows = np.repeat(np.arange(s.n), np.diff(up))
+    fold = np.where(urows == ui, GA[urows, ui], GA[urows, ui] + GA[ui, urows])
+    g_sym = oracle.grad_values("sym", up, ui, lam, x, lib=lib)
+    np.testing.assert_allclose(g_sym, fold, rtol=1e-13, atol=1e-13 * np.abs(GA).max())
+    # element gradient: sum_ab Kh_ab GA[u_a, u_b] over unknown vertices
+    nodes = el.nodes
+    ok = nodes >= 0
+    safe = np.where(ok, nodes, 0)
+    Gsub = GA[safe[:, :, None], safe[:, None, :]] * (ok[:, :, None] & ok[:, None, :])
+    gc_ref = np.einsum("eab,eab->e", el.kh, Gsub)
+    for storage, (pp, ii, gv) in (("csr", (s.ptr, s.idx, g_csr)), ("sym", (up, ui, g_sym))):
+        pos, w = femgen.element_map(el, pp, ii, storage=storage)
+        gc = oracle.element_grad(pos, w, gv, lib=lib)
+        np.testing.assert_allclose(gc, gc_ref, rtol=1e-10, atol=1e-12 * np.abs(gc_ref).max())
+
+
+def check_assemble_reproduces_the_generator(lib):
+    g = femgen.Grid(7, 6, 5, contrast=100.0, seed_mesh=8, seed_x=9)
+    s, el, _ = _diff_case(g)
+    for storage, (pp, ii, vv) in (("csr", (s.ptr, s.idx, s.val)), ("sym", s.upper())):
+        pos, w = femgen.element_map(el, pp, ii, storage=storage)
+        tptr, te, tw = femgen.assembly_map(pos, w, len(ii))
+        val = oracle.assemble(tptr, te, tw, el.coef, lib=lib)
+        np.testing.assert_allclose(val, vv, rtol=1e-12, atol=1e-13 * np.abs(vv).max())
+
+
+def check_grad_finite_differences(lib):
+    # central differences of L through the oracle's own solves (to 1e-14),
+    # step 1e-6, along random directions in b, in the stored upper values
+    # (a symmetric perturbation of A) and in the element coefficients
+    g = femgen.Grid(6, 6, 7, contrast=20.0, seed_mesh=3, seed_x=4)
+    s, el, xt = _diff_case(g)
+    up, ui, uv = s.upper()
+    pos, w = femgen.element_map(el, up, ui, storage="sym")
+    tptr, te, tw = femgen.assembly_map(pos, w, len(ui))
+    coef = el.coef.copy()
+    val = oracle.assemble(tptr, te, tw, coef, lib=lib)
+    L, x, lam, gb, gv = oracle.loss_gradients("sym", up, ui, val, s.b, xt, tol=1e-14, lib=lib)
+    gc = oracle.element_grad(pos, w, gv, lib=lib)
+
+    def loss(v, b):
+        r = oracle.cg("sym", up, ui, v, b, tol=1e-14, maxit=40 * s.n, lib=lib)
+        return float(np.dot(r.x - xt, r.x - xt))
+
+    rng = np.random.default_rng(11)
+    h = 1e-6
+    for _ in range(3):
+        d = rng.standard_normal(s.n)
+        fd = (loss(val, s.b + h * d) - loss(val, s.b - h * d)) / (2 * h)
+        assert abs(fd - gb @ d) <= 1e-6 * abs(fd) + 1e-9, ("b", fd, gb @ d)
+        dv = rng.standard_normal(len(ui)) * np.abs(val)
+        fd = (loss(val + h * dv, s.b) - loss(val - h * dv, s.b)) / (2 * h)
+        assert abs(fd - gv @ dv) <= 1e-5 * abs(fd) + 1e-9, ("values", fd, gv @ dv)
+        dc = rng.standard_normal(coef.shape[0]) * coef
+        vp = oracle.assemble(tptr, te, tw, coef + h * dc, lib=lib)
+        vm = oracle.assemble(tptr, te, tw, coef - h * dc, lib=lib)
+        fd = (loss(vp, s.b) - loss(vm, s.b)) / (2 * h)
+        assert abs(fd - gc @ dc) <= 1e-5 * abs(fd) + 1e-9, ("coefficients", fd, gc @ dc)
+
+
 ALL_CHECKS = [
     check_spmv_csr_bruteforce, check_spmv_csc_bruteforce, check_spmv_sym_bruteforce, check_abs_spmv,
     check_spmv_f32, check_dot, check_dot_f32, check_cg_vs_cholesky, check_cg_fem_vs_cholesky,
     check_cg_finite_termination, check_cg_exact_first_steps, check_cg_a_orthogonality,
     check_cg_error_a_norm_decreases, check_cg_tridiagonal_closed_form, check_cg_edge_cases,
-    check_cg_f32, check_cg_ir,
+    check_cg_f32, check_cg_ir, check_grad_dense_reference, check_assemble_reproduces_the_generator,
+    check_grad_finite_differences,
 ]

@@ -34,6 +34,12 @@ MUTANTS = {
     "abs_spmv_signed": ("double a = fabs(val[k]);", "double a = val[k];"),
     "f32_dot_left_to_right": ("  if (n <= 8) {\n    float s", "  if (1) {\n    float s"),
     "f32_dot_wrong_half": ("dot_f(n - h, a + h, b + h)", "dot_f(n - h, a + h, b)"),
+    "grad_sym_drops_transpose": ("g[k] = -(lambda[r] * x[c] + lambda[c] * x[r]);", "g[k] = -(lambda[r] * x[c]);"),
+    "grad_sym_doubles_diagonal": ("fmt == ORC_SYM_UPPER && c != r", "fmt == ORC_SYM_UPPER"),
+    "grad_csc_transposed": ("g[k] = -(lambda[c] * x[r]);", "g[k] = -(lambda[r] * x[c]);"),
+    "grad_sign": ("        g[k] = -(lambda[r] * x[c]);\n      }\n    }", "        g[k] = lambda[r] * x[c];\n      }\n    }"),
+    "element_grad_drops_weight": ("if (p >= 0) s += w[e * m + k] * g[p];", "if (p >= 0) s += g[p];"),
+    "assemble_drops_coefficient": ("s += tw[k] * coef[telem[k]];", "s += tw[k];"),
 }
 
 
