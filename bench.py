@@ -53,6 +53,7 @@ def parse():
                     help="only run solves capped at this many iterations (small case for ncu captures)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU-oracle sample")
     ap.add_argument("--only-batched", action="store_true", help="only run the batched leg")
+    ap.add_argument("--only-differentiable", action="store_true", help="only run the differentiation leg")
     ap.add_argument("--profile-batched", type=int, default=0,
                     help="only one mixed-precision solve of the first N batch instances (small case for ncu)")
     ap.add_argument("--profile-spmv", action="store_true",
@@ -225,6 +226,9 @@ def run_ours(args):
     if args.only_batched:
         print(json.dumps({"batched": batched(torch, gb, args)}), flush=True)
         return 0
+    if args.only_differentiable:
+        print(json.dumps({"differentiable": differentiable(torch, gb, args)}), flush=True)
+        return 0
     if args.profile_batched:
         bs = femgen.build_batch(femgen.batched_instances(256)[:args.profile_batched], nrhs=8)
         with gb.Batch(bs.row_off, bs.ptr, bs.idx, bs.val, nrhs=8, tune=False) as Bt:
@@ -334,6 +338,7 @@ def run_ours(args):
         line["variants"] = extras(torch, gb, s, fmt_arrays, A, args, hbm)
         line["paper_size"] = paper_size(torch, gb, args)
         line["batched"] = batched(torch, gb, args)
+        line["differentiable"] = differentiable(torch, gb, args)
         line["cpu_baseline"] = cpu_baseline(s, args, line["variants"])
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -493,6 +498,122 @@ def batched(torch, gb, args):
     out["sequential_fp64_one_rhs_s"] = seq
     out["sequential_fp64_8rhs_s"] = 8 * seq
     out["batched_speedup_vs_sequential_fp64"] = 8 * seq / out["fp32_ir"]["s"]
+    return out
+
+
+def differentiable(torch, gb, args):
+    """64^3 system, L = ||x - x_t||^2 (x_t ~ U(-1, 1) seeded), symmetric
+    storage: forward double-precision CG to 1e-10, backward = adjoint CG to
+    1e-10 + sampled-outer-product and element-gradient kernels.  Gradient
+    error: fourth-order central differences (step 1e-6) of fixed-iteration
+    solves along 8 random directions (b and stored values: relative white
+    noise; coefficients: random smooth fields), and the 6^3 dense reference."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    t0 = time.perf_counter()
+    g = femgen.DIFF
+    s = femgen.build_system(g)
+    el = femgen.elements(g)
+    up, ui, uv = s.upper()
+    pos, w = femgen.element_map(el, up, ui, storage="sym")
+    tptr, te, tw = femgen.assembly_map(pos, w, len(ui))
+    prep_s = time.perf_counter() - t0
+    asm = gb.Assembly(pos, w, tptr, te, tw)
+    xt = torch.from_numpy(femgen.random_vector(s.n, 79)).to(dev)
+    coef0 = torch.from_numpy(el.coef).to(dev)
+    vals0 = asm(coef0)
+    S = gb.SparseSolve("sym", up, ui, vals0.cpu().numpy(), tol=TOL)
+    b0 = torch.from_numpy(s.b).to(dev)
+    fw, bw = [], []
+    for k in range(4):
+        coef = coef0.clone().requires_grad_(True)
+        b = b0.clone().requires_grad_(True)
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        torch.cuda.synchronize()
+        e[0].record()
+        x = S(asm(coef), b)
+        L = ((x - xt) ** 2).sum()
+        e[1].record()
+        L.backward()
+        e[2].record()
+        torch.cuda.synchronize()
+        if k:
+            fw.append(e[0].elapsed_time(e[1]) / 1000.0)
+            bw.append(e[1].elapsed_time(e[2]) / 1000.0)
+    out = {"workload": "fem 64^3, 1 inclusion, contrast 1000, symmetric storage, L = ||x - x_t||^2, tol 1e-10",
+           "n": s.n, "nnz_stored": int(len(ui)), "elements": el.count, "prepare_s": prep_s,
+           "forward_s": statistics.median(fw), "backward_s": statistics.median(bw),
+           "forward_iterations": S.last_info.iterations, "adjoint_iterations": S.last_adjoint_info.iterations}
+    gb_, gc = b.grad.clone(), coef.grad.clone()
+    # finite differences through fixed-iteration solves (a smooth map)
+    with gb.Matrix("sym", up, ui, uv) as A:
+        _, info = A.solve(b0, tol=1e-13, maxit=100000)
+    F = gb.SparseSolve("sym", up, ui, uv, fixed_iterations=info.iterations + 50)
+    coef = coef0.clone().requires_grad_(True)
+    vals = asm(coef)
+    vals.retain_grad()
+    b = b0.clone().requires_grad_(True)
+    ((F(vals, b) - xt) ** 2).sum().backward()
+    gb_, gv, gc = b.grad, vals.grad, coef.grad
+    v0 = vals.detach()
+    h = 1e-6
+
+    def diff(vp, bp, vm, bm):
+        with torch.no_grad():
+            xp, xm = F(vp, bp), F(vm, bm)
+        return float(((xp - xm) * (xp + xm - 2.0 * xt)).sum())
+
+    def derivative(point):
+        return (8.0 * diff(*point(h), *point(-h)) - diff(*point(2 * h), *point(-2 * h))) / (12.0 * h)
+
+    gen = torch.Generator(device=dev).manual_seed(5)
+    errs = {}
+    for t in range(8):
+        if t < 3:
+            d = torch.randn(b0.shape, generator=gen, device=dev, dtype=torch.float64) * b0.abs()
+            fd, an, fam = derivative(lambda e: (v0, b0 + e * d)), float(gb_ @ d), "b"
+        elif t < 6:
+            d = torch.randn(v0.shape, generator=gen, device=dev, dtype=torch.float64) * v0.abs()
+            fd, an, fam = derivative(lambda e: (v0 + e * d, b0)), float(gv @ d), "values"
+        else:
+            ci = torch.arange(el.count, device=dev) // 6
+            p = torch.stack([((ci % (g.nx - 1)).double() + 0.5) / (g.nx - 1),
+                             (((ci // (g.nx - 1)) % (g.ny - 1)).double() + 0.5) / (g.ny - 1),
+                             ((ci // ((g.nx - 1) * (g.ny - 1))).double() + 0.5) / (g.nz - 1)], dim=1)
+            f = torch.zeros(el.count, dtype=torch.float64, device=dev)
+            for _ in range(3):
+                kv = torch.randint(0, 3, (3,), generator=gen, device=dev).double()
+                a = torch.randn((), generator=gen, device=dev, dtype=torch.float64)
+                ph = 6.283185307179586 * torch.rand((), generator=gen, device=dev, dtype=torch.float64)
+                f += a * torch.cos(6.283185307179586 * (p @ kv) + ph)
+            d = f * coef0
+            with torch.no_grad():
+                fd = derivative(lambda e: (asm(coef0 + e * d), b0))
+            an, fam = float(gc @ d), "coefficients"
+        errs.setdefault(fam, []).append(abs(fd - an) / abs(fd))
+    out["fd_max_rel_error"] = {k: max(v) for k, v in errs.items()}
+    out["fd_directions"] = {k: len(v) for k, v in errs.items()}
+    S.close()
+    F.close()
+    # 6^3 dense reference gradient
+    g6 = femgen.Grid(6, 6, 6, contrast=50.0, seed_mesh=7, seed_x=8)
+    s6 = femgen.build_system(g6)
+    el6 = femgen.elements(g6)
+    xt6 = femgen.random_vector(s6.n, 77)
+    A6 = np.zeros((s6.n, s6.n))
+    for i in range(s6.n):
+        A6[i, s6.idx[s6.ptr[i]:s6.ptr[i + 1]]] = s6.val[s6.ptr[i]:s6.ptr[i + 1]]
+    x6 = np.linalg.solve(A6, s6.b)
+    lam6 = np.linalg.solve(A6, 2.0 * (x6 - xt6))
+    u6 = s6.upper()
+    p6, w6 = femgen.element_map(el6, u6[0], u6[1], storage="sym")
+    t6 = femgen.assembly_map(p6, w6, len(u6[1]))
+    asm6 = gb.Assembly(p6, w6, *t6)
+    c6 = torch.from_numpy(el6.coef).to(dev).requires_grad_(True)
+    S6 = gb.SparseSolve("sym", u6[0], u6[1], u6[2], tol=1e-13)
+    b6 = torch.from_numpy(s6.b).to(dev).requires_grad_(True)
+    ((S6(asm6(c6), b6) - torch.from_numpy(xt6).to(dev)) ** 2).sum().backward()
+    S6.close()
+    out["dense_6cube_rel_error_grad_b"] = float(np.linalg.norm(b6.grad.cpu().numpy() - lam6) / np.linalg.norm(lam6))
     return out
 
 
