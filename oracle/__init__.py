@@ -9,7 +9,7 @@ with the CUDA path.
 
 Parity status per function (what pins it; see ``tests/test_oracle_pins.py``):
   spmv (CSR, symmetric upper, CSC)  -- dense brute force, format equivalence
-  cg                                  -- dense Cholesky, finite termination,
+  cg (also pipelined=True)            -- dense Cholesky, finite termination,
                                          A-orthogonality, A-norm monotonicity,
                                          closed-form diagonal/tridiagonal cases
   cg_f32 / cg_ir                      -- true residual in double, error vs x*
@@ -90,6 +90,8 @@ def load(path: str | None = None):
     lib.orc_cg_ir.argtypes = [ctypes.c_int, i64, vp, vp, vp, vp, vp, d, i32, d, i32,
                               ctypes.POINTER(Info)]
     lib.orc_grad_values.argtypes = [ctypes.c_int, i64, vp, vp, vp, vp, vp]
+    lib.orc_cg_pipelined.argtypes = [ctypes.c_int, i64, vp, vp, vp, vp, vp, d, i32,
+                                     ctypes.POINTER(Info), ctypes.POINTER(History)]
     lib.orc_element_grad.argtypes = [i64, i32, vp, vp, vp, vp]
     lib.orc_assemble.argtypes = [i64, vp, vp, vp, vp, vp]
     if path is None:
@@ -178,8 +180,9 @@ class Result:
     beta: np.ndarray | None = None
 
 
-def cg(fmt, ptr, idx, val, b, x0=None, tol=1e-10, maxit=None, history=0, lib=None) -> Result:
-    """Plain double-precision CG (Section III listing; readings in oracle.c)."""
+def cg(fmt, ptr, idx, val, b, x0=None, tol=1e-10, maxit=None, history=0, lib=None, pipelined=False) -> Result:
+    """Plain double-precision CG (Section III listing; readings in oracle.c);
+    pipelined=True: the single-reduction form of the same iteration."""
     lib = lib or load()
     ptr, idx, val = _arrays(ptr, idx, val)
     n = ptr.shape[0] - 1
@@ -195,8 +198,9 @@ def cg(fmt, ptr, idx, val, b, x0=None, tol=1e-10, maxit=None, history=0, lib=Non
         al = np.zeros(history)
         be = np.zeros(history)
         hist = History(history, 0, ph.ctypes.data, xh.ctypes.data, al.ctypes.data, be.ctypes.data)
-    lib.orc_cg(_fmt(fmt), n, _p(ptr), _p(idx), _p(val), _p(b), _p(x), float(tol), maxit,
-               ctypes.byref(info), ctypes.byref(hist) if hist is not None else None)
+    fn = lib.orc_cg_pipelined if pipelined else lib.orc_cg
+    fn(_fmt(fmt), n, _p(ptr), _p(idx), _p(val), _p(b), _p(x), float(tol), maxit,
+       ctypes.byref(info), ctypes.byref(hist) if hist is not None else None)
     res = Result(x, info.iterations, info.restarts, STATUS[info.status], info.rel_res_recursive,
                  info.rel_res_true)
     if history:

@@ -258,6 +258,106 @@ done:
   return status;
 }
 
+/* Single-reduction ("pipelined") CG.  The Chronopoulos-Gear form of the
+ * Section III iteration, rearranged (Ghysels and Vanroose) so that both inner
+ * products of an iteration, r'r and w'r with w = A r, are formed together
+ * and the product q = A w does not wait for them.  With s = A p and z = A s
+ * kept by recurrence:
+ *   beta = gamma / gamma_old, alpha = gamma / (delta - beta gamma / alpha_old)
+ *   (first step: beta = 0, alpha = gamma / delta); the denominator is p'Ap;
+ *   z = q + beta z, s = w + beta s, p = r + beta p,
+ *   x += alpha p, r -= alpha s, w -= alpha z.
+ * In exact arithmetic x_k equals the Section III iterate.  Stopping rule,
+ * true-residual confirmation and restarts (from r = b - A x, w = A r, p = r)
+ * as in orc_cg.  Its recurrences for r and w drift from b - A x and A r
+ * faster than the Section III ones, so it restarts more often.  The history
+ * records x after each iteration. */
+int orc_cg_pipelined(int fmt, int64_t n, const int32_t* ptr, const int32_t* idx, const double* val, const double* b,
+                     double* x, double tol, int32_t maxit, orc_info* info, orc_history* hist) {
+  memset(info, 0, sizeof(*info));
+  if (n < 0 || maxit < 0 || !(tol >= 0.0)) {
+    info->status = ORC_INVALID;
+    return ORC_INVALID;
+  }
+  const size_t nn = (size_t)(n ? n : 1);
+  double* r = (double*)malloc(sizeof(double) * nn);
+  double* w = (double*)malloc(sizeof(double) * nn);
+  double* p = (double*)malloc(sizeof(double) * nn);
+  double* s = (double*)malloc(sizeof(double) * nn);
+  double* z = (double*)malloc(sizeof(double) * nn);
+  double* q = (double*)malloc(sizeof(double) * nn);
+  if (hist) hist->count = 0;
+  int status = ORC_OK;
+  int32_t k = 0, restarts = 0;
+  double nb = sqrt(orc_dot(n, b, b));
+  double gamma = 0.0;
+  if (nb == 0.0) {
+    for (int64_t i = 0; i < n; ++i) x[i] = 0.0;
+    goto done;
+  }
+  for (;;) {
+    orc_spmv(fmt, n, ptr, idx, val, x, q);
+    for (int64_t i = 0; i < n; ++i) r[i] = b[i] - q[i];      /* r = b - A x */
+    orc_spmv(fmt, n, ptr, idx, val, r, w);                   /* w = A r */
+    double gamma_old = 0.0, alpha_old = 0.0;
+    int first = 1;
+    for (;;) {
+      gamma = orc_dot(n, r, r);
+      const double delta = orc_dot(n, w, r);
+      if (!isfinite(gamma) || !isfinite(delta)) { status = ORC_NONFINITE; goto done; }
+      if (sqrt(gamma) / nb <= tol || k >= maxit) break;
+      orc_spmv(fmt, n, ptr, idx, val, w, q);                 /* q = A w */
+      const double beta = first ? 0.0 : gamma / gamma_old;
+      const double den = first ? delta : delta - beta * gamma / alpha_old;   /* p'Ap */
+      if (!isfinite(den)) { status = ORC_NONFINITE; goto done; }
+      if (!(den > 0.0)) { status = ORC_NOT_SPD; goto done; }
+      const double alpha = gamma / den;
+      for (int64_t i = 0; i < n; ++i) {
+        z[i] = (first ? 0.0 : beta * z[i]) + q[i];
+        s[i] = (first ? 0.0 : beta * s[i]) + w[i];
+        p[i] = (first ? 0.0 : beta * p[i]) + r[i];
+      }
+      for (int64_t i = 0; i < n; ++i) {
+        x[i] += alpha * p[i];
+        r[i] -= alpha * s[i];
+        w[i] -= alpha * z[i];
+      }
+      ++k;
+      if (hist && hist->count < hist->cap) {
+        int32_t h = hist->count++;
+        if (hist->p) memcpy(hist->p + (size_t)h * n, p, sizeof(double) * n);
+        if (hist->x) memcpy(hist->x + (size_t)h * n, x, sizeof(double) * n);
+        if (hist->alpha) hist->alpha[h] = alpha;
+        if (hist->beta) hist->beta[h] = beta;
+      }
+      gamma_old = gamma;
+      alpha_old = alpha;
+      first = 0;
+    }
+    orc_spmv(fmt, n, ptr, idx, val, x, q);
+    for (int64_t i = 0; i < n; ++i) q[i] = b[i] - q[i];
+    const double rt = orc_dot(n, q, q);
+    info->rel_res_true = sqrt(rt) / nb;
+    if (info->rel_res_true <= tol) break;
+    if (k >= maxit || restarts >= 3) { status = ORC_MAXIT; break; }
+    ++restarts;
+  }
+done:
+  info->iterations = k;
+  info->restarts = restarts;
+  info->status = status;
+  info->rel_res_recursive = nb > 0.0 ? sqrt(gamma) / nb : 0.0;
+  if (status != ORC_OK && status != ORC_MAXIT) info->rel_res_true = NAN;
+  if (nb == 0.0) info->rel_res_true = 0.0;
+  free(r);
+  free(w);
+  free(p);
+  free(s);
+  free(z);
+  free(q);
+  return status;
+}
+
 /* Single-precision CG (Section IV's single-precision variant): solves
  * A32 d = rhs from d = 0 until ||r|| <= tol ||rhs|| or maxit; float
  * throughout.  Returns iterations used; *breakdown set on p'Ap <= 0. */

@@ -322,6 +322,55 @@ def check_cg_edge_cases(lib):
     assert np.linalg.norm(r.x - xe) <= 1e-10 * np.linalg.norm(xe)
 
 
+# ------------------------------------------------------ pipelined CG ---
+def check_pipelined_equals_cg_iterates(lib):
+    # in exact arithmetic the single-reduction recurrences give the iterates
+    # and step lengths of the Section III listing; on well-conditioned
+    # systems the two agree to rounding over the first steps
+    for seed, n in ((3, 30), (4, 45)):
+        (ptr, idx, val), A = spd_sparse(n, 30 + seed, density=0.3, shift=3.0)
+        b = np.random.default_rng(seed).uniform(-1, 1, n)
+        a = oracle.cg("csr", ptr, idx, val, b, tol=0.0, maxit=8, history=8, lib=lib)
+        q = oracle.cg("csr", ptr, idx, val, b, tol=0.0, maxit=8, history=8, lib=lib, pipelined=True)
+        assert a.x_hist.shape == q.x_hist.shape == (8, n)
+        np.testing.assert_allclose(q.x_hist, a.x_hist, rtol=0, atol=1e-11 * np.abs(a.x_hist).max())
+        np.testing.assert_allclose(q.alpha, a.alpha, rtol=1e-10)
+        np.testing.assert_allclose(q.beta[1:], a.beta[:-1], rtol=1e-9)   # beta of step k+1 pairs with CG's step k
+
+
+def check_pipelined_vs_cholesky_and_edges(lib):
+    for seed, n in enumerate([1, 3, 10, 25, 40]):
+        (ptr, idx, val), A = spd_sparse(n, 10 + seed, density=0.3, shift=2.0)
+        b = np.random.default_rng(seed).uniform(-1, 1, n)
+        xc = sla.cho_solve(sla.cho_factor(A), b)
+        for fmt, arrs in (("csr", (ptr, idx, val)), ("sym", femgen.upper(n, ptr, idx, val))):
+            r = oracle.cg(fmt, *arrs, b, tol=1e-13, maxit=10 * n + 10, lib=lib, pipelined=True)
+            assert r.status == "OK", (fmt, n, r.status)
+            assert np.linalg.norm(r.x - xc) <= 1e-11 * np.linalg.norm(xc), (fmt, n)
+    s = fem_small(7, 8, 6, contrast=1000.0)
+    D = dense_of(s.ptr, s.idx, s.val, s.n)
+    xc = sla.cho_solve(sla.cho_factor(D), s.b)
+    r = oracle.cg("csr", s.ptr, s.idx, s.val, s.b, tol=1e-12, maxit=20 * s.n, lib=lib, pipelined=True)
+    assert r.status == "OK" and r.rel_res_true <= 1e-12
+    assert np.linalg.norm(r.x - xc) / np.linalg.norm(xc) <= 1e-8
+    # diagonal with 3 distinct values: exactly 3 steps
+    d = np.repeat([3.0, 0.5, 7.0], 7)
+    ptr = np.arange(22, dtype=np.int32)
+    idx = np.arange(21, dtype=np.int32)
+    bb = np.random.default_rng(2).uniform(0.5, 1.0, 21)
+    r = oracle.cg("csr", ptr, idx, d, bb, tol=1e-13, lib=lib, pipelined=True)
+    assert r.status == "OK" and r.iterations == 3, r.iterations
+    assert np.allclose(r.x, bb / d, rtol=1e-12, atol=0)
+    (ptr, idx, val), A = spd_sparse(20, 5, shift=1.0)
+    b = np.random.default_rng(0).uniform(-1, 1, 20)
+    r = oracle.cg("csr", ptr, idx, val, np.zeros(20), x0=np.ones(20), lib=lib, pipelined=True)
+    assert r.status == "OK" and r.iterations == 0 and not np.any(r.x)
+    r = oracle.cg("csr", ptr, idx, val, b, tol=1e-30, maxit=3, lib=lib, pipelined=True)
+    assert r.status == "MAXIT" and r.iterations == 3
+    r = oracle.cg("csr", ptr, idx, -val, b, lib=lib, pipelined=True)
+    assert r.status == "NOT_SPD" and r.iterations == 0
+
+
 def check_cg_f32(lib):
     s = fem_small(8, 8, 8, contrast=10.0)
     u = s.upper()
@@ -446,5 +495,5 @@ ALL_CHECKS = [
     check_cg_finite_termination, check_cg_exact_first_steps, check_cg_a_orthogonality,
     check_cg_error_a_norm_decreases, check_cg_tridiagonal_closed_form, check_cg_edge_cases,
     check_cg_f32, check_cg_ir, check_grad_dense_reference, check_assemble_reproduces_the_generator,
-    check_grad_finite_differences,
+    check_grad_finite_differences, check_pipelined_equals_cg_iterates, check_pipelined_vs_cholesky_and_edges,
 ]

@@ -40,6 +40,11 @@ MUTANTS = {
     "grad_sign": ("        g[k] = -(lambda[r] * x[c]);\n      }\n    }", "        g[k] = lambda[r] * x[c];\n      }\n    }"),
     "element_grad_drops_weight": ("if (p >= 0) s += w[e * m + k] * g[p];", "if (p >= 0) s += g[p];"),
     "assemble_drops_coefficient": ("s += tw[k] * coef[telem[k]];", "s += tw[k];"),
+    "pipelined_z_drops_beta": ("z[i] = (first ? 0.0 : beta * z[i]) + q[i];", "z[i] = q[i];"),
+    "pipelined_plain_denominator": ("const double den = first ? delta : delta - beta * gamma / alpha_old;",
+                                    "const double den = delta;"),
+    "pipelined_w_sign": ("w[i] -= alpha * z[i];", "w[i] += alpha * z[i];"),
+    "pipelined_s_uses_r": ("s[i] = (first ? 0.0 : beta * s[i]) + w[i];", "s[i] = (first ? 0.0 : beta * s[i]) + r[i];"),
 }
 
 
