@@ -270,7 +270,11 @@ done:
  * In exact arithmetic x_k equals the Section III iterate.  Stopping rule,
  * true-residual confirmation and restarts (from r = b - A x, w = A r, p = r)
  * as in orc_cg.  Its recurrences for r and w drift from b - A x and A r
- * faster than the Section III ones, so it restarts more often.  The history
+ * faster than the Section III ones, so it restarts more often; and its p'Ap,
+ * formed by the recurrence delta - beta gamma / alpha_old, cancels near the
+ * attainable residual, so a non-positive value there also ends the run into
+ * the confirmation.  Only on the first step of a run (p'Ap = r'Ar) does it
+ * show that A is not positive definite.  The history
  * records x after each iteration. */
 int orc_cg_pipelined(int fmt, int64_t n, const int32_t* ptr, const int32_t* idx, const double* val, const double* b,
                      double* x, double tol, int32_t maxit, orc_info* info, orc_history* hist) {
@@ -310,7 +314,13 @@ int orc_cg_pipelined(int fmt, int64_t n, const int32_t* ptr, const int32_t* idx,
       const double beta = first ? 0.0 : gamma / gamma_old;
       const double den = first ? delta : delta - beta * gamma / alpha_old;   /* p'Ap */
       if (!isfinite(den)) { status = ORC_NONFINITE; goto done; }
-      if (!(den > 0.0)) { status = ORC_NOT_SPD; goto done; }
+      if (!(den > 0.0)) {
+        /* on a first step den = r'Ar: A is not positive definite; later, the
+         * recurrence for p'Ap has lost its accuracy (near the attainable
+         * residual): confirm and restart from the true residual */
+        if (first) { status = ORC_NOT_SPD; goto done; }
+        break;
+      }
       const double alpha = gamma / den;
       for (int64_t i = 0; i < n; ++i) {
         z[i] = (first ? 0.0 : beta * z[i]) + q[i];
