@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU-oracle sample")
     ap.add_argument("--only-batched", action="store_true", help="only run the batched leg")
     ap.add_argument("--only-differentiable", action="store_true", help="only run the differentiation leg")
+    ap.add_argument("--only-paper-size", action="store_true", help="only run the paper-size leg")
     ap.add_argument("--profile-batched", type=int, default=0,
                     help="only one mixed-precision solve of the first N batch instances (small case for ncu)")
     ap.add_argument("--profile-spmv", action="store_true",
@@ -225,6 +226,9 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     if args.only_batched:
         print(json.dumps({"batched": batched(torch, gb, args)}), flush=True)
+        return 0
+    if args.only_paper_size:
+        print(json.dumps({"paper_size": paper_size(torch, gb, args)}), flush=True)
         return 0
     if args.only_differentiable:
         print(json.dumps({"differentiable": differentiable(torch, gb, args)}), flush=True)
@@ -415,7 +419,10 @@ def paper_size(torch, gb, args):
     for fmt in ("sym", "csr"):
         with gb.Matrix(fmt, *arrays[fmt]) as M:
             out[fmt] = {"grid_ctas": M.stats()["grid_ctas"]}
-            for prec in ("fp64", "fp32_ir"):
+            runs = [("fp64", "standard"), ("fp32_ir", "standard")]
+            if fmt == "csr":
+                runs += [("fp64", "pipelined")]
+            for prec, variant in runs:
                 x = torch.zeros_like(b)
                 ts = []
                 for k in range(4):
@@ -423,15 +430,16 @@ def paper_size(torch, gb, args):
                     torch.cuda.synchronize()
                     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                     e0.record()
-                    _, info = M.solve(b, x, tol=TOL, precision=prec, inner_tol=args.inner_tol)
+                    _, info = M.solve(b, x, tol=TOL, precision=prec, inner_tol=args.inner_tol, variant=variant)
                     e1.record()
                     torch.cuda.synchronize()
                     if k:
                         ts.append(e0.elapsed_time(e1) / 1000.0)
                 t = statistics.median(ts)
-                out[fmt][prec] = {"s": t, "iterations": info.iterations, "outer": info.outer,
-                                  "status": info.status, "rel_res_true": info.rel_res_true,
-                                  "iter_us": 1000.0 * info.kernel_ms / max(info.iterations, 1)}
+                key = prec if variant == "standard" else f"{prec}_pipelined"
+                out[fmt][key] = {"s": t, "iterations": info.iterations, "outer": info.outer,
+                                 "status": info.status, "rel_res_true": info.rel_res_true,
+                                 "iter_us": 1000.0 * info.kernel_ms / max(info.iterations, 1)}
     return out
 
 

@@ -64,6 +64,19 @@ enum gbcg_precision {
 
 enum gbcg_memory { GBCG_HOST = 0, GBCG_DEVICE = 1 };
 
+/* Arrangement of the CG recurrences (both give the Section III iterates in
+ * exact arithmetic). */
+enum gbcg_variant {
+  GBCG_STANDARD = 0,      /* the Section III listing: three grid barriers per iteration */
+  GBCG_PIPELINED = 1      /* single reduction (Chronopoulos-Gear recurrences, Ghysels-
+                             Vanroose arrangement): one fused pass over the rows and one
+                             grid barrier per iteration, for three more vector streams;
+                             its recurrences drift faster, so it restarts more often.
+                             Double precision (GBCG_FP64) and row-gather layouts only
+                             (CSR, CSC, symmetric with the transpose plan); other
+                             combinations return GBCG_ERR_INVALID */
+};
+
 /* Solver options.  Zero-initialised fields take the documented defaults. */
 typedef struct {
   int32_t precision;          /* gbcg_precision; default GBCG_FP64 */
@@ -71,6 +84,8 @@ typedef struct {
   double inner_tol;           /* inner relative tolerance for GBCG_FP32_IR; default 1e-4 */
   int32_t wait_timeout_ms;    /* bound on every device-side wait; default 1000 */
   int32_t max_restarts;       /* true-residual restarts for GBCG_FP64; default 3 */
+  int32_t variant;            /* gbcg_variant; default GBCG_STANDARD */
+  int32_t pad_;
 } gbcg_opts;
 
 /* Report of one solve. */

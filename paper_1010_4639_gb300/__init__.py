@@ -23,6 +23,7 @@ from ._lib import GbcgError
 FORMATS = {"csr": _lib.GBCG_CSR, "sym": _lib.GBCG_SYM_CSR_UPPER, "sym_upper": _lib.GBCG_SYM_CSR_UPPER,
            "csc": _lib.GBCG_CSC}
 PRECISIONS = {"fp64": _lib.GBCG_FP64, "fp32_ir": _lib.GBCG_FP32_IR, "ir": _lib.GBCG_FP32_IR}
+VARIANTS = {"standard": _lib.GBCG_STANDARD, "pipelined": _lib.GBCG_PIPELINED}
 
 
 def build(verbose: bool = False) -> str:
@@ -188,7 +189,7 @@ class Matrix:
     # ------------------------------------------------------------ solve
     def solve(self, b, x=None, tol: float = 1e-10, maxit: int = 0, precision: str = "fp64",
               inner_tol: float = 1e-4, max_outer: int = 30, wait_timeout_ms: int = 1000,
-              max_restarts: int = 3, stream=None, raise_on_error: bool = True):
+              max_restarts: int = 3, variant: str = "standard", stream=None, raise_on_error: bool = True):
         """Conjugate gradient for A x = b (``gbcg_solve``).
 
         ``b`` and ``x`` are float64 CUDA tensors, or numpy arrays (host
@@ -196,7 +197,7 @@ class Matrix:
         (zeros if None) and the solution on return.  Returns (x, SolveInfo).
         """
         opts = _lib.Opts(PRECISIONS[precision], int(max_outer), float(inner_tol), int(wait_timeout_ms),
-                         int(max_restarts))
+                         int(max_restarts), VARIANTS[variant], 0)
         info = _lib.Info()
         if _is_tensor(b):
             torch = _torch()

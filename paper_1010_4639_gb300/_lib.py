@@ -15,6 +15,7 @@ LIB_PATH = os.path.join(HERE, "libgbcg.so")
 GBCG_CSR, GBCG_SYM_CSR_UPPER, GBCG_CSC = 0, 1, 2
 GBCG_FP64, GBCG_FP32_IR = 0, 1
 GBCG_HOST, GBCG_DEVICE = 0, 1
+GBCG_STANDARD, GBCG_PIPELINED = 0, 1
 STATUS_NAMES = ["OK", "INVALID", "NOT_SPD", "MAXIT", "NONFINITE", "TIMEOUT", "CUDA", "NOMEM"]
 
 # Every entry point declared in include/gbcg.h.
@@ -29,7 +30,8 @@ STATIC_MAX_N = 680000
 
 class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("max_outer", ctypes.c_int32), ("inner_tol", ctypes.c_double),
-                ("wait_timeout_ms", ctypes.c_int32), ("max_restarts", ctypes.c_int32)]
+                ("wait_timeout_ms", ctypes.c_int32), ("max_restarts", ctypes.c_int32), ("variant", ctypes.c_int32),
+                ("pad_", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):

@@ -120,6 +120,8 @@ struct gbcg_matrix_s {
   // workspace
   double *r = nullptr, *p = nullptr, *q = nullptr, *bstage = nullptr, *xstage = nullptr;
   float *r32 = nullptr, *p32 = nullptr, *q32 = nullptr, *d32 = nullptr, *rhs32 = nullptr;
+  // single-reduction CG (double precision): s = A p, z = A s, w = A r (two buffers)
+  double *s64 = nullptr, *z64 = nullptr, *w64a = nullptr, *w64b = nullptr;
   double* part = nullptr;   // max(2 * grid, one-shot blocks)
   double* sums = nullptr;   // small scalars
   int64_t part_len = 0;
@@ -212,7 +214,7 @@ void free_matrix(gbcg_matrix_s* M) {
                  M->t_tile_ns, M->t_tile_own, M->t_tile_len, M->t_tile_rlog, M->t_tile_win, M->t_win_start, M->t_win_len,
                  M->t_tile_ent, M->t_tile_meta, M->t_tile_ext, M->t_in_src, M->t_meta, M->t_val64, M->t_val32,
                  M->t_in_ptr, M->t_in_row, M->t_in_len, M->t_part, M->u_map_main, M->u_map_long, M->u_map_diag,
-                 M->u_stage};
+                 M->u_stage, M->s64, M->z64, M->w64a, M->w64b};
   for (void* d : dev)
     if (d) cudaFree(d);
   if (M->st_h) cudaFreeHost(M->st_h);
@@ -234,6 +236,19 @@ int occupancy_of(int& per_sm) {
   return 0;
 }
 
+template <int FMT>
+int pcg_occupancy_of(int& per_sm) {
+  if constexpr (FMT == kTiles) {
+    per_sm = 1 << 20;
+    return 0;
+  } else {
+    const size_t sm = product_smem<double, FMT>();
+    CUDA_TRY(cudaFuncSetAttribute(k_pcg<double, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg<double, FMT>, kCgThreads, sm));
+    return 0;
+  }
+}
+
 template <typename V, int FMT>
 int prepare_rows() {
   CUDA_TRY(cudaFuncSetAttribute(k_rows<V, FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -245,12 +260,13 @@ int prepare_rows() {
 // the shared-memory attributes of the kernels of that mode).
 template <int FMT>
 int solver_occupancy(int& per_sm) {
-  int a = 0, b = 0;
+  int a = 0, b = 0, c = 0;
   if (int rc = occupancy_of<double, FMT, true>(a)) return rc;
   if (int rc = occupancy_of<float, FMT, false>(b)) return rc;
+  if (int rc = pcg_occupancy_of<FMT>(c)) return rc;
   if (int rc = prepare_rows<double, FMT>()) return rc;
   if (int rc = prepare_rows<float, FMT>()) return rc;
-  per_sm = std::min(a, b);
+  per_sm = std::min(std::min(a, b), c);
   return 0;
 }
 
@@ -282,6 +298,25 @@ cudaError_t launch_cg_fmt(const gbcg_matrix_s* M, const CgArgs<V>& a, cudaStream
     case kPlan: return launch_cg<V, kPlan, OUTER>(a, M->grid, s);
     default: return launch_cg<V, kGather, OUTER>(a, M->grid, s);
   }
+}
+
+template <int FMT>
+cudaError_t launch_pcg(const PcgArgs<double>& args, int grid, cudaStream_t s) {
+  void* kargs[] = {(void*)&args};
+  return cudaLaunchCooperativeKernel((const void*)k_pcg<double, FMT>, dim3(grid), dim3(kCgThreads), kargs,
+                                     product_smem<double, FMT>(), s);
+}
+
+// The single-reduction CG on the handle's layout (row-gather layouts only;
+// the caller has checked the mode).
+cudaError_t launch_pcg_fmt(const gbcg_matrix_s* M, const CgArgs<double>& c, cudaStream_t s) {
+  PcgArgs<double> a;
+  a.c = c;
+  a.s = M->s64;
+  a.z = M->z64;
+  a.w0 = M->w64a;
+  a.w1 = M->w64b;
+  return M->mode == kPlan ? launch_pcg<kPlan>(a, M->grid, s) : launch_pcg<kGather>(a, M->grid, s);
 }
 
 // Product y = A x (MODE 0), or r = b - A x into y with per-CTA partial sums
@@ -357,7 +392,10 @@ int solve_fp64(gbcg_matrix_s* M, const double* b, double* x, double tol, int max
   CUDA_TRY(cudaMemsetAsync(M->bar, 0, sizeof(GridBar), s));
   CgArgs<double> a = make_args<double>(M, x, M->r, M->p, M->q, b, tol, maxit, max_restarts, timeout_ns_of(o));
   CUDA_TRY(cudaEventRecord(M->ev0, s));
-  CUDA_TRY(launch_cg_fmt<double, true>(M, a, s));
+  if (o && o->variant == GBCG_PIPELINED)
+    CUDA_TRY(launch_pcg_fmt(M, a, s));
+  else
+    CUDA_TRY(launch_cg_fmt<double, true>(M, a, s));
   CUDA_TRY(cudaEventRecord(M->ev1, s));
   if (int rc = read_state(M, s)) return rc;
   float kms = 0.f;
@@ -622,7 +660,13 @@ int gbcg_create(gbcg_matrix_t* out, int32_t format, int64_t n, int64_t nnz, cons
   TRY(dalloc(&M->q32, nn, B));
   TRY(dalloc(&M->d32, nn, B));
   TRY(dalloc(&M->rhs32, nn, B));
-  M->part_len = std::max<int64_t>({2 * (int64_t)M->grid, (int64_t)M->spmv_blocks(), 4096});
+  if (M->mode != kTiles) {  // the single-reduction CG's vectors
+    TRY(dalloc(&M->s64, nn, B));
+    TRY(dalloc(&M->z64, nn, B));
+    TRY(dalloc(&M->w64a, nn, B));
+    TRY(dalloc(&M->w64b, nn, B));
+  }
+  M->part_len = std::max<int64_t>({6 * (int64_t)M->grid, (int64_t)M->spmv_blocks(), 4096});
   TRY(dalloc(&M->part, (size_t)M->part_len, B));
   TRY(dalloc(&M->sums, 8, B));
   TRY(dalloc(&M->bar, 1, B));
@@ -664,6 +708,16 @@ int gbcg_solve(gbcg_matrix_t A, const double* b, double* x, double tol, int32_t 
   if (!(tol >= 0.0) || !std::isfinite(tol)) return fail(GBCG_ERR_INVALID, "tol must be finite and >= 0");
   if (opts && (opts->precision != GBCG_FP64 && opts->precision != GBCG_FP32_IR))
     return fail(GBCG_ERR_INVALID, "unknown precision");
+  if (opts && opts->variant != GBCG_STANDARD && opts->variant != GBCG_PIPELINED)
+    return fail(GBCG_ERR_INVALID, "unknown variant");
+  if (opts && opts->variant == GBCG_PIPELINED && opts->precision == GBCG_FP32_IR)
+    return fail(GBCG_ERR_INVALID,
+                "the single-reduction variant is double precision only: in single precision its recurrences "
+                "drift past any useful inner tolerance");
+  if (opts && opts->variant == GBCG_PIPELINED && A->mode == kTiles)
+    return fail(GBCG_ERR_INVALID,
+                "the single-reduction variant runs on row-gather layouts (CSR, CSC, or symmetric storage with "
+                "GBCG_SYM_LAYOUT=plan); the tiled symmetric product needs a barrier of its own");
   const auto t0 = std::chrono::steady_clock::now();
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t n = A->n;

@@ -1084,6 +1084,182 @@ finish:
   }
 }
 
+// Extra vectors of the single-reduction CG: s = A p, z = A s, and w = A r
+// double-buffered (the product of an iteration reads one buffer while the
+// update writes the other).
+template <typename V>
+struct PcgArgs {
+  CgArgs<V> c;
+  V* s;
+  V* z;
+  V* w0;
+  V* w1;
+};
+
+// Single-reduction ("pipelined") CG: the Chronopoulos-Gear recurrences of the
+// Section III iteration in the Ghysels-Vanroose arrangement.  Each iteration
+// is ONE pass over the CTA's rows -- the product q = A w fused, row by row,
+// with z = q + beta z, s = w + beta s, p = r + beta p, x += alpha p,
+// r -= alpha s, w' = w - alpha z and the partial sums of r'r and w'r -- and
+// ONE grid barrier, after which every CTA forms alpha and beta from the same
+// sums in the same order.  (k_cg needs three barriers per iteration.)  The
+// partial sums alternate between two halves of the partial-sum array, so a
+// CTA never overwrites sums another CTA may still be reading.  The full
+// solve from x0 with true-residual confirmation and restarts (from
+// r = b - A x), in double precision: in single precision the recurrences
+// drift past any useful inner tolerance.  p'Ap comes from the
+// recurrence delta - beta gamma / alpha_old, which cancels near the
+// attainable residual: a non-positive value after the first step of a run
+// ends the run into the confirmation instead of reporting NOT_SPD.
+// Row-gather layouts only (kGather, kPlan): their product needs no barrier
+// of its own.
+template <typename V, int FMT>
+__global__ void __launch_bounds__(kCgThreads, 1) k_pcg(PcgArgs<V> pa) {
+  static_assert(FMT != kTiles, "the tiled symmetric product needs a barrier of its own");
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ uint64_t bars[kMaxThreads / 32][kMaxStages];
+  __shared__ double red[33];
+  __shared__ int sflag;
+  const CgArgs<V>& a = pa.c;
+  const int G = gridDim.x, c = blockIdx.x;
+  const int64_t s0 = a.cta_slice[c], s1 = a.cta_slice[c + 1];
+  const int64_t l0 = a.cta_long[c], l1 = a.cta_long[c + 1];
+  const int64_t r0 = s0 * 32;
+  const int64_t r1 = s1 * 32 < a.A.n ? s1 * 32 : a.A.n;
+  const OpDev<V>& A = a.A;
+  V* __restrict__ x = a.x;
+  V* __restrict__ r = a.r;
+  V* __restrict__ p = a.p;
+  V* __restrict__ q = a.q;
+  V* __restrict__ sv = pa.s;
+  V* __restrict__ zv = pa.z;
+  V* wb[2] = {pa.w0, pa.w1};
+  const V* __restrict__ b = a.b;
+  Pipe pp;
+  pipe_init(pp, bars[threadIdx.x >> 5], gather_stages<V>(), a.timeout_ns);
+  __syncthreads();
+  int* err = &a.bar->status;
+  Stage<V>* stages = reinterpret_cast<Stage<V>*>(smem_raw) + (threadIdx.x >> 5) * gather_stages<V>();
+  unsigned long long target = 0;
+  int nbar = 0, status = kOk, k = 0, restarts = 0, par = 0, cur = 0;
+  double gamma = 0.0, delta = 0.0, nb = 0.0, rel_true = 0.0;
+  // partial-sum half `h`: sums j = 0, 1 (and 2 for b'b) of every CTA
+  auto slot = [&](int h, int j) { return a.part + (int64_t)(3 * h + j) * G; };
+  auto publish = [&](int h, double v0, double v1, double v2) -> bool {
+    const double s_0 = block_sum(v0, red);
+    if (threadIdx.x == 0) slot(h, 0)[c] = s_0;
+    const double s_1 = block_sum(v1, red);
+    if (threadIdx.x == 0) slot(h, 1)[c] = s_1;
+    const double s_2 = block_sum(v2, red);
+    if (threadIdx.x == 0) slot(h, 2)[c] = s_2;
+    return grid_barrier(a.bar, target, a.timeout_ns, &sflag, nbar++);
+  };
+  for (bool first_run = true;; first_run = false) {
+    // r = b - A x; then w = A r with r'r, w'r (and b'b)
+    spmv_rows<V, FMT == kPlan, false>(A, s0, s1, l0, l1, x, stages, pp, err, [&](int64_t row, V v) { q[row] = v; });
+    __syncthreads();
+    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) r[i] = b[i] - q[i];
+    if (!grid_barrier(a.bar, target, a.timeout_ns, &sflag, nbar++)) return;
+    {
+      V pg = V(0), pd = V(0), pb = V(0);
+      V* __restrict__ w = wb[cur];
+      spmv_rows<V, FMT == kPlan, false>(A, s0, s1, l0, l1, r, stages, pp, err, [&](int64_t row, V v) {
+        w[row] = v;
+        const V ri = r[row];
+        pg = fma_(ri, ri, pg);
+        pd = fma_(v, ri, pd);
+      });
+      if (first_run)
+        for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) pb = fma_(b[i], b[i], pb);
+      if (!publish(par, (double)pg, (double)pd, (double)pb)) return;
+      gamma = grid_sum(slot(par, 0), G, red);
+      delta = grid_sum(slot(par, 1), G, red);
+      if (first_run) nb = sqrt(grid_sum(slot(par, 2), G, red));
+      par ^= 1;
+    }
+    if (nb == 0.0) {  // b = 0: x = 0
+      for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) x[i] = V(0);
+      gamma = 0.0;
+      goto finish;
+    }
+    {
+      double gamma_old = 0.0, alpha_old = 0.0;
+      bool first = true;
+      for (;;) {
+        if (!isfinite(gamma) || !isfinite(delta)) { status = kNonfinite; goto finish; }
+        if (sqrt(gamma) / nb <= a.tol || k >= a.maxit) break;
+        const double beta = first ? 0.0 : gamma / gamma_old;
+        const double den = first ? delta : delta - beta * gamma / alpha_old;  // p'Ap
+        if (!isfinite(den)) { status = kNonfinite; goto finish; }
+        if (!(den > 0.0)) {
+          // first step: den = r'Ar, A is not positive definite; later the
+          // recurrence for p'Ap has cancelled (near the attainable residual):
+          // confirm and restart from the true residual
+          if (first) { status = kNotSpd; goto finish; }
+          break;
+        }
+        const double alpha = gamma / den;
+        const V al = (V)alpha, be = (V)beta;
+        const V* __restrict__ w = wb[cur];
+        V* __restrict__ wn = wb[cur ^ 1];
+        V pg = V(0), pd = V(0);
+        spmv_rows<V, FMT == kPlan, false>(A, s0, s1, l0, l1, w, stages, pp, err, [&](int64_t row, V qv) {
+          const V wi = w[row], ri = r[row];
+          const V zi = first ? qv : fma_(be, zv[row], qv);
+          const V si = first ? wi : fma_(be, sv[row], wi);
+          const V pi = first ? ri : fma_(be, p[row], ri);
+          zv[row] = zi;
+          sv[row] = si;
+          p[row] = pi;
+          x[row] = fma_(al, pi, x[row]);
+          const V rn = fma_(-al, si, ri);
+          const V wnv = fma_(-al, zi, wi);
+          r[row] = rn;
+          wn[row] = wnv;
+          pg = fma_(rn, rn, pg);
+          pd = fma_(wnv, rn, pd);
+        });
+        if (!publish(par, (double)pg, (double)pd, 0.0)) return;
+        gamma_old = gamma;
+        alpha_old = alpha;
+        gamma = grid_sum(slot(par, 0), G, red);
+        delta = grid_sum(slot(par, 1), G, red);
+        par ^= 1;
+        cur ^= 1;
+        ++k;
+        first = false;
+      }
+    }
+    {
+      // confirm on the true residual; restart the recurrences from it otherwise
+      spmv_rows<V, FMT == kPlan, false>(A, s0, s1, l0, l1, x, stages, pp, err, [&](int64_t row, V v) { q[row] = v; });
+      __syncthreads();
+      V ptt = V(0);
+      for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+        const V t = b[i] - q[i];
+        ptt = fma_(t, t, ptt);
+      }
+      if (!publish(par, (double)ptt, 0.0, 0.0)) return;
+      const double tt = grid_sum(slot(par, 0), G, red);
+      par ^= 1;
+      rel_true = sqrt(tt) / nb;
+      if (!isfinite(tt)) { status = kNonfinite; break; }
+      if (rel_true <= a.tol) break;
+      if (k >= a.maxit || restarts >= a.max_restarts) { status = kMaxit; break; }
+      ++restarts;
+    }
+  }
+finish:
+  if (c == 0 && threadIdx.x == 0) {
+    a.st->rr = gamma;
+    a.st->nb = nb;
+    a.st->rel_true = rel_true;
+    a.st->k = k;
+    a.st->restarts = restarts;
+    a.st->status = status;
+  }
+}
+
 // Self-test of the bounded wait: CTA 0 never arrives.
 __global__ void k_wait_selftest(GridBar* gb, long long timeout_ns) {
   __shared__ int sflag;
