@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--only-batched", action="store_true", help="only run the batched leg")
     ap.add_argument("--only-differentiable", action="store_true", help="only run the differentiation leg")
     ap.add_argument("--only-paper-size", action="store_true", help="only run the paper-size leg")
+    ap.add_argument("--only-ablation", action="store_true", help="only run the 2010-structure ablation leg")
     ap.add_argument("--profile-batched", type=int, default=0,
                     help="only one mixed-precision solve of the first N batch instances (small case for ncu)")
     ap.add_argument("--profile-spmv", action="store_true",
@@ -227,6 +228,10 @@ def run_ours(args):
     if args.only_batched:
         print(json.dumps({"batched": batched(torch, gb, args)}), flush=True)
         return 0
+    if args.only_ablation:
+        print(json.dumps({"ablation_2010": ablation(torch, gb, args, femgen.build_system(femgen.LARGE))}),
+              flush=True)
+        return 0
     if args.only_paper_size:
         print(json.dumps({"paper_size": paper_size(torch, gb, args)}), flush=True)
         return 0
@@ -343,6 +348,7 @@ def run_ours(args):
         line["paper_size"] = paper_size(torch, gb, args)
         line["batched"] = batched(torch, gb, args)
         line["differentiable"] = differentiable(torch, gb, args)
+        line["ablation_2010"] = ablation(torch, gb, args, s)
         line["cpu_baseline"] = cpu_baseline(s, args, line["variants"])
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -622,6 +628,50 @@ def differentiable(torch, gb, args):
     ((S6(asm6(c6), b6) - torch.from_numpy(xt6).to(dev)) ** 2).sum().backward()
     S6.close()
     out["dense_6cube_rel_error_grad_b"] = float(np.linalg.norm(b6.grad.cpu().numpy() - lam6) / np.linalg.norm(lam6))
+    return out
+
+
+def ablation(torch, gb, args, big):
+    """The paper's 2010 solver structure on this GPU (thread-per-row CSR
+    product, SCSR + SCSC with atomics, host-driven CG with a host round trip
+    per dot product) against the library, at the paper's size and at 128^3."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    out = {}
+    for name, s in (("paper_size", femgen.build_system(femgen.PAPER_SIZE)), ("128", big)):
+        arrays = {"csr": (s.ptr, s.idx, s.val), "sym": s.upper()}
+        xv = torch.from_numpy(femgen.random_vector(s.n, 7)).to(dev)
+        yv = torch.empty_like(xv)
+        b = torch.from_numpy(s.b).to(dev)
+        r = {}
+        for fmt in ("csr", "sym"):
+            Ab = gb.Ablation(fmt, *arrays[fmt])
+            ms_ab = time_spmv(torch, Ab, xv, yv, False)
+            with gb.Matrix(fmt, *arrays[fmt]) as M:
+                ms_lib = time_spmv(torch, M, xv, yv, False)
+                bytes_ = M.stats()["spmv_bytes_fp64"]
+                if fmt == "csr":
+                    x = torch.zeros_like(b)
+                    M.solve(b, x, tol=TOL)
+                    x.zero_()
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    _, info = M.solve(b, x, tol=TOL)
+                    lib_s = time.perf_counter() - t0
+            r[fmt] = {"spmv_2010_ms": ms_ab, "spmv_2010_GBs": bytes_ / ms_ab / 1e6,
+                      "spmv_library_ms": ms_lib, "spmv_library_GBs": bytes_ / ms_lib / 1e6,
+                      "spmv_speedup": ms_ab / ms_lib}
+            if fmt == "csr":
+                x = torch.zeros_like(b)
+                Ab.solve(b, x, tol=TOL)
+                x.zero_()
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                _, iab = Ab.solve(b, x, tol=TOL)
+                ab_s = time.perf_counter() - t0
+                r["cg_fp64"] = {"s_2010": ab_s, "iterations_2010": iab.iterations, "launches_2010": iab.launches,
+                                "s_library": lib_s, "iterations_library": info.iterations,
+                                "launches_library": info.launches, "speedup": ab_s / lib_s}
+        out[name] = r
     return out
 
 

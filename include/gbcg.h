@@ -236,6 +236,28 @@ int gbcg_element_grad(int64_t ne, int32_t m, const int32_t* pos, const double* w
 int gbcg_assemble(int64_t nnz, const int64_t* tptr, const int32_t* telem, const double* tw, const double* coef,
                   double* val, void* stream);
 
+/*
+ * Ablation baselines: the 2010 structure of the paper's GPU solver (Section
+ * III), for measurement only; the solver never uses them.  Device arrays,
+ * 0-based, full CSR (GBCG_CSR) or upper triangle and diagonal
+ * (GBCG_SYM_CSR_UPPER); no validation beyond null and size checks.
+ *
+ * gbcg_ablation_spmv -- y = A x.  GBCG_CSR: the "trivial" kernel, one thread
+ * per row reading the CSR arrays.  GBCG_SYM_CSR_UPPER: the SCSR + SCSC pair,
+ * one thread per stored row with the transpose half scattered by
+ * floating-point atomic additions (the last bits of y depend on scheduling).
+ *
+ * gbcg_ablation_solve -- CG as the paper runs it: one launch per SpMV, dot
+ * and axpy, each dot product copied to the host (two host round trips per
+ * iteration), alpha, beta and the convergence test on the host.  Same
+ * stopping rule on the recurrence residual as gbcg_solve, no confirmation;
+ * info->rel_res_true is computed at the end.  Allocates its work vectors.
+ */
+int gbcg_ablation_spmv(int32_t format, int64_t n, const int32_t* ptr, const int32_t* idx, const double* val,
+                       const double* x, double* y, void* stream);
+int gbcg_ablation_solve(int32_t format, int64_t n, const int32_t* ptr, const int32_t* idx, const double* val,
+                        const double* b, double* x, double tol, int32_t maxit, gbcg_info* info, void* stream);
+
 /* gbcg_stats -- layout facts of a handle. */
 int gbcg_stats(gbcg_matrix_t A, gbcg_matrix_stats* out);
 

@@ -422,6 +422,48 @@ def assemble(tptr, telem, tw, coef, out=None, stream=None):
     return out
 
 
+class Ablation:
+    """The paper's 2010 solver structure on device CSR arrays, a measurement
+    baseline (``gbcg_ablation_spmv`` / ``gbcg_ablation_solve``): "csr" =
+    the thread-per-row kernel, "sym" = SCSR + SCSC with atomics."""
+
+    def __init__(self, fmt, ptr, idx, val, device=None):
+        torch = _torch()
+        dev = torch.device("cuda") if device is None else torch.device(device)
+        self.format = FORMATS[fmt]
+        self.ptr = torch.from_numpy(np.ascontiguousarray(ptr, dtype=np.int32)).to(dev)
+        self.idx = torch.from_numpy(np.ascontiguousarray(idx, dtype=np.int32)).to(dev)
+        self.val = torch.from_numpy(np.ascontiguousarray(val, dtype=np.float64)).to(dev)
+        self.n = int(self.ptr.numel()) - 1
+        self._lib = _lib.load()
+
+    def _pat(self):
+        return (ctypes.c_void_p(self.ptr.data_ptr()), ctypes.c_void_p(self.idx.data_ptr()),
+                ctypes.c_void_p(self.val.data_ptr()))
+
+    def spmv(self, x, y=None, stream=None):
+        torch = _torch()
+        if y is None:
+            y = torch.empty(self.n, dtype=torch.float64, device=x.device)
+        _lib.check(self._lib.gbcg_ablation_spmv(self.format, self.n, *self._pat(), ctypes.c_void_p(x.data_ptr()),
+                                                ctypes.c_void_p(y.data_ptr()), _stream_handle(stream)),
+                   "gbcg_ablation_spmv")
+        return y
+
+    def solve(self, b, x=None, tol: float = 1e-10, maxit: int = 0, stream=None):
+        torch = _torch()
+        if x is None:
+            x = torch.zeros_like(b)
+        info = _lib.Info()
+        rc = self._lib.gbcg_ablation_solve(self.format, self.n, *self._pat(), ctypes.c_void_p(b.data_ptr()),
+                                           ctypes.c_void_p(x.data_ptr()), float(tol), int(maxit), ctypes.byref(info),
+                                           _stream_handle(stream))
+        if rc not in (0, 2, 3, 4):
+            raise GbcgError(rc, "gbcg_ablation_solve", _lib.last_error())
+        return x, SolveInfo(info.iterations, info.outer, _lib.STATUS_NAMES[rc], info.rel_res_recursive,
+                            info.rel_res_true, info.ms, info.kernel_ms, info.kernel_launches, info.launches)
+
+
 def selftest_wait_timeout(ctas: int = 0, timeout_ms: int = 50, stream=None) -> int:
     """Runs the bounded-wait self-test (``gbcg_selftest_wait_timeout``); returns its status code."""
     return _lib.load().gbcg_selftest_wait_timeout(int(ctas), int(timeout_ms), _stream_handle(stream))
@@ -429,4 +471,4 @@ def selftest_wait_timeout(ctas: int = 0, timeout_ms: int = 50, stream=None) -> i
 
 from .autograd import Assembly, SparseSolve  # noqa: E402
 
-__all__ = ["Matrix", "Batch", "SparseSolve", "Assembly", "grad_values", "element_grad", "assemble", "SolveInfo", "GbcgError", "build", "selftest_wait_timeout", "FORMATS", "PRECISIONS"]
+__all__ = ["Matrix", "Batch", "SparseSolve", "Assembly", "Ablation", "grad_values", "element_grad", "assemble", "SolveInfo", "GbcgError", "build", "selftest_wait_timeout", "FORMATS", "PRECISIONS"]

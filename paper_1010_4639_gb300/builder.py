@@ -1,11 +1,12 @@
 """Builds ``libgbcg.so`` in-tree for sm_103a (GB300).
 
-Five translation units compiled in parallel: ``csrc/gbcg.cu`` (kernels and
+Six translation units compiled in parallel: ``csrc/gbcg.cu`` (kernels and
 the C ABI, nvcc), ``csrc/static_solve.cu`` (the allocation-free solve, nvcc),
 ``csrc/batch.cu`` (the batched multi-right-hand-side solver, nvcc),
-``csrc/grad.cu`` (gradient kernels of the differentiable solve, nvcc) and
-``csrc/layout.cpp`` (host-side layout construction, g++), linked by nvcc into
-a shared library next to this file.
+``csrc/grad.cu`` (gradient kernels of the differentiable solve, nvcc),
+``csrc/ablation.cu`` (the paper's 2010 solver structure, a measurement
+baseline, nvcc) and ``csrc/layout.cpp`` (host-side layout construction,
+g++), linked by nvcc into a shared library next to this file.
 """
 from __future__ import annotations
 
@@ -19,7 +20,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgbcg.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = [os.path.join(CSRC, f) for f in ("gbcg.cu", "static_solve.cu", "batch.cu", "grad.cu", "layout.cpp",
+SOURCES = [os.path.join(CSRC, f) for f in ("gbcg.cu", "static_solve.cu", "batch.cu", "grad.cu", "ablation.cu", "layout.cpp",
                                               "kernels.cuh", "layout.h")]
 HEADERS = [os.path.join(INCLUDE, "gbcg.h")]
 
@@ -45,6 +46,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
     st_obj = os.path.join(BUILD, "static_solve.o")
     bt_obj = os.path.join(BUILD, "batch.o")
     gr_obj = os.path.join(BUILD, "grad.o")
+    ab_obj = os.path.join(BUILD, "ablation.o")
     cpp_obj = os.path.join(BUILD, "layout.o")
     cmds = [
         [nvcc, "-c", "-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC",
@@ -55,6 +57,8 @@ def build(verbose: bool = False, force: bool = False) -> str:
          "-I", INCLUDE, os.path.join(CSRC, "batch.cu"), "-o", bt_obj],
         [nvcc, "-c", "-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC",
          "-I", INCLUDE, os.path.join(CSRC, "grad.cu"), "-o", gr_obj],
+        [nvcc, "-c", "-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC",
+         "-I", INCLUDE, os.path.join(CSRC, "ablation.cu"), "-o", ab_obj],
         ["g++", "-c", "-O2", "-std=c++17", "-fPIC", "-I", INCLUDE,
          os.path.join(CSRC, "layout.cpp"), "-o", cpp_obj],
     ]
@@ -69,7 +73,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
     if errors:
         raise RuntimeError("building libgbcg.so failed:\n" + "\n".join(errors))
     tmp = LIB + ".tmp"
-    subprocess.run([nvcc, "-shared", *ARCH, cu_obj, st_obj, bt_obj, gr_obj, cpp_obj, "-o", tmp], check=True)
+    subprocess.run([nvcc, "-shared", *ARCH, cu_obj, st_obj, bt_obj, gr_obj, ab_obj, cpp_obj, "-o", tmp], check=True)
     os.replace(tmp, LIB)
     return LIB
 
