@@ -12,7 +12,8 @@ Parity status per function (what pins it; see ``tests/test_oracle_pins.py``):
   cg (also pipelined=True)            -- dense Cholesky, finite termination,
                                          A-orthogonality, A-norm monotonicity,
                                          closed-form diagonal/tridiagonal cases
-  cg_f32 / cg_ir                      -- true residual in double, error vs x*
+  cg_f32 / cg_ir / cg_ru              -- true residual in double, error vs x*, exact
+                                         float-representable special cases
   dot_long                            -- exact rational arithmetic
   dot_f32                             -- exact sum within the pairwise bound
   grad_values / element_grad /        -- central finite differences of the
@@ -90,6 +91,7 @@ def load(path: str | None = None):
     lib.orc_cg_ir.argtypes = [ctypes.c_int, i64, vp, vp, vp, vp, vp, d, i32, d, i32,
                               ctypes.POINTER(Info)]
     lib.orc_grad_values.argtypes = [ctypes.c_int, i64, vp, vp, vp, vp, vp]
+    lib.orc_cg_ru.argtypes = [ctypes.c_int, i64, vp, vp, vp, vp, vp, d, i32, d, ctypes.POINTER(Info)]
     lib.orc_cg_pipelined.argtypes = [ctypes.c_int, i64, vp, vp, vp, vp, vp, d, i32,
                                      ctypes.POINTER(Info), ctypes.POINTER(History)]
     lib.orc_element_grad.argtypes = [i64, i32, vp, vp, vp, vp]
@@ -267,6 +269,22 @@ def batch_solve(row_off, ptr, idx, val, B, X0=None, tol=1e-10, maxit=None, preci
             row.append(res)
         results.append(row)
     return X, results
+
+
+def cg_ru(fmt, ptr, idx, val, b, x0=None, tol=1e-10, maxit=None, delta=0.1, lib=None) -> Result:
+    """Single-precision CG with double-precision reliable updates (restarts =
+    number of updates)."""
+    lib = lib or load()
+    ptr, idx, val = _arrays(ptr, idx, val)
+    n = ptr.shape[0] - 1
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    x = np.zeros(n) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
+    maxit = 10 * max(n, 1) if maxit is None else int(maxit)
+    info = Info()
+    lib.orc_cg_ru(_fmt(fmt), n, _p(ptr), _p(idx), _p(val), _p(b), _p(x), float(tol), maxit, float(delta),
+                  ctypes.byref(info))
+    return Result(x, info.iterations, info.restarts, STATUS[info.status], info.rel_res_recursive,
+                  info.rel_res_true)
 
 
 # ------------------------------------------------------------ differentiation

@@ -501,3 +501,96 @@ void orc_assemble(int64_t nnz, const int64_t* tptr, const int32_t* telem, const 
     val[p] = s;
   }
 }
+
+/* Mixed precision with reliable updates.  Single-precision CG iterations on
+ * A32 (the single-precision variant of Section IV, float dots, alpha and
+ * beta) build a correction d; each time the recurrence residual has fallen
+ * by the factor delta since the last update, and when it reaches tol, the
+ * correction is added to the double-precision solution (x += d, d = 0) and the
+ * single-precision residual is replaced by the double-precision b - A x.  The
+ * search direction p is kept, so the Krylov space is not restarted (the
+ * refinement of orc_cg_ir restarts it every pass).  Converged when an
+ * update's true residual is <= tol ||b||.  restarts counts the updates. */
+int orc_cg_ru(int fmt, int64_t n, const int32_t* ptr, const int32_t* idx, const double* val, const double* b,
+              double* x, double tol, int32_t maxit, double delta, orc_info* info) {
+  memset(info, 0, sizeof(*info));
+  int64_t nnz = n > 0 ? (fmt == ORC_CSC ? ptr[n] : ptr[n]) : 0;
+  const size_t nn = (size_t)(n ? n : 1);
+  float* v32 = (float*)malloc(sizeof(float) * (size_t)(nnz ? nnz : 1));
+  float* r = (float*)malloc(sizeof(float) * nn);
+  float* p = (float*)malloc(sizeof(float) * nn);
+  float* q = (float*)malloc(sizeof(float) * nn);
+  float* d = (float*)malloc(sizeof(float) * nn);
+  double* r64 = (double*)malloc(sizeof(double) * nn);
+  for (int64_t k = 0; k < nnz; ++k) v32[k] = (float)val[k];
+  int status = ORC_MAXIT;
+  int32_t k = 0, updates = 0;
+  const double nb = sqrt(orc_dot(n, b, b));
+  double rel = 0.0;
+  float rr = 0.0f, rmax = 0.0f;
+  if (nb == 0.0) {
+    for (int64_t i = 0; i < n; ++i) x[i] = 0.0;
+    status = ORC_OK;
+    goto done;
+  }
+  /* the double-precision residual, replacing the single-precision one */
+  orc_spmv(fmt, n, ptr, idx, val, x, r64);
+  for (int64_t i = 0; i < n; ++i) r64[i] = b[i] - r64[i];
+  rel = sqrt(orc_dot(n, r64, r64)) / nb;
+  if (!isfinite(rel)) { status = ORC_NONFINITE; goto done; }
+  if (rel <= tol) { status = ORC_OK; goto done; }
+  for (int64_t i = 0; i < n; ++i) {
+    r[i] = (float)r64[i];
+    p[i] = r[i];
+    d[i] = 0.0f;
+  }
+  rr = dot_f(n, r, r);
+  rmax = sqrtf(rr);
+  while (k < maxit) {
+    orc_spmv_f32(fmt, n, ptr, idx, v32, p, q);                     /* A32 p */
+    const float pq = dot_f(n, p, q);
+    if (!isfinite(pq)) { status = ORC_NONFINITE; break; }
+    if (!(pq > 0.0f)) { status = ORC_NOT_SPD; break; }
+    const float alpha = rr / pq;
+    for (int64_t i = 0; i < n; ++i) d[i] += alpha * p[i];           /* correction */
+    for (int64_t i = 0; i < n; ++i) r[i] -= alpha * q[i];
+    float rr_new = dot_f(n, r, r);
+    ++k;
+    if (sqrtf(rr_new) < (float)delta * rmax || sqrtf(rr_new) <= (float)(tol * nb) || k >= maxit) {
+      /* reliable update: x += d in double, r = b - A x in double */
+      for (int64_t i = 0; i < n; ++i) {
+        x[i] += (double)d[i];
+        d[i] = 0.0f;
+      }
+      orc_spmv(fmt, n, ptr, idx, val, x, r64);
+      for (int64_t i = 0; i < n; ++i) r64[i] = b[i] - r64[i];
+      rel = sqrt(orc_dot(n, r64, r64)) / nb;
+      ++updates;
+      if (!isfinite(rel)) { status = ORC_NONFINITE; break; }
+      if (rel <= tol) { status = ORC_OK; break; }
+      for (int64_t i = 0; i < n; ++i) r[i] = (float)r64[i];
+      rr_new = dot_f(n, r, r);
+      rmax = sqrtf(rr_new);
+    }
+    const float beta = rr_new / rr;
+    rr = rr_new;
+    for (int64_t i = 0; i < n; ++i) p[i] = r[i] + beta * p[i];
+  }
+done:
+  if (status == ORC_NOT_SPD || status == ORC_NONFINITE || status == ORC_MAXIT) {
+    /* leave the last correction in x */
+    for (int64_t i = 0; i < n && k > 0; ++i) x[i] += (double)d[i];
+  }
+  info->iterations = k;
+  info->restarts = updates;
+  info->status = status;
+  info->rel_res_true = rel;
+  info->rel_res_recursive = rel;
+  free(v32);
+  free(r);
+  free(p);
+  free(q);
+  free(d);
+  free(r64);
+  return status;
+}

@@ -397,6 +397,43 @@ def check_cg_ir(lib):
         assert 2 <= r.restarts <= 10
 
 
+def check_cg_ru(lib):
+    # single-precision iterations with double-precision reliable updates reach
+    # double-precision accuracy: dense Cholesky at 1e-12, the manufactured x*
+    s = fem_small(7, 8, 6, contrast=1000.0)
+    D = dense_of(s.ptr, s.idx, s.val, s.n)
+    xc = sla.cho_solve(sla.cho_factor(D), s.b)
+    for fmt, arrs in (("csr", (s.ptr, s.idx, s.val)), ("sym", s.upper())):
+        r = oracle.cg_ru(fmt, *arrs, s.b, tol=1e-12, maxit=40 * s.n, lib=lib)
+        assert r.status == "OK" and r.rel_res_true <= 1e-12, (fmt, r.status, r.rel_res_true)
+        assert np.linalg.norm(r.x - xc) / np.linalg.norm(xc) <= 1e-9
+        true = np.linalg.norm(s.b - D @ r.x) / np.linalg.norm(s.b)
+        assert true <= 1.01e-12
+    # the Krylov space is kept: about the double-precision iteration count
+    # (the refinement that restarts it needs ~50% more)
+    s = fem_small(17, 15, 19)
+    f = oracle.cg("csr", s.ptr, s.idx, s.val, s.b, tol=1e-10, maxit=40 * s.n, lib=lib)
+    r = oracle.cg_ru("csr", s.ptr, s.idx, s.val, s.b, tol=1e-10, maxit=40 * s.n, lib=lib)
+    assert r.status == "OK" and r.iterations <= 1.2 * f.iterations + 5, (r.iterations, f.iterations)
+    # three distinct eigenvalues, exact in float: three steps, then updates
+    d = np.repeat([2.0, 0.5, 4.0], 5)
+    ptr = np.arange(16, dtype=np.int32)
+    idx = np.arange(15, dtype=np.int32)
+    bb = np.tile([1.0, 2.0, 3.0, -1.0, 5.0], 3)
+    r = oracle.cg_ru("csr", ptr, idx, d, bb, tol=1e-14, lib=lib)
+    assert r.status == "OK" and r.iterations <= 9, r.iterations
+    np.testing.assert_allclose(r.x, bb / d, rtol=1e-13)  # cond 8 x residual 1e-14
+    # edge cases
+    (ptr, idx, val), A = spd_sparse(20, 5, shift=1.0)
+    b = np.random.default_rng(0).uniform(-1, 1, 20)
+    r = oracle.cg_ru("csr", ptr, idx, val, np.zeros(20), x0=np.ones(20), lib=lib)
+    assert r.status == "OK" and r.iterations == 0 and not np.any(r.x)
+    r = oracle.cg_ru("csr", ptr, idx, -val, b, lib=lib)
+    assert r.status == "NOT_SPD" and r.iterations == 0
+    r = oracle.cg_ru("csr", ptr, idx, val, b, tol=1e-30, maxit=3, lib=lib)
+    assert r.status == "MAXIT" and r.iterations == 3
+
+
 # ------------------------------------------------------- differentiation ---
 def _diff_case(g):
     s = femgen.build_system(g)
@@ -494,6 +531,6 @@ ALL_CHECKS = [
     check_spmv_f32, check_dot, check_dot_f32, check_cg_vs_cholesky, check_cg_fem_vs_cholesky,
     check_cg_finite_termination, check_cg_exact_first_steps, check_cg_a_orthogonality,
     check_cg_error_a_norm_decreases, check_cg_tridiagonal_closed_form, check_cg_edge_cases,
-    check_cg_f32, check_cg_ir, check_grad_dense_reference, check_assemble_reproduces_the_generator,
+    check_cg_f32, check_cg_ir, check_cg_ru, check_grad_dense_reference, check_assemble_reproduces_the_generator,
     check_grad_finite_differences, check_pipelined_equals_cg_iterates, check_pipelined_vs_cholesky_and_edges,
 ]

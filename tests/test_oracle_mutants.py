@@ -40,6 +40,11 @@ MUTANTS = {
     "grad_sign": ("        g[k] = -(lambda[r] * x[c]);\n      }\n    }", "        g[k] = lambda[r] * x[c];\n      }\n    }"),
     "element_grad_drops_weight": ("if (p >= 0) s += w[e * m + k] * g[p];", "if (p >= 0) s += g[p];"),
     "assemble_drops_coefficient": ("s += tw[k] * coef[telem[k]];", "s += tw[k];"),
+    "ru_drops_update": ("        x[i] += (double)d[i];\n        d[i] = 0.0f;", "        d[i] = 0.0f;"),
+    "ru_keeps_correction": ("        x[i] += (double)d[i];\n        d[i] = 0.0f;", "        x[i] += (double)d[i];"),
+    "ru_replacement_sign": ("r64[i] = b[i] - r64[i];\n      rel = sqrt(orc_dot(n, r64, r64)) / nb;\n      ++updates;",
+                            "r64[i] = r64[i] - b[i];\n      rel = sqrt(orc_dot(n, r64, r64)) / nb;\n      ++updates;"),
+    "ru_alpha_inverted": ("const float alpha = rr / pq;", "const float alpha = pq / rr;"),
     "pipelined_z_drops_beta": ("z[i] = (first ? 0.0 : beta * z[i]) + q[i];", "z[i] = q[i];"),
     "pipelined_plain_denominator": ("const double den = first ? delta : delta - beta * gamma / alpha_old;",
                                     "const double den = delta;"),
