@@ -5,10 +5,14 @@ bandwidth of every storage format, mixed precision against plain FP64 CG on
 the same GPU, and the CPU oracle timed beside it.
 
 One step = one solve from x0 = 0 to a true relative residual <= 1e-10 with the
-headline method (single-precision inner CG with double-precision iterative
-refinement, full CSR storage -- the fastest storage of the library on this
-system), inputs resident in HBM.  The JSON line also carries the plain FP64 CG
-and mixed-precision times and the SpMV bandwidth of the three storage formats.
+headline method (single-precision CG iterations with double-precision
+refinement by reliable updates: the correction is accumulated in double and
+the residual replaced by the double-precision b - A x every decade of
+residual reduction; full CSR storage -- the fastest storage of the library on
+this system), inputs resident in HBM.  The JSON line also carries the plain
+FP64 CG, the restarted refinement and the SpMV bandwidth of the three storage
+formats, the paper-size system, the batched, differentiation and 2010-
+structure legs, and the CPU oracle.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -46,7 +50,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--grid", default="128", choices=sorted(GRIDS))
     ap.add_argument("--format", default="csr", choices=["sym", "csr", "csc"])
-    ap.add_argument("--precision", default="fp32_ir", choices=["fp32_ir", "fp64"])
+    ap.add_argument("--precision", default="fp32_ru", choices=["fp32_ru", "fp32_ir", "fp64"])
     ap.add_argument("--inner-tol", type=float, default=1e-4)
     ap.add_argument("--no-extras", action="store_true", help="skip the per-format and CPU-baseline legs")
     ap.add_argument("--profile-iters", type=int, default=0,
@@ -254,7 +258,8 @@ def run_ours(args):
     st = A.stats()
     b = torch.from_numpy(s.b).to(dev)
     x = torch.zeros_like(b)
-    solve_kw = dict(tol=TOL, precision=args.precision, inner_tol=args.inner_tol)
+    solve_kw = dict(tol=TOL, precision=args.precision,
+                    inner_tol=args.inner_tol if args.precision == "fp32_ir" else 0.0)
     if args.profile_spmv:
         xv = torch.from_numpy(femgen.random_vector(s.n, 7)).to(dev)
         yv = torch.empty_like(xv)
@@ -319,7 +324,7 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": ms / 1000.0, "unit": "s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32+f64" if args.precision == "fp32_ir" else "f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
         "config": {"workload": f"fem {g.nx}x{g.ny}x{g.nz} P1 stiffness, {g.n_incl} inclusion(s), contrast "
                                f"{g.contrast:g}, {args.format} storage, {args.precision}, tol 1e-10",
                    "n": s.n, "nnz": s.nnz, "nnz_stored": int(fmt_arrays[args.format][1].shape[0]),
@@ -330,7 +335,9 @@ def run_ours(args):
         "gpu_launches": int(round(sum(i.launches for i in infos) / len(infos))),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": (achieved / hbm) if achieved else None, "traffic": None,
-                     "kernel": f"k_cg<{'float' if args.precision == 'fp32_ir' else 'double'}> persistent CG",
+                     "kernel": {"fp32_ir": "k_cg<float> persistent inner CG",
+                                "fp32_ru": "k_cg_ru persistent CG, single-precision iterations",
+                                "fp64": "k_cg<double> persistent CG"}[args.precision],
                      "algorithmic_bytes_per_iteration": per_it, "iterations": iters,
                      "kernel_ms_per_step": kernel_ms, "kernel_launches_per_step": kernel_launches,
                      "peak_kind": f"{peak_kind} HBM copy bandwidth"},
@@ -390,14 +397,17 @@ def extras(torch, gb, s, fmt_arrays, A_head, args, hbm):
         r["spmv_fp32_GBs"] = st["spmv_bytes_fp32"] / r["spmv_fp32_ms"] / 1e6
         r["spmv_fp64_frac_of_measured_hbm"] = r["spmv_fp64_GBs"] / hbm
         r["spmv_fp32_frac_of_measured_hbm"] = r["spmv_fp32_GBs"] / hbm
-        for prec in ("fp64", "fp32_ir"):
+        for prec in ("fp64", "fp32_ir", "fp32_ru"):
+            if prec == "fp32_ru" and st["layout"] == 2:
+                continue  # reliable updates run on the row-gather layouts
+            itol = args.inner_tol if prec == "fp32_ir" else 0.0
             x = torch.zeros_like(b)
-            M.solve(b, x, tol=TOL, precision=prec, inner_tol=args.inner_tol)  # warm
+            M.solve(b, x, tol=TOL, precision=prec, inner_tol=itol)  # warm
             x.zero_()
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
-            _, info = M.solve(b, x, tol=TOL, precision=prec, inner_tol=args.inner_tol)
+            _, info = M.solve(b, x, tol=TOL, precision=prec, inner_tol=itol)
             e1.record()
             torch.cuda.synchronize()
             t = e0.elapsed_time(e1) / 1000.0
@@ -407,6 +417,8 @@ def extras(torch, gb, s, fmt_arrays, A_head, args, hbm):
                        "iter_us": 1000.0 * info.kernel_ms / max(info.iterations, 1),
                        "kernel_GBs": per_it * info.iterations / (info.kernel_ms / 1000.0) / 1e9}
         r["mixed_speedup_vs_fp64"] = r["fp64"]["s"] / r["fp32_ir"]["s"]
+        if "fp32_ru" in r:
+            r["reliable_update_speedup_vs_fp64"] = r["fp64"]["s"] / r["fp32_ru"]["s"]
         r["device_bytes"] = st["device_bytes"]
         out[fmt] = r
         if M is not A_head:
@@ -427,7 +439,7 @@ def paper_size(torch, gb, args):
             out[fmt] = {"grid_ctas": M.stats()["grid_ctas"]}
             runs = [("fp64", "standard"), ("fp32_ir", "standard")]
             if fmt == "csr":
-                runs += [("fp64", "pipelined")]
+                runs += [("fp64", "pipelined"), ("fp32_ru", "standard")]
             for prec, variant in runs:
                 x = torch.zeros_like(b)
                 ts = []
@@ -436,7 +448,8 @@ def paper_size(torch, gb, args):
                     torch.cuda.synchronize()
                     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                     e0.record()
-                    _, info = M.solve(b, x, tol=TOL, precision=prec, inner_tol=args.inner_tol, variant=variant)
+                    _, info = M.solve(b, x, tol=TOL, precision=prec, variant=variant,
+                                      inner_tol=args.inner_tol if prec == "fp32_ir" else 0.0)
                     e1.record()
                     torch.cuda.synchronize()
                     if k:

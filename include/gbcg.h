@@ -57,9 +57,16 @@ enum gbcg_status {
 
 enum gbcg_precision {
   GBCG_FP64 = 0,          /* CG in double precision throughout */
-  GBCG_FP32_IR = 1        /* single-precision inner CG (Section IV's
+  GBCG_FP32_IR = 1,       /* single-precision inner CG (Section IV's
                              single-precision variant) inside double-precision
-                             iterative refinement */
+                             iterative refinement: each pass restarts the inner
+                             CG on r / ||r|| */
+  GBCG_FP32_RU = 2        /* single-precision CG iterations with double-precision
+                             reliable updates: the correction is added to x and the
+                             residual replaced by b - A x in double precision each
+                             time the recurrence residual falls by inner_tol
+                             (default 0.1), keeping the search direction (the
+                             Krylov space is not restarted).  Row-gather layouts */
 };
 
 enum gbcg_memory { GBCG_HOST = 0, GBCG_DEVICE = 1 };
@@ -81,7 +88,8 @@ enum gbcg_variant {
 typedef struct {
   int32_t precision;          /* gbcg_precision; default GBCG_FP64 */
   int32_t max_outer;          /* refinement passes for GBCG_FP32_IR; default 30 */
-  double inner_tol;           /* inner relative tolerance for GBCG_FP32_IR; default 1e-4 */
+  double inner_tol;           /* GBCG_FP32_IR: inner relative tolerance, default 1e-4;
+                                 GBCG_FP32_RU: residual reduction between updates, default 0.1 */
   int32_t wait_timeout_ms;    /* bound on every device-side wait; default 1000 */
   int32_t max_restarts;       /* true-residual restarts for GBCG_FP64; default 3 */
   int32_t variant;            /* gbcg_variant; default GBCG_STANDARD */
@@ -91,7 +99,7 @@ typedef struct {
 /* Report of one solve. */
 typedef struct {
   int32_t iterations;         /* CG iterations (inner ones for GBCG_FP32_IR) */
-  int32_t outer;              /* restarts (FP64) or refinement passes (IR) */
+  int32_t outer;              /* restarts (FP64), refinement passes (IR) or reliable updates (RU) */
   int32_t status;             /* same as the return value of gbcg_solve */
   int32_t pad_;
   double rel_res_recursive;   /* ||r_k|| / ||b|| of the recurrence at exit */

@@ -22,7 +22,8 @@ from ._lib import GbcgError
 
 FORMATS = {"csr": _lib.GBCG_CSR, "sym": _lib.GBCG_SYM_CSR_UPPER, "sym_upper": _lib.GBCG_SYM_CSR_UPPER,
            "csc": _lib.GBCG_CSC}
-PRECISIONS = {"fp64": _lib.GBCG_FP64, "fp32_ir": _lib.GBCG_FP32_IR, "ir": _lib.GBCG_FP32_IR}
+PRECISIONS = {"fp64": _lib.GBCG_FP64, "fp32_ir": _lib.GBCG_FP32_IR, "ir": _lib.GBCG_FP32_IR,
+              "fp32_ru": _lib.GBCG_FP32_RU}
 VARIANTS = {"standard": _lib.GBCG_STANDARD, "pipelined": _lib.GBCG_PIPELINED}
 
 
@@ -188,9 +189,13 @@ class Matrix:
 
     # ------------------------------------------------------------ solve
     def solve(self, b, x=None, tol: float = 1e-10, maxit: int = 0, precision: str = "fp64",
-              inner_tol: float = 1e-4, max_outer: int = 30, wait_timeout_ms: int = 1000,
+              inner_tol: float = 0.0, max_outer: int = 30, wait_timeout_ms: int = 1000,
               max_restarts: int = 3, variant: str = "standard", stream=None, raise_on_error: bool = True):
         """Conjugate gradient for A x = b (``gbcg_solve``).
+
+        ``precision``: "fp64", "fp32_ir" (refinement; ``inner_tol`` the inner
+        tolerance, default 1e-4) or "fp32_ru" (reliable updates; ``inner_tol``
+        the residual reduction between updates, default 0.1); 0 = default.
 
         ``b`` and ``x`` are float64 CUDA tensors, or numpy arrays (host
         memory; the copies happen inside the call).  ``x`` holds x0 on entry

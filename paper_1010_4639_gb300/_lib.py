@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libgbcg.so")
 
 GBCG_CSR, GBCG_SYM_CSR_UPPER, GBCG_CSC = 0, 1, 2
-GBCG_FP64, GBCG_FP32_IR = 0, 1
+GBCG_FP64, GBCG_FP32_IR, GBCG_FP32_RU = 0, 1, 2
 GBCG_HOST, GBCG_DEVICE = 0, 1
 GBCG_STANDARD, GBCG_PIPELINED = 0, 1
 STATUS_NAMES = ["OK", "INVALID", "NOT_SPD", "MAXIT", "NONFINITE", "TIMEOUT", "CUDA", "NOMEM"]

@@ -236,6 +236,20 @@ int occupancy_of(int& per_sm) {
   return 0;
 }
 
+constexpr size_t ru_smem() { return (size_t)kWarps * ru_warp_stage_bytes(); }
+
+template <int FMT>
+int ru_occupancy_of(int& per_sm) {
+  if constexpr (FMT == kTiles) {
+    per_sm = 1 << 20;
+    return 0;
+  } else {
+    CUDA_TRY(cudaFuncSetAttribute(k_cg_ru<FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ru_smem()));
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cg_ru<FMT>, kCgThreads, ru_smem()));
+    return 0;
+  }
+}
+
 template <int FMT>
 int pcg_occupancy_of(int& per_sm) {
   if constexpr (FMT == kTiles) {
@@ -260,13 +274,14 @@ int prepare_rows() {
 // the shared-memory attributes of the kernels of that mode).
 template <int FMT>
 int solver_occupancy(int& per_sm) {
-  int a = 0, b = 0, c = 0;
+  int a = 0, b = 0, c = 0, e = 0;
   if (int rc = occupancy_of<double, FMT, true>(a)) return rc;
   if (int rc = occupancy_of<float, FMT, false>(b)) return rc;
   if (int rc = pcg_occupancy_of<FMT>(c)) return rc;
+  if (int rc = ru_occupancy_of<FMT>(e)) return rc;
   if (int rc = prepare_rows<double, FMT>()) return rc;
   if (int rc = prepare_rows<float, FMT>()) return rc;
-  per_sm = std::min(std::min(a, b), c);
+  per_sm = std::min(std::min(a, b), std::min(c, e));
   return 0;
 }
 
@@ -317,6 +332,12 @@ cudaError_t launch_pcg_fmt(const gbcg_matrix_s* M, const CgArgs<double>& c, cuda
   a.w0 = M->w64a;
   a.w1 = M->w64b;
   return M->mode == kPlan ? launch_pcg<kPlan>(a, M->grid, s) : launch_pcg<kGather>(a, M->grid, s);
+}
+
+template <int FMT>
+cudaError_t launch_ru(const RuArgs& args, int grid, cudaStream_t s) {
+  void* kargs[] = {(void*)&args};
+  return cudaLaunchCooperativeKernel((const void*)k_cg_ru<FMT>, dim3(grid), dim3(kCgThreads), kargs, ru_smem(), s);
 }
 
 // Product y = A x (MODE 0), or r = b - A x into y with per-CTA partial sums
@@ -413,6 +434,37 @@ int solve_fp64(gbcg_matrix_s* M, const double* b, double* x, double tol, int max
     g_last_error = "device-side wait ran out (barrier " + std::to_string(M->bar_h->where) + "; " +
                    std::to_string(M->bar_h->detail[0]) + " " + std::to_string(M->bar_h->detail[1]) + " " +
                    std::to_string(M->bar_h->detail[2]) + " " + std::to_string(M->bar_h->detail[3]) + ")";
+  return status;
+}
+
+// Single-precision iterations with double-precision reliable updates: one
+// persistent launch (row-gather layouts; the caller has checked the mode).
+int solve_ru(gbcg_matrix_s* M, const double* b, double* x, double tol, int maxit, const gbcg_opts* o,
+             gbcg_info* info, cudaStream_t s) {
+  CUDA_TRY(cudaMemsetAsync(M->bar, 0, sizeof(GridBar), s));
+  RuArgs a;
+  a.c = make_args<float>(M, M->d32, M->r32, M->p32, M->q32, nullptr, tol, maxit, 0, timeout_ns_of(o));
+  a.A64 = M->op<double>();
+  a.x64 = x;
+  a.b64 = b;
+  a.q64 = M->q;
+  a.delta = (o && o->inner_tol > 0.0 && o->inner_tol < 1.0) ? o->inner_tol : 0.1;
+  CUDA_TRY(cudaEventRecord(M->ev0, s));
+  CUDA_TRY(M->mode == kPlan ? launch_ru<kPlan>(a, M->grid, s) : launch_ru<kGather>(a, M->grid, s));
+  CUDA_TRY(cudaEventRecord(M->ev1, s));
+  if (int rc = read_state(M, s)) return rc;
+  float kms = 0.f;
+  CUDA_TRY(cudaEventElapsedTime(&kms, M->ev0, M->ev1));
+  info->kernel_ms = kms;
+  info->kernel_launches = 1;
+  info->launches = 1;
+  const int status = status_from_device(*M->st_h, *M->bar_h);
+  info->iterations = M->st_h->k;
+  info->outer = M->st_h->restarts;
+  info->status = status;
+  info->rel_res_recursive = M->st_h->rel_true;
+  info->rel_res_true = M->st_h->rel_true;
+  if (status == GBCG_ERR_TIMEOUT) g_last_error = "device-side wait ran out (reliable-update solve)";
   return status;
 }
 
@@ -706,8 +758,14 @@ int gbcg_solve(gbcg_matrix_t A, const double* b, double* x, double tol, int32_t 
   memset(info, 0, sizeof(*info));
   if (!A) return fail(GBCG_ERR_INVALID, "null matrix handle");
   if (!(tol >= 0.0) || !std::isfinite(tol)) return fail(GBCG_ERR_INVALID, "tol must be finite and >= 0");
-  if (opts && (opts->precision != GBCG_FP64 && opts->precision != GBCG_FP32_IR))
+  if (opts && (opts->precision != GBCG_FP64 && opts->precision != GBCG_FP32_IR && opts->precision != GBCG_FP32_RU))
     return fail(GBCG_ERR_INVALID, "unknown precision");
+  if (opts && opts->precision == GBCG_FP32_RU && A->mode == kTiles)
+    return fail(GBCG_ERR_INVALID,
+                "reliable updates run on row-gather layouts (CSR, CSC, or symmetric storage with "
+                "GBCG_SYM_LAYOUT=plan)");
+  if (opts && opts->precision == GBCG_FP32_RU && opts->variant == GBCG_PIPELINED)
+    return fail(GBCG_ERR_INVALID, "the single-reduction variant is double precision only");
   if (opts && opts->variant != GBCG_STANDARD && opts->variant != GBCG_PIPELINED)
     return fail(GBCG_ERR_INVALID, "unknown variant");
   if (opts && opts->variant == GBCG_PIPELINED && opts->precision == GBCG_FP32_IR)
@@ -740,6 +798,8 @@ int gbcg_solve(gbcg_matrix_t A, const double* b, double* x, double tol, int32_t 
   int status;
   if (opts && opts->precision == GBCG_FP32_IR)
     status = solve_ir(A, bd, xd, tol, maxit, opts, info, s);
+  else if (opts && opts->precision == GBCG_FP32_RU)
+    status = solve_ru(A, bd, xd, tol, maxit, opts, info, s);
   else
     status = solve_fp64(A, bd, xd, tol, maxit, opts, info, s);
   if (status == GBCG_ERR_CUDA || status == GBCG_ERR_NOMEM) return status;

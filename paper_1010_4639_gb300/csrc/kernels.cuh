@@ -1260,6 +1260,214 @@ finish:
   }
 }
 
+// Mixed precision with reliable updates.  Single-precision CG iterations on
+// A32 (the three phases of k_cg's inner solve) build a correction d; when the
+// recurrence residual has fallen by the factor delta since the last update,
+// or reaches tol, or the iteration bound is met, the correction is added to
+// the double-precision x (x += d, d = 0) and the single-precision residual is
+// replaced by the double-precision b - A x, formed by the double-precision
+// product in the same launch.  The search direction is kept: the Krylov space
+// is not restarted.  Converged when an update's true residual is <= tol ||b||.
+struct RuArgs {
+  CgArgs<float> c;        // float operator; x = correction d, r, p, q
+  OpDev<double> A64;      // the same layout with double values
+  double* x64;            // caller's x (in: x0)
+  const double* b64;
+  double* q64;            // double product scratch
+  double delta;
+};
+
+// Bytes of one warp's share of the stage buffers, used in turn by the
+// single-precision and the double-precision product.
+__host__ __device__ constexpr size_t ru_warp_stage_bytes() {
+  return gather_stages<float>() * sizeof(Stage<float>) > gather_stages<double>() * sizeof(Stage<double>)
+             ? gather_stages<float>() * sizeof(Stage<float>)
+             : gather_stages<double>() * sizeof(Stage<double>);
+}
+
+template <int FMT>
+__global__ void __launch_bounds__(kCgThreads, 1) k_cg_ru(RuArgs ra) {
+  static_assert(FMT != kTiles, "row-gather layouts only");
+  static_assert(gather_stages<float>() + gather_stages<double>() <= kMaxStages, "mbarrier sets");
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ uint64_t bars[kMaxThreads / 32][kMaxStages];
+  __shared__ double red[33];
+  __shared__ int sflag;
+  const CgArgs<float>& a = ra.c;
+  const int G = gridDim.x, c = blockIdx.x;
+  const int64_t s0 = a.cta_slice[c], s1 = a.cta_slice[c + 1];
+  const int64_t l0 = a.cta_long[c], l1 = a.cta_long[c + 1];
+  const int64_t r0 = s0 * 32;
+  const int64_t r1 = s1 * 32 < a.A.n ? s1 * 32 : a.A.n;
+  float* __restrict__ d = a.x;
+  float* __restrict__ r = a.r;
+  float* __restrict__ p = a.p;
+  float* __restrict__ q = a.q;
+  double* __restrict__ x64 = ra.x64;
+  const double* __restrict__ b64 = ra.b64;
+  double* __restrict__ q64 = ra.q64;
+  const int warp = threadIdx.x >> 5;
+  unsigned char* wst = smem_raw + (size_t)warp * ru_warp_stage_bytes();
+  Stage<float>* st32 = reinterpret_cast<Stage<float>*>(wst);
+  Stage<double>* st64 = reinterpret_cast<Stage<double>*>(wst);
+  Pipe pp32, pp64;
+  pipe_init(pp32, bars[warp], gather_stages<float>(), a.timeout_ns);
+  pipe_init(pp64, bars[warp] + gather_stages<float>(), gather_stages<double>(), a.timeout_ns);
+  __syncthreads();
+  int* err = &a.bar->status;
+  double* part0 = a.part;
+  double* part1 = a.part + G;
+  double* part2 = a.part + 2 * G;
+  unsigned long long target = 0;
+  int nbar = 0, status = kOk, k = 0, updates = 0;
+  double rr = 0.0, nb = 0.0, rel = 0.0, rmax = 0.0;
+  bool first_update = true;
+
+  // x += d, d = 0; r = float(b - A64 x); rr = r'r; rel = ||b - A x|| / ||b||
+  auto update = [&]() -> bool {
+    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+      x64[i] += (double)d[i];
+      d[i] = 0.f;
+    }
+    if (!grid_barrier(a.bar, target, a.timeout_ns, &sflag, nbar++)) return false;
+    spmv_rows<double, FMT == kPlan, false>(ra.A64, s0, s1, l0, l1, x64, st64, pp64, err,
+                                           [&](int64_t row, double v) { q64[row] = v; });
+    __syncthreads();
+    double ptt = 0.0, pbb = 0.0;
+    float prr = 0.f;
+    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+      const double bi = b64[i];
+      const double t = bi - q64[i];
+      const float tf = (float)t;
+      r[i] = tf;
+      ptt = fma(t, t, ptt);
+      prr = fmaf(tf, tf, prr);
+      if (first_update) pbb = fma(bi, bi, pbb);
+    }
+    const double s_tt = block_sum(ptt, red);
+    if (threadIdx.x == 0) part0[c] = s_tt;
+    const double s_rr = block_sum((double)prr, red);
+    if (threadIdx.x == 0) part1[c] = s_rr;
+    if (first_update) {
+      const double s_bb = block_sum(pbb, red);
+      if (threadIdx.x == 0) part2[c] = s_bb;
+    }
+    if (!grid_barrier(a.bar, target, a.timeout_ns, &sflag, nbar++)) return false;
+    const double tt = grid_sum(part0, G, red);
+    rr = grid_sum(part1, G, red);
+    if (first_update) nb = sqrt(grid_sum(part2, G, red));
+    first_update = false;
+    rel = nb > 0.0 ? sqrt(tt) / nb : 0.0;
+    rmax = sqrt(rr);
+    return true;
+  };
+
+  for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) d[i] = 0.f;
+  if (!update()) return;
+  if (nb == 0.0) {  // b = 0: x = 0
+    for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) x64[i] = 0.0;
+    rel = 0.0;
+    goto finish;
+  }
+  if (!isfinite(rel)) { status = kNonfinite; goto finish; }
+  if (rel <= a.tol) goto finish;
+  for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) p[i] = r[i];
+  if (!grid_barrier(a.bar, target, a.timeout_ns, &sflag, nbar++)) return;
+  status = kMaxit;
+  while (k < a.maxit) {
+    // A: q = A32 p, p'q
+    {
+      float ppq = 0.f;
+      spmv_rows<float, FMT == kPlan, false>(a.A, s0, s1, l0, l1, p, st32, pp32, err, [&](int64_t row, float v) {
+        q[row] = v;
+        ppq = fmaf(p[row], v, ppq);
+      });
+      const double sp = block_sum((double)ppq, red);
+      if (threadIdx.x == 0) part0[c] = sp;
+    }
+    if (!grid_barrier(a.bar, target, a.timeout_ns, &sflag, nbar++)) return;
+    const double pq = grid_sum(part0, G, red);
+    if (!isfinite(pq)) { status = kNonfinite; break; }
+    if (!(pq > 0.0)) { status = kNotSpd; break; }
+    const float al = (float)(rr / pq);
+    // B: d += alpha p, r -= alpha q, r'r  (16-byte accesses, as k_cg)
+    {
+      float prr = 0.f;
+      rows_vec<float>(
+          r0, r1,
+          [&](int64_t i) {
+            return Quad<float4>{*reinterpret_cast<const float4*>(p + i), *reinterpret_cast<const float4*>(q + i),
+                                *reinterpret_cast<const float4*>(d + i), *reinterpret_cast<const float4*>(r + i)};
+          },
+          [&](int64_t i, Quad<float4> t) {
+            const float* pe = reinterpret_cast<const float*>(&t.a);
+            const float* qe = reinterpret_cast<const float*>(&t.b);
+            float* de = reinterpret_cast<float*>(&t.c);
+            float* re = reinterpret_cast<float*>(&t.d);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              de[j] = fmaf(al, pe[j], de[j]);
+              re[j] = fmaf(-al, qe[j], re[j]);
+              prr = fmaf(re[j], re[j], prr);
+            }
+            *reinterpret_cast<float4*>(d + i) = t.c;
+            *reinterpret_cast<float4*>(r + i) = t.d;
+          },
+          [&](int64_t i) {
+            d[i] = fmaf(al, p[i], d[i]);
+            const float ri = fmaf(-al, q[i], r[i]);
+            r[i] = ri;
+            prr = fmaf(ri, ri, prr);
+          });
+      const double sr = block_sum((double)prr, red);
+      if (threadIdx.x == 0) part1[c] = sr;
+    }
+    if (!grid_barrier(a.bar, target, a.timeout_ns, &sflag, nbar++)) return;
+    double rr_new = grid_sum(part1, G, red);
+    ++k;
+    if (!isfinite(rr_new)) { status = kNonfinite; break; }
+    if (sqrt(rr_new) < ra.delta * rmax || sqrt(rr_new) <= a.tol * nb || k >= a.maxit) {
+      const double rr_keep = rr;
+      if (!update()) return;
+      ++updates;
+      if (!isfinite(rel)) { status = kNonfinite; goto finish; }
+      if (rel <= a.tol) { status = kOk; goto finish; }
+      if (k >= a.maxit) { status = kMaxit; goto finish; }
+      rr_new = rr;  // the replaced residual's r'r (update() set rr and rmax)
+      rr = rr_keep;
+    }
+    const float be = (float)(rr_new / rr);
+    rr = rr_new;
+    // C: p = r + beta p
+    rows_vec<float>(
+        r0, r1,
+        [&](int64_t i) {
+          return Quad<float4>{*reinterpret_cast<const float4*>(p + i), *reinterpret_cast<const float4*>(r + i),
+                              float4{}, float4{}};
+        },
+        [&](int64_t i, Quad<float4> t) {
+          float* pe = reinterpret_cast<float*>(&t.a);
+          const float* re = reinterpret_cast<const float*>(&t.b);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) pe[j] = fmaf(be, pe[j], re[j]);
+          *reinterpret_cast<float4*>(p + i) = t.a;
+        },
+        [&](int64_t i) { p[i] = fmaf(be, p[i], r[i]); });
+    if (!grid_barrier(a.bar, target, a.timeout_ns, &sflag, nbar++)) return;
+  }
+  // left by a breakdown: keep the last correction
+  for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) x64[i] += (double)d[i];
+finish:
+  if (c == 0 && threadIdx.x == 0) {
+    a.st->rr = rr;
+    a.st->nb = nb;
+    a.st->rel_true = rel;
+    a.st->k = k;
+    a.st->restarts = updates;
+    a.st->status = status;
+  }
+}
+
 // Self-test of the bounded wait: CTA 0 never arrives.
 __global__ void k_wait_selftest(GridBar* gb, long long timeout_ns) {
   __shared__ int sflag;
