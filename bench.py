@@ -40,6 +40,12 @@ import femgen  # noqa: E402
 METRIC = "CG time-to-1e-10 residual (s) & SpMV HBM GB/s; mixed/batched vs FP64 CG"
 GRIDS = {"128": femgen.LARGE, "31": femgen.PAPER_SIZE, "64": femgen.DIFF, "256": femgen.LARGEST}
 TOL = 1e-10
+# DRAM bytes (read + write) of the headline kernel measured by ncu on a
+# 30-iteration launch of the same 128^3 system (profiles/k_cg_ru_csr128.md):
+# per single-precision iteration, and per double-precision update.  Used
+# only for that kernel on that system; null elsewhere.
+RU_TRAFFIC_PER_ITERATION = 247e6
+RU_TRAFFIC_PER_UPDATE = 0.484e9
 
 
 def parse():
@@ -320,6 +326,9 @@ def run_ours(args):
     hbm, peak_kind = peaks()
     per_it = per_iteration_bytes(st, args.precision)
     achieved = per_it * iters / (kernel_ms / 1000.0) / 1e9 if kernel_ms > 0 else None
+    traffic = None
+    if args.precision == "fp32_ru" and args.format == "csr" and args.grid == "128":
+        traffic = RU_TRAFFIC_PER_ITERATION * iters + RU_TRAFFIC_PER_UPDATE * infos[-1].outer
     x_np = x_dev.cpu().numpy()
     line = {
         "metric": METRIC, "value": ms / 1000.0, "unit": "s", "n_gpus": world, "steps": args.steps,
@@ -334,7 +343,9 @@ def run_ours(args):
         "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": 16 * s.n, "d2h_bytes_per_step": 8 * s.n},
         "gpu_launches": int(round(sum(i.launches for i in infos) / len(infos))),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": (achieved / hbm) if achieved else None, "traffic": None,
+                     "frac": (achieved / hbm) if achieved else None, "traffic": traffic,
+                     "traffic_source": "ncu DRAM bytes of a 30-iteration launch of this kernel on this system, "
+                                       "scaled by the iterations and updates of the solve" if traffic else None,
                      "kernel": {"fp32_ir": "k_cg<float> persistent inner CG",
                                 "fp32_ru": "k_cg_ru persistent CG, single-precision iterations",
                                 "fp64": "k_cg<double> persistent CG"}[args.precision],
