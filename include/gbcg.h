@@ -340,7 +340,8 @@ typedef struct gbcg_batch_s* gbcg_batch_t;
 /* Result of one system and right-hand side. */
 typedef struct {
   int32_t iterations;     /* inner CG iterations */
-  int32_t outer;          /* refinement passes (GBCG_FP64: first run + restarts) */
+  int32_t outer;          /* refinement passes (GBCG_FP64: first run + restarts;
+                             GBCG_FP32_RU: reliable updates) */
   int32_t status;         /* gbcg_status */
   int32_t pad_;
   double rel_res_true;    /* ||b - A x|| / ||b|| in double precision at the last check */
@@ -348,10 +349,13 @@ typedef struct {
 
 /* Options of gbcg_batch_solve; zero fields take the defaults. */
 typedef struct {
-  int32_t precision;      /* gbcg_precision; default GBCG_FP64 */
+  int32_t precision;      /* gbcg_precision; default GBCG_FP64 (GBCG_FP32_RU: reliable updates,
+                             one double-precision update of every right-hand side of an
+                             instance whenever one of them has fallen by inner_tol) */
   int32_t max_outer;      /* passes: default 30 for GBCG_FP32_IR, 4 (one run and up to
                              three true-residual restarts) for GBCG_FP64 */
-  double inner_tol;       /* GBCG_FP32_IR inner relative tolerance; default 1e-4 */
+  double inner_tol;       /* GBCG_FP32_IR inner relative tolerance, default 1e-4;
+                             GBCG_FP32_RU reduction between updates, default 0.1 */
   int32_t fixed_order;    /* 1: keep the schedule (by default every solve replans the
                              queue and the group sizes from the measured time per
                              instance, for the next solve) */

@@ -244,7 +244,8 @@ def batch_solve(row_off, ptr, idx, val, B, X0=None, tol=1e-10, maxit=None, preci
                 max_outer=30, lib=None):
     """Independent systems of a block-diagonal CSR (instance i: rows
     row_off[i]..row_off[i+1], global columns), each right-hand side solved on
-    its own by ``cg_ir`` (precision "fp32_ir") or ``cg`` ("fp64").  Returns
+    its own by ``cg_ir`` (precision "fp32_ir"), ``cg_ru`` ("fp32_ru") or ``cg``
+    ("fp64").  Returns
     (X, results) with results[i][k] the Result of instance i, column k."""
     lib = lib or load()
     row_off = np.asarray(row_off, dtype=np.int64)
@@ -262,6 +263,8 @@ def batch_solve(row_off, ptr, idx, val, B, X0=None, tol=1e-10, maxit=None, preci
             m = maxit if maxit is not None else max(r1 - r0, 1)
             if precision == "fp64":
                 res = cg("csr", p_i, i_i, v_i, B[r0:r1, k], X[r0:r1, k], tol=tol, maxit=m, lib=lib)
+            elif precision == "fp32_ru":
+                res = cg_ru("csr", p_i, i_i, v_i, B[r0:r1, k], X[r0:r1, k], tol=tol, maxit=m, lib=lib)
             else:
                 res = cg_ir("csr", p_i, i_i, v_i, B[r0:r1, k], X[r0:r1, k], tol=tol, maxit=m, inner_tol=inner_tol,
                             max_outer=max_outer, lib=lib)

@@ -333,7 +333,7 @@ class Batch:
         return self._lib.gbcg_batch_selftest_group_timeout(self._h, int(timeout_ms), _host_stream(stream))
 
     def solve(self, b, x=None, tol: float = 1e-10, maxit: int = 0, precision: str = "fp32_ir",
-              inner_tol: float = 1e-4, max_outer: int = 0, fixed_order: bool = False, max_group: int = 0,
+              inner_tol: float = 0.0, max_outer: int = 0, fixed_order: bool = False, max_group: int = 0,
               force_group: int = 0, wait_timeout_ms: int = 0, stream=None, raise_on_error: bool = True):
         """Solve every instance for every right-hand side (``gbcg_batch_solve``).
 

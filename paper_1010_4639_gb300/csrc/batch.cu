@@ -101,9 +101,10 @@ struct BArgs {
   int32_t* inst_iters;      // count: products with the inner matrix
   int32_t* inst_outer;      // count: double-precision residual products
   long long* t_inst;        // 2 x count: start and end, global timer ns
-  double tol, inner_tol;
+  double tol, inner_tol;     // inner_tol: refinement tolerance, or the reliable-update factor
   long long timeout_ns;
   int count, nslots, nrhs, maxit, max_outer, force_rpw;
+  int reliable;              // 1: single-precision iterations with double-precision reliable updates
 };
 
 __device__ __forceinline__ int64_t min64(int64_t a, int64_t b) { return a < b ? a : b; }
@@ -154,7 +155,7 @@ struct Red {
 // Per-instance scalars of the eight right-hand sides; lane k of warp 0 owns
 // right-hand side k, every other thread only reads.
 struct St {
-  double rr[kRhs], nr0[kRhs], nb[kRhs], nr[kRhs], alpha[kRhs], beta[kRhs], rel[kRhs], itol[kRhs];
+  double rr[kRhs], nr0[kRhs], nb[kRhs], nr[kRhs], alpha[kRhs], beta[kRhs], rel[kRhs], itol[kRhs], rmax[kRhs];
   int used[kRhs], outer[kRhs], status[kRhs], kin[kRhs], bd[kRhs];
   unsigned fin, oact, iact, zero;
   int maxit, products, outers;
@@ -677,6 +678,269 @@ __device__ bool solve_instance(const BArgs& a, int inst, Group& g, Red& red, St&
   return true;
 }
 
+// Reliable updates for one instance (single-precision iterations, double-
+// precision updates), all right-hand sides: the single-precision CG of the
+// refinement's inner solve, but the correction d goes into x in double and
+// the residual is replaced by b - A x in double whenever an active
+// right-hand side's recurrence residual has fallen by inner_tol since its
+// last update (or reached tol, or the iteration bound); the search
+// directions are kept.  An update serves every right-hand side at once (an
+// update is valid at any time).  outer counts the updates.
+template <int NT>
+__device__ bool solve_instance_ru(const BArgs& a, int inst, Group& g, Red& red, St& st, int& par, int* s_flag) {
+  using VT = float4;
+  constexpr int VW = 4, CH = 2;
+  const int t = threadIdx.x;
+  const int ch = t % CH;
+  float* __restrict__ R = reinterpret_cast<float*>(a.R);
+  float* __restrict__ P = reinterpret_cast<float*>(a.P);
+  float* __restrict__ Q = reinterpret_cast<float*>(a.Q);
+  float* __restrict__ D = reinterpret_cast<float*>(a.D);
+  const int64_t row0 = a.inst_row[inst];
+  const int64_t nI = a.inst_row[inst + 1] - row0;
+  const int64_t GC = (int64_t)g.G * g.C, gc = (int64_t)g.p * g.C + g.cr;
+  const int64_t per = (nI + GC - 1) / GC;
+  const int64_t r0 = row0 + min64(nI, per * gc);
+  const int64_t r1 = row0 + min64(nI, per * (gc + 1));
+  const int rp = a.force_rpw > 0 ? a.force_rpw : (int)a.rpw[inst];
+  const int64_t e0 = r0 * CH, e1 = r1 * CH;
+  bool ok = true;
+  if (t < 32) {
+    if (t < kRhs) {
+      st.used[t] = 0;
+      st.outer[t] = 0;
+      st.status[t] = kMaxit;
+      st.rel[t] = 0.0;
+      st.nb[t] = 0.0;
+      st.bd[t] = 0;
+    }
+    const unsigned pad = __ballot_sync(~0u, t < kRhs && t >= a.nrhs);
+    if (t == 0) {
+      st.fin = pad;
+      st.zero = 0;
+      st.maxit = a.maxit > 0 ? a.maxit : (int)min64(nI, 0x7fffffff);
+      st.products = 0;
+      st.outers = 0;
+    }
+  }
+  for (int64_t e = e0 + t; e < e1; e += NT) reinterpret_cast<VT*>(D)[e] = VT{};
+  __syncthreads();
+  // x += d (double), d = 0, R64 = B - A64 x; then decisions, R = float(R64), r'r
+  auto update = [&](bool first) -> bool {
+    {
+      bool on[VW];
+#pragma unroll
+      for (int j = 0; j < VW; ++j) on[j] = ch * VW + j < a.nrhs;
+      for (int64_t e = e0 + t; e < e1; e += NT) {
+        VT dv = reinterpret_cast<const VT*>(D)[e];
+        const float* de = reinterpret_cast<const float*>(&dv);
+        const int64_t row = e / CH;
+#pragma unroll
+        for (int j = 0; j < VW; ++j)
+          if (on[j] && de[j] != 0.f) a.X[row * a.nrhs + ch * VW + j] += (double)de[j];
+        reinterpret_cast<VT*>(D)[e] = VT{};
+      }
+    }
+    if (!group_sync(a, g, s_flag)) return false;  // x of every CTA before the product
+    double v[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+    outer_residual(a, r0, r1, v);
+    const double s = group_reduce<2, 2>(a, v, red, par, g, s_flag, ok);
+    if (!ok) return false;
+    if (t >= kRhs && t < 2 * kRhs) red.sum[t] = s;
+    __syncthreads();
+    if (t < 32) {
+      bool zero = false, done = false;
+      if (t < kRhs && !((st.fin >> t) & 1u)) {
+        if (first) st.nb[t] = sqrt(red.sum[kRhs + t]);
+        const double nb = st.nb[t];
+        if (nb == 0.0) {
+          zero = true;
+          done = true;
+          st.status[t] = kOk;
+          st.rel[t] = 0.0;
+        } else {
+          const double rel = sqrt(s) / nb;
+          st.rel[t] = rel;
+          if (!first) st.outer[t] += 1;
+          if (!isfinite(rel)) {
+            st.status[t] = kNonfinite;
+            done = true;
+          } else if (rel <= a.tol) {
+            st.status[t] = kOk;
+            done = true;
+          } else if (st.used[t] >= st.maxit) {
+            st.status[t] = kMaxit;
+            done = true;
+          }
+        }
+      }
+      const unsigned zm = __ballot_sync(~0u, zero), dm = __ballot_sync(~0u, done);
+      if (t == 0) {
+        st.zero = zm;
+        st.fin |= dm;
+        st.outers += 1;
+      }
+    }
+    __syncthreads();
+    if (st.zero) {
+      const unsigned zm = st.zero;
+      for (int64_t row = r0 + t; row < r1; row += NT)
+        for (int k = 0; k < a.nrhs; ++k)
+          if ((zm >> k) & 1u) a.X[row * a.nrhs + k] = 0.0;
+    }
+    // R = float(R64) for the right-hand sides still running, r'r
+    {
+      const unsigned live = ~st.fin;
+      bool on[VW];
+#pragma unroll
+      for (int j = 0; j < VW; ++j) on[j] = (live >> (ch * VW + j)) & 1u;
+      float pr[VW] = {0.f, 0.f, 0.f, 0.f};
+      for (int64_t e = e0 + t; e < e1; e += NT) {
+        VT rv;
+        float* re = reinterpret_cast<float*>(&rv);
+#pragma unroll
+        for (int j = 0; j < VW; ++j) {
+          re[j] = on[j] ? (float)a.R64[e * VW + j] : 0.f;
+          pr[j] = fmaf(re[j], re[j], pr[j]);
+        }
+        reinterpret_cast<VT*>(R)[e] = rv;
+      }
+      double w[1][VW];
+#pragma unroll
+      for (int j = 0; j < VW; ++j) w[0][j] = (double)pr[j];
+      const double s2 = group_reduce<VW, 1>(a, w, red, par, g, s_flag, ok);
+      if (!ok) return false;
+      if (t < kRhs) {
+        st.nr[t] = s2;  // r'r of the replaced residual
+        st.rmax[t] = sqrt(s2);
+      }
+      __syncthreads();
+    }
+    return true;
+  };
+  if (!update(true)) return false;
+  if (t < kRhs) st.rr[t] = st.nr[t];
+  // p = r
+  for (int64_t e = e0 + t; e < e1; e += NT) reinterpret_cast<VT*>(P)[e] = reinterpret_cast<const VT*>(R)[e];
+  if (!group_sync(a, g, s_flag)) return false;
+  while (~st.fin & 0xFFu) {
+    // q = A32 p, p'q
+    {
+      float pq[VW] = {0.f, 0.f, 0.f, 0.f};
+      product_rpw<float>(rp, a.ptr, a.idx, a.val32, P, r0, r1, [&](int64_t row, int c, VT acc) {
+        const int64_t e = row * CH + c;
+        reinterpret_cast<VT*>(Q)[e] = acc;
+        const VT pv = reinterpret_cast<const VT*>(P)[e];
+        const float* pe = reinterpret_cast<const float*>(&pv);
+        const float* qe = reinterpret_cast<const float*>(&acc);
+#pragma unroll
+        for (int j = 0; j < VW; ++j) pq[j] = fmaf(pe[j], qe[j], pq[j]);
+      });
+      double v[1][VW];
+#pragma unroll
+      for (int j = 0; j < VW; ++j) v[0][j] = (double)pq[j];
+      const double s = group_reduce<VW, 1>(a, v, red, par, g, s_flag, ok);
+      if (!ok) return false;
+      if (t < 32) {
+        bool stop = false;
+        if (t < kRhs) {
+          double al = 0.0;
+          if (!((st.fin >> t) & 1u)) {
+            if (!isfinite(s)) {
+              st.status[t] = kNonfinite;
+              stop = true;
+            } else if (!(s > 0.0)) {
+              st.status[t] = kNotSpd;
+              stop = true;
+            } else {
+              al = st.rr[t] / s;
+            }
+          }
+          st.alpha[t] = al;
+        }
+        const unsigned m = __ballot_sync(~0u, stop);
+        if (t == 0) st.fin |= m;
+      }
+      __syncthreads();
+    }
+    // d += alpha p, r -= alpha q, r'r
+    {
+      float al[VW], pr[VW] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int j = 0; j < VW; ++j) al[j] = (float)st.alpha[ch * VW + j];
+      for (int64_t e = e0 + t; e < e1; e += NT) {
+        const VT pv = reinterpret_cast<const VT*>(P)[e];
+        const VT qv = reinterpret_cast<const VT*>(Q)[e];
+        VT dv = reinterpret_cast<const VT*>(D)[e];
+        VT rv = reinterpret_cast<const VT*>(R)[e];
+        const float* pe = reinterpret_cast<const float*>(&pv);
+        const float* qe = reinterpret_cast<const float*>(&qv);
+        float* de = reinterpret_cast<float*>(&dv);
+        float* re = reinterpret_cast<float*>(&rv);
+#pragma unroll
+        for (int j = 0; j < VW; ++j) {
+          de[j] = fmaf(al[j], pe[j], de[j]);
+          re[j] = fmaf(-al[j], qe[j], re[j]);
+          pr[j] = fmaf(re[j], re[j], pr[j]);
+        }
+        reinterpret_cast<VT*>(D)[e] = dv;
+        reinterpret_cast<VT*>(R)[e] = rv;
+      }
+      double v[1][VW];
+#pragma unroll
+      for (int j = 0; j < VW; ++j) v[0][j] = (double)pr[j];
+      const double s = group_reduce<VW, 1>(a, v, red, par, g, s_flag, ok);
+      if (!ok) return false;
+      if (t < 32) {
+        bool need = false;
+        if (t < kRhs && !((st.fin >> t) & 1u) && st.alpha[t] != 0.0) {
+          st.used[t] += 1;
+          st.nr[t] = s;
+          const double nr = sqrt(s);
+          need = nr < a.inner_tol * st.rmax[t] || nr <= a.tol * st.nb[t] || st.used[t] >= st.maxit;
+        } else if (t < kRhs) {
+          st.nr[t] = st.rr[t];
+        }
+        const unsigned m = __ballot_sync(~0u, need);
+        if (t == 0) {
+          st.iact = m;
+          st.products += 1;
+        }
+      }
+      __syncthreads();
+    }
+    if (st.iact || !(~st.fin & 0xFFu)) {
+      // a reliable update: x += d, r = b - A x in double (also flushes the
+      // correction of right-hand sides that just stopped)
+      if (!update(false)) return false;
+      if (!(~st.fin & 0xFFu)) break;
+    }
+    // p = r + beta p
+    {
+      if (t < kRhs) {
+        const bool live = !((st.fin >> t) & 1u);
+        st.beta[t] = live ? st.nr[t] / st.rr[t] : 0.0;
+        if (live) st.rr[t] = st.nr[t];
+      }
+      __syncthreads();
+      float be[VW];
+#pragma unroll
+      for (int j = 0; j < VW; ++j) be[j] = (float)st.beta[ch * VW + j];
+      for (int64_t e = e0 + t; e < e1; e += NT) {
+        const VT rv = reinterpret_cast<const VT*>(R)[e];
+        VT pv = reinterpret_cast<const VT*>(P)[e];
+        const float* re = reinterpret_cast<const float*>(&rv);
+        float* pe = reinterpret_cast<float*>(&pv);
+#pragma unroll
+        for (int j = 0; j < VW; ++j) pe[j] = fmaf(be[j], pe[j], re[j]);
+        reinterpret_cast<VT*>(P)[e] = pv;
+      }
+      if (!group_sync(a, g, s_flag)) return false;
+    }
+  }
+  return true;
+}
+
 // The persistent batched solver.  V is the precision of the inner CG (float:
 // Section IV's single-precision iteration inside double-precision
 // refinement; double: double precision throughout, where each refinement
@@ -717,7 +981,12 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_bcg(const BArgs* __restrict__
     __syncthreads();
     const bool lead = g.p == 0 && g.cr == 0;
     if (lead && t == 0) a.t_inst[2 * inst] = now_ns();
-    const bool ok = solve_instance<V, NT>(a, inst, g, red, st, par, &s_flag);
+    bool ok;
+    if constexpr (sizeof(V) == 4)
+      ok = a.reliable ? solve_instance_ru<NT>(a, inst, g, red, st, par, &s_flag)
+                      : solve_instance<V, NT>(a, inst, g, red, st, par, &s_flag);
+    else
+      ok = solve_instance<V, NT>(a, inst, g, red, st, par, &s_flag);
     if (!ok) {
       if (lead && t < a.nrhs) {
         gbcg_batch_info o = {st.used[t], st.outer[t], (int)kTimeout, 0, st.rel[t]};
@@ -1412,12 +1681,13 @@ int gbcg_batch_solve(gbcg_batch_t B, const double* b, double* x, double tol, int
   if (!B) return fail(GBCG_ERR_INVALID, "null batch handle");
   if (!(tol >= 0.0)) return fail(GBCG_ERR_INVALID, "tol must be >= 0");
   const int precision = opts ? opts->precision : GBCG_FP64;
-  if (precision != GBCG_FP64 && precision != GBCG_FP32_IR) return fail(GBCG_ERR_INVALID, "unknown precision");
+  if (precision != GBCG_FP64 && precision != GBCG_FP32_IR && precision != GBCG_FP32_RU)
+    return fail(GBCG_ERR_INVALID, "unknown precision");
   if (B->n_tot > 0 && (!b || !x)) return fail(GBCG_ERR_INVALID, "null b or x");
   const bool bdev = is_device_ptr(b), xdev = is_device_ptr(x);
   if (bdev != xdev) return fail(GBCG_ERR_INVALID, "b and x must both be device or both be host memory");
   const int memory = bdev ? GBCG_DEVICE : GBCG_HOST;
-  const bool f32 = precision == GBCG_FP32_IR;
+  const bool f32 = precision != GBCG_FP64;  // both single-precision forms share tuning and graph
   cudaStream_t s = (cudaStream_t)stream;
   if (rep) memset(rep, 0, sizeof(*rep));
   int rc = 0;
@@ -1456,7 +1726,11 @@ int gbcg_batch_solve(gbcg_batch_t B, const double* b, double* x, double tol, int
   a.B = bd;
   a.X = xd;
   a.tol = tol;
-  a.inner_tol = f32 ? ((opts && opts->inner_tol > 0) ? opts->inner_tol : 1e-4) : 0.0;
+  a.reliable = precision == GBCG_FP32_RU;
+  if (precision == GBCG_FP32_RU)
+    a.inner_tol = (opts && opts->inner_tol > 0 && opts->inner_tol < 1) ? opts->inner_tol : 0.1;
+  else
+    a.inner_tol = f32 ? ((opts && opts->inner_tol > 0) ? opts->inner_tol : 1e-4) : 0.0;
   a.maxit = maxit;
   a.max_outer = (opts && opts->max_outer > 0) ? opts->max_outer : (f32 ? 30 : 4);
   a.force_rpw = 0;
