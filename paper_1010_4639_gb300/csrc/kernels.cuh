@@ -27,6 +27,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 namespace gbcg {
 
 constexpr int kCgThreads = 512;
@@ -384,19 +386,31 @@ __device__ __forceinline__ void pipe_drain(Pipe& pp) {
   }
 }
 
+// Calls f(row, y) or, when f takes three arguments, f(row, y, x_row) with
+// x_row = x[row] loaded beside the product's gathers (saving the emitter a
+// dependent load of its own row).
+template <typename V, class F>
+__device__ __forceinline__ void emit_row(F&& f, int64_t row, V y, V xr) {
+  if constexpr (std::is_invocable_v<F, int64_t, V, V>)
+    f(row, y, xr);
+  else
+    f(row, y);
+}
+
 // Visits the rows of slices [s0, s1) and long rows [l0, l1) of the CTA:
-// f(row, (A x)_row) runs on the lane that computed the row.  Row-gather
-// formats use the per-warp bulk-copy pipeline; the symmetric format reads
-// global memory directly.
+// f(row, (A x)_row[, x_row]) runs on the lane that computed the row.
+// Row-gather formats use the per-warp bulk-copy pipeline; the symmetric
+// format reads global memory directly.
 template <typename V, bool SYM, bool NC, class F>
 __device__ __forceinline__ void spmv_rows(const OpDev<V>& A, int64_t s0, int64_t s1, int64_t l0, int64_t l1,
                                           const V* x, Stage<V>* stages, Pipe& pp, int* err, F&& f) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   if constexpr (SYM) {  // transpose-plan layout
     for (int64_t s = s0 + warp; s < s1; s += nw) {
-      const V v = sell_row<V, true, NC, 4>(A, s, lane, x);
       const int64_t row = s * 32 + lane;
-      if (row < A.n) f(row, v);
+      const V xr = (std::is_invocable_v<F, int64_t, V, V> && row < A.n) ? ld_vec<NC>(x + row) : V(0);
+      const V v = sell_row<V, true, NC, 4>(A, s, lane, x);
+      if (row < A.n) emit_row<V>(f, row, v, xr);
     }
   } else {
     int64_t s_issue = s0 + warp;
@@ -407,6 +421,8 @@ __device__ __forceinline__ void spmv_rows(const OpDev<V>& A, int64_t s0, int64_t
         s_issue += nw;
       }
       const int L = slice_len(A, s);
+      const int64_t row = s * 32 + lane;
+      const V xr = (std::is_invocable_v<F, int64_t, V, V> && row < A.n) ? ld_vec<NC>(x + row) : V(0);
       V acc = V(0);
       if (L > kMaxL) {
         acc = sell_row<V, false, NC, 8>(A, s, lane, x);
@@ -429,14 +445,16 @@ __device__ __forceinline__ void spmv_rows(const OpDev<V>& A, int64_t s0, int64_t
         }
         __syncwarp();
       }
-      const int64_t row = s * 32 + lane;
-      if (row < A.n && !((A.long_mask[s] >> lane) & 1u)) f(row, acc);
+      if (row < A.n && !((A.long_mask[s] >> lane) & 1u)) emit_row<V>(f, row, acc, xr);
     }
     if (pp.failed) pipe_drain(pp);
   }
   for (int64_t li = l0 + warp; li < l1; li += nw) {
     const V v = long_row<V, NC>(A, li, lane, x);
-    if (lane == 0) f((int64_t)A.long_row[li], v);
+    if (lane == 0) {
+      const int64_t row = A.long_row[li];
+      emit_row<V>(f, row, v, std::is_invocable_v<F, int64_t, V, V> ? ld_vec<NC>(x + row) : V(0));
+    }
   }
 }
 
@@ -968,9 +986,9 @@ __global__ void __launch_bounds__(FMT == kTiles ? kTileThreads : kCgThreads, 1) 
         });
       } else {
         Stage<V>* stages = reinterpret_cast<Stage<V>*>(smem_raw) + (threadIdx.x >> 5) * gather_stages<V>();
-        spmv_rows<V, FMT == kPlan, false>(A, s0, s1, l0, l1, p, stages, pp, err, [&](int64_t row, V v) {
+        spmv_rows<V, FMT == kPlan, false>(A, s0, s1, l0, l1, p, stages, pp, err, [&](int64_t row, V v, V pr) {
           q[row] = v;
-          ppq = fma_(p[row], v, ppq);
+          ppq = fma_(pr, v, ppq);
         });
       }
       {
@@ -1203,8 +1221,8 @@ __global__ void __launch_bounds__(kCgThreads, 1) k_pcg(PcgArgs<V> pa) {
         const V* __restrict__ w = wb[cur];
         V* __restrict__ wn = wb[cur ^ 1];
         V pg = V(0), pd = V(0);
-        spmv_rows<V, FMT == kPlan, false>(A, s0, s1, l0, l1, w, stages, pp, err, [&](int64_t row, V qv) {
-          const V wi = w[row], ri = r[row];
+        spmv_rows<V, FMT == kPlan, false>(A, s0, s1, l0, l1, w, stages, pp, err, [&](int64_t row, V qv, V wi) {
+          const V ri = r[row];
           const V zi = first ? qv : fma_(be, zv[row], qv);
           const V si = first ? wi : fma_(be, sv[row], wi);
           const V pi = first ? ri : fma_(be, p[row], ri);
@@ -1378,10 +1396,11 @@ __global__ void __launch_bounds__(kCgThreads, 1) k_cg_ru(RuArgs ra) {
     // A: q = A32 p, p'q
     {
       float ppq = 0.f;
-      spmv_rows<float, FMT == kPlan, false>(a.A, s0, s1, l0, l1, p, st32, pp32, err, [&](int64_t row, float v) {
-        q[row] = v;
-        ppq = fmaf(p[row], v, ppq);
-      });
+      spmv_rows<float, FMT == kPlan, false>(a.A, s0, s1, l0, l1, p, st32, pp32, err,
+                                            [&](int64_t row, float v, float pr) {
+                                              q[row] = v;
+                                              ppq = fmaf(pr, v, ppq);
+                                            });
       const double sp = block_sum((double)ppq, red);
       if (threadIdx.x == 0) part0[c] = sp;
     }

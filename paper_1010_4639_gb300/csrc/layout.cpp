@@ -471,8 +471,11 @@ bool build_sym_tiles(LayoutHost& L, int ctas, int slot_cap, int ent_cap) {
 std::vector<int32_t> partition_slices(const LayoutHost& L, int parts) {
   const int64_t ns = L.A.nslices;
   std::vector<int32_t> cut(parts + 1, 0);
+  // A slice costs its slots plus a fixed part: the warp's dependent round
+  // trips to memory (stage wait, gathers, row update), measured on GB300 as
+  // about 350 slots' worth; and the vector passes over its 32 rows.
   auto work = [&](int64_t s) {
-    int64_t w = (L.A.sl_ptr[s + 1] - L.A.sl_ptr[s]) + 32;  // slots + vector work of 32 rows
+    int64_t w = (L.A.sl_ptr[s + 1] - L.A.sl_ptr[s]) + 352;
     if (!L.plan.pl_ptr.empty()) w += L.plan.pl_ptr[s + 1] - L.plan.pl_ptr[s];
     return w;
   };
