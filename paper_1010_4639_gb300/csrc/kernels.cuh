@@ -718,26 +718,31 @@ __device__ __forceinline__ double grid_sum(const double* part, int G, double* re
 
 // Bounded grid barrier.  Returns false (uniformly within the CTA) when the
 // wait ran out or another CTA already failed.
+__device__ __forceinline__ void red_release_add(unsigned long long* p, unsigned long long v) {
+  asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
 __device__ __forceinline__ bool grid_barrier(GridBar* gb, unsigned long long& target, long long timeout_ns,
                                              int* sflag, int where) {
-  __syncthreads();
+  __syncthreads();  // the CTA's writes before thread 0's release
   target += gridDim.x;
   if (threadIdx.x == 0) {
     int ok = 1;
-    __threadfence();
-    atomicAdd(&gb->count, 1ull);
+    // arrival with release semantics (no separate fence, no returned value);
+    // the acquire loads of the spin order everything after the barrier
+    red_release_add(&gb->count, 1ull);
     const long long t0 = gtime();
-    unsigned spins = 0;
-    for (;;) {
+    for (unsigned spins = 1;; ++spins) {
       if (ld_acquire(&gb->count) >= target) break;
-      if (ld_relaxed(&gb->status) != 0) { ok = 0; break; }
-      if ((++spins & 63u) == 0 && gtime() - t0 > timeout_ns) {
-        if (atomicCAS(&gb->status, 0, (int)kTimeout) == 0) gb->where = where;
-        ok = 0;
-        break;
+      if ((spins & 63u) == 0) {
+        if (ld_relaxed(&gb->status) != 0) { ok = 0; break; }
+        if (gtime() - t0 > timeout_ns) {
+          if (atomicCAS(&gb->status, 0, (int)kTimeout) == 0) gb->where = where;
+          ok = 0;
+          break;
+        }
       }
     }
-    __threadfence();
     *sflag = ok;
   }
   __syncthreads();
