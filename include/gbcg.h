@@ -120,13 +120,19 @@ typedef struct {
   int64_t plan_slots;         /* SELL slots of the symmetric transpose plan (0 if none) */
   int64_t long_rows;          /* rows handled warp-per-row */
   int64_t device_bytes;       /* device memory held by the handle */
-  int64_t spmv_bytes_fp64;    /* algorithmic bytes of one double-precision product */
-  int64_t spmv_bytes_fp32;    /* algorithmic bytes of one single-precision product */
+  int64_t spmv_bytes_fp64;    /* algorithmic bytes of one double-precision product (value +
+                                 index per entry, row pointers, x read once, y written once) */
+  int64_t spmv_bytes_fp32;    /* the same for the single-precision product */
   int64_t ext_slots;          /* symmetric tiles: partial sums leaving the tiles */
   int32_t format;             /* gbcg_format */
   int32_t grid_ctas;          /* CTAs of the persistent CG launch */
   int32_t layout;             /* 0 row gather, 1 symmetric transpose plan, 2 symmetric tiles */
   int32_t tiles;              /* symmetric tiles: number of tiles */
+  int32_t index_bytes;        /* bytes per column index in the product's stream: 2 when the
+                                 row-gather layout stores 16-bit offsets from the row (every
+                                 offset fits; natural-order finite-element matrices up to
+                                 about 180^3 nodes), else 4 */
+  int32_t pad_;
 } gbcg_matrix_stats;
 
 /*

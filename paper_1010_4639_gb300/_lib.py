@@ -46,7 +46,8 @@ class Stats(ctypes.Structure):
                 ("stored_slots", ctypes.c_int64), ("plan_slots", ctypes.c_int64), ("long_rows", ctypes.c_int64),
                 ("device_bytes", ctypes.c_int64), ("spmv_bytes_fp64", ctypes.c_int64),
                 ("spmv_bytes_fp32", ctypes.c_int64), ("ext_slots", ctypes.c_int64), ("format", ctypes.c_int32),
-                ("grid_ctas", ctypes.c_int32), ("layout", ctypes.c_int32), ("tiles", ctypes.c_int32)]
+                ("grid_ctas", ctypes.c_int32), ("layout", ctypes.c_int32), ("tiles", ctypes.c_int32),
+                ("index_bytes", ctypes.c_int32), ("pad_", ctypes.c_int32)]
 
 
 class BatchInfo(ctypes.Structure):

@@ -100,6 +100,7 @@ struct gbcg_matrix_s {
   // layout (device)
   int64_t* sl_ptr = nullptr;
   int32_t* col = nullptr;
+  int16_t* col16 = nullptr;  // 16-bit column offsets (row-gather layout, when they fit)
   double* val64 = nullptr;
   float* val32 = nullptr;
   uint32_t* long_mask = nullptr;
@@ -170,6 +171,7 @@ OpDev<double> gbcg_matrix_s::op<double>() const {
   o.nlong = nlong;
   o.sl_ptr = sl_ptr;
   o.col = col;
+  o.col16 = col16;
   o.val = val64;
   o.long_mask = long_mask;
   o.long_row = long_row;
@@ -190,6 +192,7 @@ OpDev<float> gbcg_matrix_s::op<float>() const {
   o.nlong = nlong;
   o.sl_ptr = sl_ptr;
   o.col = col;
+  o.col16 = col16;
   o.val = val32;
   o.long_mask = long_mask;
   o.long_row = long_row;
@@ -207,7 +210,7 @@ namespace {
 
 void free_matrix(gbcg_matrix_s* M) {
   if (!M) return;
-  void* dev[] = {M->sl_ptr, M->col, M->val64, M->val32, M->long_mask, M->long_row, M->long_ptr, M->long_col,
+  void* dev[] = {M->sl_ptr, M->col, M->col16, M->val64, M->val32, M->long_mask, M->long_row, M->long_ptr, M->long_col,
                  M->long_val64, M->long_val32, M->diag64, M->diag32, M->pl_ptr, M->pl_i, M->pl_k,
                  M->cta_slice, M->cta_long, M->r, M->p, M->q, M->bstage, M->xstage, M->r32, M->p32, M->q32,
                  M->d32, M->rhs32, M->part, M->sums, M->bar, M->st, M->t_cta_tile, M->t_tile_slice,
@@ -674,6 +677,8 @@ int gbcg_create(gbcg_matrix_t* out, int32_t format, int64_t n, int64_t nnz, cons
   } else {
     TRY(upload(&M->sl_ptr, L.A.sl_ptr, s, B));
     TRY(upload(&M->col, L.A.col, s, B));
+    if (!L.A.col16.empty() && M->mode == kGather && env_int("GBCG_WIDE_INDEX", 0) == 0)
+      TRY(upload(&M->col16, L.A.col16, s, B));
     TRY(upload(&M->val64, L.A.val, s, B));
     TRY(upload(&M->val32, to_f32(L.A.val), s, B));
     TRY(upload(&M->long_mask, L.A.long_mask, s, B));
@@ -822,8 +827,12 @@ int gbcg_stats(gbcg_matrix_t A, gbcg_matrix_stats* out) {
   out->long_rows = A->nlong;
   out->device_bytes = A->bytes;
   const int64_t n = A->n, m = A->nnz_input;
-  out->spmv_bytes_fp64 = 12 * m + 4 * (n + 1) + 16 * n;
-  out->spmv_bytes_fp32 = 8 * m + 4 * (n + 1) + 8 * n;
+  // the product's matrix stream: value + column index per entry (2-byte
+  // offsets in the row-gather layout when they fit), row pointers, x, y
+  const int64_t ib = A->col16 ? 2 : 4;
+  out->spmv_bytes_fp64 = (8 + ib) * m + 4 * (n + 1) + 16 * n;
+  out->spmv_bytes_fp32 = (4 + ib) * m + 4 * (n + 1) + 8 * n;
+  out->index_bytes = (int32_t)ib;
   out->format = A->format;
   out->grid_ctas = A->grid;
   out->layout = A->mode;

@@ -50,6 +50,7 @@ struct OpDev {
   int64_t n = 0, nslices = 0, nlong = 0;
   const int64_t* __restrict__ sl_ptr = nullptr;
   const int32_t* __restrict__ col = nullptr;
+  const int16_t* __restrict__ col16 = nullptr;  // col - row, when every offset fits (row-gather layout)
   const V* __restrict__ val = nullptr;
   const uint32_t* __restrict__ long_mask = nullptr;
   const int32_t* __restrict__ long_row = nullptr;
@@ -368,10 +369,15 @@ __device__ __forceinline__ void pipe_issue(const OpDev<V>& A, Stage<V>* stages, 
   if (L == 0 || L > kMaxL || pp.failed) return;
   const uint32_t st = pp.issued % pp.nst;
   if ((threadIdx.x & 31) == 0) {
-    const uint32_t vb = (uint32_t)(L * 32 * sizeof(V)), cb = (uint32_t)(L * 32 * sizeof(int32_t));
+    const bool narrow = A.col16 != nullptr;
+    const uint32_t vb = (uint32_t)(L * 32 * sizeof(V));
+    const uint32_t cb = (uint32_t)(L * 32 * (narrow ? sizeof(int16_t) : sizeof(int32_t)));
     mbar_arrive_expect_tx(&pp.bars[st], vb + cb);
     bulk_g2s(stages[st].val, A.val + A.sl_ptr[s], vb, &pp.bars[st], pp.policy);
-    bulk_g2s(stages[st].col, A.col + A.sl_ptr[s], cb, &pp.bars[st], pp.policy);
+    if (narrow)
+      bulk_g2s(stages[st].col, A.col16 + A.sl_ptr[s], cb, &pp.bars[st], pp.policy);
+    else
+      bulk_g2s(stages[st].col, A.col + A.sl_ptr[s], cb, &pp.bars[st], pp.policy);
   }
   ++pp.issued;
 }
@@ -434,11 +440,19 @@ __device__ __forceinline__ void spmv_rows(const OpDev<V>& A, int64_t s0, int64_t
         } else {
           ++pp.consumed;
           const V* __restrict__ sv = stages[st].val;
-          const int32_t* __restrict__ sc = stages[st].col;
           V xv[kMaxL];
+          if (A.col16) {  // 16-bit offsets from the row (lanes past the last row read x[0])
+            const int16_t* __restrict__ sc = reinterpret_cast<const int16_t*>(stages[st].col);
+            const V* xb = x + (row < A.n ? row : 0);
 #pragma unroll
-          for (int k = 0; k < kMaxL; ++k)
-            if (k < L) xv[k] = ld_vec<NC>(x + sc[k * 32 + lane]);
+            for (int k = 0; k < kMaxL; ++k)
+              if (k < L) xv[k] = ld_vec<NC>(xb + sc[k * 32 + lane]);
+          } else {
+            const int32_t* __restrict__ sc = stages[st].col;
+#pragma unroll
+            for (int k = 0; k < kMaxL; ++k)
+              if (k < L) xv[k] = ld_vec<NC>(x + sc[k * 32 + lane]);
+          }
 #pragma unroll
           for (int k = 0; k < kMaxL; ++k)
             if (k < L) acc = fma_(sv[k * 32 + lane], xv[k], acc);

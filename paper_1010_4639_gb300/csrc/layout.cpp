@@ -128,6 +128,30 @@ void slice_rows(int64_t n, const Rows& R, bool allow_long, SellHost& S) {
       }
     }
   }
+  // 16-bit column offsets (col - row): a quarter less index traffic for the
+  // product when the pattern is banded enough (finite-element matrices in
+  // natural order are: offsets up to m^2 + m + 1 on an m^3 grid)
+  {
+    bool fits = true;
+    std::vector<int16_t> c16(slots, 0);
+    for (int64_t s = 0; s < ns && fits; ++s) {
+      const int64_t L = (S.sl_ptr[s + 1] - S.sl_ptr[s]) / 32;
+      for (int l = 0; l < 32 && fits; ++l) {
+        const int64_t r = 32 * s + l;
+        if (r >= n) continue;  // stays 0: the kernel reads x[0] for lanes past the last row
+        for (int64_t k = 0; k < L; ++k) {
+          const int64_t off = (int64_t)S.col[S.sl_ptr[s] + 32 * k + l] - r;
+          if (off < -32768 || off > 32767) {
+            fits = false;
+            break;
+          }
+          c16[S.sl_ptr[s] + 32 * k + l] = (int16_t)off;
+        }
+      }
+    }
+    if (fits) S.col16.swap(c16);
+    else S.col16.clear();
+  }
   S.long_row.clear();
   S.long_ptr.assign(1, 0);
   S.long_col.clear();

@@ -30,6 +30,8 @@ struct SellHost {
   int64_t nslices = 0;
   std::vector<int64_t> sl_ptr;     // nslices + 1, in slots, multiples of 32
   std::vector<int32_t> col;        // slots
+  std::vector<int16_t> col16;      // slots: col - row when every slot's offset fits 16 bits (else empty);
+                                   // 0 on padding and on lanes past the last row
   std::vector<double> val;         // slots
   std::vector<uint32_t> long_mask; // nslices: lanes whose row is a long row
   std::vector<int32_t> long_row;   // long rows, increasing

@@ -8,6 +8,8 @@ rounding scale of its terms.  Each side's error is at most about
 1e-5 * (|A32||x|)_i against the oracle's float product (each side within
 ~16 * 2^-24).
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -161,3 +163,27 @@ def test_symmetric_layouts(torch, layout, monkeypatch):
         for sol in (xs, xi):
             r = s.b - oracle.spmv("csr", s.ptr, s.idx, s.val, sol.cpu().numpy())
             assert np.linalg.norm(r) <= 1e-10 * np.linalg.norm(s.b)
+
+
+@pytest.mark.parametrize("fmt", ["csr", "csc"])
+def test_narrow_and_wide_indices_agree(torch, fmt):
+    """16-bit column offsets (chosen when every offset fits) and int32 column
+    indices give the same products bit for bit (same sums, same order)."""
+    s = fem(17, 15, 19)
+    arrs = (s.ptr, s.idx, s.val) if fmt == "csr" else s.csc()
+    x = torch.from_numpy(np.random.default_rng(9).uniform(-1, 1, s.n)).cuda()
+    with gb.Matrix(fmt, *arrs) as N:
+        assert N.stats()["index_bytes"] == 2
+        yn, yn32 = N.spmv(x), N.spmv_f32(x.float())
+    old = os.environ.get("GBCG_WIDE_INDEX")
+    os.environ["GBCG_WIDE_INDEX"] = "1"
+    try:
+        W = gb.Matrix(fmt, *arrs)
+    finally:
+        if old is None:
+            os.environ.pop("GBCG_WIDE_INDEX", None)
+        else:
+            os.environ["GBCG_WIDE_INDEX"] = old
+    with W:
+        assert W.stats()["index_bytes"] == 4
+        assert torch.equal(W.spmv(x), yn) and torch.equal(W.spmv_f32(x.float()), yn32)
