@@ -44,8 +44,8 @@ TOL = 1e-10
 # 30-iteration launch of the same 128^3 system (profiles/k_cg_ru_csr128.md):
 # per single-precision iteration, and per double-precision update.  Used
 # only for that kernel on that system; null elsewhere.
-RU_TRAFFIC_PER_ITERATION = 247e6
-RU_TRAFFIC_PER_UPDATE = 0.484e9
+RU_TRAFFIC_PER_ITERATION = 185e6
+RU_TRAFFIC_PER_UPDATE = 0.424e9
 
 
 def parse():
