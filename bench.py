@@ -671,6 +671,9 @@ def ablation(torch, gb, args, big):
         for fmt in ("csr", "sym"):
             Ab = gb.Ablation(fmt, *arrays[fmt])
             ms_ab = time_spmv(torch, Ab, xv, yv, False)
+            # the 2010 kernels read int32 indices: 12 bytes per stored entry
+            nnz_st = int(arrays[fmt][1].shape[0])
+            bytes_2010 = 12 * nnz_st + 4 * (s.n + 1) + 16 * s.n
             with gb.Matrix(fmt, *arrays[fmt]) as M:
                 ms_lib = time_spmv(torch, M, xv, yv, False)
                 bytes_ = M.stats()["spmv_bytes_fp64"]
@@ -682,7 +685,7 @@ def ablation(torch, gb, args, big):
                     t0 = time.perf_counter()
                     _, info = M.solve(b, x, tol=TOL)
                     lib_s = time.perf_counter() - t0
-            r[fmt] = {"spmv_2010_ms": ms_ab, "spmv_2010_GBs": bytes_ / ms_ab / 1e6,
+            r[fmt] = {"spmv_2010_ms": ms_ab, "spmv_2010_GBs": bytes_2010 / ms_ab / 1e6,
                       "spmv_library_ms": ms_lib, "spmv_library_GBs": bytes_ / ms_lib / 1e6,
                       "spmv_speedup": ms_ab / ms_lib}
             if fmt == "csr":
