@@ -361,6 +361,38 @@ __device__ __forceinline__ int slice_len(const OpDev<V>& A, int64_t s) {
   return (int)((A.sl_ptr[s + 1] - A.sl_ptr[s]) >> 5);
 }
 
+// Offsets and lengths of a warp's slices, 32 at a time: lane l holds the
+// warp's slice number 32w + l of window w (slices first, first + nw, ...),
+// so one load fetches the metadata of the next 32 fills and issuing a fill
+// waits on no load.  len_prev keeps the previous window's lengths for the
+// fills still in flight when the issue side moves on.
+struct SliceWin {
+  int64_t beg = 0;
+  int len = 0, len_prev = 0;
+  int w = -1;
+};
+
+template <typename V>
+__device__ __forceinline__ void win_at(const OpDev<V>& A, SliceWin& sw, int j, int64_t first, int64_t s1, int nw) {
+  const int w = j >> 5;
+  if (w == sw.w) return;
+  sw.len_prev = sw.len;
+  sw.w = w;
+  const int64_t s = first + ((int64_t)w * 32 + (threadIdx.x & 31)) * nw;
+  sw.beg = 0;
+  sw.len = 0;
+  if (s < s1) {
+    sw.beg = A.sl_ptr[s];
+    sw.len = (int)((A.sl_ptr[s + 1] - sw.beg) >> 5);
+  }
+}
+
+// Length of the warp's slice number j (issued already: its window is the
+// current one or the one before).
+__device__ __forceinline__ int win_len(const SliceWin& sw, int j) {
+  return __shfl_sync(0xffffffffu, (j >> 5) == sw.w ? sw.len : sw.len_prev, j & 31);
+}
+
 // Issue the fill of slice s into the next stage (no-op for empty or
 // oversize slices, which are read straight from global memory).
 template <typename V>
@@ -378,6 +410,30 @@ __device__ __forceinline__ void pipe_issue(const OpDev<V>& A, Stage<V>* stages, 
       bulk_g2s(stages[st].col, A.col16 + A.sl_ptr[s], cb, &pp.bars[st], pp.policy);
     else
       bulk_g2s(stages[st].col, A.col + A.sl_ptr[s], cb, &pp.bars[st], pp.policy);
+  }
+  ++pp.issued;
+}
+
+// pipe_issue for the warp's slice number j, its offset and length taken from
+// the window.
+template <typename V>
+__device__ __forceinline__ void pipe_issue_win(const OpDev<V>& A, Stage<V>* stages, Pipe& pp, SliceWin& sw, int j,
+                                               int64_t first, int64_t s1, int nw) {
+  win_at(A, sw, j, first, s1, nw);
+  const int L = __shfl_sync(0xffffffffu, sw.len, j & 31);
+  const int64_t beg = __shfl_sync(0xffffffffu, sw.beg, j & 31);
+  if (L == 0 || L > kMaxL || pp.failed) return;
+  const uint32_t st = pp.issued % pp.nst;
+  if ((threadIdx.x & 31) == 0) {
+    const bool narrow = A.col16 != nullptr;
+    const uint32_t vb = (uint32_t)(L * 32 * sizeof(V));
+    const uint32_t cb = (uint32_t)(L * 32 * (narrow ? sizeof(int16_t) : sizeof(int32_t)));
+    mbar_arrive_expect_tx(&pp.bars[st], vb + cb);
+    bulk_g2s(stages[st].val, A.val + beg, vb, &pp.bars[st], pp.policy);
+    if (narrow)
+      bulk_g2s(stages[st].col, A.col16 + beg, cb, &pp.bars[st], pp.policy);
+    else
+      bulk_g2s(stages[st].col, A.col + beg, cb, &pp.bars[st], pp.policy);
   }
   ++pp.issued;
 }
@@ -418,6 +474,58 @@ __device__ __forceinline__ void spmv_rows(const OpDev<V>& A, int64_t s0, int64_t
       const V v = sell_row<V, true, NC, 4>(A, s, lane, x);
       if (row < A.n) emit_row<V>(f, row, v, xr);
     }
+  } else if constexpr (NC) {
+    // One-shot products take their slices' offsets and lengths from the
+    // window (one load per 32 slices rather than one per slice on the issue
+    // path): 6% (single) and 11% (double precision) faster on GB300 at 128^3.
+    // The persistent solver keeps the per-slice loads below, because there a
+    // faster issue path puts more copies in flight, and they lengthen the
+    // round trip of the gathers (measured 2-4% slower per iteration).
+    const int64_t first = s0 + warp;
+    const int J = first < s1 ? (int)((s1 - first + nw - 1) / nw) : 0;  // slices of this warp
+    SliceWin sw;
+    int j_issue = 0;
+    while (j_issue + 1 < (int)pp.nst && j_issue < J)
+      pipe_issue_win(A, stages, pp, sw, j_issue++, first, s1, nw);
+    for (int j = 0; j < J; ++j) {
+      if (j_issue < J) pipe_issue_win(A, stages, pp, sw, j_issue++, first, s1, nw);
+      const int64_t s = first + (int64_t)j * nw;
+      const int L = win_len(sw, j);
+      const int64_t row = s * 32 + lane;
+      const V xr = (std::is_invocable_v<F, int64_t, V, V> && row < A.n) ? ld_vec<NC>(x + row) : V(0);
+      V acc = V(0);
+      if (L > kMaxL) {
+        acc = sell_row<V, false, NC, 8>(A, s, lane, x);
+      } else if (L > 0 && !pp.failed) {
+        const uint32_t st = pp.consumed % pp.nst, par = (pp.consumed / pp.nst) & 1u;
+        if (!mbar_wait(&pp.bars[st], par, pp.limit_ns)) {
+          pp.failed = true;
+          if (lane == 0) atomicCAS(err, 0, (int)kTimeout);
+        } else {
+          ++pp.consumed;
+          const V* __restrict__ sv = stages[st].val;
+          V xv[kMaxL];
+          if (A.col16) {  // 16-bit offsets from the row (lanes past the last row read x[0])
+            const int16_t* __restrict__ sc = reinterpret_cast<const int16_t*>(stages[st].col);
+            const V* xb = x + (row < A.n ? row : 0);
+#pragma unroll
+            for (int k = 0; k < kMaxL; ++k)
+              if (k < L) xv[k] = ld_vec<NC>(xb + sc[k * 32 + lane]);
+          } else {
+            const int32_t* __restrict__ sc = stages[st].col;
+#pragma unroll
+            for (int k = 0; k < kMaxL; ++k)
+              if (k < L) xv[k] = ld_vec<NC>(x + sc[k * 32 + lane]);
+          }
+#pragma unroll
+          for (int k = 0; k < kMaxL; ++k)
+            if (k < L) acc = fma_(sv[k * 32 + lane], xv[k], acc);
+        }
+        __syncwarp();
+      }
+      if (row < A.n && !((A.long_mask[s] >> lane) & 1u)) emit_row<V>(f, row, acc, xr);
+    }
+    if (pp.failed) pipe_drain(pp);
   } else {
     int64_t s_issue = s0 + warp;
     for (uint32_t d = 0; d + 1 < pp.nst && s_issue < s1; ++d, s_issue += nw) pipe_issue(A, stages, pp, s_issue);
