@@ -187,3 +187,32 @@ def test_narrow_and_wide_indices_agree(torch, fmt):
     with W:
         assert W.stats()["index_bytes"] == 4
         assert torch.equal(W.spmv(x), yn) and torch.equal(W.spmv_f32(x.float()), yn32)
+
+
+@pytest.mark.parametrize("ctas", [1, 3])
+def test_one_shot_product_many_slices_per_warp(torch, ctas, monkeypatch):
+    """Small grids give each warp more than 32 slices, so the one-shot
+    product's slice-metadata window moves on while fills of the previous
+    window are still in flight; mixed slice lengths (empty rows, rows past
+    the stage size) cross the window edges too.  Double and single precision,
+    16-bit offsets and int32 indices."""
+    monkeypatch.setenv("GBCG_GRID", str(ctas))
+    s = fem(31, 31, 32)
+    ptr, idx, val = random_general(20000, 20000, 6.0 / 20000, 5, empty_rows=tuple(range(0, 20000, 97)),
+                                   one_rows=tuple(range(3, 20000, 89)), long_rows=tuple(range(11, 20000, 1409)),
+                                   long_len=300)
+    cases = [("csr", (s.ptr, s.idx, s.val)), ("csc", s.csc()), ("csr", (ptr, idx, val))]
+    for wide in ("0", "1"):
+        monkeypatch.setenv("GBCG_WIDE_INDEX", wide)
+        for fmt, arrs in cases:
+            n = arrs[0].shape[0] - 1
+            x = femgen.random_vector(n, 23)
+            y, st = gpu_spmv(torch, fmt, arrs, x)
+            assert st["grid_ctas"] == ctas and st["layout"] == 0
+            check(y, oracle.spmv(fmt, *arrs, x), oracle.abs_spmv(fmt, *arrs, x), TOL64)
+            x32 = x.astype(np.float32)
+            v32 = arrs[2].astype(np.float32)
+            with gb.Matrix(fmt, *arrs) as A:
+                y32 = A.spmv_f32(torch.from_numpy(x32).cuda()).cpu().numpy().astype(np.float64)
+            check(y32, oracle.spmv_f32(fmt, arrs[0], arrs[1], v32, x32).astype(np.float64),
+                  oracle.abs_spmv(fmt, arrs[0], arrs[1], v32.astype(np.float64), x32.astype(np.float64)), TOL32)
