@@ -66,6 +66,8 @@ def parse():
     ap.add_argument("--only-differentiable", action="store_true", help="only run the differentiation leg")
     ap.add_argument("--only-paper-size", action="store_true", help="only run the paper-size leg")
     ap.add_argument("--only-ablation", action="store_true", help="only run the 2010-structure ablation leg")
+    ap.add_argument("--only-largest", action="store_true",
+                    help="only run the largest-system leg (256^3: products and solves, a few minutes)")
     ap.add_argument("--profile-batched", type=int, default=0,
                     help="only one mixed-precision solve of the first N batch instances (small case for ncu)")
     ap.add_argument("--profile-spmv", action="store_true",
@@ -242,6 +244,9 @@ def run_ours(args):
         print(json.dumps({"ablation_2010": ablation(torch, gb, args, femgen.build_system(femgen.LARGE))}),
               flush=True)
         return 0
+    if args.only_largest:
+        print(json.dumps({"largest": largest(torch, gb, args)}), flush=True)
+        return 0
     if args.only_paper_size:
         print(json.dumps({"paper_size": paper_size(torch, gb, args)}), flush=True)
         return 0
@@ -409,8 +414,6 @@ def extras(torch, gb, s, fmt_arrays, A_head, args, hbm):
         r["spmv_fp64_frac_of_measured_hbm"] = r["spmv_fp64_GBs"] / hbm
         r["spmv_fp32_frac_of_measured_hbm"] = r["spmv_fp32_GBs"] / hbm
         for prec in ("fp64", "fp32_ir", "fp32_ru"):
-            if prec == "fp32_ru" and st["layout"] == 2:
-                continue  # reliable updates run on the row-gather layouts
             itol = args.inner_tol if prec == "fp32_ir" else 0.0
             x = torch.zeros_like(b)
             M.solve(b, x, tol=TOL, precision=prec, inner_tol=itol)  # warm
@@ -448,9 +451,9 @@ def paper_size(torch, gb, args):
     for fmt in ("sym", "csr"):
         with gb.Matrix(fmt, *arrays[fmt]) as M:
             out[fmt] = {"grid_ctas": M.stats()["grid_ctas"]}
-            runs = [("fp64", "standard"), ("fp32_ir", "standard")]
+            runs = [("fp64", "standard"), ("fp32_ir", "standard"), ("fp32_ru", "standard")]
             if fmt == "csr":
-                runs += [("fp64", "pipelined"), ("fp32_ru", "standard")]
+                runs += [("fp64", "pipelined")]
             for prec, variant in runs:
                 x = torch.zeros_like(b)
                 ts = []
@@ -700,6 +703,51 @@ def ablation(torch, gb, args, big):
                                 "s_library": lib_s, "iterations_library": info.iterations,
                                 "launches_library": info.launches, "speedup": ab_s / lib_s}
         out[name] = r
+    return out
+
+
+def largest(torch, gb, args):
+    """The largest single system (256^3, four inclusions): product bandwidth
+    and time to 1e-10 of mixed precision against plain double-precision CG, in
+    symmetric and full CSR storage.  One solve per variant (each takes
+    seconds), kernel time from the library's own events, the L2 flushed
+    before it."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    hbm, _ = peaks()
+    g = femgen.LARGEST
+    t0 = time.perf_counter()
+    s = femgen.build_system(g)
+    out = {"workload": f"fem {g.nx}x{g.ny}x{g.nz} P1 stiffness, {g.n_incl} inclusions, contrast {g.contrast:g}, "
+                       f"tol 1e-10", "n": s.n, "nnz": s.nnz, "generate_s": time.perf_counter() - t0}
+    b = torch.from_numpy(s.b).to(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    xv = torch.from_numpy(femgen.random_vector(s.n, 7)).to(dev)
+    yv = torch.empty_like(xv)
+    arrays = {"sym": s.upper(), "csr": (s.ptr, s.idx, s.val)}
+    for fmt in ("sym", "csr"):
+        with gb.Matrix(fmt, *arrays[fmt]) as M:
+            st = M.stats()
+            r = {"nnz_stored": int(arrays[fmt][1].shape[0]), "device_bytes": st["device_bytes"],
+                 "spmv_fp64_ms": time_spmv(torch, M, xv, yv, False),
+                 "spmv_fp32_ms": time_spmv(torch, M, xv.float(), yv.float(), True)}
+            r["spmv_fp64_GBs"] = st["spmv_bytes_fp64"] / r["spmv_fp64_ms"] / 1e6
+            r["spmv_fp32_GBs"] = st["spmv_bytes_fp32"] / r["spmv_fp32_ms"] / 1e6
+            r["spmv_fp64_frac_of_measured_hbm"] = r["spmv_fp64_GBs"] / hbm
+            r["spmv_fp32_frac_of_measured_hbm"] = r["spmv_fp32_GBs"] / hbm
+            for prec in ("fp64", "fp32_ir", "fp32_ru"):
+                x = torch.zeros_like(b)
+                flush_l2(torch, flush)
+                torch.cuda.synchronize()
+                _, info = M.solve(b, x, tol=TOL, precision=prec, raise_on_error=False)
+                xs = x.cpu().numpy()
+                r[prec] = {"s": info.kernel_ms / 1000.0, "iterations": info.iterations, "outer": info.outer,
+                           "status": info.status, "rel_res_true": info.rel_res_true,
+                           "iter_us": 1000.0 * info.kernel_ms / max(1, info.iterations),
+                           "err_vs_xstar": float(np.linalg.norm(xs - s.xstar) / np.linalg.norm(s.xstar))}
+            r["mixed_speedup_vs_fp64"] = r["fp64"]["s"] / r["fp32_ir"]["s"]
+            if "fp32_ru" in r:
+                r["reliable_update_speedup_vs_fp64"] = r["fp64"]["s"] / r["fp32_ru"]["s"]
+            out[fmt] = r
     return out
 
 

@@ -239,18 +239,20 @@ int occupancy_of(int& per_sm) {
   return 0;
 }
 
-constexpr size_t ru_smem() { return (size_t)kWarps * ru_warp_stage_bytes(); }
+// Shared memory of the reliable-update kernel: the per-warp stages of both
+// precisions' gather pipelines, or (kTiles) the larger of the two tile
+// pipelines' carvings, used in turn.
+template <int FMT>
+constexpr size_t ru_smem() {
+  return FMT == kTiles ? std::max(sym_smem_bytes<float>(), sym_smem_bytes<double>())
+                       : (size_t)kWarps * ru_warp_stage_bytes();
+}
 
 template <int FMT>
 int ru_occupancy_of(int& per_sm) {
-  if constexpr (FMT == kTiles) {
-    per_sm = 1 << 20;
-    return 0;
-  } else {
-    CUDA_TRY(cudaFuncSetAttribute(k_cg_ru<FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ru_smem()));
-    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cg_ru<FMT>, kCgThreads, ru_smem()));
-    return 0;
-  }
+  CUDA_TRY(cudaFuncSetAttribute(k_cg_ru<FMT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ru_smem<FMT>()));
+  CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cg_ru<FMT>, block_of(FMT), ru_smem<FMT>()));
+  return 0;
 }
 
 template <int FMT>
@@ -340,7 +342,8 @@ cudaError_t launch_pcg_fmt(const gbcg_matrix_s* M, const CgArgs<double>& c, cuda
 template <int FMT>
 cudaError_t launch_ru(const RuArgs& args, int grid, cudaStream_t s) {
   void* kargs[] = {(void*)&args};
-  return cudaLaunchCooperativeKernel((const void*)k_cg_ru<FMT>, dim3(grid), dim3(kCgThreads), kargs, ru_smem(), s);
+  return cudaLaunchCooperativeKernel((const void*)k_cg_ru<FMT>, dim3(grid), dim3(block_of(FMT)), kargs,
+                                     ru_smem<FMT>(), s);
 }
 
 // Product y = A x (MODE 0), or r = b - A x into y with per-CTA partial sums
@@ -441,19 +444,22 @@ int solve_fp64(gbcg_matrix_s* M, const double* b, double* x, double tol, int max
 }
 
 // Single-precision iterations with double-precision reliable updates: one
-// persistent launch (row-gather layouts; the caller has checked the mode).
+// persistent launch, on any layout.
 int solve_ru(gbcg_matrix_s* M, const double* b, double* x, double tol, int maxit, const gbcg_opts* o,
              gbcg_info* info, cudaStream_t s) {
   CUDA_TRY(cudaMemsetAsync(M->bar, 0, sizeof(GridBar), s));
   RuArgs a;
   a.c = make_args<float>(M, M->d32, M->r32, M->p32, M->q32, nullptr, tol, maxit, 0, timeout_ns_of(o));
   a.A64 = M->op<double>();
+  a.T64 = M->tiles<double>();
   a.x64 = x;
   a.b64 = b;
   a.q64 = M->q;
   a.delta = (o && o->inner_tol > 0.0 && o->inner_tol < 1.0) ? o->inner_tol : 0.1;
   CUDA_TRY(cudaEventRecord(M->ev0, s));
-  CUDA_TRY(M->mode == kPlan ? launch_ru<kPlan>(a, M->grid, s) : launch_ru<kGather>(a, M->grid, s));
+  CUDA_TRY(M->mode == kTiles  ? launch_ru<kTiles>(a, M->grid, s)
+           : M->mode == kPlan ? launch_ru<kPlan>(a, M->grid, s)
+                              : launch_ru<kGather>(a, M->grid, s));
   CUDA_TRY(cudaEventRecord(M->ev1, s));
   if (int rc = read_state(M, s)) return rc;
   float kms = 0.f;
@@ -765,10 +771,6 @@ int gbcg_solve(gbcg_matrix_t A, const double* b, double* x, double tol, int32_t 
   if (!(tol >= 0.0) || !std::isfinite(tol)) return fail(GBCG_ERR_INVALID, "tol must be finite and >= 0");
   if (opts && (opts->precision != GBCG_FP64 && opts->precision != GBCG_FP32_IR && opts->precision != GBCG_FP32_RU))
     return fail(GBCG_ERR_INVALID, "unknown precision");
-  if (opts && opts->precision == GBCG_FP32_RU && A->mode == kTiles)
-    return fail(GBCG_ERR_INVALID,
-                "reliable updates run on row-gather layouts (CSR, CSC, or symmetric storage with "
-                "GBCG_SYM_LAYOUT=plan)");
   if (opts && opts->precision == GBCG_FP32_RU && opts->variant == GBCG_PIPELINED)
     return fail(GBCG_ERR_INVALID, "the single-reduction variant is double precision only");
   if (opts && opts->variant != GBCG_STANDARD && opts->variant != GBCG_PIPELINED)

@@ -1416,6 +1416,7 @@ finish:
 struct RuArgs {
   CgArgs<float> c;        // float operator; x = correction d, r, p, q
   OpDev<double> A64;      // the same layout with double values
+  SymDev<double> T64;     // and its tiles (kTiles)
   double* x64;            // caller's x (in: x0)
   const double* b64;
   double* q64;            // double product scratch
@@ -1430,9 +1431,12 @@ __host__ __device__ constexpr size_t ru_warp_stage_bytes() {
              : gather_stages<double>() * sizeof(Stage<double>);
 }
 
+// Tiled symmetric layout: the single- and double-precision products share
+// the tile pipeline and its shared memory (TileSmem<double> over
+// TileSmem<float>); each product drains its fills and grid barriers separate
+// them, so no fill of one lands in a stage the other is reading.
 template <int FMT>
-__global__ void __launch_bounds__(kCgThreads, 1) k_cg_ru(RuArgs ra) {
-  static_assert(FMT != kTiles, "row-gather layouts only");
+__global__ void __launch_bounds__(FMT == kTiles ? kTileThreads : kCgThreads, 1) k_cg_ru(RuArgs ra) {
   static_assert(gather_stages<float>() + gather_stages<double>() <= kMaxStages, "mbarrier sets");
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ uint64_t bars[kMaxThreads / 32][kMaxStages];
@@ -1458,6 +1462,9 @@ __global__ void __launch_bounds__(kCgThreads, 1) k_cg_ru(RuArgs ra) {
   Pipe pp32, pp64;
   pipe_init(pp32, bars[warp], gather_stages<float>(), a.timeout_ns);
   pipe_init(pp64, bars[warp] + gather_stages<float>(), gather_stages<double>(), a.timeout_ns);
+  __shared__ uint64_t tbar[6];
+  TilePipe tp;
+  if constexpr (FMT == kTiles) tile_pipe_init(tp, tbar, a.timeout_ns);
   __syncthreads();
   int* err = &a.bar->status;
   double* part0 = a.part;
@@ -1475,8 +1482,16 @@ __global__ void __launch_bounds__(kCgThreads, 1) k_cg_ru(RuArgs ra) {
       d[i] = 0.f;
     }
     if (!grid_barrier(a.bar, target, a.timeout_ns, &sflag, nbar++)) return false;
-    spmv_rows<double, FMT == kPlan, false>(ra.A64, s0, s1, l0, l1, x64, st64, pp64, err,
-                                           [&](int64_t row, double v) { q64[row] = v; });
+    if constexpr (FMT == kTiles) {
+      TileSmem<double>* sm = reinterpret_cast<TileSmem<double>*>(smem_raw);
+      sym_tiles<double, false>(ra.A64, ra.T64, x64, sm, tp, err,
+                               [&](int64_t row, double qo, double, double, double) { q64[row] = qo; });
+      if (!grid_barrier(a.bar, target, a.timeout_ns, &sflag, nbar++)) return false;
+      sym_incoming<double>(ra.T64, q64);
+    } else {
+      spmv_rows<double, FMT == kPlan, false>(ra.A64, s0, s1, l0, l1, x64, st64, pp64, err,
+                                             [&](int64_t row, double v) { q64[row] = v; });
+    }
     __syncthreads();
     double ptt = 0.0, pbb = 0.0;
     float prr = 0.f;
@@ -1523,11 +1538,20 @@ __global__ void __launch_bounds__(kCgThreads, 1) k_cg_ru(RuArgs ra) {
     // A: q = A32 p, p'q
     {
       float ppq = 0.f;
-      spmv_rows<float, FMT == kPlan, false>(a.A, s0, s1, l0, l1, p, st32, pp32, err,
-                                            [&](int64_t row, float v, float pr) {
-                                              q[row] = v;
-                                              ppq = fmaf(pr, v, ppq);
-                                            });
+      if constexpr (FMT == kTiles) {
+        // p'Ap = p'Dp + 2 p'Up from the rows' own parts: no incoming sums needed
+        TileSmem<float>* sm = reinterpret_cast<TileSmem<float>*>(smem_raw);
+        sym_tiles<float, false>(a.A, a.T, p, sm, tp, err, [&](int64_t row, float qo, float xi, float dxi, float direct) {
+          q[row] = qo;
+          ppq = fmaf(xi, fmaf(2.f, direct, dxi), ppq);
+        });
+      } else {
+        spmv_rows<float, FMT == kPlan, false>(a.A, s0, s1, l0, l1, p, st32, pp32, err,
+                                              [&](int64_t row, float v, float pr) {
+                                                q[row] = v;
+                                                ppq = fmaf(pr, v, ppq);
+                                              });
+      }
       const double sp = block_sum((double)ppq, red);
       if (threadIdx.x == 0) part0[c] = sp;
     }
@@ -1536,6 +1560,10 @@ __global__ void __launch_bounds__(kCgThreads, 1) k_cg_ru(RuArgs ra) {
     if (!isfinite(pq)) { status = kNonfinite; break; }
     if (!(pq > 0.0)) { status = kNotSpd; break; }
     const float al = (float)(rr / pq);
+    if constexpr (FMT == kTiles) {  // the transpose parts other CTAs computed for these rows
+      sym_incoming<float>(a.T, q);
+      __syncthreads();
+    }
     // B: d += alpha p, r -= alpha q, r'r  (16-byte accesses, as k_cg)
     {
       float prr = 0.f;

@@ -26,7 +26,11 @@ def torch():
 
 
 def arrays(s, fmt):
-    return {"csr": (s.ptr, s.idx, s.val), "sym": s.upper(), "csc": s.csc()}[fmt]
+    return {"csr": (s.ptr, s.idx, s.val), "sym": s.upper(), "tiles": s.upper(), "csc": s.csc()}[fmt]
+
+
+def oracle_fmt(fmt):
+    return "sym" if fmt == "tiles" else fmt
 
 
 def true_rel_res(s, x):
@@ -34,6 +38,12 @@ def true_rel_res(s, x):
 
 
 def make(fmt, s):
+    """"tiles": symmetric storage in the default (tiled) layout; "sym": the
+    transpose-plan layout."""
+    if fmt == "tiles":
+        A = gb.Matrix("sym", *arrays(s, fmt))
+        assert A.stats()["layout"] == 2
+        return A
     if fmt != "sym":
         return gb.Matrix(fmt, *arrays(s, fmt))
     old = os.environ.get("GBCG_SYM_LAYOUT")
@@ -48,21 +58,21 @@ def make(fmt, s):
 
 
 @pytest.mark.parametrize("fmt,grid", [("csr", (31, 31, 32)), ("csc", (17, 15, 19)), ("sym", (31, 31, 32)),
-                                      ("csr", (17, 15, 19))])
+                                      ("csr", (17, 15, 19)), ("tiles", (31, 31, 32)), ("tiles", (9, 10, 11))])
 def test_reliable_updates_match_oracle(torch, fmt, grid):
     s = fem(*grid)
     b = torch.from_numpy(s.b).cuda()
     with make(fmt, s) as A:
         x, info = A.solve(b, tol=1e-10, maxit=10 * s.n, precision="fp32_ru")
         assert info.status == "OK", info
-        ref = oracle.cg_ru(fmt, *arrays(s, fmt), s.b, tol=1e-10, maxit=10 * s.n)
+        ref = oracle.cg_ru(oracle_fmt(fmt), *arrays(s, fmt), s.b, tol=1e-10, maxit=10 * s.n)
         assert ref.status == "OK"
         assert true_rel_res(s, x.cpu().numpy()) <= 1e-10
         assert abs(info.iterations - ref.iterations) <= 0.10 * ref.iterations + 10, (info.iterations, ref.iterations)
         assert abs(info.outer - ref.restarts) <= 2, (info.outer, ref.restarts)
         x12, i12 = A.solve(b, tol=1e-12, maxit=10 * s.n, precision="fp32_ru")
         assert i12.status == "OK", i12
-        ref12 = oracle.cg(fmt, *arrays(s, fmt), s.b, tol=1e-12, maxit=10 * s.n)
+        ref12 = oracle.cg(oracle_fmt(fmt), *arrays(s, fmt), s.b, tol=1e-12, maxit=10 * s.n)
         assert np.linalg.norm(x12.cpu().numpy() - ref12.x) <= 1e-8 * np.linalg.norm(ref12.x)
         x2, _ = A.solve(b, tol=1e-10, maxit=10 * s.n, precision="fp32_ru")
         assert torch.equal(x, x2)
@@ -86,11 +96,35 @@ def test_reliable_updates_edge_cases(torch):
         assert info.status == ref.status == "NOT_SPD" and info.iterations == 0
 
 
-def test_reliable_updates_reject_the_tiled_layout(torch):
-    s = fem(12, 12, 12)
-    with gb.Matrix("sym", *s.upper()) as A:
-        with pytest.raises(gb.GbcgError, match="row-gather"):
-            A.solve(torch.from_numpy(s.b).cuda(), precision="fp32_ru")
+def test_reliable_updates_tiled_layout_edge_cases(torch):
+    s = fem(9, 8, 7)
+    with make("tiles", s) as A:
+        z = torch.zeros(s.n, dtype=torch.float64, device="cuda")
+        x, info = A.solve(z, torch.ones_like(z), precision="fp32_ru")
+        assert info.status == "OK" and info.iterations == 0 and not torch.any(x).item()
+        xs = torch.from_numpy(s.xstar).cuda()
+        x, info = A.solve(A.spmv(xs), xs.clone(), tol=1e-8, precision="fp32_ru")
+        assert info.status == "OK" and info.iterations == 0
+        x, info = A.solve(torch.from_numpy(s.b).cuda(), tol=1e-30, maxit=4, precision="fp32_ru",
+                          raise_on_error=False)
+        assert info.status == "MAXIT" and info.iterations == 4
+    up = s.upper()
+    with gb.Matrix("sym", up[0], up[1], -up[2]) as N:
+        assert N.stats()["layout"] == 2
+        x, info = N.solve(torch.from_numpy(s.b).cuda(), precision="fp32_ru", raise_on_error=False)
+        ref = oracle.cg_ru("sym", up[0], up[1], -up[2], s.b)
+        assert info.status == ref.status == "NOT_SPD" and info.iterations == 0
+
+
+@pytest.mark.parametrize("ctas", ["1", "7"])
+def test_reliable_updates_tiled_layout_grid_sizes(torch, ctas, monkeypatch):
+    s = fem(17, 15, 19)
+    monkeypatch.setenv("GBCG_GRID", ctas)
+    with make("tiles", s) as A:
+        assert A.stats()["grid_ctas"] == int(ctas)
+        x, info = A.solve(torch.from_numpy(s.b).cuda(), tol=1e-10, maxit=10 * s.n, precision="fp32_ru")
+    assert info.status == "OK", info
+    assert true_rel_res(s, x.cpu().numpy()) <= 1e-10
 
 
 def test_reliable_updates_full_size(torch):
@@ -101,4 +135,13 @@ def test_reliable_updates_full_size(torch):
     assert true_rel_res(s, x.cpu().numpy()) <= 1e-10
     # about the double-precision iteration count (11 143 here); the
     # refinement that restarts the inner CG needs 16 418
+    assert info.iterations <= 1.15 * 11143
+
+
+def test_reliable_updates_full_size_tiled(torch):
+    s = femgen.build_system(femgen.LARGE)
+    with make("tiles", s) as A:
+        x, info = A.solve(torch.from_numpy(s.b).cuda(), tol=1e-10, precision="fp32_ru")
+    assert info.status == "OK", info
+    assert true_rel_res(s, x.cpu().numpy()) <= 1e-10
     assert info.iterations <= 1.15 * 11143
