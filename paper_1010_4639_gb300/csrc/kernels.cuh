@@ -38,7 +38,7 @@ constexpr int kMaxThreads = kTileThreads;
 constexpr int kMaxL = 16;    // slots per row one pipeline stage holds
 constexpr int kStages = 2;   // stages per warp
 constexpr uint16_t kPlanPad = 0xFFFF;
-constexpr int kMaxStages = 3 + 2;  // gather-pipeline stages (<= 3) + 2 spare
+constexpr int kMaxStages = 3 + 2;  // mbarriers per warp: a single- (3) and a double-precision (2) pipeline
 
 // Layout modes of the product.
 enum { kGather = 0, kPlan = 1, kTiles = 2 };
@@ -332,12 +332,10 @@ __device__ __forceinline__ V long_row(const OpDev<V>& A, int64_t li, int lane, c
 
 // Per-warp pipeline state (uniform across the warp's lanes).
 struct Pipe {
-  uint64_t* bars;      // nst mbarriers of this warp (+ 2 for the x buffers)
+  uint64_t* bars;      // nst mbarriers of this warp
   uint32_t nst;        // stages
   uint32_t issued;     // stage fills issued so far
   uint32_t consumed;   // stage fills consumed so far
-  uint32_t xiss[2];    // x-buffer fills issued / waited for; like the stage
-  uint32_t xwait[2];   // counters they persist across calls of the kernel
   uint64_t policy;
   long long limit_ns;
   bool failed;
@@ -347,12 +345,11 @@ __device__ __forceinline__ void pipe_init(Pipe& pp, uint64_t* bars, uint32_t nst
   pp.bars = bars;
   pp.nst = nst;
   pp.issued = pp.consumed = 0;
-  pp.xiss[0] = pp.xiss[1] = pp.xwait[0] = pp.xwait[1] = 0;
   pp.policy = policy_evict_first();
   pp.limit_ns = limit_ns;
   pp.failed = false;
   if ((threadIdx.x & 31) == 0)
-    for (uint32_t i = 0; i < nst + 2; ++i) mbar_init(&bars[i], 1);
+    for (uint32_t i = 0; i < nst; ++i) mbar_init(&bars[i], 1);
   fence_mbar_init();
 }
 
