@@ -820,8 +820,19 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 // Sum of part[0..G) in a fixed order, broadcast to every thread of the CTA.
 __device__ __forceinline__ double grid_sum(const double* part, int G, double* red) {
   if (threadIdx.x < 32) {
+    // every load first (one round trip for G <= 256), then the additions in
+    // the same order as one strided loop would make them
+    double v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int i = threadIdx.x + 32 * u;
+      v[u] = i < G ? part[i] : 0.0;
+    }
     double t = 0.0;
-    for (int i = threadIdx.x; i < G; i += 32) t += part[i];
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (threadIdx.x + 32 * u < G) t += v[u];
+    for (int i = threadIdx.x + 256; i < G; i += 32) t += part[i];
 #pragma unroll
     for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
     if (threadIdx.x == 0) red[32] = t;
