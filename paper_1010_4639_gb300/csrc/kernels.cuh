@@ -818,7 +818,11 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 }
 
 // Sum of part[0..G) in a fixed order, broadcast to every thread of the CTA.
-__device__ __forceinline__ double grid_sum(const double* part, int G, double* red) {
+// f0(sum) runs on thread 0 before the broadcast: scalars derived from the sum
+// (step lengths, square roots, tests) are formed once per CTA and published
+// through shared memory, not by every thread on GB300's 1/64-rate FP64 pipe.
+template <class F0>
+__device__ __forceinline__ double grid_sum(const double* part, int G, double* red, F0&& f0) {
   if (threadIdx.x < 32) {
     // every load first (one round trip for G <= 256), then the additions in
     // the same order as one strided loop would make them
@@ -835,12 +839,18 @@ __device__ __forceinline__ double grid_sum(const double* part, int G, double* re
     for (int i = threadIdx.x + 256; i < G; i += 32) t += part[i];
 #pragma unroll
     for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-    if (threadIdx.x == 0) red[32] = t;
+    if (threadIdx.x == 0) {
+      red[32] = t;
+      f0(t);
+    }
   }
   __syncthreads();
   const double r = red[32];
   __syncthreads();
   return r;
+}
+__device__ __forceinline__ double grid_sum(const double* part, int G, double* red) {
+  return grid_sum(part, G, red, [](double) {});
 }
 
 // (err points at GridBar::status; err[1] is GridBar::where, a code naming
@@ -1022,6 +1032,10 @@ __global__ void __launch_bounds__(FMT == kTiles ? kTileThreads : kCgThreads, 1) 
   __shared__ uint64_t bars[kMaxThreads / 32][kMaxStages];
   __shared__ double red[33];
   __shared__ int sflag;
+  __shared__ struct {
+    double alpha, beta;
+    int code, nonfinite, conv;
+  } sc;  // the step's scalars, formed by thread 0 (grid_sum's epilogue)
   using VT = typename Vec<V>::T;
   constexpr int W = Vec<V>::W;
   const int G = gridDim.x, c = blockIdx.x;
@@ -1050,6 +1064,7 @@ __global__ void __launch_bounds__(FMT == kTiles ? kTileThreads : kCgThreads, 1) 
   int status = kOk;
   int k = 0, restarts = 0;
   double rr = 0.0, nb = 0.0, rel_true = 0.0;
+  bool conv = false;
 
   // q = A xin over the CTA's rows, complete (kTiles: across a grid barrier)
   auto full_product = [&](const V* xin) -> bool {
@@ -1108,8 +1123,9 @@ __global__ void __launch_bounds__(FMT == kTiles ? kTileThreads : kCgThreads, 1) 
     rr = 0.0;
     goto finish;
   }
+  conv = sqrt(rr) / nb <= a.tol;
   for (;;) {
-    while (k < a.maxit && !(sqrt(rr) / nb <= a.tol)) {
+    while (k < a.maxit && !conv) {
       // A: q = A p, p'q
       V ppq = V(0);
       if constexpr (FMT == kTiles) {
@@ -1131,10 +1147,12 @@ __global__ void __launch_bounds__(FMT == kTiles ? kTileThreads : kCgThreads, 1) 
         if (threadIdx.x == 0) part0[c] = s;
       }
       if (!grid_barrier(a.bar, target, a.timeout_ns, &sflag, nbar++)) return;
-      const double pq = grid_sum(part0, G, red);
-      if (!isfinite(pq)) { status = kNonfinite; goto finish; }
-      if (!(pq > 0.0)) { status = kNotSpd; goto finish; }
-      const double alpha = rr / pq;
+      grid_sum(part0, G, red, [&](double pq) {
+        sc.code = !isfinite(pq) ? kNonfinite : !(pq > 0.0) ? kNotSpd : kOk;
+        sc.alpha = rr / pq;
+      });
+      if (sc.code != kOk) { status = sc.code; goto finish; }
+      const double alpha = sc.alpha;
       if constexpr (FMT == kTiles) {
         sym_incoming<V>(T, q);
         __syncthreads();
@@ -1173,12 +1191,17 @@ __global__ void __launch_bounds__(FMT == kTiles ? kTileThreads : kCgThreads, 1) 
         if (threadIdx.x == 0) part1[c] = s;
       }
       if (!grid_barrier(a.bar, target, a.timeout_ns, &sflag, nbar++)) return;
-      const double rr_new = grid_sum(part1, G, red);
+      const double rr_new = grid_sum(part1, G, red, [&](double s) {
+        sc.nonfinite = !isfinite(s);
+        sc.beta = s / rr;
+        sc.conv = sqrt(s) / nb <= a.tol;
+      });
       ++k;
-      if (!isfinite(rr_new)) { status = kNonfinite; rr = rr_new; goto finish; }
-      const double beta = rr_new / rr;
+      if (sc.nonfinite) { status = kNonfinite; rr = rr_new; goto finish; }
+      const double beta = sc.beta;
       rr = rr_new;
-      if (sqrt(rr) / nb <= a.tol) break;
+      conv = sc.conv;
+      if (conv) break;
       // C: p = r + beta p
       {
         const V be = (V)beta;
@@ -1199,7 +1222,7 @@ __global__ void __launch_bounds__(FMT == kTiles ? kTileThreads : kCgThreads, 1) 
       if (!grid_barrier(a.bar, target, a.timeout_ns, &sflag, nbar++)) return;
     }
     if constexpr (!OUTER) {
-      if (!(sqrt(rr) / nb <= a.tol)) status = kMaxit;
+      if (!conv) status = kMaxit;
       break;
     } else {
       // confirm on the true residual; restart the recurrence from it otherwise
@@ -1222,6 +1245,7 @@ __global__ void __launch_bounds__(FMT == kTiles ? kTileThreads : kCgThreads, 1) 
       if (k >= a.maxit || restarts >= a.max_restarts) { status = kMaxit; break; }
       ++restarts;
       rr = tt;
+      conv = sqrt(rr) / nb <= a.tol;
       for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) p[i] = r[i];
       if (!grid_barrier(a.bar, target, a.timeout_ns, &sflag, nbar++)) return;
     }
@@ -1272,6 +1296,10 @@ __global__ void __launch_bounds__(kCgThreads, 1) k_pcg(PcgArgs<V> pa) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ uint64_t bars[kMaxThreads / 32][kMaxStages];
   __shared__ double red[33];
+  __shared__ struct {
+    double alpha, beta;
+    int code;
+  } sc;
   __shared__ int sflag;
   const CgArgs<V>& a = pa.c;
   const int G = gridDim.x, c = blockIdx.x;
@@ -1339,19 +1367,35 @@ __global__ void __launch_bounds__(kCgThreads, 1) k_pcg(PcgArgs<V> pa) {
       double gamma_old = 0.0, alpha_old = 0.0;
       bool first = true;
       for (;;) {
-        if (!isfinite(gamma) || !isfinite(delta)) { status = kNonfinite; goto finish; }
-        if (sqrt(gamma) / nb <= a.tol || k >= a.maxit) break;
-        const double beta = first ? 0.0 : gamma / gamma_old;
-        const double den = first ? delta : delta - beta * gamma / alpha_old;  // p'Ap
-        if (!isfinite(den)) { status = kNonfinite; goto finish; }
-        if (!(den > 0.0)) {
-          // first step: den = r'Ar, A is not positive definite; later the
-          // recurrence for p'Ap has cancelled (near the attainable residual):
-          // confirm and restart from the true residual
-          if (first) { status = kNotSpd; goto finish; }
-          break;
+        // the step's scalars once per CTA (thread 0), not by every thread on
+        // the 1/64-rate FP64 pipe: 0 step, 1 not finite, 2 leave the run, 3 not SPD
+        if (threadIdx.x == 0) {
+          int code = 0;
+          double al0 = 0.0, be0 = 0.0;
+          if (!isfinite(gamma) || !isfinite(delta)) {
+            code = 1;
+          } else if (sqrt(gamma) / nb <= a.tol || k >= a.maxit) {
+            code = 2;
+          } else {
+            be0 = first ? 0.0 : gamma / gamma_old;
+            const double den = first ? delta : delta - be0 * gamma / alpha_old;  // p'Ap
+            if (!isfinite(den)) code = 1;
+            // first step: den = r'Ar, A is not positive definite; later the
+            // recurrence for p'Ap has cancelled (near the attainable residual):
+            // confirm and restart from the true residual
+            else if (!(den > 0.0)) code = first ? 3 : 2;
+            else al0 = gamma / den;
+          }
+          sc.code = code;
+          sc.alpha = al0;
+          sc.beta = be0;
         }
-        const double alpha = gamma / den;
+        __syncthreads();
+        if (sc.code == 1) { status = kNonfinite; goto finish; }
+        if (sc.code == 3) { status = kNotSpd; goto finish; }
+        if (sc.code == 2) break;
+        const double beta = sc.beta;
+        const double alpha = sc.alpha;
         const V al = (V)alpha, be = (V)beta;
         const V* __restrict__ w = wb[cur];
         V* __restrict__ wn = wb[cur ^ 1];
@@ -1450,6 +1494,10 @@ __global__ void __launch_bounds__(FMT == kTiles ? kTileThreads : kCgThreads, 1) 
   __shared__ uint64_t bars[kMaxThreads / 32][kMaxStages];
   __shared__ double red[33];
   __shared__ int sflag;
+  __shared__ struct {
+    float al, be;
+    int code, upd;
+  } sc;  // the step's scalars, formed by thread 0 (grid_sum's epilogue)
   const CgArgs<float>& a = ra.c;
   const int G = gridDim.x, c = blockIdx.x;
   const int64_t s0 = a.cta_slice[c], s1 = a.cta_slice[c + 1];
@@ -1564,10 +1612,12 @@ __global__ void __launch_bounds__(FMT == kTiles ? kTileThreads : kCgThreads, 1) 
       if (threadIdx.x == 0) part0[c] = sp;
     }
     if (!grid_barrier(a.bar, target, a.timeout_ns, &sflag, nbar++)) return;
-    const double pq = grid_sum(part0, G, red);
-    if (!isfinite(pq)) { status = kNonfinite; break; }
-    if (!(pq > 0.0)) { status = kNotSpd; break; }
-    const float al = (float)(rr / pq);
+    grid_sum(part0, G, red, [&](double pq) {
+      sc.code = !isfinite(pq) ? kNonfinite : !(pq > 0.0) ? kNotSpd : kOk;
+      sc.al = (float)(rr / pq);
+    });
+    if (sc.code != kOk) { status = sc.code; break; }
+    const float al = sc.al;
     if constexpr (FMT == kTiles) {  // the transpose parts other CTAs computed for these rows
       sym_incoming<float>(a.T, q);
       __syncthreads();
@@ -1605,10 +1655,16 @@ __global__ void __launch_bounds__(FMT == kTiles ? kTileThreads : kCgThreads, 1) 
       if (threadIdx.x == 0) part1[c] = sr;
     }
     if (!grid_barrier(a.bar, target, a.timeout_ns, &sflag, nbar++)) return;
-    double rr_new = grid_sum(part1, G, red);
+    // 0: iterate; 1: update first (the recurrence residual fell by delta,
+    // reached tol, or the iteration bound is met); 2: not finite
+    double rr_new = grid_sum(part1, G, red, [&](double s) {
+      sc.upd = !isfinite(s) ? 2 : (sqrt(s) < ra.delta * rmax || sqrt(s) <= a.tol * nb || k + 1 >= a.maxit) ? 1 : 0;
+      sc.be = (float)(s / rr);
+    });
     ++k;
-    if (!isfinite(rr_new)) { status = kNonfinite; break; }
-    if (sqrt(rr_new) < ra.delta * rmax || sqrt(rr_new) <= a.tol * nb || k >= a.maxit) {
+    if (sc.upd == 2) { status = kNonfinite; break; }
+    float be = sc.be;
+    if (sc.upd == 1) {
       const double rr_keep = rr;
       if (!update()) return;
       ++updates;
@@ -1617,8 +1673,8 @@ __global__ void __launch_bounds__(FMT == kTiles ? kTileThreads : kCgThreads, 1) 
       if (k >= a.maxit) { status = kMaxit; goto finish; }
       rr_new = rr;  // the replaced residual's r'r (update() set rr and rmax)
       rr = rr_keep;
+      be = (float)(rr_new / rr);
     }
-    const float be = (float)(rr_new / rr);
     rr = rr_new;
     // C: p = r + beta p
     rows_vec<float>(
