@@ -628,11 +628,10 @@ int gbcg_create(gbcg_matrix_t* out, int32_t format, int64_t n, int64_t nnz, cons
     if (int rc_ = (x)) return bail(rc_); \
   } while (0)
   int64_t& B = M->bytes;
-  // persistent-solver grid: every co-resident CTA that gets a slice (row-gather
-  // layouts: even a few slices per CTA beat fewer, fuller CTAs -- at 25 230
-  // rows on GB300, 152 CTAs run 11.2 us per reliable-update iteration and 50
-  // run 12.0); the tiled layout keeps at least a slice per warp, so that its
-  // tiles stay full
+  // persistent-solver grid: every co-resident CTA that gets a slice.  Even a
+  // few slices per CTA beat fewer, fuller CTAs: at 25 230 rows on GB300, 152
+  // CTAs against 50 run a reliable-update iteration in 11.2 against 12.0 us
+  // (full CSR) and 16.4 against 18.7 us (symmetric tiles)
   int dev = 0, sms = 0, per_sm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return bail(fail(GBCG_ERR_CUDA, "cannot query the device"));
@@ -642,7 +641,7 @@ int gbcg_create(gbcg_matrix_t* out, int32_t format, int64_t n, int64_t nnz, cons
     if (int rc = mode_occupancy(M->mode, per_sm)) return rc;
     if (per_sm < 1) return fail(GBCG_ERR_CUDA, "the persistent solver kernel cannot be resident");
     per_sm = std::min(per_sm, std::max(1, env_int("GBCG_CTAS_PER_SM", 2)));
-    const int64_t want = M->mode == kTiles ? (M->nslices + kWarps - 1) / kWarps : M->nslices;
+    const int64_t want = M->nslices;
     const int env_grid = env_int("GBCG_GRID", 0);
     M->grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * sms, want));
     if (env_grid > 0) M->grid = std::min(env_grid, per_sm * sms);
