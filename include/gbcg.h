@@ -66,7 +66,8 @@ enum gbcg_precision {
                              residual replaced by b - A x in double precision each
                              time the recurrence residual falls by inner_tol
                              (default 0.1), keeping the search direction (the
-                             Krylov space is not restarted).  Row-gather layouts */
+                             Krylov space is not restarted).  Every format and
+                             layout; one persistent launch */
 };
 
 enum gbcg_memory { GBCG_HOST = 0, GBCG_DEVICE = 1 };

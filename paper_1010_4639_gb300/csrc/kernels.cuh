@@ -132,9 +132,11 @@ struct alignas(16) Stage {
   V val[kMaxL * 32];
   int32_t col[kMaxL * 32];
 };
-// Stages per warp of the row-gather pipeline: three for single precision
-// (more bytes in flight for a bandwidth-bound product), two for double
-// precision (FP64-FMA-bound; a third would not fit shared memory).
+// Stages per warp of the row-gather pipeline: three for single precision,
+// two for double precision (FP64-FMA-bound; a third would not fit shared
+// memory).  Measured on GB300, a fourth single-precision stage (or copies
+// issued further ahead) made the solver slower: the streaming copies share
+// the memory system with the latency-critical gathers, and lengthen them.
 template <typename V>
 __host__ __device__ constexpr int gather_stages() { return sizeof(V) == 4 ? 3 : kStages; }
 template <typename V>
