@@ -187,6 +187,17 @@ def per_iteration_bytes(stats, precision):
 
 
 # ---------------------------------------------------------------- reference
+def workload_config(g, s, args, world):
+    """The config object of the timed workload, the same in both arms."""
+    nnz_stored = {"sym": (s.nnz + s.n) // 2, "csr": s.nnz, "csc": s.nnz}[args.format]
+    return {"workload": f"fem {g.nx}x{g.ny}x{g.nz} P1 stiffness, {g.n_incl} inclusion(s), contrast "
+                        f"{g.contrast:g}, {args.format} storage, {args.precision}, tol 1e-10",
+            "n": s.n, "nnz": s.nnz, "nnz_stored": int(nnz_stored),
+            "l2": ("matrix larger than L2; " if 12 * nnz_stored > 129e6 else "matrix fits L2; ")
+                  + "256 MiB L2 flush before every step",
+            "parallelism": f"replicas x{world}" if world > 1 else "single GPU"}
+
+
 def run_reference(args):
     world, rank, local, pg = dist_setup(args)
     if rank != 0:
@@ -213,13 +224,12 @@ def run_reference(args):
     spi = statistics.median(times)
     value = spi * iters_needed if iters_needed else None
     sample = (f"{m} CG iterations of the double-precision oracle per step on the {g.nx}x{g.ny}x{g.nz} system "
-              f"(symmetric storage), scaled by the oracle's own iteration count to 1e-10 "
-              f"({iters_needed}, tests/golden/oracle_{args.grid}_sym.json)")
+              f"(the oracle's own method: symmetric storage, FP64), scaled by the oracle's own iteration count "
+              f"to 1e-10 ({iters_needed}, tests/golden/oracle_{args.grid}_sym.json)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * spi * m, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"fem {g.nx}x{g.ny}x{g.nz} P1 stiffness, {g.n_incl} inclusion(s), contrast "
-                                   f"{g.contrast:g}, tol 1e-10", "n": s.n, "nnz": s.nnz},
+            "config": workload_config(g, s, args, world),
             "cpu_baseline": {"value": value, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample,
                              "seconds_per_iteration": spi},
             "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -339,11 +349,7 @@ def run_ours(args):
         "metric": METRIC, "value": ms / 1000.0, "unit": "s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
-        "config": {"workload": f"fem {g.nx}x{g.ny}x{g.nz} P1 stiffness, {g.n_incl} inclusion(s), contrast "
-                               f"{g.contrast:g}, {args.format} storage, {args.precision}, tol 1e-10",
-                   "n": s.n, "nnz": s.nnz, "nnz_stored": int(fmt_arrays[args.format][1].shape[0]),
-                   "l2": "matrix larger than L2; 256 MiB L2 flush before every step",
-                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "config": workload_config(g, s, args, world),
         "clocks": clk.summary(),
         "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": 16 * s.n, "d2h_bytes_per_step": 8 * s.n},
         "gpu_launches": int(round(sum(i.launches for i in infos) / len(infos))),
