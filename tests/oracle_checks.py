@@ -415,6 +415,10 @@ def check_cg_ru(lib):
     f = oracle.cg("csr", s.ptr, s.idx, s.val, s.b, tol=1e-10, maxit=40 * s.n, lib=lib)
     r = oracle.cg_ru("csr", s.ptr, s.idx, s.val, s.b, tol=1e-10, maxit=40 * s.n, lib=lib)
     assert r.status == "OK" and r.iterations <= 1.2 * f.iterations + 5, (r.iterations, f.iterations)
+    # an update each time the recurrence residual has fallen by delta = 0.1
+    # since the last one: about one per decade from ||r0|| to 1e-10 ||b||
+    # (x0 = 0, so ||r0|| = ||b||), plus the confirming one
+    assert 8 <= r.restarts <= 14, r.restarts
     # three distinct eigenvalues, exact in float: three steps, then updates
     d = np.repeat([2.0, 0.5, 4.0], 5)
     ptr = np.arange(16, dtype=np.int32)

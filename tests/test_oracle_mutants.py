@@ -45,6 +45,9 @@ MUTANTS = {
     "ru_replacement_sign": ("r64[i] = b[i] - r64[i];\n      rel = sqrt(orc_dot(n, r64, r64)) / nb;\n      ++updates;",
                             "r64[i] = r64[i] - b[i];\n      rel = sqrt(orc_dot(n, r64, r64)) / nb;\n      ++updates;"),
     "ru_alpha_inverted": ("const float alpha = rr / pq;", "const float alpha = pq / rr;"),
+    "ru_restarts_direction": ("      rmax = sqrtf(rr_new);\n    }",
+                              "      rmax = sqrtf(rr_new);\n      for (int64_t i = 0; i < n; ++i) p[i] = 0.0f;\n    }"),
+    "ru_threshold_never_reset": ("      rmax = sqrtf(rr_new);\n    }", "    }"),
     "pipelined_z_drops_beta": ("z[i] = (first ? 0.0 : beta * z[i]) + q[i];", "z[i] = q[i];"),
     "pipelined_plain_denominator": ("const double den = first ? delta : delta - beta * gamma / alpha_old;",
                                     "const double den = delta;"),
