@@ -203,6 +203,40 @@ int gbcg_spmv_f32(gbcg_matrix_t A, const float* x, float* y, void* stream);
 int gbcg_solve(gbcg_matrix_t A, const double* b, double* x, double tol, int32_t maxit,
                const gbcg_opts* opts, gbcg_info* info, void* stream);
 
+/* Result of gbcg_solve_async, written to device memory by the solve's last
+ * kernel (the fields of gbcg_info that the device knows). */
+typedef struct {
+  int32_t status;             /* gbcg_status: OK, MAXIT, NOT_SPD, NONFINITE or TIMEOUT */
+  int32_t iterations;         /* CG iterations (single-precision ones for GBCG_FP32_RU) */
+  int32_t outer;              /* true-residual restarts, or reliable updates (GBCG_FP32_RU) */
+  int32_t pad_;
+  double rel_res_recursive;   /* ||r_k|| / ||b|| of the recurrence at exit */
+  double rel_res_true;        /* ||b - A x|| / ||b|| of the last confirmation or update */
+} gbcg_device_info;
+
+/*
+ * gbcg_solve_async -- gbcg_solve enqueued on `stream` without synchronising:
+ * the solve runs as one persistent launch (precisions GBCG_FP64, either
+ * variant, and GBCG_FP32_RU; the refinement GBCG_FP32_IR steers its passes
+ * from the host and is rejected with GBCG_ERR_INVALID), and a one-thread
+ * kernel then writes the result to `dinfo`.  No host read, no event, no
+ * allocation: the call can be captured into a CUDA graph and replayed, the
+ * handle's workspace being reused by every replay (one solve of a handle in
+ * flight at a time).
+ *
+ *   b, x   device pointers to n doubles (not checked: host pointers are the
+ *          caller's error); x holds x0 on entry and the last iterate after
+ *          the stream reaches the solve's end
+ *   dinfo  device pointer to one gbcg_device_info, written at the end
+ *   tol, maxit, opts  as for gbcg_solve
+ *
+ * Returns GBCG_OK once the work is enqueued, GBCG_ERR_INVALID for a bad
+ * argument, GBCG_ERR_CUDA if a launch fails; the solve's own status arrives
+ * in dinfo->status.
+ */
+int gbcg_solve_async(gbcg_matrix_t A, const double* b, double* x, double tol, int32_t maxit,
+                     const gbcg_opts* opts, gbcg_device_info* dinfo, void* stream);
+
 /*
  * gbcg_update_values -- replace the values of a handle, same pattern.  `val`
  * holds nnz doubles in the order of the arrays given to gbcg_create (memory:

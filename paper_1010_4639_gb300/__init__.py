@@ -232,6 +232,37 @@ class Matrix:
             raise GbcgError(rc, "gbcg_solve", _lib.last_error())
         return x, res
 
+    def solve_async(self, b, x, dinfo, tol: float = 1e-10, maxit: int = 0, precision: str = "fp64",
+                    inner_tol: float = 0.0, wait_timeout_ms: int = 1000, max_restarts: int = 3,
+                    variant: str = "standard", stream=None):
+        """``gbcg_solve_async``: the solve enqueued on ``stream`` with no host
+        synchronisation (capturable into a CUDA graph).  ``b``, ``x``: float64
+        CUDA tensors of length n (x holds x0); ``dinfo``: a CUDA uint8 tensor
+        of ``DEVICE_INFO_BYTES`` that receives the result (read it with
+        ``device_info``).  Precisions "fp64" and "fp32_ru"."""
+        torch = _torch()
+        _check_vec(b, torch.float64, self.n, "b")
+        _check_vec(x, torch.float64, self.n, "x")
+        if not (dinfo.is_cuda and dinfo.dtype == torch.uint8 and dinfo.numel() >= _lib.DEVICE_INFO_BYTES
+                and dinfo.is_contiguous() and dinfo.data_ptr() % 8 == 0):
+            raise ValueError(f"dinfo must be a contiguous, 8-byte aligned CUDA uint8 tensor of "
+                             f"{_lib.DEVICE_INFO_BYTES} bytes")
+        opts = _lib.Opts(PRECISIONS[precision], 0, float(inner_tol), int(wait_timeout_ms), int(max_restarts),
+                         VARIANTS[variant], 0)
+        _lib.check(self._lib.gbcg_solve_async(self._h, ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()),
+                                              float(tol), int(maxit), ctypes.byref(opts),
+                                              ctypes.c_void_p(dinfo.data_ptr()), _stream_handle(stream)),
+                   "gbcg_solve_async")
+        return x
+
+
+def device_info(dinfo) -> SolveInfo:
+    """Decodes the result ``Matrix.solve_async`` wrote (copies 32 bytes to the host)."""
+    raw = bytes(dinfo[:_lib.DEVICE_INFO_BYTES].cpu().numpy().tobytes())
+    status, iterations, outer, _ = np.frombuffer(raw[:16], dtype=np.int32)
+    rec, true = np.frombuffer(raw[16:32], dtype=np.float64)
+    return SolveInfo(int(iterations), int(outer), _lib.STATUS_NAMES[int(status)], float(rec), float(true), 0.0)
+
 
 BATCH_INFO_DTYPE = np.dtype([("iterations", np.int32), ("outer", np.int32), ("status", np.int32),
                              ("pad_", np.int32), ("rel_res_true", np.float64)])

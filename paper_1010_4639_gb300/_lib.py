@@ -19,7 +19,7 @@ GBCG_STANDARD, GBCG_PIPELINED = 0, 1
 STATUS_NAMES = ["OK", "INVALID", "NOT_SPD", "MAXIT", "NONFINITE", "TIMEOUT", "CUDA", "NOMEM"]
 
 # Every entry point declared in include/gbcg.h.
-EXPORTS = ["gbcg_create", "gbcg_destroy", "gbcg_spmv", "gbcg_spmv_f32", "gbcg_solve", "gbcg_stats",
+EXPORTS = ["gbcg_create", "gbcg_destroy", "gbcg_spmv", "gbcg_spmv_f32", "gbcg_solve", "gbcg_solve_async", "gbcg_stats",
            "gbcg_status_string", "gbcg_last_error", "gbcg_selftest_wait_timeout", "gbcg_solve_csr_static",
            "gbcg_batch_create", "gbcg_batch_destroy", "gbcg_batch_autotune", "gbcg_batch_set_tuning",
            "gbcg_batch_solve", "gbcg_batch_instance_times", "gbcg_batch_stats",
@@ -32,6 +32,10 @@ class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("max_outer", ctypes.c_int32), ("inner_tol", ctypes.c_double),
                 ("wait_timeout_ms", ctypes.c_int32), ("max_restarts", ctypes.c_int32), ("variant", ctypes.c_int32),
                 ("pad_", ctypes.c_int32)]
+
+
+# gbcg_device_info, the device-resident result of gbcg_solve_async (32 bytes)
+DEVICE_INFO_BYTES = 32
 
 
 class Info(ctypes.Structure):
@@ -106,6 +110,7 @@ def load(path: str = LIB_PATH):
     lib.gbcg_spmv.argtypes = [vp, vp, vp, vp]
     lib.gbcg_spmv_f32.argtypes = [vp, vp, vp, vp]
     lib.gbcg_solve.argtypes = [vp, vp, vp, d, i32, ctypes.POINTER(Opts), ctypes.POINTER(Info), vp]
+    lib.gbcg_solve_async.argtypes = [vp, vp, vp, d, i32, ctypes.POINTER(Opts), vp, vp]
     lib.gbcg_stats.argtypes = [vp, ctypes.POINTER(Stats)]
     lib.gbcg_status_string.argtypes = [ctypes.c_int]
     lib.gbcg_status_string.restype = ctypes.c_char_p

@@ -366,6 +366,29 @@ cudaError_t launch_product_fmt(const gbcg_matrix_s* M, const V* x, const V* b, V
   }
 }
 
+// The device-side half of gbcg_solve_async: the solver state as the fields
+// of gbcg_info (status mapped as status_from_device maps it on the host).
+__global__ void k_export_info(const CgState* st, const GridBar* gb, gbcg_device_info* out, int ru) {
+  int status;
+  if (gb->status != 0) {
+    status = GBCG_ERR_TIMEOUT;
+  } else {
+    switch (st->status) {
+      case kOk: status = GBCG_OK; break;
+      case kNotSpd: status = GBCG_ERR_NOT_SPD; break;
+      case kMaxit: status = GBCG_ERR_MAXIT; break;
+      case kNonfinite: status = GBCG_ERR_NONFINITE; break;
+      default: status = GBCG_ERR_TIMEOUT; break;
+    }
+  }
+  out->status = status;
+  out->iterations = st->k;
+  out->outer = st->restarts;
+  out->pad_ = 0;
+  out->rel_res_true = st->nb > 0 ? st->rel_true : 0.0;
+  out->rel_res_recursive = ru ? st->rel_true : (st->nb > 0 ? sqrt(st->rr) / st->nb : 0.0);
+}
+
 int status_from_device(const CgState& st, const GridBar& gb) {
   if (gb.status != 0) return GBCG_ERR_TIMEOUT;
   switch (st.status) {
@@ -413,17 +436,23 @@ int read_state(gbcg_matrix_s* M, cudaStream_t s) {
   return 0;
 }
 
+// Enqueues the double-precision persistent solve (either variant): the
+// barrier reset and the launch, bracketed by the handle's events when timed.
+cudaError_t enqueue_fp64(gbcg_matrix_s* M, const double* b, double* x, double tol, int maxit, const gbcg_opts* o,
+                         bool timed, cudaStream_t s) {
+  const int max_restarts = (o && o->max_restarts > 0) ? o->max_restarts : 3;
+  cudaError_t e = cudaMemsetAsync(M->bar, 0, sizeof(GridBar), s);
+  if (e != cudaSuccess) return e;
+  CgArgs<double> a = make_args<double>(M, x, M->r, M->p, M->q, b, tol, maxit, max_restarts, timeout_ns_of(o));
+  if (timed && (e = cudaEventRecord(M->ev0, s)) != cudaSuccess) return e;
+  e = (o && o->variant == GBCG_PIPELINED) ? launch_pcg_fmt(M, a, s) : launch_cg_fmt<double, true>(M, a, s);
+  if (e != cudaSuccess) return e;
+  return timed ? cudaEventRecord(M->ev1, s) : cudaSuccess;
+}
+
 int solve_fp64(gbcg_matrix_s* M, const double* b, double* x, double tol, int maxit, const gbcg_opts* o,
                gbcg_info* info, cudaStream_t s) {
-  const int max_restarts = (o && o->max_restarts > 0) ? o->max_restarts : 3;
-  CUDA_TRY(cudaMemsetAsync(M->bar, 0, sizeof(GridBar), s));
-  CgArgs<double> a = make_args<double>(M, x, M->r, M->p, M->q, b, tol, maxit, max_restarts, timeout_ns_of(o));
-  CUDA_TRY(cudaEventRecord(M->ev0, s));
-  if (o && o->variant == GBCG_PIPELINED)
-    CUDA_TRY(launch_pcg_fmt(M, a, s));
-  else
-    CUDA_TRY(launch_cg_fmt<double, true>(M, a, s));
-  CUDA_TRY(cudaEventRecord(M->ev1, s));
+  CUDA_TRY(enqueue_fp64(M, b, x, tol, maxit, o, true, s));
   if (int rc = read_state(M, s)) return rc;
   float kms = 0.f;
   CUDA_TRY(cudaEventElapsedTime(&kms, M->ev0, M->ev1));
@@ -445,9 +474,10 @@ int solve_fp64(gbcg_matrix_s* M, const double* b, double* x, double tol, int max
 
 // Single-precision iterations with double-precision reliable updates: one
 // persistent launch, on any layout.
-int solve_ru(gbcg_matrix_s* M, const double* b, double* x, double tol, int maxit, const gbcg_opts* o,
-             gbcg_info* info, cudaStream_t s) {
-  CUDA_TRY(cudaMemsetAsync(M->bar, 0, sizeof(GridBar), s));
+cudaError_t enqueue_ru(gbcg_matrix_s* M, const double* b, double* x, double tol, int maxit, const gbcg_opts* o,
+                       bool timed, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(M->bar, 0, sizeof(GridBar), s);
+  if (e != cudaSuccess) return e;
   RuArgs a;
   a.c = make_args<float>(M, M->d32, M->r32, M->p32, M->q32, nullptr, tol, maxit, 0, timeout_ns_of(o));
   a.A64 = M->op<double>();
@@ -456,11 +486,17 @@ int solve_ru(gbcg_matrix_s* M, const double* b, double* x, double tol, int maxit
   a.b64 = b;
   a.q64 = M->q;
   a.delta = (o && o->inner_tol > 0.0 && o->inner_tol < 1.0) ? o->inner_tol : 0.1;
-  CUDA_TRY(cudaEventRecord(M->ev0, s));
-  CUDA_TRY(M->mode == kTiles  ? launch_ru<kTiles>(a, M->grid, s)
-           : M->mode == kPlan ? launch_ru<kPlan>(a, M->grid, s)
-                              : launch_ru<kGather>(a, M->grid, s));
-  CUDA_TRY(cudaEventRecord(M->ev1, s));
+  if (timed && (e = cudaEventRecord(M->ev0, s)) != cudaSuccess) return e;
+  e = M->mode == kTiles  ? launch_ru<kTiles>(a, M->grid, s)
+      : M->mode == kPlan ? launch_ru<kPlan>(a, M->grid, s)
+                         : launch_ru<kGather>(a, M->grid, s);
+  if (e != cudaSuccess) return e;
+  return timed ? cudaEventRecord(M->ev1, s) : cudaSuccess;
+}
+
+int solve_ru(gbcg_matrix_s* M, const double* b, double* x, double tol, int maxit, const gbcg_opts* o,
+             gbcg_info* info, cudaStream_t s) {
+  CUDA_TRY(enqueue_ru(M, b, x, tol, maxit, o, true, s));
   if (int rc = read_state(M, s)) return rc;
   float kms = 0.f;
   CUDA_TRY(cudaEventElapsedTime(&kms, M->ev0, M->ev1));
@@ -764,14 +800,10 @@ int gbcg_spmv_f32(gbcg_matrix_t A, const float* x, float* y, void* stream) {
   return spmv_any<float>(A, x, y, (cudaStream_t)stream);
 }
 
-int gbcg_solve(gbcg_matrix_t A, const double* b, double* x, double tol, int32_t maxit, const gbcg_opts* opts,
-               gbcg_info* info, void* stream) {
-  g_last_error.clear();
-  gbcg_info local;
-  if (!info) info = &local;
-  memset(info, 0, sizeof(*info));
-  if (!A) return fail(GBCG_ERR_INVALID, "null matrix handle");
-  if (!(tol >= 0.0) || !std::isfinite(tol)) return fail(GBCG_ERR_INVALID, "tol must be finite and >= 0");
+namespace {
+
+// The combinations of precision, variant and layout a solve accepts.
+int check_solve_opts(const gbcg_matrix_s* A, const gbcg_opts* opts) {
   if (opts && (opts->precision != GBCG_FP64 && opts->precision != GBCG_FP32_IR && opts->precision != GBCG_FP32_RU))
     return fail(GBCG_ERR_INVALID, "unknown precision");
   if (opts && opts->precision == GBCG_FP32_RU && opts->variant == GBCG_PIPELINED)
@@ -786,6 +818,20 @@ int gbcg_solve(gbcg_matrix_t A, const double* b, double* x, double tol, int32_t 
     return fail(GBCG_ERR_INVALID,
                 "the single-reduction variant runs on row-gather layouts (CSR, CSC, or symmetric storage with "
                 "GBCG_SYM_LAYOUT=plan); the tiled symmetric product needs a barrier of its own");
+  return GBCG_OK;
+}
+
+}  // namespace
+
+int gbcg_solve(gbcg_matrix_t A, const double* b, double* x, double tol, int32_t maxit, const gbcg_opts* opts,
+               gbcg_info* info, void* stream) {
+  g_last_error.clear();
+  gbcg_info local;
+  if (!info) info = &local;
+  memset(info, 0, sizeof(*info));
+  if (!A) return fail(GBCG_ERR_INVALID, "null matrix handle");
+  if (!(tol >= 0.0) || !std::isfinite(tol)) return fail(GBCG_ERR_INVALID, "tol must be finite and >= 0");
+  if (int rc = check_solve_opts(A, opts)) return rc;
   const auto t0 = std::chrono::steady_clock::now();
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t n = A->n;
@@ -819,6 +865,30 @@ int gbcg_solve(gbcg_matrix_t A, const double* b, double* x, double tol, int32_t 
   }
   info->ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   return status;
+}
+
+int gbcg_solve_async(gbcg_matrix_t A, const double* b, double* x, double tol, int32_t maxit, const gbcg_opts* opts,
+                     gbcg_device_info* dinfo, void* stream) {
+  g_last_error.clear();
+  if (!A) return fail(GBCG_ERR_INVALID, "null matrix handle");
+  if (!dinfo) return fail(GBCG_ERR_INVALID, "null device info");
+  if (!(tol >= 0.0) || !std::isfinite(tol)) return fail(GBCG_ERR_INVALID, "tol must be finite and >= 0");
+  if (int rc = check_solve_opts(A, opts)) return rc;
+  if (opts && opts->precision == GBCG_FP32_IR)
+    return fail(GBCG_ERR_INVALID, "the refinement steers its passes from the host: no asynchronous form");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t n = A->n;
+  if (n == 0) {
+    CUDA_TRY(cudaMemsetAsync(dinfo, 0, sizeof(gbcg_device_info), s));  // GBCG_OK, nothing to do
+    return GBCG_OK;
+  }
+  if (!b || !x) return fail(GBCG_ERR_INVALID, "null vector");
+  if (maxit <= 0) maxit = (int32_t)std::min<int64_t>(n, 0x7fffffff);
+  const bool ru = opts && opts->precision == GBCG_FP32_RU;
+  CUDA_TRY(ru ? enqueue_ru(A, b, x, tol, maxit, opts, false, s) : enqueue_fp64(A, b, x, tol, maxit, opts, false, s));
+  k_export_info<<<1, 1, 0, s>>>(A->st, A->bar, dinfo, ru ? 1 : 0);
+  CUDA_TRY(cudaGetLastError());
+  return GBCG_OK;
 }
 
 int gbcg_stats(gbcg_matrix_t A, gbcg_matrix_stats* out) {
