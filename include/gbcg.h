@@ -151,6 +151,10 @@ typedef struct {
  *              GBCG_SYM_CSR_UPPER every idx of row i is >= i.  Symmetry of a
  *              full CSR/CSC input is the caller's promise (it is what CG
  *              needs); the products themselves are exact for any matrix.
+ *              Debug mode: with the environment variable
+ *              GBCG_CHECK_SYMMETRY=1 the call checks it (entry (i, j) equal
+ *              to (j, i) bit for bit, O(nnz) host work) and returns
+ *              GBCG_ERR_INVALID naming the first asymmetric entry.
  *   index_base 0 or 1 (the paper's kernel indexes from 1)
  *   memory     gbcg_memory: where ptr/idx/val live
  *   stream     used for the uploads

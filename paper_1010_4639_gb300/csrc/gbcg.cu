@@ -641,6 +641,10 @@ int gbcg_create(gbcg_matrix_t* out, int32_t format, int64_t n, int64_t nnz, cons
   std::string err;
   int rc = build_layout(format, n, nnz, ptr, idx, val, index_base, L, err);
   if (rc) return fail(rc, err);
+  // debug mode: full CSR/CSC inputs must be symmetric (CG's premise)
+  if (format != GBCG_SYM_CSR_UPPER && env_int("GBCG_CHECK_SYMMETRY", 0) != 0 &&
+      (rc = check_symmetry(n, nnz, ptr, idx, val, index_base, err)) != 0)
+    return fail(rc, err);
 
   gbcg_matrix_s* M = new gbcg_matrix_s();
   M->format = format;

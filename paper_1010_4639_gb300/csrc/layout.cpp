@@ -169,6 +169,43 @@ void slice_rows(int64_t n, const Rows& R, bool allow_long, SellHost& S) {
 
 }  // namespace
 
+int check_symmetry(int64_t n, int64_t nnz, const int32_t* ptr, const int32_t* idx, const double* val,
+                   int32_t base, std::string& err) {
+  // transpose by a counting sort: column c's entries, in increasing row order
+  std::vector<int64_t> tp(n + 1, 0);
+  for (int64_t k = 0; k < nnz; ++k) ++tp[(int64_t)idx[k] - base + 1];
+  for (int64_t c = 0; c < n; ++c) tp[c + 1] += tp[c];
+  std::vector<int64_t> fill(tp.begin(), tp.end() - 1);
+  std::vector<int32_t> trow(nnz);
+  std::vector<double> tval(nnz);
+  for (int64_t r = 0; r < n; ++r)
+    for (int64_t k = (int64_t)ptr[r] - base; k < (int64_t)ptr[r + 1] - base; ++k) {
+      const int64_t c = (int64_t)idx[k] - base, q = fill[c]++;
+      trow[q] = (int32_t)r;
+      tval[q] = val[k];
+    }
+  // row r of the input must equal column r, entry by entry (both sorted)
+  char buf[160];
+  for (int64_t r = 0; r < n; ++r) {
+    const int64_t k0 = (int64_t)ptr[r] - base, k1 = (int64_t)ptr[r + 1] - base;
+    if (k1 - k0 != tp[r + 1] - tp[r]) {
+      snprintf(buf, sizeof buf, "not symmetric: row %lld has %lld entries, column %lld has %lld", (long long)r,
+               (long long)(k1 - k0), (long long)r, (long long)(tp[r + 1] - tp[r]));
+      err = buf;
+      return kErrInvalid;
+    }
+    for (int64_t k = k0, q = tp[r]; k < k1; ++k, ++q) {
+      const int64_t c = (int64_t)idx[k] - base;
+      if (c != trow[q] || !(val[k] == tval[q])) {
+        snprintf(buf, sizeof buf, "not symmetric at entry (%lld, %lld)", (long long)r, (long long)c);
+        err = buf;
+        return kErrInvalid;
+      }
+    }
+  }
+  return 0;
+}
+
 int build_layout(int32_t format, int64_t n, int64_t nnz, const int32_t* ptr, const int32_t* idx,
                  const double* val, int32_t base, LayoutHost& out, std::string& err) {
   int rc = validate(format, n, nnz, ptr, idx, val, base, err);

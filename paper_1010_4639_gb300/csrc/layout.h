@@ -102,6 +102,13 @@ struct LayoutHost {
 int build_layout(int32_t format, int64_t n, int64_t nnz, const int32_t* ptr, const int32_t* idx,
                  const double* val, int32_t index_base, LayoutHost& out, std::string& err);
 
+// Checks that a full CSR or CSC input (validated) is exactly symmetric,
+// pattern and values: entry (i, j) equals entry (j, i) bit for bit.  O(nnz + n)
+// host work (a counting-sort transpose).  Returns 0, or kErrInvalid with the
+// first asymmetric entry in `err`.
+int check_symmetry(int64_t n, int64_t nnz, const int32_t* ptr, const int32_t* idx, const double* val,
+                   int32_t index_base, std::string& err);
+
 // Builds the tiled symmetric layout for `ctas` CTAs, with at most
 // `slot_cap` slots and `ent_cap` padded entries per tile.  Returns false
 // (layout left empty) when a single slice already exceeds a cap.

@@ -216,3 +216,26 @@ def test_one_shot_product_many_slices_per_warp(torch, ctas, monkeypatch):
                 y32 = A.spmv_f32(torch.from_numpy(x32).cuda()).cpu().numpy().astype(np.float64)
             check(y32, oracle.spmv_f32(fmt, arrs[0], arrs[1], v32, x32).astype(np.float64),
                   oracle.abs_spmv(fmt, arrs[0], arrs[1], v32.astype(np.float64), x32.astype(np.float64)), TOL32)
+
+
+def test_symmetry_check_in_debug_mode(torch, monkeypatch):
+    """GBCG_CHECK_SYMMETRY=1: full CSR/CSC input must be symmetric, pattern
+    and values bit for bit; off by default (the products are exact for any
+    matrix)."""
+    s = fem(5, 6, 7)
+    ptr, idx, val = random_general(60, 60, 0.1, 3)
+    with gb.Matrix("csr", ptr, idx, val):
+        pass
+    monkeypatch.setenv("GBCG_CHECK_SYMMETRY", "1")
+    with gb.Matrix("csr", s.ptr, s.idx, s.val):
+        pass
+    with gb.Matrix("csc", *s.csc()):
+        pass
+    rows = np.repeat(np.arange(s.n), np.diff(s.ptr))
+    k = int(np.nonzero(s.idx != rows)[0][0])  # an off-diagonal entry
+    v = s.val.copy()
+    v[k] = np.nextafter(v[k], np.inf)
+    with pytest.raises(gb.GbcgError, match=f"not symmetric at entry \\({rows[k]}, {s.idx[k]}\\)"):
+        gb.Matrix("csr", s.ptr, s.idx, v)
+    with pytest.raises(gb.GbcgError, match="not symmetric"):
+        gb.Matrix("csr", ptr, idx, val)
