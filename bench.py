@@ -28,6 +28,7 @@ import signal
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -127,7 +128,10 @@ class ClockSampler:
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        # the raw samples (the JSON line carries their summary); GBCG_CLOCKS_DIR
+        # keeps them somewhere else than the temporary directory
+        self.path = os.path.join(os.environ.get("GBCG_CLOCKS_DIR", tempfile.gettempdir()),
+                                 f"gbcg_clocks_rank{gpu_index}.csv")
 
     def __enter__(self):
         try:
