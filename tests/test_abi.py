@@ -101,3 +101,40 @@ def test_python_binding_fails_loudly_without_library(tmp_path):
             _lib.load(str(tmp_path / "missing.so"))
         finally:
             _lib._lib = saved
+
+
+def test_device_info_layout_and_decoder():
+    """gbcg_device_info is 32 bytes (status, iterations, outer, pad, then the
+    two residuals) and device_info() reads it field by field."""
+    import struct
+
+    import torch
+
+    import paper_1010_4639_gb300 as gb
+    assert _lib.DEVICE_INFO_BYTES == struct.calcsize("<iiiidd")
+    raw = struct.pack("<iiiidd", 2, 17, 3, 0, 1.5e-3, 2.5e-11)
+    info = gb.device_info(torch.frombuffer(bytearray(raw), dtype=torch.uint8))
+    assert (info.status, info.iterations, info.outer) == ("NOT_SPD", 17, 3)
+    assert info.rel_res_recursive == 1.5e-3 and info.rel_res_true == 2.5e-11
+
+
+def test_solve_async_rejects_bad_arguments_without_a_gpu(lib):
+    # argument checks run before any device work
+    assert lib.gbcg_solve_async(None, None, None, 1e-10, 0, None, None, None) == 1
+    assert b"null matrix handle" in lib.gbcg_last_error()
+
+
+def test_both_bench_arms_share_the_workload_config():
+    import argparse
+
+    import bench
+    import femgen
+    g = femgen.PAPER_SIZE
+    s = femgen.build_system(g)
+    for fmt in ("csr", "sym", "csc"):
+        args = argparse.Namespace(format=fmt, precision="fp32_ru")
+        c = bench.workload_config(g, s, args, 1)
+        assert c["n"] == s.n and c["nnz"] == s.nnz
+        assert c["nnz_stored"] == (s.upper()[1].shape[0] if fmt == "sym" else s.nnz)
+        assert f"{fmt} storage, fp32_ru, tol 1e-10" in c["workload"]
+        assert c["l2"].startswith("matrix fits L2")
