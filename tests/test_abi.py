@@ -138,3 +138,37 @@ def test_both_bench_arms_share_the_workload_config():
         assert c["nnz_stored"] == (s.upper()[1].shape[0] if fmt == "sym" else s.nnz)
         assert f"{fmt} storage, fp32_ru, tol 1e-10" in c["workload"]
         assert c["l2"].startswith("matrix fits L2")
+
+
+def test_header_is_plain_c_and_links(tmp_path):
+    """include/gbcg.h compiles as C99 with warnings as errors, and a C program
+    that calls the boundary links against the library (no GPU call is made:
+    only argument checks run)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "use.c"
+    src.write_text(r'''
+#include <stdio.h>
+#include <string.h>
+#include "gbcg.h"
+int main(void) {
+  gbcg_matrix_t A = NULL;
+  gbcg_info info;
+  gbcg_device_info* dinfo = NULL;
+  int rc = gbcg_solve(A, NULL, NULL, 1e-10, 0, NULL, &info, NULL);
+  int rc2 = gbcg_solve_async(A, NULL, NULL, 1e-10, 0, NULL, dinfo, NULL);
+  printf("%d %d %s\n", rc, rc2, gbcg_status_string(rc));
+  return (rc == GBCG_ERR_INVALID && rc2 == GBCG_ERR_INVALID) ? 0 : 1;
+}
+''')
+    inc = os.path.join(os.path.dirname(__file__), "..", "include")
+    libdir = os.path.dirname(_lib.LIB_PATH)
+    exe = tmp_path / "use"
+    subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-I", inc, str(src), "-L", libdir, "-lgbcg",
+                    f"-Wl,-rpath,{libdir}", "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert out.returncode == 0, out.stdout + out.stderr
+    assert out.stdout.split()[2] == "GBCG_ERR_INVALID"
