@@ -7,11 +7,14 @@
 // values and column indices into shared memory with a bulk asynchronous copy
 // (cp.async.bulk, completion on an mbarrier, L2 evict-first policy) while it
 // computes the current one, so the number of bytes in flight does not depend
-// on how many warps are resident.  The symmetric format adds the transpose
-// half U' x as a second gather through the transpose plan, reading U's values
-// in place (the paper used a separate scatter kernel with atomics; here every
-// output element is summed by one lane in a fixed order, so results are
-// bitwise reproducible).
+// on how many warps are resident.  The symmetric format is computed by
+// CTA-cooperative tiles (a producer warp streams tile stages; the transpose
+// half U' x is an FMA gather over shared memory through a 16-bit transpose
+// index, and sums leaving a tile are added after a grid barrier), or, as a
+// fallback, as a second row gather through a transpose plan that reads U's
+// values in place.  The paper used a separate scatter kernel with atomics;
+// here every output element is summed in a fixed order, so results are
+// bitwise reproducible.
 //
 // CG iteration (Section III listing): one persistent cooperative launch per
 // solve.  Each CTA owns a contiguous range of slices (and so of rows); per
@@ -20,7 +23,9 @@
 //   B: alpha = r'r / p'q; x += alpha p; r -= alpha q; partial r'r -> barrier
 //   C: beta = r_k'r_k / r_{k-1}'r_{k-1}; p = r + beta p           -> barrier
 // The partial sums of all CTAs are added by every CTA in the same fixed
-// order, so every CTA takes the same decisions.  Every wait (grid barrier,
+// order, so every CTA takes the same decisions; the step's scalars (alpha,
+// beta, the stopping tests) are formed once per CTA by thread 0 and
+// broadcast through shared memory (GB300's FP64 pipe runs at 1/64 rate).  Every wait (grid barrier,
 // mbarrier) is bounded by a global-timer limit; on expiry the CTA records
 // GBCG_ERR_TIMEOUT and leaves at the next barrier, so nothing can hang.
 #pragma once
