@@ -33,7 +33,13 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
 _SO = os.path.join(_HERE, "_oracle.so")
+# The same source compiled with -fopenmp: a separate library whose CG loops
+# run on several host threads and give the single-threaded library's bits
+# (oracle.c, "multi-threaded build").  Used for the timed CPU baseline on every
+# host core and for the large reference solves of tests/golden.
+_SO_OMP = os.path.join(_HERE, "_oracle_omp.so")
 _lib = None
+_lib_omp = None
 
 CSR, SYM_UPPER, CSC = 0, 1, 2
 FORMATS = {"csr": CSR, "sym": SYM_UPPER, "sym_upper": SYM_UPPER, "csc": CSC}
@@ -52,16 +58,34 @@ class History(ctypes.Structure):
                 ("alpha", ctypes.c_void_p), ("beta", ctypes.c_void_p)]
 
 
-def compile_oracle(src: str = _SRC, dst: str = _SO) -> str:
+def compile_oracle(src: str = _SRC, dst: str = _SO, openmp: bool = False) -> str:
     subprocess.run(["gcc", "-O2", "-fPIC", "-shared", "-ffp-contract=off", "-std=c11",
-                    src, "-o", dst, "-lm"], check=True)
+                    *(["-fopenmp"] if openmp else []), src, "-o", dst, "-lm"], check=True)
     return dst
 
 
 def build() -> str:
-    if not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
-        compile_oracle()
+    """Compiles both builds of the oracle (single- and multi-threaded)."""
+    for so, omp in ((_SO, False), (_SO_OMP, True)):
+        if not os.path.exists(so) or os.path.getmtime(so) < os.path.getmtime(_SRC):
+            compile_oracle(dst=so, openmp=omp)
     return _SO
+
+
+def load_threaded(threads: int | None = None):
+    """The multi-threaded build (same bits as ``load()``'s); ``threads``
+    sets its thread count (default: every host core)."""
+    global _lib_omp
+    if _lib_omp is None:
+        build()
+        _lib_omp = load(_SO_OMP)
+    _lib_omp.orc_set_threads(int(threads or os.cpu_count() or 1))
+    return _lib_omp
+
+
+def threads(lib=None) -> int:
+    """Threads the given build runs its CG loops on (1 for the plain build)."""
+    return int((lib or load()).orc_threads())
 
 
 def load(path: str | None = None):
@@ -96,6 +120,8 @@ def load(path: str | None = None):
                                      ctypes.POINTER(Info), ctypes.POINTER(History)]
     lib.orc_element_grad.argtypes = [i64, i32, vp, vp, vp, vp]
     lib.orc_assemble.argtypes = [i64, vp, vp, vp, vp, vp]
+    lib.orc_threads.restype = i32
+    lib.orc_set_threads.argtypes = [i32]
     if path is None:
         _lib = lib
     return lib

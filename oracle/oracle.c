@@ -44,6 +44,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 enum { ORC_OK = 0, ORC_INVALID = 1, ORC_NOT_SPD = 2, ORC_MAXIT = 3, ORC_NONFINITE = 4 };
 enum { ORC_CSR = 0, ORC_SYM_UPPER = 1, ORC_CSC = 2 };
@@ -174,6 +177,180 @@ static float dot_f(int64_t n, const float* a, const float* b) {
 
 float orc_dot_f32(int64_t n, const float* a, const float* b) { return dot_f(n, a, b); }
 
+/* ------------------------------------------------ multi-threaded build --- */
+/* The same file compiled with -fopenmp gives a second, separate library (the
+ * oracle timed on every host core, and the way its large reference solves
+ * are computed).  That build must give the single-threaded build's bits:
+ *   - element-wise vector loops run their elements on several threads (each
+ *     element is computed exactly as before);
+ *   - the double-precision dot product stays one left-to-right sum;
+ *   - the single-precision pairwise dot computes the subtrees of its top
+ *     levels on several threads and adds them in the tree's own order;
+ *   - the symmetric and column-storage products run output by output: y_j
+ *     adds the terms that the row-order loop of orc_spmv_sym_upper (or the
+ *     column-order loop of orc_spmv_csc) adds to y_j, in the same order --
+ *     transpose terms a_ij x_i by increasing source i, then (symmetric) the
+ *     entries of row j in storage order -- through an index of those terms
+ *     built once per solve.
+ * Without -fopenmp every pragma below is ignored and the products are the
+ * plain loops above. */
+int32_t orc_threads(void) {
+#ifdef _OPENMP
+  return (int32_t)omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+void orc_set_threads(int32_t t) {
+#ifdef _OPENMP
+  if (t > 0) omp_set_num_threads((int)t);
+#else
+  (void)t;
+#endif
+}
+
+/* Operand of the CG loops: the matrix in its storage format, its float
+ * values when the loop needs them, and (multi-threaded build, symmetric or
+ * column storage) the index of the terms each output receives from other
+ * rows: for output j, tk[tptr[j] .. tptr[j+1]) are the storage positions k
+ * of the entries aimed at j, by increasing source row (column for CSC), and
+ * ts[] those sources. */
+typedef struct {
+  int fmt;
+  int64_t n;
+  const int32_t* ptr;
+  const int32_t* idx;
+  const double* val;
+  const float* val32;
+  int64_t* tptr;
+  int64_t* tk;
+  int32_t* ts;
+} orc_op;
+
+static void op_init(orc_op* A, int fmt, int64_t n, const int32_t* ptr, const int32_t* idx, const double* val,
+                    const float* val32) {
+  A->fmt = fmt;
+  A->n = n;
+  A->ptr = ptr;
+  A->idx = idx;
+  A->val = val;
+  A->val32 = val32;
+  A->tptr = NULL;
+  A->tk = NULL;
+  A->ts = NULL;
+#ifdef _OPENMP
+  if (fmt == ORC_CSR || n <= 0) return;
+  /* counting sort of the terms by output, sources visited in increasing order */
+  int64_t* tptr = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t k = ptr[i]; k < ptr[i + 1]; ++k)
+      if (fmt == ORC_CSC || idx[k] > i) ++tptr[idx[k] + 1];
+  for (int64_t j = 0; j < n; ++j) tptr[j + 1] += tptr[j];
+  int64_t* fill = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);
+  memcpy(fill, tptr, sizeof(int64_t) * (size_t)n);
+  int64_t* tk = (int64_t*)malloc(sizeof(int64_t) * (size_t)(tptr[n] ? tptr[n] : 1));
+  int32_t* ts = (int32_t*)malloc(sizeof(int32_t) * (size_t)(tptr[n] ? tptr[n] : 1));
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t k = ptr[i]; k < ptr[i + 1]; ++k)
+      if (fmt == ORC_CSC || idx[k] > i) {
+        const int64_t at = fill[idx[k]]++;
+        tk[at] = k;
+        ts[at] = (int32_t)i;
+      }
+  free(fill);
+  A->tptr = tptr;
+  A->tk = tk;
+  A->ts = ts;
+#endif
+}
+
+static void op_free(orc_op* A) {
+  free(A->tptr);
+  free(A->tk);
+  free(A->ts);
+}
+
+/* y = A x in double precision (orc_spmv's arithmetic, see above). */
+static void op_spmv(const orc_op* A, const double* x, double* y) {
+#ifdef _OPENMP
+  const int64_t n = A->n;
+  if (A->fmt == ORC_CSR) {
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+      double s = 0.0;
+      for (int64_t k = A->ptr[i]; k < A->ptr[i + 1]; ++k) s += A->val[A->idx ? k : k] * x[A->idx[k]];
+      y[i] = s;
+    }
+    return;
+  }
+#pragma omp parallel for schedule(static)
+  for (int64_t j = 0; j < n; ++j) {
+    double s = 0.0;
+    for (int64_t t = A->tptr[j]; t < A->tptr[j + 1]; ++t) s += A->val[A->tk[t]] * x[A->ts[t]];
+    if (A->fmt == ORC_SYM_UPPER)
+      for (int64_t k = A->ptr[j]; k < A->ptr[j + 1]; ++k) s += A->val[k] * x[A->idx[k]];
+    y[j] = s;
+  }
+#else
+  orc_spmv(A->fmt, A->n, A->ptr, A->idx, A->val, x, y);
+#endif
+}
+
+/* y = A32 x in single precision (orc_spmv_f32's arithmetic). */
+static void op_spmv_f32(const orc_op* A, const float* x, float* y) {
+#ifdef _OPENMP
+  const int64_t n = A->n;
+  if (A->fmt == ORC_CSR) {
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+      float s = 0.0f;
+      for (int64_t k = A->ptr[i]; k < A->ptr[i + 1]; ++k) s += A->val32[k] * x[A->idx[k]];
+      y[i] = s;
+    }
+    return;
+  }
+#pragma omp parallel for schedule(static)
+  for (int64_t j = 0; j < n; ++j) {
+    float s = 0.0f;
+    for (int64_t t = A->tptr[j]; t < A->tptr[j + 1]; ++t) s += A->val32[A->tk[t]] * x[A->ts[t]];
+    if (A->fmt == ORC_SYM_UPPER)
+      for (int64_t k = A->ptr[j]; k < A->ptr[j + 1]; ++k) s += A->val32[k] * x[A->idx[k]];
+    y[j] = s;
+  }
+#else
+  orc_spmv_f32(A->fmt, A->n, A->ptr, A->idx, A->val32, x, y);
+#endif
+}
+
+/* dot_f with the subtrees of its top levels summed on several threads and
+ * combined in the tree's order (the same bits as dot_f). */
+static float dotf(int64_t n, const float* a, const float* b) {
+#ifdef _OPENMP
+  enum { DEPTH = 6, LEAVES = 1 << DEPTH };
+  if (n >= ((int64_t)1 << 16)) {
+    int64_t off[LEAVES], len[LEAVES];
+    off[0] = 0;
+    len[0] = n;
+    for (int d = 0, cnt = 1; d < DEPTH; ++d, cnt *= 2)
+      for (int u = cnt - 1; u >= 0; --u) {  /* node u splits into 2u, 2u + 1 as dot_f halves it */
+        const int64_t o = off[u], m = len[u], h = m / 2;
+        off[2 * u] = o;
+        len[2 * u] = h;
+        off[2 * u + 1] = o + h;
+        len[2 * u + 1] = m - h;
+      }
+    float part[LEAVES];
+#pragma omp parallel for schedule(static)
+    for (int u = 0; u < LEAVES; ++u) part[u] = dot_f(len[u], a + off[u], b + off[u]);
+    for (int cnt = LEAVES / 2; cnt >= 1; cnt /= 2)
+      for (int u = 0; u < cnt; ++u) part[u] = part[2 * u] + part[2 * u + 1];
+    return part[0];
+  }
+#endif
+  return dot_f(n, a, b);
+}
+
 /* ------------------------------------------------ conjugate gradient ----- */
 /* History buffers (may be NULL): for k = 0..hist_cap-1 the search direction
  * p_k and the iterate x_{k+1}, n values each; alpha/beta per iteration. */
@@ -197,6 +374,8 @@ int orc_cg(int fmt, int64_t n, const int32_t* ptr, const int32_t* idx, const dou
   double* p = (double*)malloc(sizeof(double) * (size_t)(n ? n : 1));
   double* q = (double*)malloc(sizeof(double) * (size_t)(n ? n : 1));
   if (hist) hist->count = 0;
+  orc_op A;
+  op_init(&A, fmt, n, ptr, idx, val, NULL);
   int status = ORC_OK;
   int32_t k = 0, restarts = 0;
   double nb = sqrt(orc_dot(n, b, b));
@@ -206,18 +385,22 @@ int orc_cg(int fmt, int64_t n, const int32_t* ptr, const int32_t* idx, const dou
     goto done;
   }
   /* reading 1: r0 = b - A x0, p0 = r0 */
-  orc_spmv(fmt, n, ptr, idx, val, x, q);
+  op_spmv(&A, x, q);
+#pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < n; ++i) r[i] = b[i] - q[i];
+#pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < n; ++i) p[i] = r[i];
   rr = orc_dot(n, r, r);
   for (;;) {
     while (k < maxit && !(sqrt(rr) / nb <= tol)) {
-      orc_spmv(fmt, n, ptr, idx, val, p, q);         /* A p */
+      op_spmv(&A, p, q);                             /* A p */
       double pq = orc_dot(n, p, q);                  /* p' A p */
       if (!isfinite(pq)) { status = ORC_NONFINITE; goto done; }
       if (!(pq > 0.0)) { status = ORC_NOT_SPD; goto done; }
       double alpha = rr / pq;                        /* alpha = r'r / p'Ap */
+#pragma omp parallel for schedule(static)
       for (int64_t i = 0; i < n; ++i) x[i] += alpha * p[i];   /* x += alpha p */
+#pragma omp parallel for schedule(static)
       for (int64_t i = 0; i < n; ++i) r[i] -= alpha * q[i];   /* r -= alpha A p */
       double rr_new = orc_dot(n, r, r);
       ++k;
@@ -232,10 +415,12 @@ int orc_cg(int fmt, int64_t n, const int32_t* ptr, const int32_t* idx, const dou
       rr = rr_new;
       if (!isfinite(rr)) { status = ORC_NONFINITE; goto done; }
       if (sqrt(rr) / nb <= tol) break;               /* reading 2: test after the r update */
+#pragma omp parallel for schedule(static)
       for (int64_t i = 0; i < n; ++i) p[i] = r[i] + beta * p[i];  /* p = r + beta p */
     }
     /* reading 2: confirm with the true residual; restart from it otherwise */
-    orc_spmv(fmt, n, ptr, idx, val, x, q);
+    op_spmv(&A, x, q);
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) r[i] = b[i] - q[i];
     double rt = orc_dot(n, r, r);
     info->rel_res_true = sqrt(rt) / nb;
@@ -252,6 +437,7 @@ done:
   info->rel_res_recursive = nb > 0.0 ? sqrt(rr) / nb : 0.0;
   if (status != ORC_OK && status != ORC_MAXIT) info->rel_res_true = NAN;
   if (nb == 0.0) info->rel_res_true = 0.0;
+  op_free(&A);
   free(r);
   free(p);
   free(q);
@@ -523,6 +709,8 @@ int orc_cg_ru(int fmt, int64_t n, const int32_t* ptr, const int32_t* idx, const 
   float* d = (float*)malloc(sizeof(float) * nn);
   double* r64 = (double*)malloc(sizeof(double) * nn);
   for (int64_t k = 0; k < nnz; ++k) v32[k] = (float)val[k];
+  orc_op A;
+  op_init(&A, fmt, n, ptr, idx, val, v32);
   int status = ORC_MAXIT;
   int32_t k = 0, updates = 0;
   const double nb = sqrt(orc_dot(n, b, b));
@@ -534,46 +722,54 @@ int orc_cg_ru(int fmt, int64_t n, const int32_t* ptr, const int32_t* idx, const 
     goto done;
   }
   /* the double-precision residual, replacing the single-precision one */
-  orc_spmv(fmt, n, ptr, idx, val, x, r64);
+  op_spmv(&A, x, r64);
+#pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < n; ++i) r64[i] = b[i] - r64[i];
   rel = sqrt(orc_dot(n, r64, r64)) / nb;
   if (!isfinite(rel)) { status = ORC_NONFINITE; goto done; }
   if (rel <= tol) { status = ORC_OK; goto done; }
+#pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < n; ++i) {
     r[i] = (float)r64[i];
     p[i] = r[i];
     d[i] = 0.0f;
   }
-  rr = dot_f(n, r, r);
+  rr = dotf(n, r, r);
   rmax = sqrtf(rr);
   while (k < maxit) {
-    orc_spmv_f32(fmt, n, ptr, idx, v32, p, q);                     /* A32 p */
-    const float pq = dot_f(n, p, q);
+    op_spmv_f32(&A, p, q);                                          /* A32 p */
+    const float pq = dotf(n, p, q);
     if (!isfinite(pq)) { status = ORC_NONFINITE; break; }
     if (!(pq > 0.0f)) { status = ORC_NOT_SPD; break; }
     const float alpha = rr / pq;
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) d[i] += alpha * p[i];           /* correction */
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) r[i] -= alpha * q[i];
-    float rr_new = dot_f(n, r, r);
+    float rr_new = dotf(n, r, r);
     ++k;
     if (sqrtf(rr_new) < (float)delta * rmax || sqrtf(rr_new) <= (float)(tol * nb) || k >= maxit) {
       /* reliable update: x += d in double, r = b - A x in double */
+#pragma omp parallel for schedule(static)
       for (int64_t i = 0; i < n; ++i) {
         x[i] += (double)d[i];
         d[i] = 0.0f;
       }
-      orc_spmv(fmt, n, ptr, idx, val, x, r64);
+      op_spmv(&A, x, r64);
+#pragma omp parallel for schedule(static)
       for (int64_t i = 0; i < n; ++i) r64[i] = b[i] - r64[i];
       rel = sqrt(orc_dot(n, r64, r64)) / nb;
       ++updates;
       if (!isfinite(rel)) { status = ORC_NONFINITE; break; }
       if (rel <= tol) { status = ORC_OK; break; }
+#pragma omp parallel for schedule(static)
       for (int64_t i = 0; i < n; ++i) r[i] = (float)r64[i];
-      rr_new = dot_f(n, r, r);
+      rr_new = dotf(n, r, r);
       rmax = sqrtf(rr_new);
     }
     const float beta = rr_new / rr;
     rr = rr_new;
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) p[i] = r[i] + beta * p[i];
   }
 done:
@@ -586,6 +782,7 @@ done:
   info->status = status;
   info->rel_res_true = rel;
   info->rel_res_recursive = rel;
+  op_free(&A);
   free(v32);
   free(r);
   free(p);
