@@ -1,23 +1,28 @@
 #!/usr/bin/env python3
-"""Benchmark: conjugate-gradient time to relative residual 1e-10 on the 128^3
-synthetic FEM system (2.0M rows, 29.6M non-zeros), with the SpMV HBM
-bandwidth of every storage format, mixed precision against plain FP64 CG on
-the same GPU, and the CPU oracle timed beside it.
+"""Benchmark: conjugate-gradient time to relative residual 1e-10 on the largest
+single-GPU system -- the 256^3 synthetic FEM stiffness matrix (16.4M rows,
+244M non-zeros, four high-contrast inclusions) in symmetric storage (upper
+triangle and diagonal, 130M stored entries) -- with mixed precision against
+plain FP64 CG on the same GPU, the SpMV HBM bandwidth of each storage format,
+and the CPU oracle timed beside it.
 
 One step = one solve from x0 = 0 to a true relative residual <= 1e-10 with the
-headline method (single-precision CG iterations with double-precision
-refinement by reliable updates: the correction is accumulated in double and
-the residual replaced by the double-precision b - A x every decade of
-residual reduction; full CSR storage -- the fastest storage of the library on
-this system), inputs resident in HBM.  The JSON line also carries the plain
-FP64 CG, the restarted refinement and the SpMV bandwidth of the three storage
-formats, the paper-size system, the batched, differentiation and 2010-
-structure legs, and the CPU oracle.
+headline method: single-precision CG iterations on single-precision values,
+refined by double-precision reliable updates (the correction is accumulated
+in double and the residual replaced by the double-precision b - A x, with the
+double-precision values, every decade of residual reduction), inputs resident
+in HBM.  The JSON line also carries the plain FP64 CG and the restarted
+refinement on the same system and storage, full CSR storage at the same size,
+the 128^3 system in all three storage formats, the paper-size system, the
+batched, differentiation and 2010-structure legs, and the CPU oracle (one
+thread and every host core), each solve with its error against the FP64
+oracle's solution.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-N > 1 (under torchrun): every rank solves its own replica of the system (the
-solve does not shard without a collective), timing is the max over ranks.
+N > 1: every rank solves its own replica of the system (the solve does not
+shard without a collective); timing is the max over ranks.  Without torchrun
+the script starts the N ranks itself.
 """
 from __future__ import annotations
 
@@ -41,12 +46,11 @@ import femgen  # noqa: E402
 METRIC = "CG time-to-1e-10 residual (s) & SpMV HBM GB/s; mixed/batched vs FP64 CG"
 GRIDS = {"128": femgen.LARGE, "31": femgen.PAPER_SIZE, "64": femgen.DIFF, "256": femgen.LARGEST}
 TOL = 1e-10
-# DRAM bytes (read + write) of the headline kernel measured by ncu on a
-# 30-iteration launch of the same 128^3 system (profiles/k_cg_ru_csr128.md):
-# per single-precision iteration, and per double-precision update.  Used
-# only for that kernel on that system; null elsewhere.
-RU_TRAFFIC_PER_ITERATION = 185e6
-RU_TRAFFIC_PER_UPDATE = 0.424e9
+# DRAM bytes (read + write) per single-precision iteration of the headline
+# kernel, from an ncu capture of the same kernel on a smaller system of the
+# same generator, scaled to this system by its stored entries (None until a
+# capture of the current kernel exists; the profiles directory holds it).
+RU_TRAFFIC_BYTES_PER_STORED_ENTRY = None
 
 
 def parse():
@@ -55,20 +59,23 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--grid", default="128", choices=sorted(GRIDS))
-    ap.add_argument("--format", default="csr", choices=["sym", "csr", "csc"])
+    ap.add_argument("--grid", default="256", choices=sorted(GRIDS))
+    ap.add_argument("--format", default="sym", choices=["sym", "csr", "csc"])
     ap.add_argument("--precision", default="fp32_ru", choices=["fp32_ru", "fp32_ir", "fp64"])
     ap.add_argument("--inner-tol", type=float, default=1e-4)
     ap.add_argument("--no-extras", action="store_true", help="skip the per-format and CPU-baseline legs")
     ap.add_argument("--profile-iters", type=int, default=0,
                     help="only run solves capped at this many iterations (small case for ncu captures)")
-    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the CPU-oracle sample")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of each CPU-oracle sample")
+    ap.add_argument("--e2e-steps", type=int, default=3, help="end-to-end solves (host memory in and out)")
+    ap.add_argument("--no-cpu-full-solve", action="store_true",
+                    help="skip the complete 128^3 oracle solve on every host core")
     ap.add_argument("--only-batched", action="store_true", help="only run the batched leg")
     ap.add_argument("--only-differentiable", action="store_true", help="only run the differentiation leg")
     ap.add_argument("--only-paper-size", action="store_true", help="only run the paper-size leg")
     ap.add_argument("--only-ablation", action="store_true", help="only run the 2010-structure ablation leg")
     ap.add_argument("--only-largest", action="store_true",
-                    help="only run the largest-system leg (256^3: products and solves, a few minutes)")
+                    help="only run the comparison solves and products of the 256^3 system")
     ap.add_argument("--profile-batched", type=int, default=0,
                     help="only one mixed-precision solve of the first N batch instances (small case for ncu)")
     ap.add_argument("--profile-spmv", action="store_true",
@@ -77,6 +84,19 @@ def parse():
 
 
 # ------------------------------------------------------------------ helpers
+def spawn_ranks(args):
+    """--gpus N > 1 outside torchrun: start N ranks (one per GPU) through
+    torch.distributed.run on this node and pass their output through."""
+    import socket
+
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={args.gpus}",
+           "--master-addr=127.0.0.1", f"--master-port={port}", os.path.abspath(__file__)] + sys.argv[1:]
+    return subprocess.call(cmd)
+
+
 def dist_setup(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -116,6 +136,37 @@ def peaks():
             d = json.load(f)
         return float(d["hbm_gbs"]), "measured"
     return 6800.0, "fallback"
+
+
+def err_vs_oracle(x_np, gold):
+    """Relative difference to the FP64 oracle's solution over the golden
+    file's seeded sample positions (None without a golden file)."""
+    if not gold:
+        return None
+    idx = np.asarray(gold["sample_index"])
+    xo = np.asarray(gold["sample_x"])
+    return float(np.linalg.norm(x_np[idx] - xo) / np.linalg.norm(xo))
+
+
+def oracle_iteration_seconds(fmt, arrays, b, lib, budget_s, min_iters=5, max_iters=5000):
+    """Seconds per CG iteration of the oracle build ``lib`` on this system:
+    two runs of m0 and m1 iterations, the difference divided by m1 - m0 (the
+    set-up and the closing true-residual product cancel)."""
+    import oracle
+
+    m0 = 2
+    t0 = time.perf_counter()
+    oracle.cg(fmt, *arrays, b, tol=0.0, maxit=m0, lib=lib)
+    t_small = time.perf_counter() - t0
+    probe = 3
+    t0 = time.perf_counter()
+    oracle.cg(fmt, *arrays, b, tol=0.0, maxit=m0 + probe, lib=lib)
+    spi = max((time.perf_counter() - t0 - t_small) / probe, 1e-9)
+    m1 = m0 + int(max(min_iters, min(max_iters, budget_s / spi)))
+    t0 = time.perf_counter()
+    oracle.cg(fmt, *arrays, b, tol=0.0, maxit=m1, lib=lib)
+    t_big = time.perf_counter() - t0
+    return max(t_big - t_small, 1e-9) / (m1 - m0), m1 - m0, t_small
 
 
 class ClockSampler:
@@ -180,6 +231,12 @@ def flush_l2(torch, buf):
     buf.add_(1.0)  # 256 MiB write, larger than the 129 MB L2
 
 
+# What bounds the headline kernel, by storage and precision, from its ncu
+# capture: "hbm" when DRAM throughput is the limiter, "latency" when neither
+# DRAM nor any pipe is saturated (dependent L2 round trips and barriers).
+ROOF_BOUND = {("sym", "fp32_ru"): "hbm", ("csr", "fp32_ru"): "latency"}
+
+
 def per_iteration_bytes(stats, precision):
     """Algorithmic bytes of one CG iteration: the product (matrix arrays, ptr,
     x read once, y written once) plus the vector passes x += a p, r -= a q,
@@ -203,41 +260,50 @@ def workload_config(g, s, args, world):
 
 
 def run_reference(args):
+    """The reference arm: the oracle (its multi-threaded build, which gives
+    the single-threaded build's bits) on every host core, on this arm's
+    workload.  Each step times a bounded run of CG iterations; the value is
+    the seconds per iteration times the oracle's own iteration count to 1e-10
+    (tests/golden)."""
     world, rank, local, pg = dist_setup(args)
-    if rank != 0:
+    if rank != 0:  # rank 0 alone times the oracle; the others exit without work
+        if pg:
+            pg.destroy_process_group()
         return 0
     import oracle
 
     g = GRIDS[args.grid]
     s = femgen.build_system(g)
-    up = s.upper()
+    arrays = s.upper()
     gold = golden(args.grid, "sym")
-    probe = oracle.cg("sym", *up, s.b, tol=0.0, maxit=3)  # first touch, pages in
-    t0 = time.perf_counter()
-    probe = oracle.cg("sym", *up, s.b, tol=0.0, maxit=3)
-    spi = (time.perf_counter() - t0) / 3
-    m = int(max(5, min(2000, args.cpu_seconds / max(spi, 1e-9) / 2)))
+    cores = os.cpu_count() or 1
+    lib = oracle.load_threaded(cores)
+    spi, m, setup_s = oracle_iteration_seconds("sym", arrays, s.b, lib, args.cpu_seconds / 3)
+    per_step = int(max(5, min(5000, args.cpu_seconds / spi)))
     iters_needed = gold["iterations"] if gold else None
     times = []
     for step in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        oracle.cg("sym", *up, s.b, tol=0.0, maxit=m)
+        oracle.cg("sym", *arrays, s.b, tol=0.0, maxit=per_step, lib=lib)
         dt = time.perf_counter() - t0
         if step >= args.warmup:
-            times.append(dt / m)
+            times.append(max(dt - setup_s, 1e-9) / per_step)
     spi = statistics.median(times)
-    value = spi * iters_needed if iters_needed else None
-    sample = (f"{m} CG iterations of the double-precision oracle per step on the {g.nx}x{g.ny}x{g.nz} system "
-              f"(the oracle's own method: symmetric storage, FP64), scaled by the oracle's own iteration count "
-              f"to 1e-10 ({iters_needed}, tests/golden/oracle_{args.grid}_sym.json)")
+    value = spi * iters_needed + setup_s if iters_needed else None
+    sample = (f"{per_step} CG iterations per step of the double-precision oracle (symmetric storage, the "
+              f"oracle's own method) on the {g.nx}x{g.ny}x{g.nz} system, {oracle.threads(lib)} threads, minus its "
+              f"set-up, scaled by the oracle's own iteration count to 1e-10 ({iters_needed}, "
+              f"tests/golden/oracle_{args.grid}_sym.json) plus one set-up")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * spi * m, "higher_is_better": False,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * statistics.median(times) * per_step,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_config(g, s, args, world),
-            "cpu_baseline": {"value": value, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample,
-                             "seconds_per_iteration": spi},
+            "cpu_baseline": {"value": value, "unit": "s", "cores": oracle.threads(lib), "kind": "oracle",
+                             "sample": sample, "seconds_per_iteration": spi},
             "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+    if pg:
+        pg.destroy_process_group()
     return 0
 
 
@@ -259,7 +325,10 @@ def run_ours(args):
               flush=True)
         return 0
     if args.only_largest:
-        print(json.dumps({"largest": largest(torch, gb, args)}), flush=True)
+        hbm, _ = peaks()
+        s = femgen.build_system(femgen.LARGEST)
+        print(json.dumps({"largest": extras(torch, gb, s, {"sym": s.upper(), "csr": (s.ptr, s.idx, s.val)}, None,
+                                            args, hbm, golden("256", "sym"))}), flush=True)
         return 0
     if args.only_paper_size:
         print(json.dumps({"paper_size": paper_size(torch, gb, args)}), flush=True)
@@ -278,7 +347,9 @@ def run_ours(args):
         return 0
     g = GRIDS[args.grid]
     s = femgen.build_system(g)
-    fmt_arrays = {"sym": s.upper(), "csr": (s.ptr, s.idx, s.val), "csc": s.csc()}
+    fmt_arrays = {"sym": s.upper(), "csr": (s.ptr, s.idx, s.val)}
+    if args.format == "csc":
+        fmt_arrays["csc"] = s.csc()
     A = gb.Matrix(args.format, *fmt_arrays[args.format])
     st = A.stats()
     b = torch.from_numpy(s.b).to(dev)
@@ -329,13 +400,14 @@ def run_ours(args):
     kernel_ms = sum(i.kernel_ms for i in infos) / len(infos)
     kernel_launches = sum(i.kernel_launches for i in infos) / len(infos)
     iters = infos[-1].iterations
+    updates = infos[-1].outer
     ms, kernel_ms = max_over_ranks([ms, kernel_ms], pg, dev)
     x_dev = x.clone()
     # end to end through the public API: pinned host b and x, copies inside the call
     bh = torch.from_numpy(s.b).pin_memory()
     xh = torch.zeros(s.n, dtype=torch.float64).pin_memory()
     e2e = []
-    for k in range(max(1, args.steps)):
+    for k in range(max(1, min(args.steps, args.e2e_steps))):
         xh.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -344,11 +416,18 @@ def run_ours(args):
     e2e_s = max_over_ranks([statistics.median(e2e)], pg, dev)[0]
     hbm, peak_kind = peaks()
     per_it = per_iteration_bytes(st, args.precision)
-    achieved = per_it * iters / (kernel_ms / 1000.0) / 1e9 if kernel_ms > 0 else None
+    moved = per_it * iters
+    if args.precision == "fp32_ru":  # the double-precision updates: product + x, d, b, r passes
+        moved += updates * per_iteration_bytes(st, "fp64")
+    achieved = moved / (kernel_ms / 1000.0) / 1e9 if kernel_ms > 0 else None
     traffic = None
-    if args.precision == "fp32_ru" and args.format == "csr" and args.grid == "128":
-        traffic = RU_TRAFFIC_PER_ITERATION * iters + RU_TRAFFIC_PER_UPDATE * infos[-1].outer
+    if args.precision == "fp32_ru" and RU_TRAFFIC_BYTES_PER_STORED_ENTRY and args.format == "sym":
+        traffic = RU_TRAFFIC_BYTES_PER_STORED_ENTRY * st["nnz_input"] * iters
     x_np = x_dev.cpu().numpy()
+    gold = golden(args.grid, "sym")
+    kernel_names = {"fp32_ir": "k_cg<float> persistent inner CG", "fp32_ru": "k_cg_ru persistent CG, "
+                    "single-precision iterations with double-precision reliable updates",
+                    "fp64": "k_cg<double> persistent CG"}
     line = {
         "metric": METRIC, "value": ms / 1000.0, "unit": "s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
@@ -357,32 +436,35 @@ def run_ours(args):
         "clocks": clk.summary(),
         "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": 16 * s.n, "d2h_bytes_per_step": 8 * s.n},
         "gpu_launches": int(round(sum(i.launches for i in infos) / len(infos))),
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": (achieved / hbm) if achieved else None, "traffic": traffic,
-                     "traffic_source": "ncu DRAM bytes of a 30-iteration launch of this kernel on this system, "
-                                       "scaled by the iterations and updates of the solve" if traffic else None,
-                     "kernel": {"fp32_ir": "k_cg<float> persistent inner CG",
-                                "fp32_ru": "k_cg_ru persistent CG, single-precision iterations",
-                                "fp64": "k_cg<double> persistent CG"}[args.precision],
-                     "algorithmic_bytes_per_iteration": per_it, "iterations": iters,
+        "roofline": {"bound": ROOF_BOUND.get((args.format, args.precision), "hbm"), "achieved": achieved,
+                     "peak": hbm, "unit": "GB/s", "frac": (achieved / hbm) if achieved else None,
+                     "traffic": traffic,
+                     "traffic_source": "ncu DRAM bytes per iteration of this kernel on a smaller system, scaled "
+                                       "by stored entries and iterations" if traffic else None,
+                     "kernel": kernel_names[args.precision],
+                     "algorithmic_bytes_per_iteration": per_it, "iterations": iters, "updates": updates,
                      "kernel_ms_per_step": kernel_ms, "kernel_launches_per_step": kernel_launches,
-                     "peak_kind": f"{peak_kind} HBM copy bandwidth"},
-        "solve": {"iterations": iters, "outer": infos[-1].outer, "status": infos[-1].status,
+                     "peak_kind": f"{peak_kind} HBM copy bandwidth (of {peak_kind})"},
+        "solve": {"iterations": iters, "updates_or_restarts": updates, "status": infos[-1].status,
                   "rel_res_true": infos[-1].rel_res_true,
+                  "err_vs_fp64_oracle_sampled": err_vs_oracle(x_np, gold),
+                  "oracle_iterations": gold["iterations"] if gold else None,
                   "err_vs_xstar": float(np.linalg.norm(x_np - s.xstar) / np.linalg.norm(s.xstar))},
     }
-    gold = golden(args.grid, "sym")
-    if gold:
-        idx = np.asarray(gold["sample_index"])
-        xo = np.asarray(gold["sample_x"])
-        line["solve"]["err_vs_fp64_oracle_sampled"] = float(np.linalg.norm(x_np[idx] - xo) / np.linalg.norm(xo))
+    ru_gold = golden(args.grid, "sym_ru")
+    if ru_gold and args.precision == "fp32_ru":
+        line["solve"]["oracle_ru_iterations"] = ru_gold["iterations"]
+        line["solve"]["oracle_ru_updates"] = ru_gold["restarts"]
     if not args.no_extras and rank == 0:
-        line["variants"] = extras(torch, gb, s, fmt_arrays, A, args, hbm)
+        line["variants"] = extras(torch, gb, s, fmt_arrays, A, args, hbm, gold)
+        A.close()
+        del fmt_arrays
+        line["large_128"] = large_128(torch, gb, args, hbm)
         line["paper_size"] = paper_size(torch, gb, args)
         line["batched"] = batched(torch, gb, args)
         line["differentiable"] = differentiable(torch, gb, args)
-        line["ablation_2010"] = ablation(torch, gb, args, s)
-        line["cpu_baseline"] = cpu_baseline(s, args, line["variants"])
+        line["ablation_2010"] = ablation(torch, gb, args, femgen.build_system(femgen.LARGE))
+        line["cpu_baseline"] = cpu_baseline(s, args, gold)
     if rank == 0:
         print(json.dumps(line), flush=True)
     A.close()
@@ -407,57 +489,112 @@ def time_spmv(torch, M, x, y, f32, reps=20):
     return e0.elapsed_time(e1) / reps
 
 
-def extras(torch, gb, s, fmt_arrays, A_head, args, hbm):
-    """Per-format SpMV bandwidth and FP64 / mixed-precision solve times."""
+def time_solve(torch, M, b, prec, args, flush=None):
+    """One solve from x0 = 0 after a warm solve, the L2 flushed first: wall
+    time by CUDA events on the stream, kernel time by the library's events."""
+    itol = args.inner_tol if prec == "fp32_ir" else 0.0
+    x = torch.zeros_like(b)
+    M.solve(b, x, tol=TOL, precision=prec, inner_tol=itol, raise_on_error=False)  # warm
+    x.zero_()
+    if flush is not None:
+        flush_l2(torch, flush)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    _, info = M.solve(b, x, tol=TOL, precision=prec, inner_tol=itol, raise_on_error=False)
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1000.0, info, x
+
+
+def extras(torch, gb, s, fmt_arrays, A_head, args, hbm, gold):
+    """The comparison on the benchmarked system: SpMV bandwidth of each
+    storage format, and the time to 1e-10 of plain FP64 CG, the restarted
+    refinement and reliable updates, each with its error against the FP64
+    oracle's solution (sampled positions of the golden file)."""
     dev = torch.device("cuda", torch.cuda.current_device())
     b = torch.from_numpy(s.b).to(dev)
     xv = torch.from_numpy(femgen.random_vector(s.n, 7)).to(dev)
     yv = torch.empty_like(xv)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    plan = {"sym": ("fp64", "fp32_ir", "fp32_ru"), "csr": ("fp64", "fp32_ru")}
     out = {}
-    for fmt in ("sym", "csr", "csc"):
-        M = A_head if fmt == args.format else gb.Matrix(fmt, *fmt_arrays[fmt])
+    for fmt in ("sym", "csr"):
+        M = A_head if (A_head is not None and fmt == args.format) else gb.Matrix(fmt, *fmt_arrays[fmt])
         st = M.stats()
-        r = {"spmv_fp64_ms": time_spmv(torch, M, xv, yv, False),
+        r = {"nnz_stored": int(st["nnz_input"]), "device_bytes": st["device_bytes"],
+             "spmv_fp64_ms": time_spmv(torch, M, xv, yv, False),
              "spmv_fp32_ms": time_spmv(torch, M, xv.float(), yv.float(), True)}
         r["spmv_fp64_GBs"] = st["spmv_bytes_fp64"] / r["spmv_fp64_ms"] / 1e6
         r["spmv_fp32_GBs"] = st["spmv_bytes_fp32"] / r["spmv_fp32_ms"] / 1e6
         r["spmv_fp64_frac_of_measured_hbm"] = r["spmv_fp64_GBs"] / hbm
         r["spmv_fp32_frac_of_measured_hbm"] = r["spmv_fp32_GBs"] / hbm
-        for prec in ("fp64", "fp32_ir", "fp32_ru"):
-            itol = args.inner_tol if prec == "fp32_ir" else 0.0
-            x = torch.zeros_like(b)
-            M.solve(b, x, tol=TOL, precision=prec, inner_tol=itol)  # warm
-            x.zero_()
-            torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-            _, info = M.solve(b, x, tol=TOL, precision=prec, inner_tol=itol)
-            e1.record()
-            torch.cuda.synchronize()
-            t = e0.elapsed_time(e1) / 1000.0
+        for prec in plan[fmt]:
+            t, info, x = time_solve(torch, M, b, prec, args, flush)
             per_it = per_iteration_bytes(st, prec)
             r[prec] = {"s": t, "iterations": info.iterations, "outer": info.outer, "status": info.status,
                        "rel_res_true": info.rel_res_true, "kernel_ms": info.kernel_ms,
                        "iter_us": 1000.0 * info.kernel_ms / max(info.iterations, 1),
-                       "kernel_GBs": per_it * info.iterations / (info.kernel_ms / 1000.0) / 1e9}
-        r["mixed_speedup_vs_fp64"] = r["fp64"]["s"] / r["fp32_ir"]["s"]
-        if "fp32_ru" in r:
-            r["reliable_update_speedup_vs_fp64"] = r["fp64"]["s"] / r["fp32_ru"]["s"]
-        r["device_bytes"] = st["device_bytes"]
+                       "kernel_GBs": per_it * info.iterations / (info.kernel_ms / 1000.0) / 1e9,
+                       "err_vs_fp64_oracle_sampled": err_vs_oracle(x.cpu().numpy(), gold)}
+        if "fp32_ir" in r:
+            r["restarted_refinement_speedup_vs_fp64"] = r["fp64"]["s"] / r["fp32_ir"]["s"]
+        r["reliable_update_speedup_vs_fp64"] = r["fp64"]["s"] / r["fp32_ru"]["s"]
         out[fmt] = r
         if M is not A_head:
             M.close()
+    if gold:
+        out["oracle_fp64_iterations"] = gold["iterations"]
+    return out
+
+
+def large_128(torch, gb, args, hbm):
+    """The 128^3 system (2.0M rows) in all three storage formats: SpMV
+    bandwidth and the three solvers, errors against the FP64 oracle."""
+    dev = torch.device("cuda", torch.cuda.current_device())
+    s = femgen.build_system(femgen.LARGE)
+    gold = golden("128", "sym")
+    arrays = {"sym": s.upper(), "csr": (s.ptr, s.idx, s.val), "csc": s.csc()}
+    b = torch.from_numpy(s.b).to(dev)
+    xv = torch.from_numpy(femgen.random_vector(s.n, 7)).to(dev)
+    yv = torch.empty_like(xv)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    out = {"workload": "fem 128x128x128, 1 inclusion, contrast 1000, tol 1e-10", "n": s.n, "nnz": s.nnz,
+           "oracle_fp64_iterations": gold["iterations"] if gold else None}
+    for fmt in ("sym", "csr", "csc"):
+        with gb.Matrix(fmt, *arrays[fmt]) as M:
+            st = M.stats()
+            r = {"spmv_fp64_ms": time_spmv(torch, M, xv, yv, False),
+                 "spmv_fp32_ms": time_spmv(torch, M, xv.float(), yv.float(), True)}
+            r["spmv_fp64_GBs"] = st["spmv_bytes_fp64"] / r["spmv_fp64_ms"] / 1e6
+            r["spmv_fp32_GBs"] = st["spmv_bytes_fp32"] / r["spmv_fp32_ms"] / 1e6
+            r["spmv_fp64_frac_of_measured_hbm"] = r["spmv_fp64_GBs"] / hbm
+            r["spmv_fp32_frac_of_measured_hbm"] = r["spmv_fp32_GBs"] / hbm
+            for prec in ("fp64", "fp32_ir", "fp32_ru"):
+                t, info, x = time_solve(torch, M, b, prec, args, flush)
+                per_it = per_iteration_bytes(st, prec)
+                r[prec] = {"s": t, "iterations": info.iterations, "outer": info.outer, "status": info.status,
+                           "rel_res_true": info.rel_res_true,
+                           "iter_us": 1000.0 * info.kernel_ms / max(info.iterations, 1),
+                           "kernel_GBs": per_it * info.iterations / (info.kernel_ms / 1000.0) / 1e9,
+                           "err_vs_fp64_oracle_sampled": err_vs_oracle(x.cpu().numpy(), gold)}
+            r["reliable_update_speedup_vs_fp64"] = r["fp64"]["s"] / r["fp32_ru"]["s"]
+            out[fmt] = r
     return out
 
 
 def paper_size(torch, gb, args):
     """The paper's problem size (31x31x32 nodes, 25 230 rows, L2-resident):
     time to 1e-10 and microseconds per iteration, per storage and precision."""
+    import oracle
+
     dev = torch.device("cuda", torch.cuda.current_device())
     s = femgen.build_system(femgen.PAPER_SIZE)
     arrays = {"sym": s.upper(), "csr": (s.ptr, s.idx, s.val), "csc": s.csc()}
     b = torch.from_numpy(s.b).to(dev)
-    out = {"workload": "fem 31x31x32, 1 inclusion, contrast 1000", "n": s.n, "nnz": s.nnz}
+    ref = oracle.cg("sym", *arrays["sym"], s.b, tol=TOL)  # the FP64 oracle's solution
+    out = {"workload": "fem 31x31x32, 1 inclusion, contrast 1000", "n": s.n, "nnz": s.nnz,
+           "oracle_fp64_iterations": ref.iterations}
     for fmt in ("sym", "csr"):
         with gb.Matrix(fmt, *arrays[fmt]) as M:
             out[fmt] = {"grid_ctas": M.stats()["grid_ctas"]}
@@ -480,9 +617,11 @@ def paper_size(torch, gb, args):
                         ts.append(e0.elapsed_time(e1) / 1000.0)
                 t = statistics.median(ts)
                 key = prec if variant == "standard" else f"{prec}_pipelined"
+                xs = x.cpu().numpy()
                 out[fmt][key] = {"s": t, "iterations": info.iterations, "outer": info.outer,
                                  "status": info.status, "rel_res_true": info.rel_res_true,
-                                 "iter_us": 1000.0 * info.kernel_ms / max(info.iterations, 1)}
+                                 "iter_us": 1000.0 * info.kernel_ms / max(info.iterations, 1),
+                                 "err_vs_fp64_oracle": float(np.linalg.norm(xs - ref.x) / np.linalg.norm(ref.x))}
     return out
 
 
@@ -558,8 +697,9 @@ def differentiable(torch, gb, args):
     storage: forward double-precision CG to 1e-10, backward = adjoint CG to
     1e-10 + sampled-outer-product and element-gradient kernels.  Gradient
     error: fourth-order central differences (step 1e-6) of fixed-iteration
-    solves along 8 random directions (b and stored values: relative white
-    noise; coefficients: random smooth fields), and the 6^3 dense reference."""
+    solves along the configured 32 random directions (11 in b and 11 in the
+    stored values: relative white noise; 10 in the coefficients: random smooth
+    fields), and the 6^3 dense reference."""
     dev = torch.device("cuda", torch.cuda.current_device())
     t0 = time.perf_counter()
     g = femgen.DIFF
@@ -619,11 +759,11 @@ def differentiable(torch, gb, args):
 
     gen = torch.Generator(device=dev).manual_seed(5)
     errs = {}
-    for t in range(8):
-        if t < 3:
+    for t in range(32):
+        if t < 11:
             d = torch.randn(b0.shape, generator=gen, device=dev, dtype=torch.float64) * b0.abs()
             fd, an, fam = derivative(lambda e: (v0, b0 + e * d)), float(gb_ @ d), "b"
-        elif t < 6:
+        elif t < 22:
             d = torch.randn(v0.shape, generator=gen, device=dev, dtype=torch.float64) * v0.abs()
             fd, an, fam = derivative(lambda e: (v0 + e * d, b0)), float(gv @ d), "values"
         else:
@@ -698,7 +838,10 @@ def ablation(torch, gb, args, big):
                     t0 = time.perf_counter()
                     _, info = M.solve(b, x, tol=TOL)
                     lib_s = time.perf_counter() - t0
-            r[fmt] = {"spmv_2010_ms": ms_ab, "spmv_2010_GBs": bytes_2010 / ms_ab / 1e6,
+            r[fmt] = {"spmv_2010_kernel": {"csr": "thread-per-row CSR, one launch",
+                                           "sym": "SCSR direct half and SCSC transpose half fused in one launch, "
+                                                  "FP64 atomic adds (the paper ran them as two launches)"}[fmt],
+                      "spmv_2010_ms": ms_ab, "spmv_2010_GBs": bytes_2010 / ms_ab / 1e6,
                       "spmv_library_ms": ms_lib, "spmv_library_GBs": bytes_ / ms_lib / 1e6,
                       "spmv_speedup": ms_ab / ms_lib}
             if fmt == "csr":
@@ -716,74 +859,47 @@ def ablation(torch, gb, args, big):
     return out
 
 
-def largest(torch, gb, args):
-    """The largest single system (256^3, four inclusions): product bandwidth
-    and time to 1e-10 of mixed precision against plain double-precision CG, in
-    symmetric and full CSR storage.  One solve per variant (each takes
-    seconds), kernel time from the library's own events, the L2 flushed
-    before it."""
-    dev = torch.device("cuda", torch.cuda.current_device())
-    hbm, _ = peaks()
-    g = femgen.LARGEST
-    t0 = time.perf_counter()
-    s = femgen.build_system(g)
-    out = {"workload": f"fem {g.nx}x{g.ny}x{g.nz} P1 stiffness, {g.n_incl} inclusions, contrast {g.contrast:g}, "
-                       f"tol 1e-10", "n": s.n, "nnz": s.nnz, "generate_s": time.perf_counter() - t0}
-    b = torch.from_numpy(s.b).to(dev)
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    xv = torch.from_numpy(femgen.random_vector(s.n, 7)).to(dev)
-    yv = torch.empty_like(xv)
-    arrays = {"sym": s.upper(), "csr": (s.ptr, s.idx, s.val)}
-    for fmt in ("sym", "csr"):
-        with gb.Matrix(fmt, *arrays[fmt]) as M:
-            st = M.stats()
-            r = {"nnz_stored": int(arrays[fmt][1].shape[0]), "device_bytes": st["device_bytes"],
-                 "spmv_fp64_ms": time_spmv(torch, M, xv, yv, False),
-                 "spmv_fp32_ms": time_spmv(torch, M, xv.float(), yv.float(), True)}
-            r["spmv_fp64_GBs"] = st["spmv_bytes_fp64"] / r["spmv_fp64_ms"] / 1e6
-            r["spmv_fp32_GBs"] = st["spmv_bytes_fp32"] / r["spmv_fp32_ms"] / 1e6
-            r["spmv_fp64_frac_of_measured_hbm"] = r["spmv_fp64_GBs"] / hbm
-            r["spmv_fp32_frac_of_measured_hbm"] = r["spmv_fp32_GBs"] / hbm
-            for prec in ("fp64", "fp32_ir", "fp32_ru"):
-                x = torch.zeros_like(b)
-                flush_l2(torch, flush)
-                torch.cuda.synchronize()
-                _, info = M.solve(b, x, tol=TOL, precision=prec, raise_on_error=False)
-                xs = x.cpu().numpy()
-                r[prec] = {"s": info.kernel_ms / 1000.0, "iterations": info.iterations, "outer": info.outer,
-                           "status": info.status, "rel_res_true": info.rel_res_true,
-                           "iter_us": 1000.0 * info.kernel_ms / max(1, info.iterations),
-                           "err_vs_xstar": float(np.linalg.norm(xs - s.xstar) / np.linalg.norm(s.xstar))}
-            r["mixed_speedup_vs_fp64"] = r["fp64"]["s"] / r["fp32_ir"]["s"]
-            if "fp32_ru" in r:
-                r["reliable_update_speedup_vs_fp64"] = r["fp64"]["s"] / r["fp32_ru"]["s"]
-            out[fmt] = r
-    return out
-
-
-def cpu_baseline(s, args, variants):
+def cpu_baseline(s, args, gold):
+    """The oracle as it stands on the host cores: its single-threaded build
+    and its multi-threaded build (same bits) on every core, each on a bounded
+    run of CG iterations of the benchmarked system (double precision,
+    symmetric storage: the oracle's own method), scaled by the oracle's own
+    iteration count to 1e-10; and one complete 1e-10 solve of the 128^3
+    system on every core."""
     import oracle
 
     up = s.upper()
-    gold = golden(args.grid, "sym")
-    oracle.cg("sym", *up, s.b, tol=0.0, maxit=2)
-    t0 = time.perf_counter()
-    oracle.cg("sym", *up, s.b, tol=0.0, maxit=3)
-    spi = (time.perf_counter() - t0) / 3
-    m = int(max(5, min(2000, args.cpu_seconds / max(spi, 1e-9))))
-    t0 = time.perf_counter()
-    oracle.cg("sym", *up, s.b, tol=0.0, maxit=m)
-    spi = (time.perf_counter() - t0) / m
-    iters = gold["iterations"] if gold else variants["sym"]["fp64"]["iterations"]
-    src = "the oracle's own count (tests/golden)" if gold else "the GPU FP64 solve's count (no oracle golden file)"
-    return {"value": spi * iters, "unit": "s", "cores": 1, "kind": "oracle",
-            "sample": f"{m} double-precision oracle CG iterations (symmetric storage, 1 thread) on the same system, "
-                      f"{spi * 1000:.1f} ms each, scaled by {iters} iterations to 1e-10 from {src}",
-            "seconds_per_iteration": spi}
+    cores = os.cpu_count() or 1
+    lib1 = oracle.load()
+    libn = oracle.load_threaded(cores)
+    iters = gold["iterations"] if gold else None
+    spn, mn, setn = oracle_iteration_seconds("sym", up, s.b, libn, args.cpu_seconds)
+    sp1, m1, set1 = oracle_iteration_seconds("sym", up, s.b, lib1, args.cpu_seconds)
+    out = {"value": spn * iters + setn if iters else None, "unit": "s", "cores": oracle.threads(libn),
+           "kind": "oracle",
+           "sample": f"{mn} CG iterations of the double-precision oracle (symmetric storage) on the benchmarked "
+                     f"system with its multi-threaded build on {oracle.threads(libn)} threads ({spn * 1000:.1f} ms "
+                     f"each) and {m1} with its single-threaded build ({sp1 * 1000:.1f} ms each), scaled by the "
+                     f"oracle's own {iters} iterations to 1e-10 (tests/golden) plus one set-up",
+           "seconds_per_iteration": spn, "single_thread": {"value": sp1 * iters + set1 if iters else None,
+                                                            "seconds_per_iteration": sp1, "cores": 1},
+           "host_cores": cores}
+    if not args.no_cpu_full_solve:
+        s128 = femgen.build_system(femgen.LARGE)
+        u128 = s128.upper()
+        t0 = time.perf_counter()
+        r = oracle.cg("sym", *u128, s128.b, tol=TOL, lib=libn)
+        g128 = golden("128", "sym")
+        out["full_solve_128"] = {"s": time.perf_counter() - t0, "iterations": r.iterations, "status": r.status,
+                                 "rel_res_true": r.rel_res_true, "threads": oracle.threads(libn),
+                                 "same_as_golden": (g128 is not None and r.iterations == g128["iterations"])}
+    return out
 
 
 def main():
     args = parse()
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        return spawn_ranks(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -352,9 +352,11 @@ int gbcg_selftest_wait_timeout(int32_t ctas, int32_t timeout_ms, void* stream);
  * lives in one fixed device array of GBCG_STATIC_SCRATCH_BYTES defined in the
  * library, so n must not exceed GBCG_STATIC_MAX_N; larger n is rejected with
  * GBCG_ERR_INVALID.  Every GPU that loads the library holds that array until
- * the process exits.  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress); make that first call before any stream
- * capture.  All calls share the array and the call clears what must start at
+ * the process exits.  Every call looks up the array's device address on the
+ * current device (cudaGetSymbolAddress; the address is not cached, so a call
+ * after cudaDeviceReset finds the array where the reloaded module put it).
+ * The first call on a device also loads the library's device code there;
+ * make that first call before any stream capture.  All calls share the array and the call clears what must start at
  * zero, so calls whose GPU work overlaps (several streams or host threads on
  * one device) race: issue one at a time per device.  The call synchronises
  * `stream` before it returns.

@@ -1117,13 +1117,18 @@ __global__ void __launch_bounds__(FMT == kTiles ? kTileThreads : kCgThreads, 1) 
           });
       pb = pr;
     }
+    // r'r and b'b go to the third and fourth partial-sum slots: the first
+    // iteration writes p'q to part0 (and r'r to part1) with no barrier after
+    // these sums, while a slower CTA may still be adding them up
+    double* part2 = a.part + 2 * G;
+    double* part3 = a.part + 3 * G;
     const double s_rr = block_sum((double)pr, red);
-    if (threadIdx.x == 0) part0[c] = s_rr;
+    if (threadIdx.x == 0) part2[c] = s_rr;
     const double s_bb = block_sum((double)pb, red);
-    if (threadIdx.x == 0) part1[c] = s_bb;
+    if (threadIdx.x == 0) part3[c] = s_bb;
     if (!grid_barrier(a.bar, target, a.timeout_ns, &sflag, nbar++)) return;
-    rr = grid_sum(part0, G, red);
-    nb = sqrt(grid_sum(part1, G, red));
+    rr = grid_sum(part2, G, red);
+    nb = sqrt(grid_sum(part3, G, red));
   }
   if (nb == 0.0) {  // b = 0: x = 0
     for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) x[i] = V(0);

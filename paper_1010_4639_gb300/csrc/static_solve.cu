@@ -18,7 +18,6 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
-#include <mutex>
 #include <string>
 
 #include "../../include/gbcg.h"
@@ -160,6 +159,9 @@ __global__ void __launch_bounds__(kThreads) k_cg_static(int64_t n, const int32_t
     if (!barrier(bar, target, limit_ns, &flag)) return;
     rr = all_sum(part0, G, red);
     nb = sqrt(all_sum(part1, G, red));
+    // the first iteration writes part0 again: no CTA may do so while another
+    // is still adding up the sums above
+    if (!barrier(bar, target, limit_ns, &flag)) return;
   }
   if (nb == 0.0) {
     for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) x[i] = 0.0;
@@ -231,10 +233,6 @@ done:
   }
 }
 
-// Device address of the scratch, looked up once per device.
-std::mutex g_mu;
-void* g_addr[64] = {nullptr};
-
 }  // namespace
 
 namespace gbcg {
@@ -267,19 +265,19 @@ extern "C" int gbcg_solve_csr_static(int64_t n, int64_t nnz, const int32_t* ptr,
   if (maxit <= 0) maxit = (int32_t)n;
   cudaStream_t s = (cudaStream_t)stream;
   int dev = 0, sms = 0, per_sm = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return fail(GBCG_ERR_CUDA, "cudaGetDevice failed");
+  if (cudaGetDevice(&dev) != cudaSuccess) return fail(GBCG_ERR_CUDA, "cudaGetDevice failed");
+  // The array's device address on the current device, looked up on every
+  // call (no allocation once the library's module is loaded on the device;
+  // the first call on a device loads it).  Not cached: after cudaDeviceReset
+  // or a new primary context the module is loaded again and the array may
+  // sit elsewhere.
   unsigned char* scratch = nullptr;
   {
-    // set-up on the first call on each device: the array's device address
-    std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_addr[dev]) {
-      void* p = nullptr;
-      cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
-      if (e != cudaSuccess || !p)
-        return fail(GBCG_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-      g_addr[dev] = p;
-    }
-    scratch = (unsigned char*)g_addr[dev];
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess || !p)
+      return fail(GBCG_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    scratch = (unsigned char*)p;
   }
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cg_static, kThreads, 0) != cudaSuccess || per_sm < 1)
