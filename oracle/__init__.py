@@ -208,9 +208,12 @@ class Result:
     beta: np.ndarray | None = None
 
 
-def cg(fmt, ptr, idx, val, b, x0=None, tol=1e-10, maxit=None, history=0, lib=None, pipelined=False) -> Result:
+def cg(fmt, ptr, idx, val, b, x0=None, tol=1e-10, maxit=None, history=0, lib=None, pipelined=False,
+       scalar_history=0) -> Result:
     """Plain double-precision CG (Section III listing; readings in oracle.c);
-    pipelined=True: the single-reduction form of the same iteration."""
+    pipelined=True: the single-reduction form of the same iteration.
+    history=h records p, x, alpha and beta of the first h iterations;
+    scalar_history=h only alpha and beta (no n-sized copies)."""
     lib = lib or load()
     ptr, idx, val = _arrays(ptr, idx, val)
     n = ptr.shape[0] - 1
@@ -226,6 +229,10 @@ def cg(fmt, ptr, idx, val, b, x0=None, tol=1e-10, maxit=None, history=0, lib=Non
         al = np.zeros(history)
         be = np.zeros(history)
         hist = History(history, 0, ph.ctypes.data, xh.ctypes.data, al.ctypes.data, be.ctypes.data)
+    elif scalar_history:
+        al = np.zeros(scalar_history)
+        be = np.zeros(scalar_history)
+        hist = History(scalar_history, 0, None, None, al.ctypes.data, be.ctypes.data)
     fn = lib.orc_cg_pipelined if pipelined else lib.orc_cg
     fn(_fmt(fmt), n, _p(ptr), _p(idx), _p(val), _p(b), _p(x), float(tol), maxit,
        ctypes.byref(info), ctypes.byref(hist) if hist is not None else None)
@@ -234,7 +241,28 @@ def cg(fmt, ptr, idx, val, b, x0=None, tol=1e-10, maxit=None, history=0, lib=Non
     if history:
         c = hist.count
         res.p_hist, res.x_hist, res.alpha, res.beta = ph[:c], xh[:c], al[:c], be[:c]
+    elif scalar_history:
+        c = hist.count
+        res.alpha, res.beta = al[:c], be[:c]
     return res
+
+
+def lanczos_extremes(alpha, beta):
+    """Extreme eigenvalue estimates of A from the CG step lengths of one run
+    (no restart): the Lanczos tridiagonal T with T_00 = 1/alpha_0,
+    T_kk = 1/alpha_k + beta_{k-1}/alpha_{k-1}, T_{k,k+1} = sqrt(beta_k)/alpha_k
+    (the CG-Lanczos relation).  Its eigenvalues are Ritz values of A, so
+    lambda_max(T) <= lambda_max(A) and lambda_min(T) >= lambda_min(A)."""
+    from scipy.linalg import eigvalsh_tridiagonal
+
+    alpha = np.asarray(alpha, dtype=np.float64)
+    beta = np.asarray(beta, dtype=np.float64)
+    m = alpha.shape[0]
+    d = 1.0 / alpha
+    d[1:] += beta[:m - 1] / alpha[:m - 1]
+    e = np.sqrt(beta[:m - 1]) / alpha[:m - 1]
+    w = eigvalsh_tridiagonal(d, e)
+    return float(w[0]), float(w[-1])
 
 
 def cg_f32(fmt, ptr, idx, val32, rhs32, tol, maxit, lib=None):

@@ -42,7 +42,7 @@ def main():
     lib = oracle.load_threaded(a.threads) if a.threads > 1 else oracle.load()
     t0 = time.time()
     if a.method == "cg":
-        r = oracle.cg(a.fmt, *arrs, s.b, tol=a.tol, lib=lib)
+        r = oracle.cg(a.fmt, *arrs, s.b, tol=a.tol, lib=lib, scalar_history=min(s.n, 400000))
     else:
         r = oracle.cg_ru(a.fmt, *arrs, s.b, tol=a.tol, lib=lib)
     secs = time.time() - t0
@@ -63,6 +63,14 @@ def main():
     }
     if a.method == "cg" and oracle.threads(lib) == 1:
         out["oracle_seconds_single_thread"] = secs
+    if a.method == "cg":
+        # extreme eigenvalue estimates (Ritz values of the CG-Lanczos
+        # tridiagonal) of the run before any restart: kappa_hat bounds the
+        # solution difference of two solves to relative residual tol by
+        # 2 kappa tol
+        m = r.alpha.shape[0] if r.restarts == 0 else int(0.9 * r.alpha.shape[0])
+        lo, hi = oracle.lanczos_extremes(r.alpha[:m], r.beta[:m])
+        out.update({"lanczos_steps": m, "lambda_min_ritz": lo, "lambda_max_ritz": hi, "kappa_hat": hi / lo})
     suffix = "" if a.method == "cg" else "_ru"
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)), f"oracle_{a.grid}_{a.fmt}{suffix}.json")
     with open(path, "w") as f:

@@ -530,6 +530,41 @@ def check_grad_finite_differences(lib):
         assert abs(fd - gc @ dc) <= 1e-5 * abs(fd) + 1e-9, ("coefficients", fd, gc @ dc)
 
 
+def check_lanczos_extremes(lib):
+    """The Ritz values from the CG step lengths (oracle.lanczos_extremes) are
+    the extreme eigenvalues of A, to the accuracy of a converged run: against
+    numpy's dense symmetric eigensolver on a FEM grid and on a random SPD
+    matrix, and exactly (in exact arithmetic) on a diagonal with known
+    spectrum."""
+    import oracle
+
+    fem = fem_small(9, 8, 7)
+    (sp_ptr, sp_idx, sp_val), _ = spd_sparse(60, 4)
+    for ptr, idx, val, sym in (fem.upper() + (True,), (sp_ptr, sp_idx, sp_val, False)):
+        n = len(ptr) - 1
+        fmt = "sym" if sym else "csr"
+        A = dense_of(ptr, idx, val, n)
+        if sym:
+            A = A + np.triu(A, 1).T
+        b = np.random.default_rng(2).uniform(-1, 1, n)
+        r = oracle.cg(fmt, ptr, idx, val, b, tol=1e-13, maxit=20 * n, scalar_history=20 * n, lib=lib)
+        lo, hi = oracle.lanczos_extremes(r.alpha, r.beta)
+        w = np.linalg.eigvalsh(A)
+        # Ritz values lie inside the spectrum ...
+        assert lo >= w[0] * (1 - 1e-12) and hi <= w[-1] * (1 + 1e-12), (lo, w[0], hi, w[-1])
+        # ... and a run to 1e-13 has found the ends: to 1e-6 on the FEM grid
+        # (well separated ends), to 1% on the random matrix (whose smallest
+        # eigenvalues cluster at the shift, where the run stops first)
+        rt = 1e-6 if sym else 1e-2
+        assert abs(lo - w[0]) <= rt * w[0] and abs(hi - w[-1]) <= rt * w[-1], (lo, w[0], hi, w[-1])
+    # diag(1, 2, ..., 10): CG terminates in 10 steps, T_10 has exactly A's spectrum
+    n = 10
+    ptr, idx, val = np.arange(n + 1), np.arange(n), np.arange(1.0, n + 1)
+    r = oracle.cg("csr", ptr, idx, val, np.ones(n), tol=1e-15, maxit=n, scalar_history=n, lib=lib)
+    lo, hi = oracle.lanczos_extremes(r.alpha, r.beta)
+    assert abs(lo - 1.0) < 1e-10 and abs(hi - 10.0) < 1e-9, (lo, hi)
+
+
 ALL_CHECKS = [
     check_spmv_csr_bruteforce, check_spmv_csc_bruteforce, check_spmv_sym_bruteforce, check_abs_spmv,
     check_spmv_f32, check_dot, check_dot_f32, check_cg_vs_cholesky, check_cg_fem_vs_cholesky,
@@ -537,4 +572,5 @@ ALL_CHECKS = [
     check_cg_error_a_norm_decreases, check_cg_tridiagonal_closed_form, check_cg_edge_cases,
     check_cg_f32, check_cg_ir, check_cg_ru, check_grad_dense_reference, check_assemble_reproduces_the_generator,
     check_grad_finite_differences, check_pipelined_equals_cg_iterates, check_pipelined_vs_cholesky_and_edges,
+    check_lanczos_extremes,
 ]
