@@ -47,9 +47,9 @@ METRIC = "CG time-to-1e-10 residual (s) & SpMV HBM GB/s; mixed/batched vs FP64 C
 GRIDS = {"128": femgen.LARGE, "31": femgen.PAPER_SIZE, "64": femgen.DIFF, "256": femgen.LARGEST}
 TOL = 1e-10
 # DRAM bytes (read + write) per single-precision iteration of the headline
-# kernel, from an ncu capture of the same kernel on a smaller system of the
-# same generator, scaled to this system by its stored entries (None until a
-# capture of the current kernel exists; the profiles directory holds it).
+# kernel and stored entry, from an ncu capture of the same kernel on a
+# smaller system of the same generator (None until a capture of the current
+# kernel exists).
 RU_TRAFFIC_BYTES_PER_STORED_ENTRY = None
 
 
@@ -696,10 +696,10 @@ def differentiable(torch, gb, args):
     """64^3 system, L = ||x - x_t||^2 (x_t ~ U(-1, 1) seeded), symmetric
     storage: forward double-precision CG to 1e-10, backward = adjoint CG to
     1e-10 + sampled-outer-product and element-gradient kernels.  Gradient
-    error: fourth-order central differences (step 1e-6) of fixed-iteration
-    solves along the configured 32 random directions (11 in b and 11 in the
-    stored values: relative white noise; 10 in the coefficients: random smooth
-    fields), and the 6^3 dense reference."""
+    error: fourth-order central differences of fixed-iteration solves along
+    the configured 32 random directions (11 in b and 11 in the stored values:
+    relative white noise, step 1e-6; 10 in the coefficients: random smooth
+    fields, step 1e-5), and the 6^3 dense reference."""
     dev = torch.device("cuda", torch.cuda.current_device())
     t0 = time.perf_counter()
     g = femgen.DIFF
@@ -754,8 +754,8 @@ def differentiable(torch, gb, args):
             xp, xm = F(vp, bp), F(vm, bm)
         return float(((xp - xm) * (xp + xm - 2.0 * xt)).sum())
 
-    def derivative(point):
-        return (8.0 * diff(*point(h), *point(-h)) - diff(*point(2 * h), *point(-2 * h))) / (12.0 * h)
+    def derivative(point, hh=h):
+        return (8.0 * diff(*point(hh), *point(-hh)) - diff(*point(2 * hh), *point(-2 * hh))) / (12.0 * hh)
 
     gen = torch.Generator(device=dev).manual_seed(5)
     errs = {}
@@ -779,7 +779,7 @@ def differentiable(torch, gb, args):
                 f += a * torch.cos(6.283185307179586 * (p @ kv) + ph)
             d = f * coef0
             with torch.no_grad():
-                fd = derivative(lambda e: (asm(coef0 + e * d), b0))
+                fd = derivative(lambda e: (asm(coef0 + e * d), b0), 1e-5)  # step 1e-5: see the tests
             an, fam = float(gc @ d), "coefficients"
         errs.setdefault(fam, []).append(abs(fd - an) / abs(fd))
     out["fd_max_rel_error"] = {k: max(v) for k, v in errs.items()}
@@ -839,8 +839,8 @@ def ablation(torch, gb, args, big):
                     _, info = M.solve(b, x, tol=TOL)
                     lib_s = time.perf_counter() - t0
             r[fmt] = {"spmv_2010_kernel": {"csr": "thread-per-row CSR, one launch",
-                                           "sym": "SCSR direct half and SCSC transpose half fused in one launch, "
-                                                  "FP64 atomic adds (the paper ran them as two launches)"}[fmt],
+                                           "sym": "SCSR direct half, then SCSC transpose half with FP64 "
+                                                  "atomic adds: two launches, as in the paper"}[fmt],
                       "spmv_2010_ms": ms_ab, "spmv_2010_GBs": bytes_2010 / ms_ab / 1e6,
                       "spmv_library_ms": ms_lib, "spmv_library_GBs": bytes_ / ms_lib / 1e6,
                       "spmv_speedup": ms_ab / ms_lib}

@@ -296,9 +296,11 @@ int gbcg_assemble(int64_t nnz, const int64_t* tptr, const int32_t* telem, const 
  * (GBCG_SYM_CSR_UPPER); no validation beyond null and size checks.
  *
  * gbcg_ablation_spmv -- y = A x.  GBCG_CSR: the "trivial" kernel, one thread
- * per row reading the CSR arrays.  GBCG_SYM_CSR_UPPER: the SCSR + SCSC pair,
- * one thread per stored row with the transpose half scattered by
- * floating-point atomic additions (the last bits of y depend on scheduling).
+ * per row reading the CSR arrays.  GBCG_SYM_CSR_UPPER: the SCSR + SCSC pair
+ * as two launches one after the other: SCSR writes the direct half (D + U) x
+ * by rows, SCSC reads the same arrays as columns and scatters the transpose
+ * half with floating-point atomic additions (the last bits of y depend on
+ * scheduling).
  *
  * gbcg_ablation_solve -- CG as the paper runs it: one launch per SpMV, dot
  * and axpy, each dot product copied to the host (two host round trips per

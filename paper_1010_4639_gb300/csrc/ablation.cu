@@ -7,10 +7,12 @@
 // and decides convergence.  Its SpMV kernels are
 //   - the "trivial" CSR kernel: one thread per row, reading the CSR arrays
 //     directly;
-//   - the symmetric pair SCSR + SCSC: one thread per row of the stored
-//     triangle, the direct half summed in a register and the transpose half
-//     scattered with floating-point atomic additions (so the result's last
-//     bits depend on the scheduling).
+//   - the symmetric pair SCSR + SCSC, two launches one after the other (one
+//     kernel at a time per device on the paper's GPUs): SCSR reads the
+//     stored triangle by rows and writes the direct half, one thread per
+//     row; SCSC reads the same arrays as columns and scatters the transpose
+//     half with floating-point atomic additions (so the result's last bits
+//     depend on the scheduling).
 // Here the same structure runs on GB300 with the library's own simple
 // kernels standing in for CuBLAS.
 #include <cuda_runtime.h>
@@ -56,21 +58,28 @@ __global__ void k_spmv_trivial(int64_t n, const int32_t* __restrict__ ptr, const
   y[i] = s;
 }
 
-// Symmetric storage (upper triangle and diagonal by rows): row i adds its
-// direct half to y_i and scatters U_ij x_i into y_j (j > i) with atomics.
-// y must be zero on entry.
-__global__ void k_spmv_sym_atomic(int64_t n, const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx,
-                                  const double* __restrict__ val, const double* __restrict__ x, double* y) {
+// Symmetric storage (upper triangle and diagonal by rows), first launch
+// (SCSR): y_i = sum over row i's stored entries (D + U) of a_ij x_j.
+__global__ void k_spmv_scsr(int64_t n, const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx,
+                            const double* __restrict__ val, const double* __restrict__ x, double* __restrict__ y) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double s = 0.0;
+  for (int32_t k = ptr[i]; k < ptr[i + 1]; ++k) s = fma(val[k], x[idx[k]], s);
+  y[i] = s;
+}
+
+// Second launch (SCSC): the same arrays read as columns of L = U'; column i
+// scatters a_ij x_i into y_j for its entries j > i, with atomic additions.
+__global__ void k_spmv_scsc(int64_t n, const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx,
+                            const double* __restrict__ val, const double* __restrict__ x, double* y) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const double xi = x[i];
-  double s = 0.0;
   for (int32_t k = ptr[i]; k < ptr[i + 1]; ++k) {
     const int32_t j = idx[k];
-    s = fma(val[k], x[j], s);
     if (j != i) atomicAdd(&y[j], val[k] * xi);
   }
-  atomicAdd(&y[i], s);
 }
 
 // Scalar product in two launches, the result copied to the host.
@@ -123,13 +132,14 @@ __global__ void k_sub(int64_t n, const double* __restrict__ b, const double* __r
 int spmv(int32_t format, int64_t n, const int32_t* ptr, const int32_t* idx, const double* val, const double* x,
          double* y, cudaStream_t s, int& launches) {
   if (format == GBCG_SYM_CSR_UPPER) {
-    ACUDA(cudaMemsetAsync(y, 0, sizeof(double) * n, s));
-    k_spmv_sym_atomic<<<blocks_for(n), kThreads, 0, s>>>(n, ptr, idx, val, x, y);
+    k_spmv_scsr<<<blocks_for(n), kThreads, 0, s>>>(n, ptr, idx, val, x, y);
+    k_spmv_scsc<<<blocks_for(n), kThreads, 0, s>>>(n, ptr, idx, val, x, y);
+    launches += 2;
   } else {
     k_spmv_trivial<<<blocks_for(n), kThreads, 0, s>>>(n, ptr, idx, val, x, y);
+    ++launches;
   }
   ACUDA(cudaGetLastError());
-  ++launches;
   return 0;
 }
 

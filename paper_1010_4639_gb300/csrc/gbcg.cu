@@ -21,6 +21,9 @@
 
 using namespace gbcg;
 
+static_assert(kTilePad == kPadSlot, "the layout's padding flag is the kernels'");
+static_assert(kTileSlot < kPadSlot, "slot numbers stay below the padding flag");
+
 namespace {
 
 thread_local std::string g_last_error;
@@ -89,10 +92,13 @@ struct gbcg_matrix_s {
   int64_t ntiles = 0, next = 0, tile_slots = 0;
   // tiled symmetric layout (device)
   int32_t *t_cta_tile = nullptr, *t_tile_slice = nullptr, *t_tile_ns = nullptr, *t_tile_own = nullptr;
-  int32_t *t_tile_len = nullptr, *t_tile_rlog = nullptr, *t_tile_win = nullptr, *t_win_start = nullptr,
+  int32_t *t_tile_len = nullptr, *t_tile_stride = nullptr, *t_tile_win = nullptr, *t_win_start = nullptr,
           *t_win_len = nullptr;
   int64_t *t_tile_ent = nullptr, *t_tile_meta = nullptr, *t_tile_ext = nullptr, *t_in_src = nullptr;
   uint16_t* t_meta = nullptr;
+  TileDesc* t_desc = nullptr;
+  int32_t *t_carry_src = nullptr, *t_carry_dst = nullptr, *t_carry_len = nullptr, *t_flush_src = nullptr,
+          *t_flush_len = nullptr;
   double* t_val64 = nullptr;
   float* t_val32 = nullptr;
   int32_t *t_in_ptr = nullptr, *t_in_row = nullptr, *t_in_len = nullptr;
@@ -139,12 +145,18 @@ struct gbcg_matrix_s {
   template <typename V>
   SymDev<V> tiles() const {
     SymDev<V> t;
+    t.desc = t_desc;
+    t.carry_src = t_carry_src;
+    t.carry_dst = t_carry_dst;
+    t.carry_len = t_carry_len;
+    t.flush_src = t_flush_src;
+    t.flush_len = t_flush_len;
     t.cta_tile = t_cta_tile;
     t.tile_slice = t_tile_slice;
     t.tile_ns = t_tile_ns;
     t.tile_own = t_tile_own;
     t.tile_len = t_tile_len;
-    t.tile_rlog = t_tile_rlog;
+    t.tile_stride = t_tile_stride;
     t.tile_ent = t_tile_ent;
     t.tile_meta = t_tile_meta;
     t.tile_ext = t_tile_ext;
@@ -214,10 +226,11 @@ void free_matrix(gbcg_matrix_s* M) {
                  M->long_val64, M->long_val32, M->diag64, M->diag32, M->pl_ptr, M->pl_i, M->pl_k,
                  M->cta_slice, M->cta_long, M->r, M->p, M->q, M->bstage, M->xstage, M->r32, M->p32, M->q32,
                  M->d32, M->rhs32, M->part, M->sums, M->bar, M->st, M->t_cta_tile, M->t_tile_slice,
-                 M->t_tile_ns, M->t_tile_own, M->t_tile_len, M->t_tile_rlog, M->t_tile_win, M->t_win_start, M->t_win_len,
+                 M->t_tile_ns, M->t_tile_own, M->t_tile_len, M->t_tile_stride, M->t_tile_win, M->t_win_start, M->t_win_len,
                  M->t_tile_ent, M->t_tile_meta, M->t_tile_ext, M->t_in_src, M->t_meta, M->t_val64, M->t_val32,
                  M->t_in_ptr, M->t_in_row, M->t_in_len, M->t_part, M->u_map_main, M->u_map_long, M->u_map_diag,
-                 M->u_stage, M->s64, M->z64, M->w64a, M->w64b};
+                 M->u_stage, M->s64, M->z64, M->w64a, M->w64b, M->t_desc, M->t_carry_src, M->t_carry_dst,
+                 M->t_carry_len, M->t_flush_src, M->t_flush_len};
   for (void* d : dev)
     if (d) cudaFree(d);
   if (M->st_h) cudaFreeHost(M->st_h);
@@ -705,7 +718,7 @@ int gbcg_create(gbcg_matrix_t* out, int32_t format, int64_t n, int64_t nnz, cons
     TRY(upload(&M->t_tile_ns, Tl.tile_ns, s, B));
     TRY(upload(&M->t_tile_own, Tl.tile_own, s, B));
     TRY(upload(&M->t_tile_len, Tl.tile_len, s, B));
-    TRY(upload(&M->t_tile_rlog, Tl.tile_rlog, s, B));
+    TRY(upload(&M->t_tile_stride, Tl.tile_stride, s, B));
     TRY(upload(&M->t_tile_ent, Tl.tile_ent, s, B));
     TRY(upload(&M->t_tile_meta, Tl.tile_meta, s, B));
     TRY(upload(&M->t_tile_ext, Tl.tile_ext, s, B));
@@ -719,6 +732,12 @@ int gbcg_create(gbcg_matrix_t* out, int32_t format, int64_t n, int64_t nnz, cons
     TRY(upload(&M->t_in_row, Tl.in_row, s, B));
     TRY(upload(&M->t_in_len, Tl.in_len, s, B));
     TRY(upload(&M->t_in_src, Tl.in_src, s, B));
+    TRY(upload(&M->t_desc, Tl.desc, s, B));
+    TRY(upload(&M->t_carry_src, Tl.carry_src, s, B));
+    TRY(upload(&M->t_carry_dst, Tl.carry_dst, s, B));
+    TRY(upload(&M->t_carry_len, Tl.carry_len, s, B));
+    TRY(upload(&M->t_flush_src, Tl.flush_src, s, B));
+    TRY(upload(&M->t_flush_len, Tl.flush_len, s, B));
     TRY(dalloc(&M->t_part, (size_t)std::max<int64_t>(M->next, 1), B));
     M->slots = M->tile_slots;
     M->plan_slots = 0;

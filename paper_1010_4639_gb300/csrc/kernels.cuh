@@ -8,11 +8,11 @@
 // (cp.async.bulk, completion on an mbarrier, L2 evict-first policy) while it
 // computes the current one, so the number of bytes in flight does not depend
 // on how many warps are resident.  The symmetric format is computed by
-// CTA-cooperative tiles (a producer warp streams tile stages; the transpose
-// half U' x is an FMA gather over shared memory through a 16-bit transpose
-// index, and sums leaving a tile are added after a grid barrier), or, as a
-// fallback, as a second row gather through a transpose plan that reads U's
-// values in place.  The paper used a separate scatter kernel with atomics;
+// CTA-cooperative tiles (a producer warp streams tile stages; the entries of
+// a tile come in conflict-free rounds, so the transpose half U' x is a
+// shared-memory scatter without atomics, one barrier per round, and sums
+// leaving a tile are added after a grid barrier), or, as a fallback, as a
+// second row gather through a transpose plan that reads U's values in place.  The paper used a separate scatter kernel with atomics;
 // here every output element is summed in a fixed order, so results are
 // bitwise reproducible.
 //
@@ -32,14 +32,20 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "layout.h"  // TileDesc: the packed per-tile descriptor of the tiled symmetric layout
+
 #include <type_traits>
 
 namespace gbcg {
 
 constexpr int kCgThreads = 512;
 constexpr int kWarps = kCgThreads / 32;
-constexpr int kTileThreads = kCgThreads + 32;  // tiled symmetric kernels: + one producer warp
-constexpr int kMaxThreads = kTileThreads;
+// Tiled symmetric kernels: 15 consumer warps and one producer warp, so every
+// persistent kernel runs 16 warps and keeps 128 registers per thread (a 17th
+// warp puts five warps on one SM sub-partition and caps registers at 96).
+constexpr int kTileThreads = kCgThreads;
+constexpr int kTileWarps = kWarps - 1;  // consumer warps of a tile
+constexpr int kMaxThreads = kCgThreads;
 constexpr int kMaxL = 16;    // slots per row one pipeline stage holds
 constexpr int kStages = 2;   // stages per warp
 constexpr uint16_t kPlanPad = 0xFFFF;
@@ -72,12 +78,18 @@ struct OpDev {
 // Tiled symmetric layout (layout.h, SymTilesHost).
 template <typename V>
 struct SymDev {
+  const TileDesc* __restrict__ desc = nullptr;
+  const int32_t* __restrict__ carry_src = nullptr;
+  const int32_t* __restrict__ carry_dst = nullptr;
+  const int32_t* __restrict__ carry_len = nullptr;
+  const int32_t* __restrict__ flush_src = nullptr;
+  const int32_t* __restrict__ flush_len = nullptr;
   const int32_t* __restrict__ cta_tile = nullptr;
   const int32_t* __restrict__ tile_slice = nullptr;
   const int32_t* __restrict__ tile_ns = nullptr;
   const int32_t* __restrict__ tile_own = nullptr;
   const int32_t* __restrict__ tile_len = nullptr;
-  const int32_t* __restrict__ tile_rlog = nullptr;
+  const int32_t* __restrict__ tile_stride = nullptr;
   const int64_t* __restrict__ tile_ent = nullptr;
   const int64_t* __restrict__ tile_meta = nullptr;
   const int64_t* __restrict__ tile_ext = nullptr;
@@ -147,38 +159,39 @@ __host__ __device__ constexpr int gather_stages() { return sizeof(V) == 4 ? 3 : 
 template <typename V>
 constexpr size_t pipe_smem_bytes() { return sizeof(Stage<V>) * gather_stages<V>() * kWarps; }
 
-// Shared memory of the tiled symmetric product: two stages (the current tile
-// and the next one, filled by bulk copies), the entries' transpose products
-// and the tile rows' transpose sums.
+// Shared memory of the tiled symmetric product: the tile stages (filled by
+// bulk copies: values, slots, diagonal, x over the tile's slots) and two
+// accumulators over the slots (tiles alternate between them, so one can be
+// cleared while the other is still being read).
 constexpr int kTileEnt = 4096;   // padded entries of a tile
 constexpr int kTileSlot = 2048;  // slots of a tile
-constexpr int kTileRows = 512;   // 16 slices
-// Geometry of the tile a stage holds, written by the producer with the
-// stage's copies (published to the consumers by the same mbarrier phase).
-struct TileInfo {
-  int64_t row0, ext0, e8;
-  int32_t rows, nsl, L, S, own, tail;  // tail: some x slots need plain loads
-  int32_t rmask;                       // R - 1: entry e belongs to local row e & rmask
-  int32_t pad_[3];
-};
+constexpr int kTileRows = 32 * kTileWarps;  // 15 slices
+constexpr uint16_t kPadSlot = 0x8000;  // slot flag of a padding entry
+// A stage: the tile's descriptor (copied in by the producer warp before it
+// issues the stage's bulk copies, published to the consumers by the same
+// mbarrier phase), then the copied arrays.
 template <typename V>
 struct alignas(16) TileStage {
-  TileInfo info;
+  TileDesc desc;
   V val[kTileEnt];
-  uint16_t meta[2 * kTileEnt + kTileSlot + 8];  // slots, transpose index, index offsets
+  uint16_t meta[kTileEnt + 8];  // slot of each entry (kPadSlot: padding)
   V diag[kTileRows];
   V xs[kTileSlot];
 };
-// Tiles in flight per CTA: three in single precision (bandwidth-bound), two
-// in double precision (FP64-FMA-bound; a third stage would not fit).
+// Tile stages per CTA.  A stage holds ~35 KB (single precision) or ~61 KB
+// (double); at about 44 GB/s of HBM per SM and a fill latency of 1-2 us an
+// SM needs ~90 KB in flight, so single precision keeps five stages (four in
+// flight while one is consumed) and double precision three.
 template <typename V>
-__host__ __device__ constexpr int tile_stages() { return sizeof(V) == 4 ? 3 : 2; }
+__host__ __device__ constexpr int tile_stages() { return sizeof(V) == 4 ? 5 : 3; }
+constexpr int kMaxTileStages = 5;  // "full" and "empty" mbarriers per CTA: one pair per stage
 template <typename V>
 struct alignas(16) TileSmem {
   TileStage<V> st[tile_stages<V>()];
-  V acc[kTileRows];
+  V acc[2][kTileSlot];
+  uint16_t runs[5 * kDescRun];  // the current tile's inline carry and flush runs (the consumers' copy)
 };
-static_assert(sizeof(TileInfo) % 16 == 0, "stage payload alignment");
+static_assert(sizeof(TileDesc) % 16 == 0, "stage payload alignment");
 template <typename V>
 constexpr size_t sym_smem_bytes() { return sizeof(TileSmem<V>); }
 static_assert(sizeof(TileSmem<float>) <= 220 * 1024, "symmetric tiles: shared memory (float)");
@@ -188,9 +201,11 @@ static_assert(sizeof(TileSmem<double>) <= 220 * 1024, "symmetric tiles: shared m
 // across calls within one launch.
 struct TilePipe {
   uint64_t* bar;      // "full" mbarrier per stage (shared memory): the stage's copies landed
-  uint64_t* empty;    // "empty" mbarrier per stage: the consumers are done with it
-  uint32_t iss[3];    // fills issued per stage (producer) / waited for (consumers)
-  uint32_t wait[3];
+  uint64_t* empty;    // "empty" mbarrier per stage: the consumers are done with it (kMaxTileStages each)
+  // per stage b (bit b), kept in registers: parity of the fills issued
+  // (producer) and of the fills waited for (consumers), and whether the
+  // stage has been filled at all in this launch
+  uint32_t iss_par, wait_par, used;
   uint64_t policy;
   long long limit_ns;
   bool failed;
@@ -605,177 +620,209 @@ __device__ __forceinline__ void batched(int lane, int len, LD&& ld, ST&& st) {
   }
 }
 
+// Window w of the tile (inline in the descriptor, else from the global list).
 template <typename V>
-struct TileGeom {
-  int64_t row0, rows;
-  int nsl, L, S, own;
-};
-
-template <typename V>
-__device__ __forceinline__ TileGeom<V> tile_geom(const OpDev<V>& A, const SymDev<V>& T, int32_t t) {
-  TileGeom<V> g;
-  const int64_t s0 = T.tile_slice[t], s1 = T.tile_slice[t + 1];
-  g.row0 = s0 * 32;
-  g.rows = (s1 * 32 < A.n ? s1 * 32 : A.n) - g.row0;
-  g.nsl = (int)(s1 - s0);
-  g.L = T.tile_len[t];
-  g.S = T.tile_ns[t];
-  g.own = T.tile_own[t];
-  return g;
+__device__ __forceinline__ void tile_window(const TileDesc& d, const SymDev<V>& T, int w, int32_t& ws, int32_t& wl) {
+  if (w < kDescWin) {
+    ws = d.ws[w];
+    wl = d.wl[w];
+  } else {
+    ws = T.win_start[d.win0 + w];
+    wl = T.win_len[d.win0 + w];
+  }
 }
 
-// Issues (thread 0) the bulk copies of tile t into stage bf: values, index
-// blob, diagonal, and the x slots (own rows and windows) that are 16-byte
-// aligned; the rest is loaded by tile_tail.
+// Issues (producer lane 0) the bulk copies of the tile whose descriptor
+// stage bf holds: values, slot blob, diagonal, and the x slots (own rows and
+// windows) that are 16-byte aligned; the rest is loaded by tile_tail.
 template <typename V>
-__device__ __forceinline__ void tile_issue(const OpDev<V>& A, const SymDev<V>& T, TileSmem<V>* sm, TilePipe& tp,
-                                           int32_t t, int bf, const V* x) {
-  const TileGeom<V> g = tile_geom(A, T, t);
-  TileStage<V>& st = sm->st[bf];
+__device__ __forceinline__ void tile_issue(const OpDev<V>& A, const SymDev<V>& T, TileStage<V>& st, TilePipe& tp,
+                                           int bf, const V* x) {
+  const TileDesc& d = st.desc;
   uint64_t* bar = &tp.bar[bf];
-  const int64_t e0 = T.tile_ent[t], e1 = T.tile_ent[t + 1];
-  const int64_t m0 = T.tile_meta[t], m1 = T.tile_meta[t + 1];
-  const uint32_t vb = (uint32_t)((e1 - e0) * sizeof(V)), mb = (uint32_t)((m1 - m0) * sizeof(uint16_t));
-  const uint32_t db = (uint32_t)(g.nsl * 32 * sizeof(V));
-  const bool own_bulk = (g.rows & 3) == 0;
-  uint32_t bytes = vb + mb + db + (own_bulk ? (uint32_t)(g.rows * sizeof(V)) : 0u);
-  const int32_t w0 = T.tile_win[t], w1 = T.tile_win[t + 1];
-  for (int32_t w = w0; w < w1; ++w)
-    if (((T.win_start[w] | T.win_len[w]) & 3) == 0) bytes += (uint32_t)(T.win_len[w] * sizeof(V));
-  int tail = own_bulk ? 0 : 1;
-  for (int32_t w = w0; w < w1; ++w)
-    if (((T.win_start[w] | T.win_len[w]) & 3) != 0) tail = 1;
-  st.info.row0 = g.row0;
-  st.info.ext0 = T.tile_ext[t];
-  st.info.e8 = e1 - e0;
-  st.info.rows = (int32_t)g.rows;
-  st.info.nsl = g.nsl;
-  st.info.L = g.L;
-  st.info.S = g.S;
-  st.info.own = g.own;
-  st.info.tail = tail;
-  st.info.rmask = (1 << T.tile_rlog[t]) - 1;
+  const uint32_t vb = (uint32_t)(d.E8 * sizeof(V)), mb = (uint32_t)(d.E8 * sizeof(uint16_t));
+  const uint32_t db = (uint32_t)(d.nsl * 32 * sizeof(V));
+  const bool own_bulk = (d.rows & 3) == 0;
+  uint32_t bytes = vb + mb + db + (own_bulk ? (uint32_t)(d.rows * sizeof(V)) : 0u);
+  for (int w = 0; w < d.nwin; ++w) {
+    int32_t ws, wl;
+    tile_window(d, T, w, ws, wl);
+    if (((ws | wl) & 3) == 0) bytes += (uint32_t)(wl * sizeof(V));
+  }
   fence_proxy_async_global();
   mbar_arrive_expect_tx(bar, bytes);
-  if (vb) bulk_g2s(st.val, T.val + e0, vb, bar, tp.policy);
-  if (mb) bulk_g2s(st.meta, T.meta + m0, mb, bar, tp.policy);
-  bulk_g2s(st.diag, A.diag + g.row0, db, bar, tp.policy);
-  if (own_bulk && g.rows > 0) bulk_g2s(st.xs, x + g.row0, (uint32_t)(g.rows * sizeof(V)), bar, tp.policy);
-  int32_t slot = g.own;
-  for (int32_t w = w0; w < w1; ++w) {
-    const int32_t ws0 = T.win_start[w], wl = T.win_len[w];
-    if (((ws0 | wl) & 3) == 0 && wl > 0) bulk_g2s(st.xs + slot, x + ws0, (uint32_t)(wl * sizeof(V)), bar, tp.policy);
+  if (vb) bulk_g2s(st.val, T.val + d.e0, vb, bar, tp.policy);
+  if (mb) bulk_g2s(st.meta, T.meta + d.m0, mb, bar, tp.policy);
+  bulk_g2s(st.diag, A.diag + d.row0, db, bar, tp.policy);
+  if (own_bulk && d.rows > 0) bulk_g2s(st.xs, x + d.row0, (uint32_t)(d.rows * sizeof(V)), bar, tp.policy);
+  int32_t slot = d.own;
+  for (int w = 0; w < d.nwin; ++w) {
+    int32_t ws, wl;
+    tile_window(d, T, w, ws, wl);
+    if (((ws | wl) & 3) == 0 && wl > 0) bulk_g2s(st.xs + slot, x + ws, (uint32_t)(wl * sizeof(V)), bar, tp.policy);
     slot += wl;
   }
-  ++tp.iss[bf];
+  tp.iss_par ^= 1u << bf;
+  tp.used |= 1u << bf;
 }
 
-// Plain loads of the x slots tile_issue left out (only at the end of the matrix).
+// Plain loads (consumer threads) of the x slots tile_issue left out: rows or
+// windows not 16-byte aligned, which occur only at the end of the matrix.
 template <typename V, bool NC>
-__device__ __forceinline__ void tile_tail(const OpDev<V>& A, const SymDev<V>& T, V* xs, int32_t t, const V* x) {
-  const TileGeom<V> g = tile_geom(A, T, t);
-  if ((g.rows & 3) != 0)
-    for (int64_t i = threadIdx.x; i < g.rows; i += blockDim.x) xs[i] = ld_vec<NC>(x + g.row0 + i);
-  int32_t slot = g.own;
-  for (int32_t w = T.tile_win[t]; w < T.tile_win[t + 1]; ++w) {
-    const int32_t ws0 = T.win_start[w], wl = T.win_len[w];
-    if (((ws0 | wl) & 3) != 0)
-      for (int i = threadIdx.x; i < wl; i += blockDim.x) xs[slot + i] = ld_vec<NC>(x + ws0 + i);
+__device__ __forceinline__ void tile_tail(const SymDev<V>& T, TileStage<V>& st, const V* x, int nthreads) {
+  const TileDesc& d = st.desc;
+  if ((d.rows & 3) != 0)
+    for (int i = threadIdx.x; i < d.rows; i += nthreads) st.xs[i] = ld_vec<NC>(x + d.row0 + i);
+  int32_t slot = d.own;
+  for (int w = 0; w < d.nwin; ++w) {
+    int32_t ws, wl;
+    tile_window(d, T, w, ws, wl);
+    if (((ws | wl) & 3) != 0)
+      for (int i = threadIdx.x; i < wl; i += nthreads) st.xs[slot + i] = ld_vec<NC>(x + ws + i);
     slot += wl;
   }
 }
 
 // Symmetric product over the CTA's tiles (a producer warp streams tiles into
-// the stages; 16 consumer warps cooperate on each tile):
-//   pass 1, one warp per slice, one lane per row: the direct sum (U x)_i
-//           from the staged x;
-//   pass 2, one thread per slot s: sum over the entries e that target s of
-//           val[e] * x[row(e)], in the layout's fixed order -- the tile's own
-//           rows keep theirs, the window slots leave as partial sums;
-//   then f(row, own part of (A x)_row, x_i, D_i x_i, (U x)_i) on the row's lane.
-// Uniform control flow: every thread takes every __syncthreads.
+// the stages; 15 consumer warps cooperate on each tile, one lane per row).
+// In round k every row takes its round-k entry (i, j): the direct sum
+// (U x)_i gains U_ij x_j from the staged x, and slot j's accumulator gains
+// U_ij x_i; the layout guarantees that no two entries of a round target the
+// same slot, and a barrier separates the rounds, so each slot's sum is formed
+// in round order without atomics.  The accumulator of a tile starts with what
+// the previous tile of the CTA carried into it (window rows both tiles
+// cover).  Then f(row, own part of (A x)_row, x_i, D_i x_i, (U x)_i) runs on
+// the row's lane; window slots are carried into the next tile's accumulator
+// or leave as partial sums.  Uniform control flow: every consumer thread
+// takes every barrier.
 template <typename V, bool NC, class F>
 __device__ __forceinline__ void sym_tiles(const OpDev<V>& A, const SymDev<V>& T, const V* x, TileSmem<V>* sm,
                                           TilePipe& tp, int* err, F&& f) {
   constexpr int NST = tile_stages<V>();
-  constexpr int NC_THREADS = kCgThreads;  // consumers: warps 0..15; warp 16 produces
+  constexpr int NC_THREADS = 32 * kTileWarps;  // consumers: warps 0..14; warp 15 produces
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, c = blockIdx.x;
   const int32_t t0 = T.cta_tile[c], t1 = T.cta_tile[c + 1];
   if (t0 >= t1) return;
-  if (warp == kWarps) {
-    // producer: lane 0 fills stages as the consumers release them
-    if (lane == 0) {
-      for (int32_t t = t0; t < t1 && !tp.failed; ++t) {
-        const int b = (int)((t - t0) % NST);
-        if (tp.iss[b] > 0 && !mbar_wait(&tp.empty[b], (tp.iss[b] - 1u) & 1u, tp.limit_ns)) {
-          tp.failed = true;
-          if (atomicCAS(err, 0, (int)kTimeout) == 0) err[1] = 400000000 + (int)(t % 1000000) * 10 + b;
-          break;
-        }
-        tile_issue(A, T, sm, tp, t, b, x);
+  if (warp == kTileWarps) {
+    // producer: lane 0 waits for a free stage and issues its copies; lanes
+    // 0..15 bring the tile's descriptor into the stage first.  The next
+    // tile's descriptor is loaded while the current one is issued, so its
+    // round trip overlaps the wait for the next free stage.
+    constexpr int kDescVecs = (int)(sizeof(TileDesc) / 16);
+    int4 dnext = make_int4(0, 0, 0, 0);
+    if (lane < kDescVecs) dnext = __ldg(reinterpret_cast<const int4*>(T.desc + t0) + lane);
+    for (int32_t t = t0; t < t1; ++t) {
+      const int b = (int)((t - t0) % NST);
+      int ok = !tp.failed;
+      if (lane == 0 && ok && ((tp.used >> b) & 1u) &&
+          !mbar_wait(&tp.empty[b], ((tp.iss_par >> b) & 1u) ^ 1u, tp.limit_ns)) {
+        ok = 0;
+        if (atomicCAS(err, 0, (int)kTimeout) == 0) err[1] = 400000000 + (int)(t % 1000000) * 10 + b;
       }
-      // the CTA must not move on while its copies are in flight: wait
-      // (bounded) for the last fill of every stage to land
-      for (int b = 0; b < NST; ++b)
-        if (tp.iss[b] > 0) mbar_wait(&tp.bar[b], (tp.iss[b] - 1u) & 1u, tp.limit_ns);
+      if (!__shfl_sync(0xffffffffu, ok, 0)) {
+        tp.failed = true;
+        break;
+      }
+      __syncwarp();  // lane 0's wait for the free stage is ordered before the lanes' writes
+      TileStage<V>& st = sm->st[b];
+      if (lane < kDescVecs) reinterpret_cast<int4*>(&st.desc)[lane] = dnext;
+      if (lane < kDescVecs && t + 1 < t1) dnext = __ldg(reinterpret_cast<const int4*>(T.desc + t + 1) + lane);
+      __syncwarp();
+      if (lane == 0) tile_issue(A, T, st, tp, b, x);
+      __syncwarp();
     }
+    // the CTA must not move on while its copies are in flight: wait
+    // (bounded) for the last fill of every stage to land
+    if (lane == 0)
+      for (int b = 0; b < NST; ++b)
+        if ((tp.used >> b) & 1u) mbar_wait(&tp.bar[b], ((tp.iss_par >> b) & 1u) ^ 1u, tp.limit_ns);
     __syncwarp();
     return;
   }
+  // the first tile's accumulator starts at zero (the barrier of the first
+  // tile orders this before its rounds)
+  for (int sl = threadIdx.x; sl < kTileSlot; sl += NC_THREADS) sm->acc[0][sl] = V(0);
   for (int32_t t = t0; t < t1; ++t) {
-    const int bf = (int)((t - t0) % NST);
+    const int j = (int)(t - t0), bf = j % NST;
     TileStage<V>& st = sm->st[bf];
+    V* __restrict__ acc = sm->acc[j & 1];
+    V* __restrict__ acc_next = sm->acc[(j + 1) & 1];
     bool ok = !tp.failed;
     if (ok) {
-      ok = mbar_wait(&tp.bar[bf], tp.wait[bf] & 1u, tp.limit_ns);
+      ok = mbar_wait(&tp.bar[bf], (tp.wait_par >> bf) & 1u, tp.limit_ns);
       if (!ok && atomicCAS(err, 0, (int)kTimeout) == 0) err[1] = 300000000 + (int)(t % 1000000) * 10 + bf;
     }
-    if (ok && st.info.tail) tile_tail<V, NC>(A, T, st.xs, t, x);
+    if (ok && st.desc.tail) tile_tail<V, NC>(T, st, x, NC_THREADS);
     ok = consumers_and(NC_THREADS, ok);
     if (!ok) {
       tp.failed = true;
       continue;
     }
-    ++tp.wait[bf];
-    const TileInfo g = st.info;
-    const uint16_t* slot = st.meta;
-    const uint16_t* tidx = st.meta + g.e8;
-    const uint16_t* tptr = st.meta + 2 * g.e8;
-    // pass 1 (row gather of D + U) and pass 2 (transpose gather of U') read
-    // only the stage, so they run back to back without a barrier
+    tp.wait_par ^= 1u << bf;
+    // the tile's geometry into registers (the descriptor goes with the stage)
+    const TileDesc& d = st.desc;
+    const int g_rows = d.rows, g_nsl = d.nsl, g_D = d.D, g_S = d.S, g_own = d.own, R = d.R;
+    const int g_nc = d.nc, g_nf = d.nf, g_c0 = d.carry0, g_f0 = d.flush0;
+    const int64_t g_row0 = d.row0, g_ext0 = d.ext0;
+    // the next tile's accumulator is cleared here, its carried values are
+    // written after this tile's rounds; this tile's inline runs are kept for
+    // the end of the tile (the stage is released before)
+    for (int sl = threadIdx.x; sl < kTileSlot; sl += NC_THREADS) acc_next[sl] = V(0);
+    if (threadIdx.x < 5 * kDescRun) sm->runs[threadIdx.x] = (&d.cs[0])[threadIdx.x];  // cs, cd, cl, fs, fl in order
+    const uint16_t* __restrict__ slot = st.meta;
+    const V* __restrict__ val = st.val;
+    const V* __restrict__ xs = st.xs;
+    // rounds: in round k the row's round-k entry (i, j) adds U_ij x_j to the
+    // row's direct sum and U_ij x_i to slot j's accumulator; no two entries of
+    // a round share a slot, so the scatter needs no atomics, and the barrier
+    // after each round orders the additions into a slot
     V xi = V(0), dg = V(0), direct = V(0);
-    const bool mine = warp < g.nsl;
     const int own_row = warp * 32 + lane;
+    const bool mine = warp < g_nsl && own_row < g_rows;
     if (mine) {
-      if (own_row < g.rows) {
-        xi = st.xs[own_row];
-        dg = st.diag[own_row];
-      }
-      const int R = g.rmask + 1;
-      for (int k = 0; k < g.L; ++k) {
-        const int e = k * R + own_row;
-        direct = fma_(st.val[e], st.xs[slot[e]], direct);
-      }
+      xi = xs[own_row];
+      dg = st.diag[own_row];
     }
-    V* __restrict__ part = T.part + g.ext0;
-    for (int sl = threadIdx.x; sl < g.S; sl += NC_THREADS) {
-      if (sl >= g.rows && sl < g.own) continue;  // padding of the own rows
-      V sum = V(0);
-      const int j1 = tptr[sl + 1];
-      for (int j = tptr[sl]; j < j1; ++j) {
-        const int e = tidx[j];
-        sum = fma_(st.val[e], st.xs[e & g.rmask], sum);
+    int e = own_row;
+    uint16_t sn = mine && g_D > 0 ? slot[e] : kPadSlot;
+    V vn = mine && g_D > 0 ? val[e] : V(0);
+    for (int k = 0; k < g_D; ++k) {
+      const uint16_t s16 = sn;
+      const V v = vn;
+      e += R;
+      if (mine && k + 1 < g_D) {  // the next round's entry, loaded before this round's chain
+        sn = slot[e];
+        vn = val[e];
       }
-      if (sl < g.rows) sm->acc[sl] = sum;
-      else part[sl - g.own] = sum;
+      if (!(s16 & kPadSlot)) {
+        direct = fma_(v, xs[s16], direct);
+        acc[s16] = fma_(v, xi, acc[s16]);
+      }
+      consumers_sync(NC_THREADS);
     }
-    consumers_sync(NC_THREADS);
+    if (g_D == 0) consumers_sync(NC_THREADS);  // every read of the stage is done
     // the stage is free: release it to the producer
     if (threadIdx.x == 0) mbar_arrive(&tp.empty[bf]);
-    if (mine && own_row < g.rows) {
+    if (mine) {
       const V dxi = dg * xi;
-      f(g.row0 + own_row, dxi + direct + sm->acc[own_row], xi, dxi, direct);
+      f(g_row0 + own_row, dxi + direct + acc[own_row], xi, dxi, direct);
     }
+    // window slots: carried into the next tile's accumulator, or out as
+    // partial sums (runs past the inline ones come from the global lists)
+    const uint16_t* cs = sm->runs;
+    for (int u = 0; u < g_nc; ++u) {
+      const int s0 = u < kDescRun ? cs[u] : T.carry_src[g_c0 + u];
+      const int d0 = u < kDescRun ? cs[kDescRun + u] : T.carry_dst[g_c0 + u];
+      const int len = u < kDescRun ? cs[2 * kDescRun + u] : T.carry_len[g_c0 + u];
+      for (int i = threadIdx.x; i < len; i += NC_THREADS) acc_next[d0 + i] = acc[s0 + i];
+    }
+    V* __restrict__ part = T.part + g_ext0 - g_own;
+    for (int u = 0; u < g_nf; ++u) {
+      const int s0 = u < kDescRun ? cs[3 * kDescRun + u] : T.flush_src[g_f0 + u];
+      const int len = u < kDescRun ? cs[4 * kDescRun + u] : T.flush_len[g_f0 + u];
+      for (int i = threadIdx.x; i < len; i += NC_THREADS) part[s0 + i] = acc[s0 + i];
+    }
+    (void)g_S;
   }
 }
 
@@ -795,15 +842,15 @@ __device__ __forceinline__ void sym_incoming(const SymDev<V>& T, V* y) {
   }
 }
 
-__device__ __forceinline__ void tile_pipe_init(TilePipe& tp, uint64_t* bar6, long long limit_ns) {
-  tp.bar = bar6;
-  tp.empty = bar6 + 3;
-  for (int b = 0; b < 3; ++b) tp.iss[b] = tp.wait[b] = 0;
+__device__ __forceinline__ void tile_pipe_init(TilePipe& tp, uint64_t* bars, long long limit_ns) {
+  tp.bar = bars;
+  tp.empty = bars + kMaxTileStages;
+  tp.iss_par = tp.wait_par = tp.used = 0;
   tp.policy = policy_evict_first();
   tp.limit_ns = limit_ns;
   tp.failed = false;
   if (threadIdx.x == 0)
-    for (int b = 0; b < 6; ++b) mbar_init(&bar6[b], 1);
+    for (int b = 0; b < 2 * kMaxTileStages; ++b) mbar_init(&bars[b], 1);
   fence_mbar_init();
 }
 
@@ -926,7 +973,7 @@ __global__ void __launch_bounds__(FMT == kTiles ? kTileThreads : kCgThreads, 1)
            const V* __restrict__ x, V* __restrict__ y, int* err, long long limit_ns) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ uint64_t bars[kMaxThreads / 32][kMaxStages];
-  __shared__ uint64_t tbar[6];
+  __shared__ uint64_t tbar[2 * kMaxTileStages];
   Pipe pp;
   pipe_init(pp, bars[threadIdx.x >> 5], gather_stages<V>(), limit_ns);
   TilePipe tp;
@@ -1059,7 +1106,7 @@ __global__ void __launch_bounds__(FMT == kTiles ? kTileThreads : kCgThreads, 1) 
   const V* __restrict__ b = a.b;
   double* part0 = a.part;
   double* part1 = a.part + G;
-  __shared__ uint64_t tbar[6];
+  __shared__ uint64_t tbar[2 * kMaxTileStages];
   Pipe pp;
   pipe_init(pp, bars[threadIdx.x >> 5], gather_stages<V>(), a.timeout_ns);
   TilePipe tp;
@@ -1530,7 +1577,7 @@ __global__ void __launch_bounds__(FMT == kTiles ? kTileThreads : kCgThreads, 1) 
   Pipe pp32, pp64;
   pipe_init(pp32, bars[warp], gather_stages<float>(), a.timeout_ns);
   pipe_init(pp64, bars[warp] + gather_stages<float>(), gather_stages<double>(), a.timeout_ns);
-  __shared__ uint64_t tbar[6];
+  __shared__ uint64_t tbar[2 * kMaxTileStages];
   TilePipe tp;
   if constexpr (FMT == kTiles) tile_pipe_init(tp, tbar, a.timeout_ns);
   __syncthreads();

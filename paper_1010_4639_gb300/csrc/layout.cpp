@@ -2,6 +2,7 @@
 #include "layout.h"
 
 #include <algorithm>
+#include <cstring>
 #include <cmath>
 #include <cstdio>
 
@@ -338,6 +339,56 @@ void make_windows(const std::vector<int32_t>& tg, int64_t n, std::vector<Window>
   }
 }
 
+// Colours the entries of one tile so that, in every colour (round), each
+// row has at most one entry and each target slot receives at most one:
+// a proper edge colouring of the bipartite graph rows x slots.  By Konig's
+// theorem max(row degree, slot degree) colours suffice; edges are coloured
+// in order, each taking the lowest colour free at its row, and when that
+// colour is taken at its slot the alternating path of the two colours from
+// the slot is flipped first (it cannot reach the row).  Returns the colour of
+// each edge.
+std::vector<int> colour_edges(const std::vector<int32_t>& eu, const std::vector<int32_t>& ev, int nrow, int nslot,
+                              int D) {
+  const int E = (int)eu.size();
+  std::vector<int> col(E, -1);
+  std::vector<int32_t> at_u((size_t)nrow * D, -1), at_v((size_t)nslot * D, -1);
+  std::vector<int32_t> path;
+  for (int e = 0; e < E; ++e) {
+    const int u = eu[e], v = ev[e];
+    int a = 0;
+    while (at_u[(size_t)u * D + a] >= 0) ++a;
+    if (at_v[(size_t)v * D + a] >= 0) {
+      int b = 0;
+      while (at_v[(size_t)v * D + b] >= 0) ++b;
+      // the a/b path from slot v: slot -a-> row -b-> slot -a-> ...
+      path.clear();
+      int cur = v, c = a;
+      bool on_slot = true;
+      for (;;) {
+        const int32_t f = on_slot ? at_v[(size_t)cur * D + c] : at_u[(size_t)cur * D + c];
+        if (f < 0) break;
+        path.push_back(f);
+        cur = on_slot ? eu[f] : ev[f];
+        on_slot = !on_slot;
+        c = c == a ? b : a;
+      }
+      for (int32_t f : path) {
+        at_u[(size_t)eu[f] * D + col[f]] = -1;
+        at_v[(size_t)ev[f] * D + col[f]] = -1;
+      }
+      for (int32_t f : path) {
+        col[f] = col[f] == a ? b : a;
+        at_u[(size_t)eu[f] * D + col[f]] = f;
+        at_v[(size_t)ev[f] * D + col[f]] = f;
+      }
+    }
+    col[e] = a;
+    at_u[(size_t)u * D + a] = e;
+    at_v[(size_t)v * D + a] = e;
+  }
+  return col;
+}
+
 }  // namespace
 
 bool build_sym_tiles(LayoutHost& L, int ctas, int slot_cap, int ent_cap) {
@@ -371,15 +422,23 @@ bool build_sym_tiles(LayoutHost& L, int ctas, int slot_cap, int ent_cap) {
     }
     ccut[ctas] = ns;
   }
-  // targets beyond a candidate tile, its windows and slot count
+  // targets beyond a candidate tile, its windows and slot count; the largest
+  // number of entries any one column receives from the tile's rows
   std::vector<int32_t> tg;
   std::vector<Window> wins;
+  std::vector<int32_t> hits(n > 0 ? n : 1, 0);
+  int64_t max_hits = 0;
   auto targets = [&](int64_t sa, int64_t sb) {
     const int64_t a = 32 * sa, b = std::min<int64_t>(n, 32 * sb);
     tg.clear();
+    max_hits = 0;
     for (int64_t r = a; r < b; ++r)
-      for (int64_t q = rp[r]; q < rp[r + 1]; ++q)
+      for (int64_t q = rp[r]; q < rp[r + 1]; ++q) {
         if (rc[q] >= b) tg.push_back(rc[q]);
+        if (rc[q] != r) max_hits = std::max<int64_t>(max_hits, ++hits[rc[q]]);
+      }
+    for (int64_t r = a; r < b; ++r)
+      for (int64_t q = rp[r]; q < rp[r + 1]; ++q) hits[rc[q]] = 0;
     std::sort(tg.begin(), tg.end());
     tg.erase(std::unique(tg.begin(), tg.end()), tg.end());
     make_windows(tg, n, wins);
@@ -387,17 +446,16 @@ bool build_sym_tiles(LayoutHost& L, int ctas, int slot_cap, int ent_cap) {
     for (const Window& w : wins) slots += w.len;
     return slots;
   };
-  auto pow2 = [](int64_t v) {
-    int64_t p = 1;
-    while (p < v) p <<= 1;
-    return p;
-  };
-  auto fits = [&](int64_t sa, int64_t sb) {
-    if (sb - sa > 16) return false;
+  // rounds of a tile: its longest row or its most-hit column, whichever is more
+  auto rounds = [&](int64_t sa, int64_t sb) {
     int64_t lmax = 0;
     for (int64_t s = sa; s < sb; ++s) lmax = std::max(lmax, slice_len(s));
-    if (32 * pow2(sb - sa) * lmax > ent_cap) return false;
-    return targets(sa, sb) <= slot_cap;
+    return std::max(lmax, max_hits);
+  };
+  auto fits = [&](int64_t sa, int64_t sb) {
+    if (sb - sa > 15) return false;
+    if (targets(sa, sb) > slot_cap) return false;
+    return 32 * (sb - sa) * rounds(sa, sb) <= ent_cap;
   };
   // 2. tiles inside each CTA range: the longest prefix that fits
   Tl.cta_tile.assign(ctas + 1, 0);
@@ -420,32 +478,30 @@ bool build_sym_tiles(LayoutHost& L, int ctas, int slot_cap, int ent_cap) {
   Tl.cta_tile[ctas] = tile_id;
   Tl.tile_slice.push_back((int32_t)ns);
   const int32_t T = tile_id;
-  // 3. per tile: windows, slot map, entries, transpose index
+  // 3. per tile: windows, slot map, entries in conflict-free rounds
   Tl.tile_ns.assign(T, 0);
   Tl.tile_own.assign(T, 0);
   Tl.tile_len.assign(T, 0);
-  Tl.tile_rlog.assign(T, 0);
+  Tl.tile_stride.assign(T, 0);
   Tl.tile_ent.assign(T + 1, 0);
   Tl.tile_meta.assign(T + 1, 0);
   Tl.tile_ext.assign(T + 1, 0);
   Tl.tile_win.assign(T + 1, 0);
   std::vector<int32_t> slot_of(n > 0 ? n : 1, -1);
   auto up8 = [](int64_t v) { return (v + 7) & ~int64_t(7); };
-  std::vector<std::vector<uint16_t>> lists;
+  std::vector<int32_t> eu, ev;
+  std::vector<int64_t> eq;
   for (int32_t t = 0; t < T; ++t) {
     const int64_t s0 = Tl.tile_slice[t], s1 = Tl.tile_slice[t + 1];
     const int64_t a = 32 * s0, b = std::min<int64_t>(n, 32 * s1);
     const int64_t S = targets(s0, s1);
     const int32_t own = (int32_t)(((b - a) + 3) & ~int64_t(3));
-    int64_t lmax = 0;
-    for (int64_t s = s0; s < s1; ++s) lmax = std::max(lmax, slice_len(s));
+    const int64_t D = rounds(s0, s1);
     Tl.tile_ns[t] = (int32_t)S;
     Tl.tile_own[t] = own;
-    Tl.tile_len[t] = (int32_t)lmax;
-    const int64_t R = 32 * pow2(s1 - s0);
-    int32_t rlog = 0;
-    while ((int64_t(1) << rlog) < R) ++rlog;
-    Tl.tile_rlog[t] = rlog;
+    Tl.tile_len[t] = (int32_t)D;
+    const int64_t R = 32 * (s1 - s0);
+    Tl.tile_stride[t] = (int32_t)R;
     Tl.tile_ext[t + 1] = Tl.tile_ext[t] + (S - own);
     Tl.tile_win[t + 1] = Tl.tile_win[t] + (int32_t)wins.size();
     int32_t slot0 = own;
@@ -455,42 +511,55 @@ bool build_sym_tiles(LayoutHost& L, int ctas, int slot_cap, int ent_cap) {
       for (int64_t r = w.start; r < w.start + w.len; ++r) slot_of[r] = slot0 + (int32_t)(r - w.start);
       slot0 += (int32_t)w.len;
     }
-    const int64_t E = R * lmax, E8 = up8(E);
+    // the strict upper entries as edges (local row, target slot), rows in
+    // increasing order and each row's entries by increasing column
+    eu.clear();
+    ev.clear();
+    eq.clear();
+    for (int64_t r = a; r < b; ++r)
+      for (int64_t q = rp[r]; q < rp[r + 1]; ++q) {
+        const int64_t c = rc[q];
+        eu.push_back((int32_t)(r - a));
+        ev.push_back((int32_t)(c < b ? c - a : slot_of[c]));
+        eq.push_back(q);
+      }
+    const std::vector<int> colour = colour_edges(eu, ev, (int)(b - a), (int)S, (int)std::max<int64_t>(D, 1));
+    const int64_t E = R * D, E8 = up8(E);
     const int64_t e0 = Tl.tile_ent[t];
     Tl.tile_ent[t + 1] = e0 + E8;
     Tl.val.resize(e0 + E8, 0.0);
-    std::vector<uint16_t> slot(E8, 0);
-    lists.assign(S, {});
-    // entry e = k * R + l for the k-th stored entry of local row l = r - a; rows
-    // are visited in increasing order, so each slot's list is in increasing source row
-    for (int64_t r = a; r < b; ++r) {
-      int64_t k = 0;
-      for (int64_t q = rp[r]; q < rp[r + 1]; ++q, ++k) {
-        const int64_t c = rc[q];
-        const int32_t sl = (int32_t)(c < b ? c - a : slot_of[c]);
-        const int64_t e = k * R + (r - a);
-        slot[e] = (uint16_t)sl;
-        Tl.val[e0 + e] = L.urv[q];
-        lists[sl].push_back((uint16_t)e);
-      }
-    }
-    // blob: slots[E8], transpose index[E8], index offsets[S + 1 rounded up to 8]
+    // blob: slots[E8]; entry e = k * R + l holds the round-k entry of local
+    // row l; a position without one is padding: value 0, slot l | kTilePad
     const int64_t m0 = Tl.tile_meta[t];
-    const int64_t P8 = up8(S + 1);
-    Tl.tile_meta[t + 1] = m0 + 2 * E8 + P8;
-    Tl.meta.resize(m0 + 2 * E8 + P8, 0);
-    std::copy(slot.begin(), slot.end(), Tl.meta.begin() + m0);
-    int64_t pos = 0;
-    for (int64_t sl = 0; sl < S; ++sl) {
-      Tl.meta[m0 + 2 * E8 + sl] = (uint16_t)pos;
-      for (uint16_t e : lists[sl]) Tl.meta[m0 + E8 + pos++] = e;
+    Tl.tile_meta[t + 1] = m0 + E8;
+    Tl.meta.resize(m0 + E8, 0);
+    for (int64_t e = 0; e < E8; ++e) Tl.meta[m0 + e] = (uint16_t)((e % R) | kTilePad);
+    for (size_t i = 0; i < eu.size(); ++i) {
+      const int64_t e = (int64_t)colour[i] * R + eu[i];
+      Tl.meta[m0 + e] = (uint16_t)ev[i];
+      Tl.val[e0 + e] = L.urv[eq[i]];
     }
-    Tl.meta[m0 + 2 * E8 + S] = (uint16_t)pos;
   }
-  // 4. incoming runs: each window's rows, split by the tile that owns them
+  // 4. what becomes of each window slot after its tile: a row that the next
+  // tile of the same CTA also covers (as an own row or in a window) is
+  // carried into that tile's accumulator; the others leave as partial sums,
+  // added to their rows by the tile that owns them ("incoming runs")
   std::vector<int32_t> tile_of_slice(ns, 0);
   for (int32_t t = 0; t < T; ++t)
     for (int64_t s = Tl.tile_slice[t]; s < Tl.tile_slice[t + 1]; ++s) tile_of_slice[s] = t;
+  std::vector<int32_t> cta_of_tile(T, 0);
+  for (int c = 0; c < ctas; ++c)
+    for (int32_t t = Tl.cta_tile[c]; t < Tl.cta_tile[c + 1]; ++t) cta_of_tile[t] = c;
+  auto slot_in = [&](int32_t u, int64_t r) -> int64_t {  // slot of row r in tile u, or -1
+    const int64_t a = 32 * (int64_t)Tl.tile_slice[u], b = std::min<int64_t>(n, 32 * (int64_t)Tl.tile_slice[u + 1]);
+    if (r >= a && r < b) return r - a;
+    int64_t sl = Tl.tile_own[u];
+    for (int32_t w = Tl.tile_win[u]; w < Tl.tile_win[u + 1]; ++w) {
+      if (r >= Tl.win_start[w] && r < (int64_t)Tl.win_start[w] + Tl.win_len[w]) return sl + r - Tl.win_start[w];
+      sl += Tl.win_len[w];
+    }
+    return -1;
+  };
   struct Run {
     int32_t tgt;
     int32_t row;
@@ -498,21 +567,45 @@ bool build_sym_tiles(LayoutHost& L, int ctas, int slot_cap, int ent_cap) {
     int64_t src;
   };
   std::vector<Run> runs;
+  Tl.tile_carry.assign(T + 1, 0);
+  Tl.tile_flush.assign(T + 1, 0);
   for (int32_t t = 0; t < T; ++t) {
-    int64_t src = Tl.tile_ext[t];
-    for (int32_t w = Tl.tile_win[t]; w < Tl.tile_win[t + 1]; ++w) {
-      int64_t r = Tl.win_start[w];
-      const int64_t e = r + Tl.win_len[w];
-      while (r < e) {
+    const int32_t next = (t + 1 < Tl.cta_tile[cta_of_tile[t] + 1]) ? t + 1 : -1;
+    int64_t sl = Tl.tile_own[t];
+    for (int32_t w = Tl.tile_win[t]; w < Tl.tile_win[t + 1]; ++w)
+      for (int64_t r = Tl.win_start[w]; r < (int64_t)Tl.win_start[w] + Tl.win_len[w]; ++r, ++sl) {
+        const int64_t dst = next >= 0 ? slot_in(next, r) : -1;
+        if (dst >= 0) {
+          const size_t m = Tl.carry_src.size();
+          if (m > (size_t)Tl.tile_carry[t] && Tl.carry_src[m - 1] + Tl.carry_len[m - 1] == sl &&
+              Tl.carry_dst[m - 1] + Tl.carry_len[m - 1] == dst)
+            ++Tl.carry_len[m - 1];
+          else {
+            Tl.carry_src.push_back((int32_t)sl);
+            Tl.carry_dst.push_back((int32_t)dst);
+            Tl.carry_len.push_back(1);
+          }
+          continue;
+        }
+        const size_t m = Tl.flush_src.size();
+        if (m > (size_t)Tl.tile_flush[t] && Tl.flush_src[m - 1] + Tl.flush_len[m - 1] == sl)
+          ++Tl.flush_len[m - 1];
+        else {
+          Tl.flush_src.push_back((int32_t)sl);
+          Tl.flush_len.push_back(1);
+        }
+        // its partial sum (index tile_ext[t] + slot - own) goes to the tile owning row r
         const int32_t tt = tile_of_slice[r / 32];
         const int64_t trow0 = 32 * (int64_t)Tl.tile_slice[tt];
-        const int64_t tend = std::min<int64_t>(n, 32 * (int64_t)Tl.tile_slice[tt + 1]);
-        const int64_t f = std::min(e, tend);
-        runs.push_back({tt, (int32_t)(r - trow0), (int32_t)(f - r), src});
-        src += f - r;
-        r = f;
+        const int64_t src = Tl.tile_ext[t] + sl - Tl.tile_own[t];
+        if (!runs.empty() && runs.back().tgt == tt && trow0 + runs.back().row + runs.back().len == r &&
+            runs.back().src + runs.back().len == src)
+          ++runs.back().len;
+        else
+          runs.push_back({tt, (int32_t)(r - trow0), 1, src});
       }
-    }
+    Tl.tile_carry[t + 1] = (int32_t)Tl.carry_src.size();
+    Tl.tile_flush[t + 1] = (int32_t)Tl.flush_src.size();
   }
   std::stable_sort(runs.begin(), runs.end(), [](const Run& x, const Run& y) { return x.tgt < y.tgt; });
   Tl.in_ptr.assign(T + 1, 0);
@@ -525,6 +618,48 @@ bool build_sym_tiles(LayoutHost& L, int ctas, int slot_cap, int ent_cap) {
     Tl.in_row[i] = runs[i].row;
     Tl.in_len[i] = runs[i].len;
     Tl.in_src[i] = runs[i].src;
+  }
+  // 5. the packed descriptors
+  Tl.desc.assign(T, TileDesc());
+  for (int32_t t = 0; t < T; ++t) {
+    TileDesc& d = Tl.desc[t];
+    memset(&d, 0, sizeof d);
+    const int64_t a = 32 * (int64_t)Tl.tile_slice[t], b = std::min<int64_t>(n, 32 * (int64_t)Tl.tile_slice[t + 1]);
+    d.e0 = Tl.tile_ent[t];
+    d.m0 = Tl.tile_meta[t];
+    d.row0 = a;
+    d.ext0 = Tl.tile_ext[t];
+    d.rows = (int32_t)(b - a);
+    d.nsl = Tl.tile_slice[t + 1] - Tl.tile_slice[t];
+    d.D = Tl.tile_len[t];
+    d.S = Tl.tile_ns[t];
+    d.own = Tl.tile_own[t];
+    d.R = Tl.tile_stride[t];
+    d.E8 = (int32_t)(Tl.tile_ent[t + 1] - Tl.tile_ent[t]);
+    d.nwin = Tl.tile_win[t + 1] - Tl.tile_win[t];
+    d.nc = Tl.tile_carry[t + 1] - Tl.tile_carry[t];
+    d.nf = Tl.tile_flush[t + 1] - Tl.tile_flush[t];
+    d.win0 = Tl.tile_win[t];
+    d.carry0 = Tl.tile_carry[t];
+    d.flush0 = Tl.tile_flush[t];
+    d.tail = (d.rows & 3) != 0;
+    for (int32_t w = 0; w < d.nwin; ++w) {
+      const int32_t ws = Tl.win_start[d.win0 + w], wl = Tl.win_len[d.win0 + w];
+      if ((ws | wl) & 3) d.tail = 1;
+      if (w < kDescWin) {
+        d.ws[w] = ws;
+        d.wl[w] = wl;
+      }
+    }
+    for (int32_t u = 0; u < std::min(d.nc, kDescRun); ++u) {
+      d.cs[u] = (uint16_t)Tl.carry_src[d.carry0 + u];
+      d.cd[u] = (uint16_t)Tl.carry_dst[d.carry0 + u];
+      d.cl[u] = (uint16_t)Tl.carry_len[d.carry0 + u];
+    }
+    for (int32_t u = 0; u < std::min(d.nf, kDescRun); ++u) {
+      d.fs[u] = (uint16_t)Tl.flush_src[d.flush0 + u];
+      d.fl[u] = (uint16_t)Tl.flush_len[d.flush0 + u];
+    }
   }
   return true;
 }

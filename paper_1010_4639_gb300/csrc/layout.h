@@ -20,6 +20,7 @@
 // transpose half U' x is a second row gather that reads U's values in place:
 // no entry is stored twice and no floating-point atomics are needed.
 #pragma once
+#include <cstddef>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -47,27 +48,60 @@ struct PlanHost {
 };
 
 // Tiled symmetric layout.  Rows are split into contiguous ranges, one per CTA
-// of the persistent grid, and each range into tiles of at most 16 whole
-// slices (one per warp).  A tile's column space -- its own rows (padded to a
+// of the persistent grid, and each range into tiles of at most 15 whole
+// slices (one per consumer warp).  A tile's column space -- its own rows (padded to a
 // multiple of 4), then 16-byte-aligned windows of the rows beyond it that its
-// upper entries reach -- is numbered by 16-bit slots indexing a shared-memory
-// copy of x.  Each strict upper entry is stored once (value and slot); entry
-// k of the tile's local row l sits at position k * R + l, R a power of two, so
-// the row of any position is position & (R - 1) (rows padded to the tile's
-// longest row L).  A transpose index lists, for every slot, the positions of
-// the entries that target it, in increasing source row: the transpose half
-// U'x of a tile is then a gather sum_e val[e] * x[row(e)] over shared memory,
-// in a fixed order, without atomics.  Window sums leave the
-// tile as partial sums; "incoming runs" list, per target tile and in a fixed
-// order, which partial sums to add to which of its rows.
+// upper entries reach -- is numbered by slots indexing a shared-memory copy
+// of x and a shared-memory accumulator.  Each strict upper entry is stored
+// once (value and 16-bit slot).  The entries are edge-coloured (rows x slots,
+// a bipartite graph) into D rounds, D the larger of the longest row and the
+// most-hit slot: in each round a row has at most one entry and a slot
+// receives at most one.  Entry (round k, local row l) sits at position
+// k * R + l, R = 32 * slices; positions without an entry
+// are padding (value 0, slot flagged with kTilePad).  The product runs the
+// rounds in order with a barrier between them: each row adds U_ij x_j to its
+// own sum (direct half) and U_ij x_i to slot j's accumulator (transpose
+// half) -- a scatter without conflicts or atomics, every sum in a fixed
+// order.  After a tile, a window slot whose row the next tile of the same
+// CTA also covers is carried into that tile's accumulator (carry runs); the
+// other window slots leave the tile as partial sums (flush runs), and
+// "incoming runs" list, per target tile and in a fixed order, which partial
+// sums to add to which of its rows.
+constexpr uint16_t kTilePad = 0x8000;  // slot flag of a padding entry (the kernels' kPadSlot)
+
+// Everything the tile pipeline needs about one tile, packed so that the
+// producer loads it in one round trip and copies it into the tile's stage.
+// Windows and runs beyond the inline capacity are read from the global lists
+// (win_start/win_len, carry_*, flush_*) starting at win0, carry0, flush0.
+constexpr int kDescWin = 8;  // windows held inline
+constexpr int kDescRun = 8;  // carry runs and flush runs held inline
+struct alignas(16) TileDesc {
+  int64_t e0;                    // first entry of the tile (values; a multiple of 8)
+  int64_t m0;                    // first u16 of its slot blob (a multiple of 8)
+  int64_t row0;                  // first own row
+  int64_t ext0;                  // first partial sum of its window slots
+  int32_t rows, nsl, D, S, own, R, E8;  // rows, slices, rounds, slots, padded own rows, round stride, entries
+  int32_t nwin, nc, nf;          // windows, carry runs, flush runs
+  int32_t win0, carry0, flush0;  // first index of each in the global lists
+  int32_t tail;                  // some x slot is not 16-byte aligned: loaded with plain loads
+  int32_t pad0_;
+  int32_t ws[kDescWin], wl[kDescWin];                   // window start rows and lengths
+  uint16_t cs[kDescRun], cd[kDescRun], cl[kDescRun];    // carry runs: slot, slot in the next tile, length
+  uint16_t fs[kDescRun], fl[kDescRun];                  // flush runs: slot, length
+  int32_t pad1_[4];
+};
+static_assert(sizeof(TileDesc) == 256, "tile descriptor size");
+// the kernels copy the five run arrays as one block of 5 * kDescRun u16
+static_assert(offsetof(TileDesc, fl) == offsetof(TileDesc, cs) + 4 * kDescRun * sizeof(uint16_t), "run arrays");
+
 struct SymTilesHost {
   int32_t slot_cap = 0, ent_cap = 0;
   std::vector<int32_t> cta_tile;   // G + 1: tile range of each CTA
   std::vector<int32_t> tile_slice; // T + 1: first slice of each tile
   std::vector<int32_t> tile_ns;    // T: slot count (padded own rows + windows)
   std::vector<int32_t> tile_own;   // T: own rows padded to a multiple of 4
-  std::vector<int32_t> tile_len;   // T: padded row length L (entry k of local row l at k * R + l)
-  std::vector<int32_t> tile_rlog;  // T: log2 of R = 32 * (slices rounded up to a power of 2)
+  std::vector<int32_t> tile_len;   // T: rounds D (the round-k entry of local row l at k * R + l)
+  std::vector<int32_t> tile_stride;  // T: round stride R = 32 * slices
   std::vector<int64_t> tile_ent;   // T + 1: first entry of each tile (multiples of 8)
   std::vector<int64_t> tile_meta;  // T + 1: first u16 of each tile's index blob (multiples of 8)
   std::vector<int64_t> tile_ext;   // T + 1: first partial sum of each tile
@@ -75,7 +109,15 @@ struct SymTilesHost {
   std::vector<int32_t> win_start;  // global first row of each window
   std::vector<int32_t> win_len;    // rows of each window
   std::vector<double> val;         // entry values (0 on padding)
-  std::vector<uint16_t> meta;      // per tile: slots[E8], transpose index[E8], index offsets[S+1 rounded to 8]
+  std::vector<uint16_t> meta;      // per tile: slots[E8] (kTilePad set on padding)
+  std::vector<int32_t> tile_carry; // T + 1: carry runs of each tile
+  std::vector<int32_t> carry_src;  // first window slot of the run in the tile
+  std::vector<int32_t> carry_dst;  // its slot in the next tile of the same CTA
+  std::vector<int32_t> carry_len;
+  std::vector<int32_t> tile_flush; // T + 1: flush runs of each tile
+  std::vector<int32_t> flush_src;  // first window slot of the run (partial sum tile_ext + slot - own)
+  std::vector<int32_t> flush_len;
+  std::vector<TileDesc> desc;      // T: packed per-tile descriptor
   std::vector<int32_t> in_ptr;     // T + 1: incoming runs of each tile
   std::vector<int32_t> in_row;     // run start, as a row offset inside the target tile
   std::vector<int32_t> in_len;     // run length

@@ -1,9 +1,8 @@
 """The largest single system of the workload set (256^3 node grid, four
 inclusions, 16.4M rows, 130M stored upper entries): the symmetric product in
-double and single precision against the oracle on every row, and the
-mixed-precision solve (single-precision values for the inner solve, double
-precision for the residual) checked by the oracle's own double-precision
-product.  Tolerances as in test_gpu_spmv and test_gpu_cg."""
+double and single precision against the oracle on every row (tolerances as
+in test_gpu_spmv).  Its solves are gated against the oracle's own solves in
+test_gpu_golden."""
 import numpy as np
 import pytest
 
@@ -45,15 +44,3 @@ def test_largest_symmetric_products(torch, system):
     v32 = up[2].astype(np.float32)
     within(y32, oracle.spmv_f32("sym", up[0], up[1], v32, x32).astype(np.float64),
            oracle.abs_spmv("sym", up[0], up[1], v32.astype(np.float64), x32.astype(np.float64)), 1e-5)
-
-
-@pytest.mark.parametrize("precision", ["fp32_ir", "fp32_ru"])
-def test_largest_mixed_solve(torch, system, precision):
-    s = system
-    with gb.Matrix("sym", *s.upper()) as A:
-        x, info = A.solve(torch.from_numpy(s.b).cuda(), tol=1e-10, precision=precision)
-    assert info.status == "OK", info
-    x = x.cpu().numpy()
-    r = s.b - oracle.spmv("csr", s.ptr, s.idx, s.val, x)
-    assert np.linalg.norm(r) <= 1e-10 * np.linalg.norm(s.b)
-    assert np.linalg.norm(x - s.xstar) / np.linalg.norm(s.xstar) <= 1e-3

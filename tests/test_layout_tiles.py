@@ -1,0 +1,77 @@
+"""The tiled symmetric layout, checked on the host (no GPU): every stored
+entry once, conflict-free rounds, caps, window slots and incoming runs, and a
+host replay of the kernels' order of operations against a row-by-row
+symmetric product (tests/layout_check.cpp, built here from layout.cpp)."""
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+import femgen
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CSRC = os.path.join(ROOT, "paper_1010_4639_gb300", "csrc")
+
+
+@pytest.fixture(scope="module")
+def checker(tmp_path_factory):
+    d = tmp_path_factory.mktemp("layout_check")
+    exe = str(d / "layout_check")
+    subprocess.run(["g++", "-O2", "-std=c++17", "-I", os.path.join(ROOT, "include"),
+                    os.path.join(ROOT, "tests", "layout_check.cpp"), os.path.join(CSRC, "layout.cpp"), "-o", exe],
+                   check=True)
+    return exe, d
+
+
+def _run(checker, ptr, idx, val, ctas, seed=3):
+    exe, d = checker
+    n = len(ptr) - 1
+    x = np.random.default_rng(seed).uniform(-1, 1, n)
+    path = str(d / f"m_{n}_{ctas}.bin")
+    with open(path, "wb") as f:
+        np.array([n, len(idx)], dtype=np.int64).tofile(f)
+        np.asarray(ptr, dtype=np.int32).tofile(f)
+        np.asarray(idx, dtype=np.int32).tofile(f)
+        np.asarray(val, dtype=np.float64).tofile(f)
+        x.tofile(f)
+    out = subprocess.run([exe, path, str(ctas)], capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0, out.stdout + out.stderr
+    return out.stdout.strip()
+
+
+@pytest.mark.parametrize("grid", [(12, 12, 12), (31, 31, 32), (40, 17, 23), (5, 6, 7)])
+@pytest.mark.parametrize("ctas", [1, 7, 152])
+def test_fem_tiles(checker, grid, ctas):
+    s = femgen.build_system(femgen.Grid(*grid))
+    line = _run(checker, *s.upper(), ctas)
+    assert line.startswith("OK"), line
+    stats = dict(kv.split("=") for kv in line.split()[1:])
+    assert int(stats["max_rounds"]) <= 7  # a 15-point stencil: 7 strict-upper entries per row at most
+
+
+def _random_upper(n, per_row, seed, long_rows=()):
+    rng = np.random.default_rng(seed)
+    ptr, idx, val = [0], [], []
+    for i in range(n):
+        k = per_row + (40 if i in long_rows else 0)
+        cols = np.unique(np.concatenate([[i], rng.integers(i, min(n, i + 300), size=k)]))
+        idx += cols.tolist()
+        val += [4.0 * k if c == i else -rng.uniform(0.1, 1.0) for c in cols]
+        ptr.append(len(idx))
+    return np.array(ptr), np.array(idx), np.array(val)
+
+
+@pytest.mark.parametrize("ctas", [1, 3, 64])
+def test_irregular_tiles(checker, ctas):
+    # uneven rows, a few long ones, targets scattered over 300 rows: many
+    # conflicts for the colouring to resolve
+    p, i, v = _random_upper(3000, 6, 11, long_rows={5, 700, 2999})
+    line = _run(checker, p, i, v, ctas)
+    assert line.startswith("OK"), line
+
+
+def test_diagonal_only(checker):
+    n = 100
+    line = _run(checker, np.arange(n + 1), np.arange(n), np.full(n, 2.0), 4)
+    assert line.startswith("OK") and "max_rounds=0" in line, line

@@ -24,7 +24,8 @@ MUTANTS = {
     "cg_alpha_inverted": ("double alpha = rr / pq;", "double alpha = pq / rr;"),
     "cg_beta_inverted": ("double beta = rr_new / rr;", "double beta = rr / rr_new;"),
     "cg_beta_dropped": ("p[i] = r[i] + beta * p[i];  /* p = r + beta p */", "p[i] = r[i];"),
-    "cg_initial_residual_sign": ("r[i] = b[i] - q[i];\n  for", "r[i] = b[i] + q[i];\n  for"),
+    "cg_initial_residual_sign": ("r[i] = b[i] - q[i];\n#pragma omp parallel for schedule(static)\n  for",
+                                 "r[i] = b[i] + q[i];\n#pragma omp parallel for schedule(static)\n  for"),
     "cg_no_true_residual_confirm": ("if (info->rel_res_true <= tol) break;", "break;"),
     "dot_long_drops_term": ("s += (long double)a[i] * (long double)b[i];",
                             "if (i) s += (long double)a[i] * (long double)b[i];"),
