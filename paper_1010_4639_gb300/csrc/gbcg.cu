@@ -22,7 +22,8 @@
 using namespace gbcg;
 
 static_assert(kTilePad == kPadSlot, "the layout's padding flag is the kernels'");
-static_assert(kTileSlot < kPadSlot, "slot numbers stay below the padding flag");
+static_assert(TileCaps<float>::kSlot < kPadSlot && TileCaps<double>::kSlot < kPadSlot,
+              "slot numbers stay below the padding flag");
 
 namespace {
 
@@ -64,6 +65,9 @@ std::vector<float> to_f32(const std::vector<double>& v) {
   return o;
 }
 
+// Tile caps of each precision's layout (the kernels' TileCaps).
+constexpr int kTileSlices32 = kTileWarps * TileCaps<float>::kRpt, kTileSlices64 = kTileWarps * TileCaps<double>::kRpt;
+
 int env_int(const char* name, int dflt) {
   const char* s = getenv(name);
   return (s && *s) ? atoi(s) : dflt;
@@ -77,6 +81,103 @@ namespace gbcg {
 void set_last_error(const std::string& m) { g_last_error = m; }
 }  // namespace gbcg
 
+// One tiled symmetric layout on the device (layout.h, SymTilesHost): the
+// single-precision product and the double-precision product each have their
+// own (tiles of up to 30 and 15 slices), over the same CTA row ranges.
+struct DevTiles {
+  int32_t *cta_tile = nullptr, *tile_slice = nullptr, *tile_ns = nullptr, *tile_own = nullptr, *tile_len = nullptr,
+          *tile_stride = nullptr, *tile_win = nullptr, *win_start = nullptr, *win_len = nullptr;
+  int64_t *tile_ent = nullptr, *tile_meta = nullptr, *tile_ext = nullptr, *in_src = nullptr;
+  uint16_t* meta = nullptr;
+  TileDesc* desc = nullptr;
+  int32_t *carry_src = nullptr, *carry_dst = nullptr, *carry_len = nullptr, *flush_src = nullptr, *flush_len = nullptr;
+  int32_t *in_ptr = nullptr, *in_row = nullptr, *in_len = nullptr;
+  void* val = nullptr;   // float or double values, in the layout's order
+  void* part = nullptr;  // window partial sums, same type
+  int64_t ntiles = 0, next = 0, slots = 0;
+
+  void release() {
+    void* p[] = {cta_tile, tile_slice, tile_ns, tile_own, tile_len, tile_stride, tile_win, win_start, win_len,
+                 tile_ent, tile_meta, tile_ext, in_src, meta, desc, carry_src, carry_dst, carry_len, flush_src,
+                 flush_len, in_ptr, in_row, in_len, val, part};
+    for (void* d : p)
+      if (d) cudaFree(d);
+    *this = DevTiles();
+  }
+  template <typename V>
+  SymDev<V> dev() const {
+    SymDev<V> t;
+    t.desc = desc;
+    t.carry_src = carry_src;
+    t.carry_dst = carry_dst;
+    t.carry_len = carry_len;
+    t.flush_src = flush_src;
+    t.flush_len = flush_len;
+    t.cta_tile = cta_tile;
+    t.tile_slice = tile_slice;
+    t.tile_ns = tile_ns;
+    t.tile_own = tile_own;
+    t.tile_len = tile_len;
+    t.tile_stride = tile_stride;
+    t.tile_ent = tile_ent;
+    t.tile_meta = tile_meta;
+    t.tile_ext = tile_ext;
+    t.tile_win = tile_win;
+    t.win_start = win_start;
+    t.win_len = win_len;
+    t.val = (const V*)val;
+    t.meta = meta;
+    t.in_ptr = in_ptr;
+    t.in_row = in_row;
+    t.in_len = in_len;
+    t.in_src = in_src;
+    t.part = (V*)part;
+    return t;
+  }
+};
+
+// Uploads one tiled layout; V is the type of its values.
+template <typename V>
+int upload_tiles(DevTiles& D, const SymTilesHost& Tl, cudaStream_t s, int64_t& B) {
+  D.ntiles = (int64_t)Tl.tile_ns.size();
+  D.next = Tl.tile_ext.back();
+  D.slots = (int64_t)Tl.val.size();
+  if (int rc = upload(&D.cta_tile, Tl.cta_tile, s, B)) return rc;
+  if (int rc = upload(&D.tile_slice, Tl.tile_slice, s, B)) return rc;
+  if (int rc = upload(&D.tile_ns, Tl.tile_ns, s, B)) return rc;
+  if (int rc = upload(&D.tile_own, Tl.tile_own, s, B)) return rc;
+  if (int rc = upload(&D.tile_len, Tl.tile_len, s, B)) return rc;
+  if (int rc = upload(&D.tile_stride, Tl.tile_stride, s, B)) return rc;
+  if (int rc = upload(&D.tile_ent, Tl.tile_ent, s, B)) return rc;
+  if (int rc = upload(&D.tile_meta, Tl.tile_meta, s, B)) return rc;
+  if (int rc = upload(&D.tile_ext, Tl.tile_ext, s, B)) return rc;
+  if (int rc = upload(&D.tile_win, Tl.tile_win, s, B)) return rc;
+  if (int rc = upload(&D.win_start, Tl.win_start, s, B)) return rc;
+  if (int rc = upload(&D.win_len, Tl.win_len, s, B)) return rc;
+  if (int rc = upload(&D.meta, Tl.meta, s, B)) return rc;
+  if (int rc = upload(&D.in_ptr, Tl.in_ptr, s, B)) return rc;
+  if (int rc = upload(&D.in_row, Tl.in_row, s, B)) return rc;
+  if (int rc = upload(&D.in_len, Tl.in_len, s, B)) return rc;
+  if (int rc = upload(&D.in_src, Tl.in_src, s, B)) return rc;
+  if (int rc = upload(&D.desc, Tl.desc, s, B)) return rc;
+  if (int rc = upload(&D.carry_src, Tl.carry_src, s, B)) return rc;
+  if (int rc = upload(&D.carry_dst, Tl.carry_dst, s, B)) return rc;
+  if (int rc = upload(&D.carry_len, Tl.carry_len, s, B)) return rc;
+  if (int rc = upload(&D.flush_src, Tl.flush_src, s, B)) return rc;
+  if (int rc = upload(&D.flush_len, Tl.flush_len, s, B)) return rc;
+  V* val = nullptr;
+  if constexpr (sizeof(V) == 4) {
+    if (int rc = upload(&val, to_f32(Tl.val), s, B)) return rc;
+  } else {
+    if (int rc = upload(&val, Tl.val, s, B)) return rc;
+  }
+  D.val = val;
+  V* part = nullptr;
+  if (int rc = dalloc(&part, (size_t)std::max<int64_t>(D.next, 1), B)) return rc;
+  D.part = part;
+  return 0;
+}
+
 struct gbcg_matrix_s {
   int32_t format = 0, index_base = 0;
   int64_t n = 0, nnz_input = 0, nnz_full = 0, slots = 0, plan_slots = 0;
@@ -89,20 +190,10 @@ struct gbcg_matrix_s {
   int64_t nslices = 0, nlong = 0, bytes = 0;
   int sym = 0;
   int mode = kGather;       // kGather (CSR/CSC), kPlan or kTiles (symmetric)
-  int64_t ntiles = 0, next = 0, tile_slots = 0;
-  // tiled symmetric layout (device)
-  int32_t *t_cta_tile = nullptr, *t_tile_slice = nullptr, *t_tile_ns = nullptr, *t_tile_own = nullptr;
-  int32_t *t_tile_len = nullptr, *t_tile_stride = nullptr, *t_tile_win = nullptr, *t_win_start = nullptr,
-          *t_win_len = nullptr;
-  int64_t *t_tile_ent = nullptr, *t_tile_meta = nullptr, *t_tile_ext = nullptr, *t_in_src = nullptr;
-  uint16_t* t_meta = nullptr;
-  TileDesc* t_desc = nullptr;
-  int32_t *t_carry_src = nullptr, *t_carry_dst = nullptr, *t_carry_len = nullptr, *t_flush_src = nullptr,
-          *t_flush_len = nullptr;
-  double* t_val64 = nullptr;
-  float* t_val32 = nullptr;
-  int32_t *t_in_ptr = nullptr, *t_in_row = nullptr, *t_in_len = nullptr;
-  double* t_part = nullptr;  // window partial sums (used as float for the single-precision product)
+  // tiled symmetric layouts (device): single- and double-precision products
+  DevTiles t32, t64;
+  int32_t *u_map_t32 = nullptr;  // value map of the single-precision tiles (u_map_main: double-precision)
+  int64_t u_len_t32 = 0;
   // layout (device)
   int64_t* sl_ptr = nullptr;
   int32_t* col = nullptr;
@@ -144,33 +235,7 @@ struct gbcg_matrix_s {
   OpDev<V> op() const;
   template <typename V>
   SymDev<V> tiles() const {
-    SymDev<V> t;
-    t.desc = t_desc;
-    t.carry_src = t_carry_src;
-    t.carry_dst = t_carry_dst;
-    t.carry_len = t_carry_len;
-    t.flush_src = t_flush_src;
-    t.flush_len = t_flush_len;
-    t.cta_tile = t_cta_tile;
-    t.tile_slice = t_tile_slice;
-    t.tile_ns = t_tile_ns;
-    t.tile_own = t_tile_own;
-    t.tile_len = t_tile_len;
-    t.tile_stride = t_tile_stride;
-    t.tile_ent = t_tile_ent;
-    t.tile_meta = t_tile_meta;
-    t.tile_ext = t_tile_ext;
-    t.tile_win = t_tile_win;
-    t.win_start = t_win_start;
-    t.win_len = t_win_len;
-    t.val = sizeof(V) == 8 ? (const V*)(const void*)t_val64 : (const V*)(const void*)t_val32;
-    t.meta = t_meta;
-    t.in_ptr = t_in_ptr;
-    t.in_row = t_in_row;
-    t.in_len = t_in_len;
-    t.in_src = t_in_src;
-    t.part = (V*)(void*)t_part;
-    return t;
+    return sizeof(V) == 4 ? t32.dev<V>() : t64.dev<V>();
   }
   int spmv_blocks() const { return (int)std::max<int64_t>(1, (nslices + nlong + 7) / 8); }
 };
@@ -225,12 +290,10 @@ void free_matrix(gbcg_matrix_s* M) {
   void* dev[] = {M->sl_ptr, M->col, M->col16, M->val64, M->val32, M->long_mask, M->long_row, M->long_ptr, M->long_col,
                  M->long_val64, M->long_val32, M->diag64, M->diag32, M->pl_ptr, M->pl_i, M->pl_k,
                  M->cta_slice, M->cta_long, M->r, M->p, M->q, M->bstage, M->xstage, M->r32, M->p32, M->q32,
-                 M->d32, M->rhs32, M->part, M->sums, M->bar, M->st, M->t_cta_tile, M->t_tile_slice,
-                 M->t_tile_ns, M->t_tile_own, M->t_tile_len, M->t_tile_stride, M->t_tile_win, M->t_win_start, M->t_win_len,
-                 M->t_tile_ent, M->t_tile_meta, M->t_tile_ext, M->t_in_src, M->t_meta, M->t_val64, M->t_val32,
-                 M->t_in_ptr, M->t_in_row, M->t_in_len, M->t_part, M->u_map_main, M->u_map_long, M->u_map_diag,
-                 M->u_stage, M->s64, M->z64, M->w64a, M->w64b, M->t_desc, M->t_carry_src, M->t_carry_dst,
-                 M->t_carry_len, M->t_flush_src, M->t_flush_len};
+                 M->d32, M->rhs32, M->part, M->sums, M->bar, M->st, M->u_map_main, M->u_map_long, M->u_map_diag,
+                 M->u_map_t32, M->u_stage, M->s64, M->z64, M->w64a, M->w64b};
+  M->t32.release();
+  M->t64.release();
   for (void* d : dev)
     if (d) cudaFree(d);
   if (M->st_h) cudaFreeHost(M->st_h);
@@ -701,45 +764,26 @@ int gbcg_create(gbcg_matrix_t* out, int32_t format, int64_t n, int64_t nnz, cons
     return 0;
   };
   TRY(choose_grid());
-  if (M->mode == kTiles && !build_sym_tiles(L, M->grid, kTileSlot, kTileEnt)) {
+  SymTilesHost T32, T64;
+  if (M->mode == kTiles &&
+      (!build_sym_tiles(L, M->grid, TileCaps<float>::kSlot, TileCaps<float>::kEnt, kTileSlices32, T32) ||
+       !build_sym_tiles(L, M->grid, TileCaps<double>::kSlot, TileCaps<double>::kEnt, kTileSlices64, T64))) {
     M->mode = kPlan;  // a single slice exceeds what a tile holds
     TRY(choose_grid());
   }
   std::vector<int32_t> cs, cl(M->grid + 1, 0);
   if (M->mode == kTiles) {
-    const SymTilesHost& Tl = L.tiles;
+    // both layouts cut the rows at the same CTA boundaries (the vector
+    // phases of a solve run over those rows)
     cs.resize(M->grid + 1);
-    for (int c = 0; c <= M->grid; ++c) cs[c] = Tl.tile_slice[Tl.cta_tile[c]];
-    M->ntiles = (int64_t)Tl.tile_ns.size();
-    M->next = Tl.tile_ext.back();
-    M->tile_slots = (int64_t)Tl.val.size();
-    TRY(upload(&M->t_cta_tile, Tl.cta_tile, s, B));
-    TRY(upload(&M->t_tile_slice, Tl.tile_slice, s, B));
-    TRY(upload(&M->t_tile_ns, Tl.tile_ns, s, B));
-    TRY(upload(&M->t_tile_own, Tl.tile_own, s, B));
-    TRY(upload(&M->t_tile_len, Tl.tile_len, s, B));
-    TRY(upload(&M->t_tile_stride, Tl.tile_stride, s, B));
-    TRY(upload(&M->t_tile_ent, Tl.tile_ent, s, B));
-    TRY(upload(&M->t_tile_meta, Tl.tile_meta, s, B));
-    TRY(upload(&M->t_tile_ext, Tl.tile_ext, s, B));
-    TRY(upload(&M->t_tile_win, Tl.tile_win, s, B));
-    TRY(upload(&M->t_win_start, Tl.win_start, s, B));
-    TRY(upload(&M->t_win_len, Tl.win_len, s, B));
-    TRY(upload(&M->t_meta, Tl.meta, s, B));
-    TRY(upload(&M->t_val64, Tl.val, s, B));
-    TRY(upload(&M->t_val32, to_f32(Tl.val), s, B));
-    TRY(upload(&M->t_in_ptr, Tl.in_ptr, s, B));
-    TRY(upload(&M->t_in_row, Tl.in_row, s, B));
-    TRY(upload(&M->t_in_len, Tl.in_len, s, B));
-    TRY(upload(&M->t_in_src, Tl.in_src, s, B));
-    TRY(upload(&M->t_desc, Tl.desc, s, B));
-    TRY(upload(&M->t_carry_src, Tl.carry_src, s, B));
-    TRY(upload(&M->t_carry_dst, Tl.carry_dst, s, B));
-    TRY(upload(&M->t_carry_len, Tl.carry_len, s, B));
-    TRY(upload(&M->t_flush_src, Tl.flush_src, s, B));
-    TRY(upload(&M->t_flush_len, Tl.flush_len, s, B));
-    TRY(dalloc(&M->t_part, (size_t)std::max<int64_t>(M->next, 1), B));
-    M->slots = M->tile_slots;
+    for (int c = 0; c <= M->grid; ++c) {
+      cs[c] = T64.tile_slice[T64.cta_tile[c]];
+      if (cs[c] != T32.tile_slice[T32.cta_tile[c]])
+        return bail(fail(GBCG_ERR_INVALID, "tile layouts of the two precisions cut the rows differently"));
+    }
+    TRY(upload_tiles<float>(M->t32, T32, s, B));
+    TRY(upload_tiles<double>(M->t64, T64, s, B));
+    M->slots = M->t64.slots;
     M->plan_slots = 0;
     TRY(upload(&M->long_mask, std::vector<uint32_t>(std::max<int64_t>(M->nslices, 1), 0u), s, B));
   } else {
@@ -934,8 +978,8 @@ int gbcg_stats(gbcg_matrix_t A, gbcg_matrix_stats* out) {
   out->format = A->format;
   out->grid_ctas = A->grid;
   out->layout = A->mode;
-  out->tiles = (int32_t)A->ntiles;
-  out->ext_slots = A->next;
+  out->tiles = (int32_t)A->t64.ntiles;  // the double-precision layout's (the single-precision one has about half)
+  out->ext_slots = A->t64.next;
   return GBCG_OK;
 }
 
@@ -956,7 +1000,10 @@ int gbcg_update_values(gbcg_matrix_t A, const double* val, int32_t memory, void*
     std::string err;
     if (int rc = build_layout(A->format, A->n, nnz, A->h_ptr.data(), A->h_idx.data(), iv.data(), A->index_base, L, err))
       return fail(rc, "rebuilding the value map: " + err);
-    if (A->mode == kTiles && !build_sym_tiles(L, A->grid, kTileSlot, kTileEnt))
+    SymTilesHost T32, T64;
+    if (A->mode == kTiles &&
+        (!build_sym_tiles(L, A->grid, TileCaps<float>::kSlot, TileCaps<float>::kEnt, kTileSlices32, T32) ||
+         !build_sym_tiles(L, A->grid, TileCaps<double>::kSlot, TileCaps<double>::kEnt, kTileSlices64, T64)))
       return fail(GBCG_ERR_INVALID, "rebuilding the value map: tiles differ from the handle's");
     auto to_map = [](const std::vector<double>& v) {
       std::vector<int32_t> m(v.size());
@@ -965,9 +1012,12 @@ int gbcg_update_values(gbcg_matrix_t A, const double* val, int32_t memory, void*
     };
     int64_t& B = A->bytes;
     if (A->mode == kTiles) {
-      if ((int64_t)L.tiles.val.size() != A->tile_slots) return fail(GBCG_ERR_INVALID, "value map: tile size mismatch");
-      if (int rc = upload(&A->u_map_main, to_map(L.tiles.val), s, B)) return rc;
-      A->u_len_main = (int64_t)L.tiles.val.size();
+      if ((int64_t)T64.val.size() != A->t64.slots || (int64_t)T32.val.size() != A->t32.slots)
+        return fail(GBCG_ERR_INVALID, "value map: tile size mismatch");
+      if (int rc = upload(&A->u_map_main, to_map(T64.val), s, B)) return rc;
+      A->u_len_main = (int64_t)T64.val.size();
+      if (int rc = upload(&A->u_map_t32, to_map(T32.val), s, B)) return rc;
+      A->u_len_t32 = (int64_t)T32.val.size();
     } else {
       if (int rc = upload(&A->u_map_main, to_map(L.A.val), s, B)) return rc;
       A->u_len_main = (int64_t)L.A.val.size();
@@ -995,7 +1045,8 @@ int gbcg_update_values(gbcg_matrix_t A, const double* val, int32_t memory, void*
     return 0;
   };
   if (A->mode == kTiles) {
-    if (int rc = run(A->u_map_main, A->u_len_main, A->t_val64, A->t_val32)) return rc;
+    if (int rc = run(A->u_map_main, A->u_len_main, (double*)A->t64.val, nullptr)) return rc;
+    if (int rc = run(A->u_map_t32, A->u_len_t32, nullptr, (float*)A->t32.val)) return rc;
   } else {
     if (int rc = run(A->u_map_main, A->u_len_main, A->val64, A->val32)) return rc;
     if (int rc = run(A->u_map_long, A->u_len_long, A->long_val64, A->long_val32)) return rc;

@@ -163,9 +163,20 @@ constexpr size_t pipe_smem_bytes() { return sizeof(Stage<V>) * gather_stages<V>(
 // bulk copies: values, slots, diagonal, x over the tile's slots) and two
 // accumulators over the slots (tiles alternate between them, so one can be
 // cleared while the other is still being read).
-constexpr int kTileEnt = 4096;   // padded entries of a tile
-constexpr int kTileSlot = 2048;  // slots of a tile
-constexpr int kTileRows = 32 * kTileWarps;  // 15 slices
+// Caps of a tile, per precision: a consumer thread takes kRpt rows of the
+// tile (rows l and l + 480), so single-precision tiles run up to 30 slices
+// (960 rows) and amortise the per-tile work (stage wait, clears, epilogue:
+// ~1000-1400 cycles on GB300) over twice the rows; double-precision tiles,
+// whose stages are twice as large, stay at 15 slices.
+template <typename V> struct TileCaps;
+template <> struct TileCaps<float> {
+  static constexpr int kRpt = 2, kEnt = 8192, kSlot = 3072;
+};
+template <> struct TileCaps<double> {
+  static constexpr int kRpt = 1, kEnt = 4096, kSlot = 2048;
+};
+template <typename V>
+constexpr int tile_rows() { return 32 * kTileWarps * TileCaps<V>::kRpt; }
 constexpr uint16_t kPadSlot = 0x8000;  // slot flag of a padding entry
 // A stage: the tile's descriptor (copied in by the producer warp before it
 // issues the stage's bulk copies, published to the consumers by the same
@@ -173,22 +184,21 @@ constexpr uint16_t kPadSlot = 0x8000;  // slot flag of a padding entry
 template <typename V>
 struct alignas(16) TileStage {
   TileDesc desc;
-  V val[kTileEnt];
-  uint16_t meta[kTileEnt + 8];  // slot of each entry (kPadSlot: padding)
-  V diag[kTileRows];
-  V xs[kTileSlot];
+  V val[TileCaps<V>::kEnt];
+  uint16_t meta[TileCaps<V>::kEnt + 8];  // slot of each entry (kPadSlot: padding)
+  V diag[tile_rows<V>()];
+  V xs[TileCaps<V>::kSlot];
 };
-// Tile stages per CTA.  A stage holds ~35 KB (single precision) or ~61 KB
-// (double); at about 44 GB/s of HBM per SM and a fill latency of 1-2 us an
-// SM needs ~90 KB in flight, so single precision keeps five stages (four in
-// flight while one is consumed) and double precision three.
+// Tile stages per CTA: three in each precision (~64 KB each in single,
+// ~61 KB in double precision), two in flight while one is consumed, which
+// keeps the copies several tiles ahead of the consumers at GB300's HBM rate.
 template <typename V>
-__host__ __device__ constexpr int tile_stages() { return sizeof(V) == 4 ? 5 : 3; }
-constexpr int kMaxTileStages = 5;  // "full" and "empty" mbarriers per CTA: one pair per stage
+__host__ __device__ constexpr int tile_stages() { return 3; }
+constexpr int kMaxTileStages = 3;  // "full" and "empty" mbarriers per CTA: one pair per stage
 template <typename V>
 struct alignas(16) TileSmem {
   TileStage<V> st[tile_stages<V>()];
-  V acc[2][kTileSlot];
+  V acc[2][TileCaps<V>::kSlot];
   uint16_t runs[5 * kDescRun];  // the current tile's inline carry and flush runs (the consumers' copy)
 };
 static_assert(sizeof(TileDesc) % 16 == 0, "stage payload alignment");
@@ -206,7 +216,9 @@ struct TilePipe {
   // (producer) and of the fills waited for (consumers), and whether the
   // stage has been filled at all in this launch
   uint32_t iss_par, wait_par, used;
-  uint64_t policy;
+  uint64_t policy;       // matrix streams (read once per product): evict first
+  uint64_t policy_x;     // x windows (each x read by up to three tiles' windows): normal, so they
+                         // outlive the evict-first matrix stream in L2
   long long limit_ns;
   bool failed;
 };
@@ -281,6 +293,11 @@ __device__ __forceinline__ void fence_proxy_async_global() {
 __device__ __forceinline__ uint64_t policy_evict_first() {
   uint64_t p;
   asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t policy_evict_normal() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(p));
   return p;
 }
 // Global -> shared bulk copy (16-byte aligned addresses, size a multiple of 16).
@@ -654,12 +671,12 @@ __device__ __forceinline__ void tile_issue(const OpDev<V>& A, const SymDev<V>& T
   if (vb) bulk_g2s(st.val, T.val + d.e0, vb, bar, tp.policy);
   if (mb) bulk_g2s(st.meta, T.meta + d.m0, mb, bar, tp.policy);
   bulk_g2s(st.diag, A.diag + d.row0, db, bar, tp.policy);
-  if (own_bulk && d.rows > 0) bulk_g2s(st.xs, x + d.row0, (uint32_t)(d.rows * sizeof(V)), bar, tp.policy);
+  if (own_bulk && d.rows > 0) bulk_g2s(st.xs, x + d.row0, (uint32_t)(d.rows * sizeof(V)), bar, tp.policy_x);
   int32_t slot = d.own;
   for (int w = 0; w < d.nwin; ++w) {
     int32_t ws, wl;
     tile_window(d, T, w, ws, wl);
-    if (((ws | wl) & 3) == 0 && wl > 0) bulk_g2s(st.xs + slot, x + ws, (uint32_t)(wl * sizeof(V)), bar, tp.policy);
+    if (((ws | wl) & 3) == 0 && wl > 0) bulk_g2s(st.xs + slot, x + ws, (uint32_t)(wl * sizeof(V)), bar, tp.policy_x);
     slot += wl;
   }
   tp.iss_par ^= 1u << bf;
@@ -705,12 +722,19 @@ __device__ __forceinline__ void sym_tiles(const OpDev<V>& A, const SymDev<V>& T,
   if (t0 >= t1) return;
   if (warp == kTileWarps) {
     // producer: lane 0 waits for a free stage and issues its copies; lanes
-    // 0..15 bring the tile's descriptor into the stage first.  The next
-    // tile's descriptor is loaded while the current one is issued, so its
-    // round trip overlaps the wait for the next free stage.
+    // 0..15 bring the tile's descriptor into the stage first.  Descriptors
+    // are loaded kDescAhead tiles ahead into a register ring (lane l holds
+    // the l-th 16 bytes of each): with only the next one in flight, the
+    // producer issued one tile per DRAM round trip (~1 us), which bounded the
+    // product (measured 1.3 us per tile against ~0.4 us of consumer work).
     constexpr int kDescVecs = (int)(sizeof(TileDesc) / 16);
-    int4 dnext = make_int4(0, 0, 0, 0);
-    if (lane < kDescVecs) dnext = __ldg(reinterpret_cast<const int4*>(T.desc + t0) + lane);
+    constexpr int kDescAhead = 6;
+    int4 dq[kDescAhead];
+#pragma unroll
+    for (int k = 0; k < kDescAhead; ++k) {
+      dq[k] = make_int4(0, 0, 0, 0);
+      if (lane < kDescVecs && t0 + k < t1) dq[k] = __ldg(reinterpret_cast<const int4*>(T.desc + t0 + k) + lane);
+    }
     for (int32_t t = t0; t < t1; ++t) {
       const int b = (int)((t - t0) % NST);
       int ok = !tp.failed;
@@ -725,8 +749,11 @@ __device__ __forceinline__ void sym_tiles(const OpDev<V>& A, const SymDev<V>& T,
       }
       __syncwarp();  // lane 0's wait for the free stage is ordered before the lanes' writes
       TileStage<V>& st = sm->st[b];
-      if (lane < kDescVecs) reinterpret_cast<int4*>(&st.desc)[lane] = dnext;
-      if (lane < kDescVecs && t + 1 < t1) dnext = __ldg(reinterpret_cast<const int4*>(T.desc + t + 1) + lane);
+      if (lane < kDescVecs) reinterpret_cast<int4*>(&st.desc)[lane] = dq[0];
+#pragma unroll
+      for (int k = 0; k + 1 < kDescAhead; ++k) dq[k] = dq[k + 1];
+      if (lane < kDescVecs && t + kDescAhead < t1)
+        dq[kDescAhead - 1] = __ldg(reinterpret_cast<const int4*>(T.desc + t + kDescAhead) + lane);
       __syncwarp();
       if (lane == 0) tile_issue(A, T, st, tp, b, x);
       __syncwarp();
@@ -741,7 +768,8 @@ __device__ __forceinline__ void sym_tiles(const OpDev<V>& A, const SymDev<V>& T,
   }
   // the first tile's accumulator starts at zero (the barrier of the first
   // tile orders this before its rounds)
-  for (int sl = threadIdx.x; sl < kTileSlot; sl += NC_THREADS) sm->acc[0][sl] = V(0);
+  for (int v4 = threadIdx.x; v4 < (int)(TileCaps<V>::kSlot * sizeof(V) / 16); v4 += NC_THREADS)
+    reinterpret_cast<int4*>(sm->acc[0])[v4] = make_int4(0, 0, 0, 0);
   for (int32_t t = t0; t < t1; ++t) {
     const int j = (int)(t - t0), bf = j % NST;
     TileStage<V>& st = sm->st[bf];
@@ -761,52 +789,78 @@ __device__ __forceinline__ void sym_tiles(const OpDev<V>& A, const SymDev<V>& T,
     tp.wait_par ^= 1u << bf;
     // the tile's geometry into registers (the descriptor goes with the stage)
     const TileDesc& d = st.desc;
-    const int g_rows = d.rows, g_nsl = d.nsl, g_D = d.D, g_S = d.S, g_own = d.own, R = d.R;
+    const int g_rows = d.rows, g_D = d.D, g_S = d.S, g_own = d.own, R = d.R;
     const int g_nc = d.nc, g_nf = d.nf, g_c0 = d.carry0, g_f0 = d.flush0;
     const int64_t g_row0 = d.row0, g_ext0 = d.ext0;
     // the next tile's accumulator is cleared here, its carried values are
     // written after this tile's rounds; this tile's inline runs are kept for
     // the end of the tile (the stage is released before)
-    for (int sl = threadIdx.x; sl < kTileSlot; sl += NC_THREADS) acc_next[sl] = V(0);
+    for (int v4 = threadIdx.x; v4 < (int)(TileCaps<V>::kSlot * sizeof(V) / 16); v4 += NC_THREADS)
+      reinterpret_cast<int4*>(acc_next)[v4] = make_int4(0, 0, 0, 0);
     if (threadIdx.x < 5 * kDescRun) sm->runs[threadIdx.x] = (&d.cs[0])[threadIdx.x];  // cs, cd, cl, fs, fl in order
     const uint16_t* __restrict__ slot = st.meta;
     const V* __restrict__ val = st.val;
     const V* __restrict__ xs = st.xs;
-    // rounds: in round k the row's round-k entry (i, j) adds U_ij x_j to the
-    // row's direct sum and U_ij x_i to slot j's accumulator; no two entries of
-    // a round share a slot, so the scatter needs no atomics, and the barrier
-    // after each round orders the additions into a slot
-    V xi = V(0), dg = V(0), direct = V(0);
-    const int own_row = warp * 32 + lane;
-    const bool mine = warp < g_nsl && own_row < g_rows;
-    if (mine) {
-      xi = xs[own_row];
-      dg = st.diag[own_row];
+    // rounds: in round k each row's round-k entry (i, j) adds U_ij x_j to
+    // the row's direct sum and U_ij x_i to slot j's accumulator; no two
+    // entries of a round share a slot (over all the tile's rows), so the
+    // scatter needs no atomics, and the barrier after each round orders the
+    // additions into a slot.  Thread t takes rows t and t + 480 (single
+    // precision) or row t (double precision).
+    constexpr int RPT = TileCaps<V>::kRpt;
+    V xi[RPT], dg[RPT], direct[RPT];
+    bool mine[RPT];
+#pragma unroll
+    for (int h = 0; h < RPT; ++h) {
+      const int row = threadIdx.x + h * NC_THREADS;
+      mine[h] = row < g_rows;
+      xi[h] = mine[h] ? xs[row] : V(0);
+      dg[h] = mine[h] ? st.diag[row] : V(0);
+      direct[h] = V(0);
     }
-    int e = own_row;
-    uint16_t sn = mine && g_D > 0 ? slot[e] : kPadSlot;
-    V vn = mine && g_D > 0 ? val[e] : V(0);
-    for (int k = 0; k < g_D; ++k) {
-      const uint16_t s16 = sn;
-      const V v = vn;
-      e += R;
-      if (mine && k + 1 < g_D) {  // the next round's entry, loaded before this round's chain
-        sn = slot[e];
-        vn = val[e];
+    {
+      // each round's entries are loaded one round ahead, before the current
+      // round's chain of dependent shared-memory accesses
+      uint32_t sn[RPT];
+      V vn[RPT];
+#pragma unroll
+      for (int h = 0; h < RPT; ++h) {
+        const int e = threadIdx.x + h * NC_THREADS;
+        sn[h] = mine[h] && g_D > 0 ? (uint32_t)slot[e] : (uint32_t)kPadSlot;
+        vn[h] = mine[h] && g_D > 0 ? val[e] : V(0);
       }
-      if (!(s16 & kPadSlot)) {
-        direct = fma_(v, xs[s16], direct);
-        acc[s16] = fma_(v, xi, acc[s16]);
+      for (int k = 0; k < g_D; ++k) {
+        uint32_t s16[RPT];
+        V v[RPT];
+#pragma unroll
+        for (int h = 0; h < RPT; ++h) {
+          s16[h] = sn[h];
+          v[h] = vn[h];
+          if (mine[h] && k + 1 < g_D) {
+            const int e = threadIdx.x + h * NC_THREADS + (k + 1) * R;
+            sn[h] = slot[e];
+            vn[h] = val[e];
+          }
+        }
+#pragma unroll
+        for (int h = 0; h < RPT; ++h)
+          if (!(s16[h] & kPadSlot)) {
+            direct[h] = fma_(v[h], xs[s16[h]], direct[h]);
+            acc[s16[h]] = fma_(v[h], xi[h], acc[s16[h]]);
+          }
+        consumers_sync(NC_THREADS);
       }
-      consumers_sync(NC_THREADS);
     }
     if (g_D == 0) consumers_sync(NC_THREADS);  // every read of the stage is done
     // the stage is free: release it to the producer
     if (threadIdx.x == 0) mbar_arrive(&tp.empty[bf]);
-    if (mine) {
-      const V dxi = dg * xi;
-      f(g_row0 + own_row, dxi + direct + acc[own_row], xi, dxi, direct);
-    }
+#pragma unroll
+    for (int h = 0; h < RPT; ++h)
+      if (mine[h]) {
+        const int row = threadIdx.x + h * NC_THREADS;
+        const V dxi = dg[h] * xi[h];
+        f(g_row0 + row, dxi + direct[h] + acc[row], xi[h], dxi, direct[h]);
+      }
     // window slots: carried into the next tile's accumulator, or out as
     // partial sums (runs past the inline ones come from the global lists)
     const uint16_t* cs = sm->runs;
@@ -847,6 +901,7 @@ __device__ __forceinline__ void tile_pipe_init(TilePipe& tp, uint64_t* bars, lon
   tp.empty = bars + kMaxTileStages;
   tp.iss_par = tp.wait_par = tp.used = 0;
   tp.policy = policy_evict_first();
+  tp.policy_x = policy_evict_normal();
   tp.limit_ns = limit_ns;
   tp.failed = false;
   if (threadIdx.x == 0)
@@ -1034,14 +1089,15 @@ __global__ void k_scale_to_f32(const double* __restrict__ r, double scale, int64
 }
 
 // Value update of a handle: slot i of a device value array takes input
-// value map[i] (0 where map[i] < 0: padding), in both precisions.
+// value map[i] (0 where map[i] < 0: padding), in double precision into d64
+// and in single precision into d32 (either may be null).
 __global__ void k_place_values(const int32_t* __restrict__ map, int64_t len, const double* __restrict__ src,
                                double* __restrict__ d64, float* __restrict__ d32) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x) {
     const int32_t k = map[i];
     const double v = k >= 0 ? src[k] : 0.0;
-    d64[i] = v;
-    d32[i] = (float)v;
+    if (d64) d64[i] = v;
+    if (d32) d32[i] = (float)v;
   }
 }
 

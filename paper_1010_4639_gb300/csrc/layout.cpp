@@ -391,8 +391,7 @@ std::vector<int> colour_edges(const std::vector<int32_t>& eu, const std::vector<
 
 }  // namespace
 
-bool build_sym_tiles(LayoutHost& L, int ctas, int slot_cap, int ent_cap) {
-  SymTilesHost& Tl = L.tiles;
+bool build_sym_tiles(const LayoutHost& L, int ctas, int slot_cap, int ent_cap, int max_slices, SymTilesHost& Tl) {
   Tl = SymTilesHost();
   Tl.slot_cap = slot_cap;
   Tl.ent_cap = ent_cap;
@@ -404,14 +403,18 @@ bool build_sym_tiles(LayoutHost& L, int ctas, int slot_cap, int ent_cap) {
     for (int64_t r = 32 * s; r < std::min<int64_t>(n, 32 * s + 32); ++r) m = std::max(m, rp[r + 1] - rp[r]);
     return m;
   };
-  // 1. contiguous slice ranges per CTA, balanced by entries + rows
+  // 1. contiguous slice ranges per CTA, balanced by the work of the rounds:
+  // a tile runs one barrier-separated round per entry of its longest row
+  // (latency-bound in single precision), plus a fixed part (the stage wait,
+  // the clears and the epilogue, about three rounds' worth on GB300); a
+  // slice's share is its padded entries plus that fixed part.  Balancing
+  // stored entries instead gave the last CTA, whose rows have few upper
+  // entries, 1.6 times the tiles of the others (its product took 1.37 times
+  // as long at 128^3).
   std::vector<int64_t> ccut(ctas + 1, ns);
   {
     int64_t total = 0;
-    auto work = [&](int64_t s) {
-      const int64_t a = 32 * s, b = std::min<int64_t>(n, 32 * s + 32);
-      return (rp[b] - rp[a]) + 32;
-    };
+    auto work = [&](int64_t s) { return 32 * (slice_len(s) + 3); };
     for (int64_t s = 0; s < ns; ++s) total += work(s);
     int64_t acc = 0, s = 0;
     ccut[0] = 0;
@@ -453,7 +456,7 @@ bool build_sym_tiles(LayoutHost& L, int ctas, int slot_cap, int ent_cap) {
     return std::max(lmax, max_hits);
   };
   auto fits = [&](int64_t sa, int64_t sb) {
-    if (sb - sa > 15) return false;
+    if (sb - sa > max_slices) return false;
     if (targets(sa, sb) > slot_cap) return false;
     return 32 * (sb - sa) * rounds(sa, sb) <= ent_cap;
   };

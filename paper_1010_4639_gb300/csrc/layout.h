@@ -48,8 +48,9 @@ struct PlanHost {
 };
 
 // Tiled symmetric layout.  Rows are split into contiguous ranges, one per CTA
-// of the persistent grid, and each range into tiles of at most 15 whole
-// slices (one per consumer warp).  A tile's column space -- its own rows (padded to a
+// of the persistent grid, and each range into tiles of whole slices (up to
+// 15 for double precision, one per consumer warp; up to 30 for single
+// precision, two per consumer warp).  A tile's column space -- its own rows (padded to a
 // multiple of 4), then 16-byte-aligned windows of the rows beyond it that its
 // upper entries reach -- is numbered by slots indexing a shared-memory copy
 // of x and a shared-memory accumulator.  Each strict upper entry is stored
@@ -132,7 +133,6 @@ struct LayoutHost {
   SellHost A;                      // full operator (CSR/CSC) or strict upper U (symmetric)
   std::vector<double> diag;        // symmetric only: nslices * 32, zero padded
   PlanHost plan;                   // symmetric only
-  SymTilesHost tiles;              // symmetric only, when built
   // strict upper rows of the symmetric input (kept for the tile builder)
   std::vector<int64_t> urp;
   std::vector<int32_t> urc;
@@ -151,10 +151,12 @@ int build_layout(int32_t format, int64_t n, int64_t nnz, const int32_t* ptr, con
 int check_symmetry(int64_t n, int64_t nnz, const int32_t* ptr, const int32_t* idx, const double* val,
                    int32_t index_base, std::string& err);
 
-// Builds the tiled symmetric layout for `ctas` CTAs, with at most
-// `slot_cap` slots and `ent_cap` padded entries per tile.  Returns false
-// (layout left empty) when a single slice already exceeds a cap.
-bool build_sym_tiles(LayoutHost& L, int ctas, int slot_cap, int ent_cap);
+// Builds the tiled symmetric layout of L (symmetric input) into `out` for
+// `ctas` CTAs, with at most `max_slices` slices, `slot_cap` slots and
+// `ent_cap` padded entries per tile.  The CTA row ranges depend only on L
+// and `ctas`, so layouts built with different caps share them.  Returns
+// false (`out` left empty) when a single slice already exceeds a cap.
+bool build_sym_tiles(const LayoutHost& L, int ctas, int slot_cap, int ent_cap, int max_slices, SymTilesHost& out);
 
 // Contiguous slice ranges for `parts` workers, balanced by stored slots
 // (plus plan slots for the symmetric layout).  Returns parts + 1 offsets.

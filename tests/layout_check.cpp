@@ -32,7 +32,7 @@ static int fail(const char* what, long long a = -1, long long b = -1) {
 }
 
 int main(int argc, char** argv) {
-  if (argc < 3) return fail("usage: layout_check matrix.bin ctas");
+  if (argc < 3) return fail("usage: layout_check matrix.bin ctas [max_slices slot_cap ent_cap]");
   FILE* f = fopen(argv[1], "rb");
   if (!f) return fail("open");
   int64_t n = 0, nnz = 0;
@@ -44,15 +44,21 @@ int main(int argc, char** argv) {
     return fail("body");
   fclose(f);
   const int ctas = atoi(argv[2]);
-  const int slot_cap = 2048, ent_cap = 4096;
+  const int max_slices = argc > 3 ? atoi(argv[3]) : 15;
+  const int slot_cap = argc > 4 ? atoi(argv[4]) : 2048, ent_cap = argc > 5 ? atoi(argv[5]) : 4096;
   LayoutHost L;
   std::string err;
   if (build_layout(1, n, nnz, ptr.data(), idx.data(), val.data(), 0, L, err)) return fail(err.c_str());
-  if (!build_sym_tiles(L, ctas, slot_cap, ent_cap)) {
+  SymTilesHost T;
+  if (!build_sym_tiles(L, ctas, slot_cap, ent_cap, max_slices, T)) {
     printf("NOTILES\n");
     return 0;
   }
-  const SymTilesHost& T = L.tiles;
+  // the CTA row ranges do not depend on the caps
+  SymTilesHost T15;
+  if (!build_sym_tiles(L, ctas, 2048, 4096, 15, T15)) return fail("reference tiles");
+  for (int c = 0; c <= ctas; ++c)
+    if (T.tile_slice[T.cta_tile[c]] != T15.tile_slice[T15.cta_tile[c]]) return fail("CTA ranges differ", c);
   const int32_t NT = (int32_t)T.tile_ns.size();
   if ((int)T.cta_tile.size() != ctas + 1 || T.cta_tile[ctas] != NT) return fail("cta_tile");
   std::vector<int64_t> seen(L.urc.size(), 0);
@@ -77,7 +83,7 @@ int main(int argc, char** argv) {
     const int64_t a = 32 * s0, b = std::min<int64_t>(n, 32 * s1), rows = b - a;
     const int64_t D = T.tile_len[t], S = T.tile_ns[t], own = T.tile_own[t];
     const int64_t R = T.tile_stride[t];
-    if (s1 - s0 > 15 || R != 32 * (s1 - s0) || D * R > ent_cap || S > slot_cap || own != ((rows + 3) & ~3))
+    if (s1 - s0 > max_slices || R != 32 * (s1 - s0) || D * R > ent_cap || S > slot_cap || own != ((rows + 3) & ~3))
       return fail("caps", t, D * R);
     const int64_t e0 = T.tile_ent[t], E8 = T.tile_ent[t + 1] - e0, m0 = T.tile_meta[t];
     if (E8 != ((D * R + 7) & ~int64_t(7)) || T.tile_meta[t + 1] - m0 != E8 || (e0 & 7) || (m0 & 7))

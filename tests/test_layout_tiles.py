@@ -24,7 +24,12 @@ def checker(tmp_path_factory):
     return exe, d
 
 
-def _run(checker, ptr, idx, val, ctas, seed=3):
+# the two layouts a handle builds: single precision (30 slices, 3072 slots,
+# 8192 entries) and double precision (15, 2048, 4096)
+CAPS = {"fp32": (30, 3072, 8192), "fp64": (15, 2048, 4096)}
+
+
+def _run(checker, ptr, idx, val, ctas, seed=3, caps="fp64"):
     exe, d = checker
     n = len(ptr) - 1
     x = np.random.default_rng(seed).uniform(-1, 1, n)
@@ -35,16 +40,17 @@ def _run(checker, ptr, idx, val, ctas, seed=3):
         np.asarray(idx, dtype=np.int32).tofile(f)
         np.asarray(val, dtype=np.float64).tofile(f)
         x.tofile(f)
-    out = subprocess.run([exe, path, str(ctas)], capture_output=True, text=True, timeout=600)
+    out = subprocess.run([exe, path, str(ctas), *map(str, CAPS[caps])], capture_output=True, text=True, timeout=600)
     assert out.returncode == 0, out.stdout + out.stderr
     return out.stdout.strip()
 
 
+@pytest.mark.parametrize("caps", sorted(CAPS))
 @pytest.mark.parametrize("grid", [(12, 12, 12), (31, 31, 32), (40, 17, 23), (5, 6, 7)])
 @pytest.mark.parametrize("ctas", [1, 7, 152])
-def test_fem_tiles(checker, grid, ctas):
+def test_fem_tiles(checker, grid, ctas, caps):
     s = femgen.build_system(femgen.Grid(*grid))
-    line = _run(checker, *s.upper(), ctas)
+    line = _run(checker, *s.upper(), ctas, caps=caps)
     assert line.startswith("OK"), line
     stats = dict(kv.split("=") for kv in line.split()[1:])
     assert int(stats["max_rounds"]) <= 7  # a 15-point stencil: 7 strict-upper entries per row at most
@@ -62,12 +68,13 @@ def _random_upper(n, per_row, seed, long_rows=()):
     return np.array(ptr), np.array(idx), np.array(val)
 
 
+@pytest.mark.parametrize("caps", sorted(CAPS))
 @pytest.mark.parametrize("ctas", [1, 3, 64])
-def test_irregular_tiles(checker, ctas):
+def test_irregular_tiles(checker, ctas, caps):
     # uneven rows, a few long ones, targets scattered over 300 rows: many
     # conflicts for the colouring to resolve
     p, i, v = _random_upper(3000, 6, 11, long_rows={5, 700, 2999})
-    line = _run(checker, p, i, v, ctas)
+    line = _run(checker, p, i, v, ctas, caps=caps)
     assert line.startswith("OK"), line
 
 
