@@ -174,13 +174,15 @@ int gbcg_destroy(gbcg_matrix_t A);
 /*
  * gbcg_spmv -- y = A x in double precision (Section III: the A p product of
  * the CG listing), for every storage format.  x and y are device pointers to
- * n doubles and must not overlap.  Deterministic: the same inputs give the
+ * n doubles, 16-byte aligned (GBCG_ERR_INVALID otherwise), and must not
+ * overlap.  Deterministic: the same inputs give the
  * same bits on every call (no floating-point atomics).
  */
 int gbcg_spmv(gbcg_matrix_t A, const double* x, double* y, void* stream);
 
 /* gbcg_spmv_f32 -- y = A32 x with the single-precision copy of the values
- * and float vectors (the product of the single-precision variant, Section IV). */
+ * and float vectors (the product of the single-precision variant, Section IV);
+ * the same pointer rules as gbcg_spmv. */
 int gbcg_spmv_f32(gbcg_matrix_t A, const float* x, float* y, void* stream);
 
 /*
@@ -188,7 +190,9 @@ int gbcg_spmv_f32(gbcg_matrix_t A, const float* x, float* y, void* stream);
  *
  *   b      n doubles, device or host memory
  *   x      n doubles, device or host memory (both b and x in the same
- *          space); on input the initial guess x0, on output the last iterate
+ *          space; device vectors 16-byte aligned, GBCG_ERR_INVALID
+ *          otherwise); on input the initial guess x0, on output the last
+ *          iterate
  *   tol    relative residual target: stop when ||b - A x||_2 <= tol ||b||_2,
  *          checked on the recurrence residual after each r update and then
  *          confirmed on the true residual in double precision
@@ -228,8 +232,8 @@ typedef struct {
  * handle's workspace being reused by every replay (one solve of a handle in
  * flight at a time).
  *
- *   b, x   device pointers to n doubles (not checked: host pointers are the
- *          caller's error); x holds x0 on entry and the last iterate after
+ *   b, x   device pointers to n doubles, 16-byte aligned (not checked to be
+ *          device memory: host pointers are the caller's error); x holds x0 on entry and the last iterate after
  *          the stream reaches the solve's end
  *   dinfo  device pointer to one gbcg_device_info, written at the end
  *   tol, maxit, opts  as for gbcg_solve
@@ -505,7 +509,8 @@ int gbcg_batch_set_tuning(gbcg_batch_t B, int32_t precision, const gbcg_batch_tu
 /*
  * gbcg_batch_solve -- solve every instance for every right-hand side.
  *
- *   b, x     n_tot x nrhs doubles, both device or both host memory; x holds
+ *   b, x     n_tot x nrhs doubles, both device or both host memory (device
+ *            vectors 16-byte aligned, GBCG_ERR_INVALID otherwise); x holds
  *            x0 on entry and the solutions on return
  *   tol      relative residual target per system and right-hand side, checked
  *            on the true residual in double precision

@@ -23,6 +23,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdint>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -1148,6 +1149,9 @@ void free_batch(gbcg_batch_s* B) {
   delete B;
 }
 
+// The kernels read and write vectors with 16-byte loads and bulk copies.
+bool misaligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) != 0; }
+
 bool is_device_ptr(const void* p) {
   if (!p) return false;
   cudaPointerAttributes at;
@@ -1686,6 +1690,8 @@ int gbcg_batch_solve(gbcg_batch_t B, const double* b, double* x, double tol, int
   if (B->n_tot > 0 && (!b || !x)) return fail(GBCG_ERR_INVALID, "null b or x");
   const bool bdev = is_device_ptr(b), xdev = is_device_ptr(x);
   if (bdev != xdev) return fail(GBCG_ERR_INVALID, "b and x must both be device or both be host memory");
+  if (bdev && (misaligned16(b) || misaligned16(x)))
+    return fail(GBCG_ERR_INVALID, "device b and x must be 16-byte aligned");
   const int memory = bdev ? GBCG_DEVICE : GBCG_HOST;
   const bool f32 = precision != GBCG_FP64;  // both single-precision forms share tuning and graph
   cudaStream_t s = (cudaStream_t)stream;

@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdint>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -90,16 +91,18 @@ struct DevTiles {
   int64_t *tile_ent = nullptr, *tile_meta = nullptr, *tile_ext = nullptr, *in_src = nullptr;
   uint16_t* meta = nullptr;
   TileDesc* desc = nullptr;
-  int32_t *carry_src = nullptr, *carry_dst = nullptr, *carry_len = nullptr, *flush_src = nullptr, *flush_len = nullptr;
+  int32_t *carry_src = nullptr, *carry_dst = nullptr, *carry_len = nullptr, *flush_src = nullptr, *flush_len = nullptr,
+          *flush_row = nullptr;
   int32_t *in_ptr = nullptr, *in_row = nullptr, *in_len = nullptr;
   void* val = nullptr;   // float or double values, in the layout's order
-  void* part = nullptr;  // window partial sums, same type
+  void* part = nullptr;  // further window partial sums, same type
+  void* p1 = nullptr;    // each row's first window partial sum, n values (zero where a row has none)
   int64_t ntiles = 0, next = 0, slots = 0;
 
   void release() {
     void* p[] = {cta_tile, tile_slice, tile_ns, tile_own, tile_len, tile_stride, tile_win, win_start, win_len,
                  tile_ent, tile_meta, tile_ext, in_src, meta, desc, carry_src, carry_dst, carry_len, flush_src,
-                 flush_len, in_ptr, in_row, in_len, val, part};
+                 flush_len, flush_row, in_ptr, in_row, in_len, val, part, p1};
     for (void* d : p)
       if (d) cudaFree(d);
     *this = DevTiles();
@@ -113,6 +116,8 @@ struct DevTiles {
     t.carry_len = carry_len;
     t.flush_src = flush_src;
     t.flush_len = flush_len;
+    t.flush_row = flush_row;
+    t.p1 = (V*)p1;
     t.cta_tile = cta_tile;
     t.tile_slice = tile_slice;
     t.tile_ns = tile_ns;
@@ -138,7 +143,7 @@ struct DevTiles {
 
 // Uploads one tiled layout; V is the type of its values.
 template <typename V>
-int upload_tiles(DevTiles& D, const SymTilesHost& Tl, cudaStream_t s, int64_t& B) {
+int upload_tiles(DevTiles& D, const SymTilesHost& Tl, int64_t n, cudaStream_t s, int64_t& B) {
   D.ntiles = (int64_t)Tl.tile_ns.size();
   D.next = Tl.tile_ext.back();
   D.slots = (int64_t)Tl.val.size();
@@ -165,6 +170,7 @@ int upload_tiles(DevTiles& D, const SymTilesHost& Tl, cudaStream_t s, int64_t& B
   if (int rc = upload(&D.carry_len, Tl.carry_len, s, B)) return rc;
   if (int rc = upload(&D.flush_src, Tl.flush_src, s, B)) return rc;
   if (int rc = upload(&D.flush_len, Tl.flush_len, s, B)) return rc;
+  if (int rc = upload(&D.flush_row, Tl.flush_row, s, B)) return rc;
   V* val = nullptr;
   if constexpr (sizeof(V) == 4) {
     if (int rc = upload(&val, to_f32(Tl.val), s, B)) return rc;
@@ -175,6 +181,11 @@ int upload_tiles(DevTiles& D, const SymTilesHost& Tl, cudaStream_t s, int64_t& B
   V* part = nullptr;
   if (int rc = dalloc(&part, (size_t)std::max<int64_t>(D.next, 1), B)) return rc;
   D.part = part;
+  // rows that receive no first partial sum keep this zero for good
+  V* p1 = nullptr;
+  if (int rc = dalloc(&p1, (size_t)std::max<int64_t>(n, 1), B)) return rc;
+  D.p1 = p1;
+  CUDA_TRY(cudaMemsetAsync(p1, 0, sizeof(V) * (size_t)std::max<int64_t>(n, 1), s));
   return 0;
 }
 
@@ -370,6 +381,9 @@ int mode_occupancy(int mode, int& per_sm) {
   return mode == kTiles ? solver_occupancy<kTiles>(per_sm)
                         : mode == kPlan ? solver_occupancy<kPlan>(per_sm) : solver_occupancy<kGather>(per_sm);
 }
+
+// The kernels read and write vectors with 16-byte loads and bulk copies.
+bool misaligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) != 0; }
 
 bool is_device_ptr(const void* p) {
   cudaPointerAttributes at;
@@ -679,6 +693,7 @@ int spmv_any(gbcg_matrix_t A, const V* x, V* y, cudaStream_t s) {
   if (!A) return fail(GBCG_ERR_INVALID, "null matrix handle");
   if (A->n == 0) return GBCG_OK;
   if (!x || !y) return fail(GBCG_ERR_INVALID, "null vector");
+  if (misaligned16(x) || misaligned16(y)) return fail(GBCG_ERR_INVALID, "x and y must be 16-byte aligned");
   CUDA_TRY(launch_product_fmt<V, 0>(A, x, nullptr, y, s));
   return GBCG_OK;
 }
@@ -781,8 +796,8 @@ int gbcg_create(gbcg_matrix_t* out, int32_t format, int64_t n, int64_t nnz, cons
       if (cs[c] != T32.tile_slice[T32.cta_tile[c]])
         return bail(fail(GBCG_ERR_INVALID, "tile layouts of the two precisions cut the rows differently"));
     }
-    TRY(upload_tiles<float>(M->t32, T32, s, B));
-    TRY(upload_tiles<double>(M->t64, T64, s, B));
+    TRY(upload_tiles<float>(M->t32, T32, n, s, B));
+    TRY(upload_tiles<double>(M->t64, T64, n, s, B));
     M->slots = M->t64.slots;
     M->plan_slots = 0;
     TRY(upload(&M->long_mask, std::vector<uint32_t>(std::max<int64_t>(M->nslices, 1), 0u), s, B));
@@ -910,6 +925,8 @@ int gbcg_solve(gbcg_matrix_t A, const double* b, double* x, double tol, int32_t 
   if (maxit <= 0) maxit = (int32_t)std::min<int64_t>(n, 0x7fffffff);
   const bool bdev = is_device_ptr(b), xdev = is_device_ptr(x);
   if (bdev != xdev) return fail(GBCG_ERR_INVALID, "b and x must both be device or both be host memory");
+  if (bdev && (misaligned16(b) || misaligned16(x)))
+    return fail(GBCG_ERR_INVALID, "device b and x must be 16-byte aligned");
   const double* bd = b;
   double* xd = x;
   if (!bdev) {  // host vectors: stage through the buffers allocated at create time
@@ -950,6 +967,7 @@ int gbcg_solve_async(gbcg_matrix_t A, const double* b, double* x, double tol, in
     return GBCG_OK;
   }
   if (!b || !x) return fail(GBCG_ERR_INVALID, "null vector");
+  if (misaligned16(b) || misaligned16(x)) return fail(GBCG_ERR_INVALID, "b and x must be 16-byte aligned");
   if (maxit <= 0) maxit = (int32_t)std::min<int64_t>(n, 0x7fffffff);
   const bool ru = opts && opts->precision == GBCG_FP32_RU;
   CUDA_TRY(ru ? enqueue_ru(A, b, x, tol, maxit, opts, false, s) : enqueue_fp64(A, b, x, tol, maxit, opts, false, s));

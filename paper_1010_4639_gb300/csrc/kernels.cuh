@@ -84,6 +84,7 @@ struct SymDev {
   const int32_t* __restrict__ carry_len = nullptr;
   const int32_t* __restrict__ flush_src = nullptr;
   const int32_t* __restrict__ flush_len = nullptr;
+  const int32_t* __restrict__ flush_row = nullptr;
   const int32_t* __restrict__ cta_tile = nullptr;
   const int32_t* __restrict__ tile_slice = nullptr;
   const int32_t* __restrict__ tile_ns = nullptr;
@@ -102,7 +103,8 @@ struct SymDev {
   const int32_t* __restrict__ in_row = nullptr;
   const int32_t* __restrict__ in_len = nullptr;
   const int64_t* __restrict__ in_src = nullptr;
-  V* part = nullptr;                      // window partial sums (scratch)
+  V* part = nullptr;                      // further window partial sums (scratch)
+  V* p1 = nullptr;                        // each row's first window partial sum (dense; 0 where none)
 };
 
 struct GridBar {
@@ -199,7 +201,7 @@ template <typename V>
 struct alignas(16) TileSmem {
   TileStage<V> st[tile_stages<V>()];
   V acc[2][TileCaps<V>::kSlot];
-  uint16_t runs[5 * kDescRun];  // the current tile's inline carry and flush runs (the consumers' copy)
+  uint16_t runs[7 * kDescRun];  // the current tile's inline carry and flush runs (the consumers' copy)
 };
 static_assert(sizeof(TileDesc) % 16 == 0, "stage payload alignment");
 template <typename V>
@@ -797,7 +799,7 @@ __device__ __forceinline__ void sym_tiles(const OpDev<V>& A, const SymDev<V>& T,
     // the end of the tile (the stage is released before)
     for (int v4 = threadIdx.x; v4 < (int)(TileCaps<V>::kSlot * sizeof(V) / 16); v4 += NC_THREADS)
       reinterpret_cast<int4*>(acc_next)[v4] = make_int4(0, 0, 0, 0);
-    if (threadIdx.x < 5 * kDescRun) sm->runs[threadIdx.x] = (&d.cs[0])[threadIdx.x];  // cs, cd, cl, fs, fl in order
+    if (threadIdx.x < 7 * kDescRun) sm->runs[threadIdx.x] = (&d.cs[0])[threadIdx.x];  // cs, cd, cl, fs, fl, fr
     const uint16_t* __restrict__ slot = st.meta;
     const V* __restrict__ val = st.val;
     const V* __restrict__ xs = st.xs;
@@ -870,11 +872,16 @@ __device__ __forceinline__ void sym_tiles(const OpDev<V>& A, const SymDev<V>& T,
       const int len = u < kDescRun ? cs[2 * kDescRun + u] : T.carry_len[g_c0 + u];
       for (int i = threadIdx.x; i < len; i += NC_THREADS) acc_next[d0 + i] = acc[s0 + i];
     }
+    // a direct run writes its rows' first partial sums to the dense array;
+    // the others go to the compact one
     V* __restrict__ part = T.part + g_ext0 - g_own;
+    const int32_t* frow = reinterpret_cast<const int32_t*>(cs + 5 * kDescRun);
     for (int u = 0; u < g_nf; ++u) {
       const int s0 = u < kDescRun ? cs[3 * kDescRun + u] : T.flush_src[g_f0 + u];
       const int len = u < kDescRun ? cs[4 * kDescRun + u] : T.flush_len[g_f0 + u];
-      for (int i = threadIdx.x; i < len; i += NC_THREADS) part[s0 + i] = acc[s0 + i];
+      const int r0 = u < kDescRun ? frow[u] : T.flush_row[g_f0 + u];
+      V* __restrict__ dst = r0 >= 0 ? T.p1 + r0 - s0 : part;
+      for (int i = threadIdx.x; i < len; i += NC_THREADS) dst[s0 + i] = acc[s0 + i];
     }
     (void)g_S;
   }
@@ -894,6 +901,36 @@ __device__ __forceinline__ void sym_incoming(const SymDev<V>& T, V* y) {
       __syncwarp();
     }
   }
+}
+
+__device__ __forceinline__ double2 vadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float4 vadd(float4 a, float4 b) {
+  return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+}
+
+// y += the dense first partial sums over rows [r0, r1) of the CTA (after
+// sym_incoming: the product of the tiled layout is then complete).  16-byte
+// vectors, four per thread in flight (r0 is a multiple of 32).
+template <typename V>
+__device__ __forceinline__ void add_first_partials(const SymDev<V>& T, V* y, int64_t r0, int64_t r1) {
+  using VT = typename Vec<V>::T;
+  constexpr int W = Vec<V>::W, U = 4;
+  const int64_t g0 = r0 / W, g1 = r1 / W, bd = blockDim.x;
+  const VT* __restrict__ pv = reinterpret_cast<const VT*>(T.p1);
+  VT* __restrict__ yv = reinterpret_cast<VT*>(y);
+  for (int64_t g = g0 + threadIdx.x; g < g1; g += U * bd) {
+    VT a[U], b[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (g + u * bd < g1) {
+        a[u] = yv[g + u * bd];
+        b[u] = pv[g + u * bd];
+      }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (g + u * bd < g1) yv[g + u * bd] = vadd(a[u], b[u]);
+  }
+  for (int64_t i = g1 * W + threadIdx.x; i < r1; i += bd) y[i] += T.p1[i];
 }
 
 __device__ __forceinline__ void tile_pipe_init(TilePipe& tp, uint64_t* bars, long long limit_ns) {
@@ -1039,22 +1076,29 @@ __global__ void __launch_bounds__(FMT == kTiles ? kTileThreads : kCgThreads, 1)
                              pp, tp, err);
 }
 
-// Second pass: for kTiles adds the incoming partial sums; with MODE 1 then
-// forms r = b - y in place (double precision) with per-CTA sums of r'r.
+// Second pass: for kTiles adds the partial sums (the listed ones, then the
+// dense first ones); with MODE 1 then forms r = b - y in place (double
+// precision) with per-CTA sums of r'r.
 template <typename V, int FMT, int MODE>
 __global__ void __launch_bounds__(kCgThreads, 1)
     k_finish(SymDev<V> T, const int32_t* __restrict__ cta_slice, int64_t n, const V* __restrict__ b,
              V* __restrict__ y, double* __restrict__ part) {
   __shared__ double red[33];
-  if constexpr (FMT == kTiles) sym_incoming<V>(T, y);
+  const int c = blockIdx.x;
+  const int64_t r0 = (int64_t)cta_slice[c] * 32;
+  const int64_t r1 = (int64_t)cta_slice[c + 1] * 32 < n ? (int64_t)cta_slice[c + 1] * 32 : n;
+  if constexpr (FMT == kTiles) {
+    sym_incoming<V>(T, y);
+    __syncthreads();
+    if constexpr (MODE == 0) add_first_partials<V>(T, y, r0, r1);
+  }
   if constexpr (MODE == 1) {
     __syncthreads();
-    const int c = blockIdx.x;
-    const int64_t r0 = (int64_t)cta_slice[c] * 32;
-    const int64_t r1 = (int64_t)cta_slice[c + 1] * 32 < n ? (int64_t)cta_slice[c + 1] * 32 : n;
     double acc = 0.0;
     for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
-      const V t = b[i] - y[i];
+      V yi = y[i];
+      if constexpr (FMT == kTiles) yi += T.p1[i];
+      const V t = b[i] - yi;
       y[i] = t;
       acc = fma((double)t, (double)t, acc);
     }
@@ -1182,6 +1226,8 @@ __global__ void __launch_bounds__(FMT == kTiles ? kTileThreads : kCgThreads, 1) 
     if constexpr (FMT == kTiles) {
       if (!grid_barrier(a.bar, target, a.timeout_ns, &sflag, nbar++)) return false;
       sym_incoming<V>(T, q);
+      __syncthreads();
+      add_first_partials<V>(T, q, r0, r1);
     }
     __syncthreads();
     return true;
@@ -1279,8 +1325,10 @@ __global__ void __launch_bounds__(FMT == kTiles ? kTileThreads : kCgThreads, 1) 
         rows_vec<V>(
             r0, r1,
             [&](int64_t i) {
-              return Quad<VT>{*reinterpret_cast<const VT*>(p + i), *reinterpret_cast<const VT*>(q + i),
-                              *reinterpret_cast<const VT*>(x + i), *reinterpret_cast<const VT*>(r + i)};
+              VT qv = *reinterpret_cast<const VT*>(q + i);
+              if constexpr (FMT == kTiles) qv = vadd(qv, *reinterpret_cast<const VT*>(T.p1 + i));
+              return Quad<VT>{*reinterpret_cast<const VT*>(p + i), qv, *reinterpret_cast<const VT*>(x + i),
+                              *reinterpret_cast<const VT*>(r + i)};
             },
             [&](int64_t i, Quad<VT> t) {
               const V* pe = reinterpret_cast<const V*>(&t.a);
@@ -1298,7 +1346,9 @@ __global__ void __launch_bounds__(FMT == kTiles ? kTileThreads : kCgThreads, 1) 
             },
             [&](int64_t i) {
               x[i] = fma_(al, p[i], x[i]);
-              const V ri = fma_(-al, q[i], r[i]);
+              V qi = q[i];
+              if constexpr (FMT == kTiles) qi += T.p1[i];
+              const V ri = fma_(-al, qi, r[i]);
               r[i] = ri;
               prr = fma_(ri, ri, prr);
             });
@@ -1668,7 +1718,9 @@ __global__ void __launch_bounds__(FMT == kTiles ? kTileThreads : kCgThreads, 1) 
     float prr = 0.f;
     for (int64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
       const double bi = b64[i];
-      const double t = bi - q64[i];
+      double qi = q64[i];
+      if constexpr (FMT == kTiles) qi += ra.T64.p1[i];
+      const double t = bi - qi;
       const float tf = (float)t;
       r[i] = tf;
       ptt = fma(t, t, ptt);
@@ -1743,8 +1795,10 @@ __global__ void __launch_bounds__(FMT == kTiles ? kTileThreads : kCgThreads, 1) 
       rows_vec<float>(
           r0, r1,
           [&](int64_t i) {
-            return Quad<float4>{*reinterpret_cast<const float4*>(p + i), *reinterpret_cast<const float4*>(q + i),
-                                *reinterpret_cast<const float4*>(d + i), *reinterpret_cast<const float4*>(r + i)};
+            float4 qv = *reinterpret_cast<const float4*>(q + i);
+            if constexpr (FMT == kTiles) qv = vadd(qv, *reinterpret_cast<const float4*>(a.T.p1 + i));
+            return Quad<float4>{*reinterpret_cast<const float4*>(p + i), qv, *reinterpret_cast<const float4*>(d + i),
+                                *reinterpret_cast<const float4*>(r + i)};
           },
           [&](int64_t i, Quad<float4> t) {
             const float* pe = reinterpret_cast<const float*>(&t.a);
@@ -1762,7 +1816,9 @@ __global__ void __launch_bounds__(FMT == kTiles ? kTileThreads : kCgThreads, 1) 
           },
           [&](int64_t i) {
             d[i] = fmaf(al, p[i], d[i]);
-            const float ri = fmaf(-al, q[i], r[i]);
+            float qi = q[i];
+            if constexpr (FMT == kTiles) qi += a.T.p1[i];
+            const float ri = fmaf(-al, qi, r[i]);
             r[i] = ri;
             prr = fmaf(ri, ri, prr);
           });

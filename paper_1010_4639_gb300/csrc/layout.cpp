@@ -545,8 +545,12 @@ bool build_sym_tiles(const LayoutHost& L, int ctas, int slot_cap, int ent_cap, i
   }
   // 4. what becomes of each window slot after its tile: a row that the next
   // tile of the same CTA also covers (as an own row or in a window) is
-  // carried into that tile's accumulator; the others leave as partial sums,
-  // added to their rows by the tile that owns them ("incoming runs")
+  // carried into that tile's accumulator; the others leave as partial sums.
+  // A row's first partial sum (in tile order) is written straight to the
+  // row's entry of a dense array, which the pass that reads the product adds
+  // ("direct" flush runs); any further one (only where the sources of a row
+  // span two CTAs) goes to the compact partial-sum array and is added to its
+  // row by the tile that owns it ("incoming runs")
   std::vector<int32_t> tile_of_slice(ns, 0);
   for (int32_t t = 0; t < T; ++t)
     for (int64_t s = Tl.tile_slice[t]; s < Tl.tile_slice[t + 1]; ++s) tile_of_slice[s] = t;
@@ -570,6 +574,7 @@ bool build_sym_tiles(const LayoutHost& L, int ctas, int slot_cap, int ent_cap, i
     int64_t src;
   };
   std::vector<Run> runs;
+  std::vector<char> has_direct(n > 0 ? n : 1, 0);
   Tl.tile_carry.assign(T + 1, 0);
   Tl.tile_flush.assign(T + 1, 0);
   for (int32_t t = 0; t < T; ++t) {
@@ -590,14 +595,21 @@ bool build_sym_tiles(const LayoutHost& L, int ctas, int slot_cap, int ent_cap, i
           }
           continue;
         }
+        const bool direct = !has_direct[r];
+        has_direct[r] = 1;
+        const int32_t frow = direct ? (int32_t)r : -1;
         const size_t m = Tl.flush_src.size();
-        if (m > (size_t)Tl.tile_flush[t] && Tl.flush_src[m - 1] + Tl.flush_len[m - 1] == sl)
+        if (m > (size_t)Tl.tile_flush[t] && Tl.flush_src[m - 1] + Tl.flush_len[m - 1] == sl &&
+            (direct ? Tl.flush_row[m - 1] >= 0 && Tl.flush_row[m - 1] + Tl.flush_len[m - 1] == r
+                    : Tl.flush_row[m - 1] < 0))
           ++Tl.flush_len[m - 1];
         else {
           Tl.flush_src.push_back((int32_t)sl);
           Tl.flush_len.push_back(1);
+          Tl.flush_row.push_back(frow);
         }
-        // its partial sum (index tile_ext[t] + slot - own) goes to the tile owning row r
+        if (direct) continue;
+        // a further partial sum (index tile_ext[t] + slot - own) goes to the tile owning row r
         const int32_t tt = tile_of_slice[r / 32];
         const int64_t trow0 = 32 * (int64_t)Tl.tile_slice[tt];
         const int64_t src = Tl.tile_ext[t] + sl - Tl.tile_own[t];
@@ -662,6 +674,7 @@ bool build_sym_tiles(const LayoutHost& L, int ctas, int slot_cap, int ent_cap, i
     for (int32_t u = 0; u < std::min(d.nf, kDescRun); ++u) {
       d.fs[u] = (uint16_t)Tl.flush_src[d.flush0 + u];
       d.fl[u] = (uint16_t)Tl.flush_len[d.flush0 + u];
+      d.fr[u] = Tl.flush_row[d.flush0 + u];
     }
   }
   return true;

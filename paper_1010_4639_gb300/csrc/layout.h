@@ -65,9 +65,11 @@ struct PlanHost {
 // half) -- a scatter without conflicts or atomics, every sum in a fixed
 // order.  After a tile, a window slot whose row the next tile of the same
 // CTA also covers is carried into that tile's accumulator (carry runs); the
-// other window slots leave the tile as partial sums (flush runs), and
-// "incoming runs" list, per target tile and in a fixed order, which partial
-// sums to add to which of its rows.
+// other window slots leave the tile as partial sums (flush runs).  A row's
+// first partial sum goes straight to the row's entry of a dense array (zero
+// for rows that never receive one), added by the pass that reads the
+// product; further ones go to a compact array, and "incoming runs" list, per
+// target tile and in a fixed order, which of those to add to which rows.
 constexpr uint16_t kTilePad = 0x8000;  // slot flag of a padding entry (the kernels' kPadSlot)
 
 // Everything the tile pipeline needs about one tile, packed so that the
@@ -89,11 +91,14 @@ struct alignas(16) TileDesc {
   int32_t ws[kDescWin], wl[kDescWin];                   // window start rows and lengths
   uint16_t cs[kDescRun], cd[kDescRun], cl[kDescRun];    // carry runs: slot, slot in the next tile, length
   uint16_t fs[kDescRun], fl[kDescRun];                  // flush runs: slot, length
+  int32_t fr[kDescRun];                                 // flush runs: first target row (direct), or -1
   int32_t pad1_[4];
 };
-static_assert(sizeof(TileDesc) == 256, "tile descriptor size");
+static_assert(sizeof(TileDesc) == 288, "tile descriptor size");
 // the kernels copy the five run arrays as one block of 5 * kDescRun u16
-static_assert(offsetof(TileDesc, fl) == offsetof(TileDesc, cs) + 4 * kDescRun * sizeof(uint16_t), "run arrays");
+static_assert(offsetof(TileDesc, fl) == offsetof(TileDesc, cs) + 4 * kDescRun * sizeof(uint16_t) &&
+                  offsetof(TileDesc, fr) == offsetof(TileDesc, cs) + 5 * kDescRun * sizeof(uint16_t),
+              "run arrays: the kernels copy cs .. fr as one block");
 
 struct SymTilesHost {
   int32_t slot_cap = 0, ent_cap = 0;
@@ -116,8 +121,10 @@ struct SymTilesHost {
   std::vector<int32_t> carry_dst;  // its slot in the next tile of the same CTA
   std::vector<int32_t> carry_len;
   std::vector<int32_t> tile_flush; // T + 1: flush runs of each tile
-  std::vector<int32_t> flush_src;  // first window slot of the run (partial sum tile_ext + slot - own)
+  std::vector<int32_t> flush_src;  // first window slot of the run
   std::vector<int32_t> flush_len;
+  std::vector<int32_t> flush_row;  // direct run: its first target row (the rows' first partial sums, written
+                                   // to a dense per-row array); -1: partial sums tile_ext + slot - own
   std::vector<TileDesc> desc;      // T: packed per-tile descriptor
   std::vector<int32_t> in_ptr;     // T + 1: incoming runs of each tile
   std::vector<int32_t> in_row;     // run start, as a row offset inside the target tile

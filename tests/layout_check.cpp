@@ -9,10 +9,13 @@
 //   - slots, rounds and entries stay within the caps the kernels assume;
 //   - each slot names the right column (own rows, then the windows);
 //   - every window slot is either carried to the same row's slot in the
-//     next tile of the same CTA or flushed as a partial sum, and the
-//     incoming runs cover every flushed partial sum exactly once;
+//     next tile of the same CTA or flushed as a partial sum; a direct
+//     flush run writes the first partial sums of consecutive rows into the
+//     dense per-row array (each row at most once), and the incoming runs
+//     cover every other flushed partial sum exactly once;
 // then replays the kernels' order of operations on the host (rounds,
-// accumulators, partial sums, incoming runs) in double precision and
+// accumulators, dense first partials, partial sums, incoming runs) in double
+// precision and
 // compares y with a row-by-row symmetric product, entry by entry within the
 // componentwise rounding bound.  Prints one line of statistics, or FAIL.
 #include <cmath>
@@ -62,7 +65,9 @@ int main(int argc, char** argv) {
   const int32_t NT = (int32_t)T.tile_ns.size();
   if ((int)T.cta_tile.size() != ctas + 1 || T.cta_tile[ctas] != NT) return fail("cta_tile");
   std::vector<int64_t> seen(L.urc.size(), 0);
-  std::vector<double> y(n, 0.0), part(T.tile_ext[NT], 0.0);
+  std::vector<double> y(n, 0.0), part(T.tile_ext[NT], 0.0), p1(n, 0.0);
+  std::vector<int32_t> p1_hit(n, 0);
+  if (T.flush_row.size() != T.flush_src.size()) return fail("flush_row size");
   std::vector<int32_t> win_hit(T.tile_ext[NT], 0), flushed(T.tile_ext[NT], 0);
   int64_t max_d = 0, max_s = 0, pads = 0, stored = 0, carried = 0, max_runs = 0, max_wins = 0;
   std::vector<int> cta_of(NT, -1);
@@ -114,7 +119,8 @@ int main(int argc, char** argv) {
           dd.cl[u] != T.carry_len[dd.carry0 + u])
         return fail("descriptor carry runs", t);
     for (int u = 0; u < std::min(dd.nf, kDescRun); ++u)
-      if (dd.fs[u] != T.flush_src[dd.flush0 + u] || dd.fl[u] != T.flush_len[dd.flush0 + u])
+      if (dd.fs[u] != T.flush_src[dd.flush0 + u] || dd.fl[u] != T.flush_len[dd.flush0 + u] ||
+          dd.fr[u] != T.flush_row[dd.flush0 + u])
         return fail("descriptor flush runs", t);
     max_runs = std::max<int64_t>(max_runs, std::max(dd.nc, dd.nf));
     max_wins = std::max<int64_t>(max_wins, dd.nwin);
@@ -170,6 +176,13 @@ int main(int argc, char** argv) {
         const int64_t src = T.flush_src[u] + i;
         if (src < own || src >= S) return fail("flush", t, src);
         ++fate[src];
+        if (T.flush_row[u] >= 0) {  // direct: the row's first partial sum, in the dense array
+          const int64_t r = (int64_t)T.flush_row[u] + i;
+          if (r != col_of[src] || r >= n || p1_hit[r]++ != 0) return fail("direct flush", t, src);
+          p1[r] = acc[src];
+          continue;
+        }
+        if (p1_hit[col_of[src]] == 0) return fail("overflow partial before a direct one", t, src);
         part[T.tile_ext[t] + src - own] = acc[src];
         flushed[T.tile_ext[t] + src - own] = 1;
       }
@@ -187,7 +200,11 @@ int main(int argc, char** argv) {
         win_hit[T.in_src[u] + l]++;
       }
   }
-  int64_t partials = 0;
+  int64_t partials = 0, directs = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    y[i] += p1[i];
+    directs += p1_hit[i];
+  }
   for (size_t i = 0; i < win_hit.size(); ++i) {
     if (win_hit[i] != flushed[i]) return fail("incoming coverage", (long long)i, win_hit[i]);
     partials += flushed[i];
@@ -206,9 +223,9 @@ int main(int argc, char** argv) {
     }
   for (int64_t i = 0; i < n; ++i)
     if (std::fabs(y[i] - z[i]) > 1e-13 * scale[i]) return fail("product", i);
-  printf("OK tiles=%d max_rounds=%lld max_slots=%lld stored=%lld pads=%lld partials=%lld carried=%lld max_runs=%lld "
-         "max_windows=%lld\n",
-         NT, (long long)max_d, (long long)max_s, (long long)stored, (long long)pads, (long long)partials,
-         (long long)carried, (long long)max_runs, (long long)max_wins);
+  printf("OK tiles=%d max_rounds=%lld max_slots=%lld stored=%lld pads=%lld directs=%lld partials=%lld carried=%lld "
+         "max_runs=%lld max_windows=%lld\n",
+         NT, (long long)max_d, (long long)max_s, (long long)stored, (long long)pads, (long long)directs,
+         (long long)partials, (long long)carried, (long long)max_runs, (long long)max_wins);
   return 0;
 }

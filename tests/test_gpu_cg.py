@@ -150,3 +150,23 @@ def test_wait_timeout_is_bounded_and_recoverable(torch):
     s = fem(8, 8, 8)
     x, info = gpu_solve(torch, s, "sym", 1e-10)                        # context still usable
     assert info.status == "OK"
+
+
+def test_misaligned_device_vectors_are_rejected(torch):
+    # the kernels move vectors with 16-byte loads and bulk copies: an 8-byte
+    # offset view is refused on the host with GBCG_ERR_INVALID, no launch
+    s = fem(9, 8, 7)
+    with gb.Matrix("sym", *s.upper()) as A:
+        buf = torch.zeros(2 * s.n + 2, dtype=torch.float64, device="cuda")
+        xo, yo = buf[1:s.n + 1], buf[s.n + 2:]
+        assert xo.data_ptr() % 16 == 8
+        with pytest.raises(gb.GbcgError, match="16-byte aligned"):
+            A.spmv(xo, torch.empty_like(xo))
+        with pytest.raises(gb.GbcgError, match="16-byte aligned"):
+            A.solve(xo, yo)
+        with pytest.raises(gb.GbcgError, match="16-byte aligned"):
+            A.spmv_f32(torch.zeros(s.n, dtype=torch.float32, device="cuda"),
+                       torch.empty(s.n + 2, dtype=torch.float32, device="cuda")[2:])
+        # aligned views of the same buffer are accepted
+        x, info = A.solve(torch.from_numpy(s.b).cuda(), buf[:s.n])
+        assert info.status == "OK"
