@@ -47,10 +47,10 @@ METRIC = "CG time-to-1e-10 residual (s) & SpMV HBM GB/s; mixed/batched vs FP64 C
 GRIDS = {"128": femgen.LARGE, "31": femgen.PAPER_SIZE, "64": femgen.DIFF, "256": femgen.LARGEST}
 TOL = 1e-10
 # DRAM bytes (read + write) per single-precision iteration of the headline
-# kernel and stored entry, from an ncu capture of the same kernel on a
-# smaller system of the same generator (None until a capture of the current
-# kernel exists).
-RU_TRAFFIC_BYTES_PER_STORED_ENTRY = None
+# kernel on the same system, by (storage, precision, grid): the difference of
+# two ncu captures of one launch, 130 and 30 iterations (None until a capture
+# of the current kernel exists).
+DRAM_BYTES_PER_ITERATION = {}
 
 
 def parse():
@@ -231,10 +231,13 @@ def flush_l2(torch, buf):
     buf.add_(1.0)  # 256 MiB write, larger than the 129 MB L2
 
 
-# What bounds the headline kernel, by storage and precision, from its ncu
-# capture: "hbm" when DRAM throughput is the limiter, "latency" when neither
-# DRAM nor any pipe is saturated (dependent L2 round trips and barriers).
-ROOF_BOUND = {("sym", "fp32_ru"): "hbm", ("csr", "fp32_ru"): "latency"}
+# What bounds the headline kernel, by storage, precision and grid, from its
+# ncu captures: "hbm" when DRAM throughput is the limiter, "latency" when
+# neither DRAM nor any pipe is saturated (barriers and dependent round trips;
+# at 128^3 the symmetric iteration's bytes largely stay in L2, 24% DRAM
+# throughput, barrier stalls first).
+ROOF_BOUND = {("sym", "fp32_ru", "256"): "hbm", ("sym", "fp32_ru", "128"): "latency",
+              ("csr", "fp32_ru", "128"): "latency"}
 
 
 def per_iteration_bytes(stats, precision):
@@ -420,9 +423,8 @@ def run_ours(args):
     if args.precision == "fp32_ru":  # the double-precision updates: product + x, d, b, r passes
         moved += updates * per_iteration_bytes(st, "fp64")
     achieved = moved / (kernel_ms / 1000.0) / 1e9 if kernel_ms > 0 else None
-    traffic = None
-    if args.precision == "fp32_ru" and RU_TRAFFIC_BYTES_PER_STORED_ENTRY and args.format == "sym":
-        traffic = RU_TRAFFIC_BYTES_PER_STORED_ENTRY * st["nnz_input"] * iters
+    dram_it = DRAM_BYTES_PER_ITERATION.get((args.format, args.precision, args.grid))
+    traffic = dram_it * iters if dram_it else None  # the 10 updates' share (< 0.1%) left out
     x_np = x_dev.cpu().numpy()
     gold = golden(args.grid, "sym")
     kernel_names = {"fp32_ir": "k_cg<float> persistent inner CG", "fp32_ru": "k_cg_ru persistent CG, "
@@ -436,11 +438,13 @@ def run_ours(args):
         "clocks": clk.summary(),
         "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": 16 * s.n, "d2h_bytes_per_step": 8 * s.n},
         "gpu_launches": int(round(sum(i.launches for i in infos) / len(infos))),
-        "roofline": {"bound": ROOF_BOUND.get((args.format, args.precision), "hbm"), "achieved": achieved,
+        "roofline": {"bound": ROOF_BOUND.get((args.format, args.precision, args.grid), "hbm"), "achieved": achieved,
                      "peak": hbm, "unit": "GB/s", "frac": (achieved / hbm) if achieved else None,
                      "traffic": traffic,
-                     "traffic_source": "ncu DRAM bytes per iteration of this kernel on a smaller system, scaled "
-                                       "by stored entries and iterations" if traffic else None,
+                     "traffic_source": "ncu DRAM bytes per iteration of this kernel on this system (difference "
+                                       "of 130- and 30-iteration launches) x iterations" if traffic else None,
+                     "frac_dram": (traffic / (kernel_ms / 1000.0) / 1e9 / hbm) if traffic and kernel_ms > 0
+                     else None,
                      "kernel": kernel_names[args.precision],
                      "algorithmic_bytes_per_iteration": per_it, "iterations": iters, "updates": updates,
                      "kernel_ms_per_step": kernel_ms, "kernel_launches_per_step": kernel_launches,

@@ -201,6 +201,7 @@ struct gbcg_matrix_s {
   int64_t nslices = 0, nlong = 0, bytes = 0;
   int sym = 0;
   int mode = kGather;       // kGather (CSR/CSC), kPlan or kTiles (symmetric)
+  int64_t l2_bytes = 0;     // the device's L2 size
   // tiled symmetric layouts (device): single- and double-precision products
   DevTiles t32, t64;
   int32_t *u_map_t32 = nullptr;  // value map of the single-precision tiles (u_map_main: double-precision)
@@ -576,6 +577,11 @@ cudaError_t enqueue_ru(gbcg_matrix_s* M, const double* b, double* x, double tol,
   a.b64 = b;
   a.q64 = M->q;
   a.delta = (o && o->inner_tol > 0.0 && o->inner_tol < 1.0) ? o->inner_tol : 0.1;
+  // the vector passes stream through shared memory when their 20 bytes per
+  // row outgrow the L2 (from L2 the register-pipelined passes are faster:
+  // 46.2 against 44.7 us per iteration at 128^3, 320 against 351 at 256^3)
+  a.stream_vec = M->mode == kTiles && 20 * M->n > M->l2_bytes ? 1 : 0;
+  if (const int f = env_int("GBCG_STREAM_VEC", -1); f >= 0 && M->mode == kTiles) a.stream_vec = f;
   if (timed && (e = cudaEventRecord(M->ev0, s)) != cudaSuccess) return e;
   e = M->mode == kTiles  ? launch_ru<kTiles>(a, M->grid, s)
       : M->mode == kPlan ? launch_ru<kPlan>(a, M->grid, s)
@@ -764,8 +770,11 @@ int gbcg_create(gbcg_matrix_t* out, int32_t format, int64_t n, int64_t nnz, cons
   // CTAs against 50 run a reliable-update iteration in 11.2 against 12.0 us
   // (full CSR) and 16.4 against 18.7 us (symmetric tiles)
   int dev = 0, sms = 0, per_sm = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+  int l2 = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) != cudaSuccess)
     return bail(fail(GBCG_ERR_CUDA, "cannot query the device"));
+  M->l2_bytes = l2;
   const char* sym_mode = getenv("GBCG_SYM_LAYOUT");
   M->mode = !M->sym ? kGather : (sym_mode && !strcmp(sym_mode, "plan")) ? kPlan : kTiles;
   auto choose_grid = [&]() -> int {

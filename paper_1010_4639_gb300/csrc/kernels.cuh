@@ -292,6 +292,11 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 __device__ __forceinline__ void fence_proxy_async_global() {
   asm volatile("fence.proxy.async.global;" ::: "memory");
 }
+// Orders this thread's earlier generic-proxy accesses of shared memory
+// before later bulk copies into it.
+__device__ __forceinline__ void fence_proxy_async_shared() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
 __device__ __forceinline__ uint64_t policy_evict_first() {
   uint64_t p;
   asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
@@ -910,11 +915,12 @@ __device__ __forceinline__ float4 vadd(float4 a, float4 b) {
 
 // y += the dense first partial sums over rows [r0, r1) of the CTA (after
 // sym_incoming: the product of the tiled layout is then complete).  16-byte
-// vectors, four per thread in flight (r0 is a multiple of 32).
-template <typename V>
+// vectors, U per thread in flight (r0 is a multiple of 32): 4 in the
+// standalone product, 1 inside the solvers, whose registers are taken.
+template <typename V, int U = 4>
 __device__ __forceinline__ void add_first_partials(const SymDev<V>& T, V* y, int64_t r0, int64_t r1) {
   using VT = typename Vec<V>::T;
-  constexpr int W = Vec<V>::W, U = 4;
+  constexpr int W = Vec<V>::W;
   const int64_t g0 = r0 / W, g1 = r1 / W, bd = blockDim.x;
   const VT* __restrict__ pv = reinterpret_cast<const VT*>(T.p1);
   VT* __restrict__ yv = reinterpret_cast<VT*>(y);
@@ -1155,12 +1161,15 @@ __global__ void k_axpy_f32(double a, const float* __restrict__ d, int64_t n, dou
 // Vector pass over rows [r0, r1) with 16-byte accesses.  ld(i) loads the
 // group of W elements from i into a register tuple and st(i, tuple) finishes
 // it; each thread keeps two groups in flight (both loaded before either is
-// finished).  The tail runs element-wise through f1(i).
-template <typename V, class LD, class ST, class F1>
+// finished), or one with ONE.  The tail runs element-wise through f1(i).
+template <typename V, bool ONE = false, class LD, class ST, class F1>
 __device__ __forceinline__ void rows_vec(int64_t r0, int64_t r1, LD&& ld, ST&& st, F1&& f1) {
   constexpr int W = Vec<V>::W;
   const int64_t g0 = r0 / W, g1 = r1 / W;  // r0 is a multiple of 32
   const int64_t bd = blockDim.x;
+  if constexpr (ONE) {
+    for (int64_t g = g0 + threadIdx.x; g < g1; g += bd) st(g * W, ld(g * W));
+  } else
   for (int64_t g = g0 + threadIdx.x; g < g1; g += 2 * bd) {
     const bool two = g + bd < g1;
     auto t0 = ld(g * W);
@@ -1176,6 +1185,96 @@ template <typename VT>
 struct Quad {
   VT a, b, c, d;
 };
+
+// ------------------------------------------------ streamed vector passes ---
+// A vector pass of the single-precision tiled solver streams its input
+// vectors through shared memory (the tile stages' space, idle between
+// products): one thread issues bulk copies of kVecChunk-row chunks of the
+// arrays, kVecBufs chunks ahead, so an SM keeps up to kVecBufs x NA x 8 KB of
+// reads in flight without holding them in registers.  A register-pipelined
+// pass (two 16-byte groups per thread and array) kept far less in flight and
+// streamed the 256^3 system's vectors at about 4.8 TB/s.
+constexpr int kVecChunk = 2048;  // rows per chunk (8 KB per float array)
+constexpr int kVecBufs = 4;      // chunks in flight
+struct VecPipe {
+  uint64_t* bar;  // one mbarrier per buffer (shared memory)
+  uint32_t par;   // per buffer (bit b): parity of its next completion, kept alike by every thread
+  uint64_t policy;
+  long long limit_ns;
+};
+__device__ __forceinline__ void vec_pipe_init(VecPipe& vp, uint64_t* bars, long long limit_ns) {
+  vp.bar = bars;
+  vp.par = 0;
+  vp.policy = policy_evict_normal();
+  vp.limit_ns = limit_ns;
+  if (threadIdx.x == 0)
+    for (int b = 0; b < kVecBufs; ++b) mbar_init(&bars[b], 1);
+  fence_mbar_init();
+}
+template <int NA>
+__host__ __device__ constexpr size_t stream_smem_bytes() { return sizeof(float) * (size_t)kVecBufs * NA * kVecChunk; }
+
+// f(i, v) for every 4-row group at row i of [r0, rv), rv = r0 + 4 floor((r1 -
+// r0) / 4), with v[k] = src[k][i .. i + 3] (r0 a multiple of 32, every
+// src[k] 16-byte aligned); tail(i) for each row of [rv, r1).  Every thread of
+// the CTA calls it.  Returns false, with the timeout recorded in err, when a
+// chunk did not land within the pipe's limit; the copies still in flight are
+// waited for (bounded) first.
+template <int NA, class F, class FT>
+__device__ __forceinline__ bool stream_rows(const float* const (&src)[NA], int64_t r0, int64_t r1, float* buf,
+                                            VecPipe& vp, int* err, F&& f, FT&& tail) {
+  const int64_t rv = r0 + ((r1 - r0) & ~(int64_t)3);
+  const int64_t nch = (rv - r0 + kVecChunk - 1) / kVecChunk;
+  fence_proxy_async_shared();  // the buffers' earlier generic writes (tile accumulators) come first
+  __syncthreads();
+  auto issue = [&](int64_t j) {
+    const int b = (int)(j % kVecBufs);
+    const int64_t a = r0 + j * kVecChunk;
+    const uint32_t bytes = (uint32_t)((rv - a < kVecChunk ? rv - a : kVecChunk) * (int64_t)sizeof(float));
+    mbar_arrive_expect_tx(&vp.bar[b], (uint32_t)NA * bytes);
+#pragma unroll
+    for (int k = 0; k < NA; ++k) bulk_g2s(buf + (b * NA + k) * kVecChunk, src[k] + a, bytes, &vp.bar[b], vp.policy);
+  };
+  if (threadIdx.x == 0) {
+    fence_proxy_async_global();  // the arrays were written by plain stores before the last grid barrier
+    for (int64_t j = 0; j < nch && j < kVecBufs; ++j) issue(j);
+  }
+  bool ok = true;
+  int64_t j = 0;
+  for (; j < nch; ++j) {
+    const int b = (int)(j % kVecBufs);
+    ok = mbar_wait(&vp.bar[b], (vp.par >> b) & 1u, vp.limit_ns);
+    if (ok) {
+      const int64_t a = r0 + j * kVecChunk;
+      const int groups = (int)((rv - a < kVecChunk ? rv - a : kVecChunk) >> 2);
+      for (int g = threadIdx.x; g < groups; g += blockDim.x) {
+        float4 v[NA];
+#pragma unroll
+        for (int k = 0; k < NA; ++k) v[k] = reinterpret_cast<const float4*>(buf + (b * NA + k) * kVecChunk)[g];
+        f(a + 4 * (int64_t)g, v);
+      }
+    }
+    ok = __syncthreads_and(ok);  // buffer b is free on every thread, or some wait ran out
+    if (!ok) break;
+    vp.par ^= 1u << b;
+    if (threadIdx.x == 0 && j + kVecBufs < nch) issue(j + kVecBufs);
+  }
+  if (!ok) {
+    // chunks j .. min(j + kVecBufs, nch) - 1 were issued: wait (bounded) for
+    // them to land before anything else uses the buffers
+    if (threadIdx.x == 0) {
+      if (atomicCAS(err, 0, (int)kTimeout) == 0) err[1] = 500000000 + (int)(j % 1000000);
+      for (int64_t i = j; i < nch && i < j + kVecBufs; ++i) {
+        const int b = (int)(i % kVecBufs);
+        mbar_wait(&vp.bar[b], (vp.par >> b) & 1u, vp.limit_ns);
+        vp.par ^= 1u << b;
+      }
+    }
+    return false;
+  }
+  for (int64_t i = rv + threadIdx.x; i < r1; i += blockDim.x) tail(i);
+  return true;
+}
 
 // OUTER = false: inner single-precision solve from x = 0 (rhs in b), no
 // true-residual confirmation.  OUTER = true: the full solve of Section III
@@ -1227,7 +1326,7 @@ __global__ void __launch_bounds__(FMT == kTiles ? kTileThreads : kCgThreads, 1) 
       if (!grid_barrier(a.bar, target, a.timeout_ns, &sflag, nbar++)) return false;
       sym_incoming<V>(T, q);
       __syncthreads();
-      add_first_partials<V>(T, q, r0, r1);
+      add_first_partials<V, 1>(T, q, r0, r1);
     }
     __syncthreads();
     return true;
@@ -1322,7 +1421,9 @@ __global__ void __launch_bounds__(FMT == kTiles ? kTileThreads : kCgThreads, 1) 
       {
         const V al = (V)alpha;
         V prr = V(0);
-        rows_vec<V>(
+        // (one 16-byte group per thread at a time in the double-precision
+        // tiled solve, whose registers are otherwise taken)
+        rows_vec<V, FMT == kTiles && OUTER && sizeof(V) == 8>(
             r0, r1,
             [&](int64_t i) {
               VT qv = *reinterpret_cast<const VT*>(q + i);
@@ -1638,6 +1739,7 @@ struct RuArgs {
   const double* b64;
   double* q64;            // double product scratch
   double delta;
+  int32_t stream_vec;     // tiled layout: stream the vector passes through shared memory
 };
 
 // Bytes of one warp's share of the stage buffers, used in turn by the
@@ -1686,6 +1788,10 @@ __global__ void __launch_bounds__(FMT == kTiles ? kTileThreads : kCgThreads, 1) 
   __shared__ uint64_t tbar[2 * kMaxTileStages];
   TilePipe tp;
   if constexpr (FMT == kTiles) tile_pipe_init(tp, tbar, a.timeout_ns);
+  __shared__ uint64_t vbar[kVecBufs];
+  VecPipe vp;
+  if constexpr (FMT == kTiles) vec_pipe_init(vp, vbar, a.timeout_ns);
+  static_assert(stream_smem_bytes<5>() <= sizeof(TileSmem<float>), "vector stream buffers");
   __syncthreads();
   int* err = &a.bar->status;
   double* part0 = a.part;
@@ -1789,8 +1895,43 @@ __global__ void __launch_bounds__(FMT == kTiles ? kTileThreads : kCgThreads, 1) 
       sym_incoming<float>(a.T, q);
       __syncthreads();
     }
-    // B: d += alpha p, r -= alpha q, r'r  (16-byte accesses, as k_cg)
-    {
+    // B: d += alpha p, r -= alpha q, r'r  (16-byte accesses, as k_cg; on the
+    // tiled layout q_i = own part + first partial, and when the vectors
+    // outgrow the L2, p, q, the first partials, d and r stream through
+    // shared memory)
+    if (FMT == kTiles && ra.stream_vec) {
+      float prr = 0.f;
+      const float* const src[5] = {p, q, a.T.p1, d, r};
+      const bool ok = stream_rows<5>(
+          src, r0, r1, reinterpret_cast<float*>(smem_raw), vp, err,
+          [&](int64_t i, const float4 (&v)[5]) {
+            const float* pe = reinterpret_cast<const float*>(&v[0]);
+            const float* qe = reinterpret_cast<const float*>(&v[1]);
+            const float* fe = reinterpret_cast<const float*>(&v[2]);
+            const float* de = reinterpret_cast<const float*>(&v[3]);
+            const float* re = reinterpret_cast<const float*>(&v[4]);
+            float4 dn, rn;
+            float* dno = reinterpret_cast<float*>(&dn);
+            float* rno = reinterpret_cast<float*>(&rn);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              dno[j] = fmaf(al, pe[j], de[j]);
+              rno[j] = fmaf(-al, qe[j] + fe[j], re[j]);
+              prr = fmaf(rno[j], rno[j], prr);
+            }
+            *reinterpret_cast<float4*>(d + i) = dn;
+            *reinterpret_cast<float4*>(r + i) = rn;
+          },
+          [&](int64_t i) {
+            d[i] = fmaf(al, p[i], d[i]);
+            const float ri = fmaf(-al, q[i] + a.T.p1[i], r[i]);
+            r[i] = ri;
+            prr = fmaf(ri, ri, prr);
+          });
+      if (!ok) return;
+      const double sr = block_sum((double)prr, red);
+      if (threadIdx.x == 0) part1[c] = sr;
+    } else {
       float prr = 0.f;
       rows_vec<float>(
           r0, r1,
@@ -1848,20 +1989,37 @@ __global__ void __launch_bounds__(FMT == kTiles ? kTileThreads : kCgThreads, 1) 
     }
     rr = rr_new;
     // C: p = r + beta p
-    rows_vec<float>(
-        r0, r1,
-        [&](int64_t i) {
-          return Quad<float4>{*reinterpret_cast<const float4*>(p + i), *reinterpret_cast<const float4*>(r + i),
-                              float4{}, float4{}};
-        },
-        [&](int64_t i, Quad<float4> t) {
-          float* pe = reinterpret_cast<float*>(&t.a);
-          const float* re = reinterpret_cast<const float*>(&t.b);
+    if (FMT == kTiles && ra.stream_vec) {
+      const float* const src[2] = {p, r};
+      const bool ok = stream_rows<2>(
+          src, r0, r1, reinterpret_cast<float*>(smem_raw), vp, err,
+          [&](int64_t i, const float4 (&v)[2]) {
+            const float* pe = reinterpret_cast<const float*>(&v[0]);
+            const float* re = reinterpret_cast<const float*>(&v[1]);
+            float4 pn;
+            float* pno = reinterpret_cast<float*>(&pn);
 #pragma unroll
-          for (int j = 0; j < 4; ++j) pe[j] = fmaf(be, pe[j], re[j]);
-          *reinterpret_cast<float4*>(p + i) = t.a;
-        },
-        [&](int64_t i) { p[i] = fmaf(be, p[i], r[i]); });
+            for (int j = 0; j < 4; ++j) pno[j] = fmaf(be, pe[j], re[j]);
+            *reinterpret_cast<float4*>(p + i) = pn;
+          },
+          [&](int64_t i) { p[i] = fmaf(be, p[i], r[i]); });
+      if (!ok) return;
+    } else {
+      rows_vec<float>(
+          r0, r1,
+          [&](int64_t i) {
+            return Quad<float4>{*reinterpret_cast<const float4*>(p + i), *reinterpret_cast<const float4*>(r + i),
+                                float4{}, float4{}};
+          },
+          [&](int64_t i, Quad<float4> t) {
+            float* pe = reinterpret_cast<float*>(&t.a);
+            const float* re = reinterpret_cast<const float*>(&t.b);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) pe[j] = fmaf(be, pe[j], re[j]);
+            *reinterpret_cast<float4*>(p + i) = t.a;
+          },
+          [&](int64_t i) { p[i] = fmaf(be, p[i], r[i]); });
+    }
     if (!grid_barrier(a.bar, target, a.timeout_ns, &sflag, nbar++)) return;
   }
   // left by a breakdown: keep the last correction

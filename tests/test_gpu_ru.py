@@ -125,3 +125,29 @@ def test_reliable_updates_tiled_layout_grid_sizes(torch, ctas, monkeypatch):
         x, info = A.solve(torch.from_numpy(s.b).cuda(), tol=1e-10, maxit=10 * s.n, precision="fp32_ru")
     assert info.status == "OK", info
     assert true_rel_res(s, x.cpu().numpy()) <= 1e-10
+
+
+@pytest.mark.parametrize("grid,ctas", [((9, 10, 11), "7"), ((31, 31, 32), None), ((128, 128, 128), None)])
+def test_streamed_vector_passes(torch, grid, ctas, monkeypatch):
+    # the tiled solver's vector passes either stream their vectors through
+    # shared memory (bulk copies, chunks of 2048 rows, four in flight; the
+    # default once they outgrow the L2) or keep them in registers.  Each
+    # thread visits the same rows in the same order either way, so the
+    # iterates are bit for bit the same.  Ragged CTA ranges and a tail of
+    # rows past the last 4-row group (n = 990), one chunk per CTA (31^3)
+    # and chunks reusing buffers (128^3: 13 000 rows per CTA)
+    s = fem(*grid)
+    if ctas:
+        monkeypatch.setenv("GBCG_GRID", ctas)
+    b = torch.from_numpy(s.b).cuda()
+    out = {}
+    for flag in ("0", "1"):
+        monkeypatch.setenv("GBCG_STREAM_VEC", flag)
+        with make("tiles", s) as A:
+            x, info = A.solve(b, tol=1e-10, maxit=10 * s.n, precision="fp32_ru")
+        assert info.status == "OK", info
+        out[flag] = (x, info)
+    (x0, i0), (x1, i1) = out["0"], out["1"]
+    assert (i0.iterations, i0.outer) == (i1.iterations, i1.outer)
+    assert torch.equal(x0, x1)
+    assert true_rel_res(s, x1.cpu().numpy()) <= 1e-10
