@@ -515,6 +515,13 @@ CgArgs<V> make_args(const gbcg_matrix_s* M, V* x, V* r, V* p, V* q, const V* b, 
   a.tol = tol;
   a.maxit = maxit;
   a.max_restarts = max_restarts;
+  // on the tiled layout the vector passes stream through shared memory when
+  // the five vectors of the r update (5 values per row) outgrow the L2; from
+  // L2 the register-pipelined passes are faster (reliable updates: 46.2
+  // against 44.7 us per iteration at 128^3, 320 against 351 at 256^3).
+  // GBCG_STREAM_VEC=0/1 forces either (tests)
+  a.stream_vec = M->mode == kTiles && (int64_t)(5 * sizeof(V)) * M->n > M->l2_bytes ? 1 : 0;
+  if (const int f = env_int("GBCG_STREAM_VEC", -1); f >= 0 && M->mode == kTiles) a.stream_vec = f ? 1 : 0;
   a.timeout_ns = timeout_ns;
   return a;
 }
@@ -577,11 +584,6 @@ cudaError_t enqueue_ru(gbcg_matrix_s* M, const double* b, double* x, double tol,
   a.b64 = b;
   a.q64 = M->q;
   a.delta = (o && o->inner_tol > 0.0 && o->inner_tol < 1.0) ? o->inner_tol : 0.1;
-  // the vector passes stream through shared memory when their 20 bytes per
-  // row outgrow the L2 (from L2 the register-pipelined passes are faster:
-  // 46.2 against 44.7 us per iteration at 128^3, 320 against 351 at 256^3)
-  a.stream_vec = M->mode == kTiles && 20 * M->n > M->l2_bytes ? 1 : 0;
-  if (const int f = env_int("GBCG_STREAM_VEC", -1); f >= 0 && M->mode == kTiles) a.stream_vec = f;
   if (timed && (e = cudaEventRecord(M->ev0, s)) != cudaSuccess) return e;
   e = M->mode == kTiles  ? launch_ru<kTiles>(a, M->grid, s)
       : M->mode == kPlan ? launch_ru<kPlan>(a, M->grid, s)

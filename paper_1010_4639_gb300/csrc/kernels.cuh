@@ -141,6 +141,7 @@ struct CgArgs {
   double tol;
   int32_t maxit;
   int32_t max_restarts;
+  int32_t stream_vec;         // tiled layout: stream the vector passes through shared memory
   long long timeout_ns;
 };
 
@@ -1187,15 +1188,17 @@ struct Quad {
 };
 
 // ------------------------------------------------ streamed vector passes ---
-// A vector pass of the single-precision tiled solver streams its input
-// vectors through shared memory (the tile stages' space, idle between
-// products): one thread issues bulk copies of kVecChunk-row chunks of the
-// arrays, kVecBufs chunks ahead, so an SM keeps up to kVecBufs x NA x 8 KB of
-// reads in flight without holding them in registers.  A register-pipelined
-// pass (two 16-byte groups per thread and array) kept far less in flight and
-// streamed the 256^3 system's vectors at about 4.8 TB/s.
-constexpr int kVecChunk = 2048;  // rows per chunk (8 KB per float array)
-constexpr int kVecBufs = 4;      // chunks in flight
+// A vector pass of a tiled solver streams its input vectors through shared
+// memory (the tile stages' space, idle between products): one thread issues
+// bulk copies of 8 KB chunks of the arrays (2048 float or 1024 double rows),
+// kVecBufs chunks ahead, so an SM keeps up to kVecBufs x NA x 8 KB of reads in
+// flight without holding them in registers.  A register-pipelined pass (two
+// 16-byte groups per thread and array) kept far less in flight and streamed
+// the 256^3 system's vectors at about 4.8 TB/s.
+constexpr int kVecChunkBytes = 8192;  // per array and chunk
+constexpr int kVecBufs = 4;           // chunks in flight
+template <typename V>
+__host__ __device__ constexpr int vec_chunk() { return kVecChunkBytes / (int)sizeof(V); }
 struct VecPipe {
   uint64_t* bar;  // one mbarrier per buffer (shared memory)
   uint32_t par;   // per buffer (bit b): parity of its next completion, kept alike by every thread
@@ -1212,25 +1215,27 @@ __device__ __forceinline__ void vec_pipe_init(VecPipe& vp, uint64_t* bars, long 
   fence_mbar_init();
 }
 template <int NA>
-__host__ __device__ constexpr size_t stream_smem_bytes() { return sizeof(float) * (size_t)kVecBufs * NA * kVecChunk; }
+__host__ __device__ constexpr size_t stream_smem_bytes() { return (size_t)kVecBufs * NA * kVecChunkBytes; }
 
-// f(i, v) for every 4-row group at row i of [r0, rv), rv = r0 + 4 floor((r1 -
-// r0) / 4), with v[k] = src[k][i .. i + 3] (r0 a multiple of 32, every
-// src[k] 16-byte aligned); tail(i) for each row of [rv, r1).  Every thread of
-// the CTA calls it.  Returns false, with the timeout recorded in err, when a
-// chunk did not land within the pipe's limit; the copies still in flight are
-// waited for (bounded) first.
-template <int NA, class F, class FT>
-__device__ __forceinline__ bool stream_rows(const float* const (&src)[NA], int64_t r0, int64_t r1, float* buf,
-                                            VecPipe& vp, int* err, F&& f, FT&& tail) {
-  const int64_t rv = r0 + ((r1 - r0) & ~(int64_t)3);
+// f(i, v) for every 16-byte group of W rows at row i of [r0, rv), rv = r0 +
+// W floor((r1 - r0) / W), with v[k] = src[k][i .. i + W - 1] (r0 a multiple
+// of 32, every src[k] 16-byte aligned); tail(i) for each row of [rv, r1).
+// Every thread of the CTA calls it.  Returns false, with the timeout
+// recorded in err, when a chunk did not land within the pipe's limit; the
+// copies still in flight are waited for (bounded) first.
+template <typename V, int NA, class F, class FT>
+__device__ __forceinline__ bool stream_rows(const V* const (&src)[NA], int64_t r0, int64_t r1, V* buf, VecPipe& vp,
+                                            int* err, F&& f, FT&& tail) {
+  using VT = typename Vec<V>::T;
+  constexpr int W = Vec<V>::W, kVecChunk = vec_chunk<V>();
+  const int64_t rv = r0 + ((r1 - r0) & ~(int64_t)(W - 1));
   const int64_t nch = (rv - r0 + kVecChunk - 1) / kVecChunk;
   fence_proxy_async_shared();  // the buffers' earlier generic writes (tile accumulators) come first
   __syncthreads();
   auto issue = [&](int64_t j) {
     const int b = (int)(j % kVecBufs);
     const int64_t a = r0 + j * kVecChunk;
-    const uint32_t bytes = (uint32_t)((rv - a < kVecChunk ? rv - a : kVecChunk) * (int64_t)sizeof(float));
+    const uint32_t bytes = (uint32_t)((rv - a < kVecChunk ? rv - a : kVecChunk) * (int64_t)sizeof(V));
     mbar_arrive_expect_tx(&vp.bar[b], (uint32_t)NA * bytes);
 #pragma unroll
     for (int k = 0; k < NA; ++k) bulk_g2s(buf + (b * NA + k) * kVecChunk, src[k] + a, bytes, &vp.bar[b], vp.policy);
@@ -1246,12 +1251,12 @@ __device__ __forceinline__ bool stream_rows(const float* const (&src)[NA], int64
     ok = mbar_wait(&vp.bar[b], (vp.par >> b) & 1u, vp.limit_ns);
     if (ok) {
       const int64_t a = r0 + j * kVecChunk;
-      const int groups = (int)((rv - a < kVecChunk ? rv - a : kVecChunk) >> 2);
+      const int groups = (int)(rv - a < kVecChunk ? rv - a : kVecChunk) / W;
       for (int g = threadIdx.x; g < groups; g += blockDim.x) {
-        float4 v[NA];
+        VT v[NA];
 #pragma unroll
-        for (int k = 0; k < NA; ++k) v[k] = reinterpret_cast<const float4*>(buf + (b * NA + k) * kVecChunk)[g];
-        f(a + 4 * (int64_t)g, v);
+        for (int k = 0; k < NA; ++k) v[k] = reinterpret_cast<const VT*>(buf + (b * NA + k) * kVecChunk)[g];
+        f(a + W * (int64_t)g, v);
       }
     }
     ok = __syncthreads_and(ok);  // buffer b is free on every thread, or some wait ran out
@@ -1310,6 +1315,10 @@ __global__ void __launch_bounds__(FMT == kTiles ? kTileThreads : kCgThreads, 1) 
   pipe_init(pp, bars[threadIdx.x >> 5], gather_stages<V>(), a.timeout_ns);
   TilePipe tp;
   tile_pipe_init(tp, tbar, a.timeout_ns);
+  __shared__ uint64_t vbar[kVecBufs];
+  VecPipe vp;
+  if constexpr (FMT == kTiles) vec_pipe_init(vp, vbar, a.timeout_ns);
+  static_assert(FMT != kTiles || stream_smem_bytes<5>() <= sizeof(TileSmem<V>), "vector stream buffers");
   __syncthreads();
   int* err = &a.bar->status;
   unsigned long long target = 0;
@@ -1421,8 +1430,46 @@ __global__ void __launch_bounds__(FMT == kTiles ? kTileThreads : kCgThreads, 1) 
       {
         const V al = (V)alpha;
         V prr = V(0);
+        bool streamed = false;
+        if constexpr (FMT == kTiles) {
+          // vectors larger than the L2: p, q, the first partials, x and r
+          // stream through shared memory (the same rows per thread, in the
+          // same order, as the register-pipelined pass below)
+          if (a.stream_vec) {
+            const V* const src[5] = {p, q, T.p1, x, r};
+            const bool ok = stream_rows<V, 5>(
+                src, r0, r1, reinterpret_cast<V*>(smem_raw), vp, err,
+                [&](int64_t i, const VT (&v)[5]) {
+                  const V* pe = reinterpret_cast<const V*>(&v[0]);
+                  const V* qe = reinterpret_cast<const V*>(&v[1]);
+                  const V* fe = reinterpret_cast<const V*>(&v[2]);
+                  const V* xe = reinterpret_cast<const V*>(&v[3]);
+                  const V* re = reinterpret_cast<const V*>(&v[4]);
+                  VT xn, rn;
+                  V* xo = reinterpret_cast<V*>(&xn);
+                  V* ro = reinterpret_cast<V*>(&rn);
+#pragma unroll
+                  for (int j = 0; j < W; ++j) {
+                    xo[j] = fma_(al, pe[j], xe[j]);
+                    ro[j] = fma_(-al, qe[j] + fe[j], re[j]);
+                    prr = fma_(ro[j], ro[j], prr);
+                  }
+                  *reinterpret_cast<VT*>(x + i) = xn;
+                  *reinterpret_cast<VT*>(r + i) = rn;
+                },
+                [&](int64_t i) {
+                  x[i] = fma_(al, p[i], x[i]);
+                  const V ri = fma_(-al, q[i] + T.p1[i], r[i]);
+                  r[i] = ri;
+                  prr = fma_(ri, ri, prr);
+                });
+            if (!ok) return;
+            streamed = true;
+          }
+        }
         // (one 16-byte group per thread at a time in the double-precision
         // tiled solve, whose registers are otherwise taken)
+        if (!streamed)
         rows_vec<V, FMT == kTiles && OUTER && sizeof(V) == 8>(
             r0, r1,
             [&](int64_t i) {
@@ -1471,6 +1518,27 @@ __global__ void __launch_bounds__(FMT == kTiles ? kTileThreads : kCgThreads, 1) 
       // C: p = r + beta p
       {
         const V be = (V)beta;
+        bool streamed = false;
+        if constexpr (FMT == kTiles) {
+          if (a.stream_vec) {
+            const V* const src[2] = {p, r};
+            const bool ok = stream_rows<V, 2>(
+                src, r0, r1, reinterpret_cast<V*>(smem_raw), vp, err,
+                [&](int64_t i, const VT (&v)[2]) {
+                  const V* pe = reinterpret_cast<const V*>(&v[0]);
+                  const V* re = reinterpret_cast<const V*>(&v[1]);
+                  VT pn;
+                  V* po = reinterpret_cast<V*>(&pn);
+#pragma unroll
+                  for (int j = 0; j < W; ++j) po[j] = fma_(be, pe[j], re[j]);
+                  *reinterpret_cast<VT*>(p + i) = pn;
+                },
+                [&](int64_t i) { p[i] = fma_(be, p[i], r[i]); });
+            if (!ok) return;
+            streamed = true;
+          }
+        }
+        if (!streamed)
         rows_vec<V>(
             r0, r1,
             [&](int64_t i) {
@@ -1739,7 +1807,6 @@ struct RuArgs {
   const double* b64;
   double* q64;            // double product scratch
   double delta;
-  int32_t stream_vec;     // tiled layout: stream the vector passes through shared memory
 };
 
 // Bytes of one warp's share of the stage buffers, used in turn by the
@@ -1899,10 +1966,10 @@ __global__ void __launch_bounds__(FMT == kTiles ? kTileThreads : kCgThreads, 1) 
     // tiled layout q_i = own part + first partial, and when the vectors
     // outgrow the L2, p, q, the first partials, d and r stream through
     // shared memory)
-    if (FMT == kTiles && ra.stream_vec) {
+    if (FMT == kTiles && ra.c.stream_vec) {
       float prr = 0.f;
       const float* const src[5] = {p, q, a.T.p1, d, r};
-      const bool ok = stream_rows<5>(
+      const bool ok = stream_rows<float, 5>(
           src, r0, r1, reinterpret_cast<float*>(smem_raw), vp, err,
           [&](int64_t i, const float4 (&v)[5]) {
             const float* pe = reinterpret_cast<const float*>(&v[0]);
@@ -1989,9 +2056,9 @@ __global__ void __launch_bounds__(FMT == kTiles ? kTileThreads : kCgThreads, 1) 
     }
     rr = rr_new;
     // C: p = r + beta p
-    if (FMT == kTiles && ra.stream_vec) {
+    if (FMT == kTiles && ra.c.stream_vec) {
       const float* const src[2] = {p, r};
-      const bool ok = stream_rows<2>(
+      const bool ok = stream_rows<float, 2>(
           src, r0, r1, reinterpret_cast<float*>(smem_raw), vp, err,
           [&](int64_t i, const float4 (&v)[2]) {
             const float* pe = reinterpret_cast<const float*>(&v[0]);

@@ -127,15 +127,18 @@ def test_reliable_updates_tiled_layout_grid_sizes(torch, ctas, monkeypatch):
     assert true_rel_res(s, x.cpu().numpy()) <= 1e-10
 
 
-@pytest.mark.parametrize("grid,ctas", [((9, 10, 11), "7"), ((31, 31, 32), None), ((128, 128, 128), None)])
-def test_streamed_vector_passes(torch, grid, ctas, monkeypatch):
-    # the tiled solver's vector passes either stream their vectors through
-    # shared memory (bulk copies, chunks of 2048 rows, four in flight; the
+@pytest.mark.parametrize("grid,ctas,precision", [((9, 10, 11), "7", "fp32_ru"), ((31, 31, 32), None, "fp32_ru"),
+                                                 ((128, 128, 128), None, "fp32_ru"), ((9, 10, 11), "7", "fp64"),
+                                                 ((64, 64, 64), None, "fp64"), ((31, 31, 32), None, "fp32_ir")])
+def test_streamed_vector_passes(torch, grid, ctas, precision, monkeypatch):
+    # the tiled solvers' vector passes either stream their vectors through
+    # shared memory (bulk copies, 8 KB chunks per vector, four in flight; the
     # default once they outgrow the L2) or keep them in registers.  Each
     # thread visits the same rows in the same order either way, so the
     # iterates are bit for bit the same.  Ragged CTA ranges and a tail of
-    # rows past the last 4-row group (n = 990), one chunk per CTA (31^3)
-    # and chunks reusing buffers (128^3: 13 000 rows per CTA)
+    # rows past the last 16-byte group (n = 990), one chunk per CTA (31^3),
+    # chunks reusing buffers (128^3: 13 000 rows per CTA; 64^3 in double
+    # precision: 1 600 rows per CTA, 1 024 per chunk)
     s = fem(*grid)
     if ctas:
         monkeypatch.setenv("GBCG_GRID", ctas)
@@ -144,7 +147,7 @@ def test_streamed_vector_passes(torch, grid, ctas, monkeypatch):
     for flag in ("0", "1"):
         monkeypatch.setenv("GBCG_STREAM_VEC", flag)
         with make("tiles", s) as A:
-            x, info = A.solve(b, tol=1e-10, maxit=10 * s.n, precision="fp32_ru")
+            x, info = A.solve(b, tol=1e-10, maxit=10 * s.n, precision=precision)
         assert info.status == "OK", info
         out[flag] = (x, info)
     (x0, i0), (x1, i1) = out["0"], out["1"]
