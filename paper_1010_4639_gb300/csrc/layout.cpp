@@ -406,15 +406,18 @@ bool build_sym_tiles(const LayoutHost& L, int ctas, int slot_cap, int ent_cap, i
   // 1. contiguous slice ranges per CTA, balanced by the work of the rounds:
   // a tile runs one barrier-separated round per entry of its longest row
   // (latency-bound in single precision), plus a fixed part (the stage wait,
-  // the clears and the epilogue, about three rounds' worth on GB300); a
-  // slice's share is its padded entries plus that fixed part.  Balancing
-  // stored entries instead gave the last CTA, whose rows have few upper
-  // entries, 1.6 times the tiles of the others (its product took 1.37 times
-  // as long at 128^3).
+  // the clears and the epilogue); a slice's share is its padded entries plus
+  // that fixed part.  Measured per single-precision tile of 960 rows on
+  // GB300: 269 cycles per round, ~1550 for the rest, i.e. about six rounds'
+  // worth (double precision: 640 and ~1930, about three).  Six balances the
+  // single-precision product, which the solvers iterate on, and moves the
+  // double-precision one by less than 0.1%.  With three, the last CTA ran
+  // 9% longer than the others at 256^3; balancing stored entries had given
+  // it 1.6 times the tiles of the others.
   std::vector<int64_t> ccut(ctas + 1, ns);
   {
     int64_t total = 0;
-    auto work = [&](int64_t s) { return 32 * (slice_len(s) + 3); };
+    auto work = [&](int64_t s) { return 32 * (slice_len(s) + 6); };
     for (int64_t s = 0; s < ns; ++s) total += work(s);
     int64_t acc = 0, s = 0;
     ccut[0] = 0;
