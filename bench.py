@@ -478,6 +478,27 @@ def run_ours(args):
     return 0
 
 
+_FMA_RATE = []
+
+
+def fp64_roofline(gb, st, ms, hbm):
+    """The double-precision product against min(HBM, FP64 FMA rate): its FMAs
+    (two per stored off-diagonal entry in symmetric storage, one per entry in
+    full storage) over the device's measured FP64 FMA rate, and the bound
+    that is reached first."""
+    if not _FMA_RATE:
+        _FMA_RATE.append(gb.measure_fp64_fma_rate())
+    rate = _FMA_RATE[0]
+    fmas = 2 * (st["nnz_input"] - st["n"]) + st["n"] if st["format"] == 1 else st["nnz_full"]
+    t_hbm = st["spmv_bytes_fp64"] / (hbm * 1e9)
+    t_fma = fmas / rate if rate > 0 else 0.0
+    t = ms / 1000.0
+    return {"spmv_fp64_fmas": int(fmas), "measured_fp64_fma_per_s": rate,
+            "spmv_fp64_frac_of_measured_fp64_fma": t_fma / t,
+            "spmv_fp64_bound": "fp64_fma" if t_fma > t_hbm else "hbm",
+            "spmv_fp64_frac_of_roofline": max(t_hbm, t_fma) / t}
+
+
 def time_spmv(torch, M, x, y, f32, reps=20):
     stream = torch.cuda.current_stream()
     fn = M.spmv_f32 if f32 else M.spmv
@@ -533,6 +554,7 @@ def extras(torch, gb, s, fmt_arrays, A_head, args, hbm, gold):
         r["spmv_fp32_GBs"] = st["spmv_bytes_fp32"] / r["spmv_fp32_ms"] / 1e6
         r["spmv_fp64_frac_of_measured_hbm"] = r["spmv_fp64_GBs"] / hbm
         r["spmv_fp32_frac_of_measured_hbm"] = r["spmv_fp32_GBs"] / hbm
+        r.update(fp64_roofline(gb, st, r["spmv_fp64_ms"], hbm))
         for prec in plan[fmt]:
             t, info, x = time_solve(torch, M, b, prec, args, flush)
             per_it = per_iteration_bytes(st, prec)
@@ -574,6 +596,7 @@ def large_128(torch, gb, args, hbm):
             r["spmv_fp32_GBs"] = st["spmv_bytes_fp32"] / r["spmv_fp32_ms"] / 1e6
             r["spmv_fp64_frac_of_measured_hbm"] = r["spmv_fp64_GBs"] / hbm
             r["spmv_fp32_frac_of_measured_hbm"] = r["spmv_fp32_GBs"] / hbm
+            r.update(fp64_roofline(gb, st, r["spmv_fp64_ms"], hbm))
             for prec in ("fp64", "fp32_ir", "fp32_ru"):
                 t, info, x = time_solve(torch, M, b, prec, args, flush)
                 per_it = per_iteration_bytes(st, prec)

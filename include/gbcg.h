@@ -317,6 +317,17 @@ int gbcg_ablation_spmv(int32_t format, int64_t n, const int32_t* ptr, const int3
 int gbcg_ablation_solve(int32_t format, int64_t n, const int32_t* ptr, const int32_t* idx, const double* val,
                         const double* b, double* x, double tol, int32_t maxit, gbcg_info* info, void* stream);
 
+/*
+ * gbcg_measure_fp64_fma_rate -- measurement only: the device's FP64 FMA
+ * throughput (FMAs per second, not flops), the second roof of the
+ * double-precision symmetric product, which spends two FMAs per stored
+ * off-diagonal entry (Section III: the direct and the transpose half).
+ * Runs a kernel of independent FMA chains at full occupancy on every SM
+ * four times on `stream` and reports the fastest of the last three.  Allocates
+ * and frees one double of device memory; synchronises.
+ */
+int gbcg_measure_fp64_fma_rate(double* fma_per_s, void* stream);
+
 /* gbcg_stats -- layout facts of a handle. */
 int gbcg_stats(gbcg_matrix_t A, gbcg_matrix_stats* out);
 

@@ -505,6 +505,14 @@ def selftest_wait_timeout(ctas: int = 0, timeout_ms: int = 50, stream=None) -> i
     return _lib.load().gbcg_selftest_wait_timeout(int(ctas), int(timeout_ms), _stream_handle(stream))
 
 
+def measure_fp64_fma_rate(stream=None) -> float:
+    """FP64 FMAs per second of the device (``gbcg_measure_fp64_fma_rate``; measurement only)."""
+    out = ctypes.c_double(0.0)
+    _lib.check(_lib.load().gbcg_measure_fp64_fma_rate(ctypes.byref(out), _stream_handle(stream)),
+               "gbcg_measure_fp64_fma_rate")
+    return out.value
+
+
 from .autograd import Assembly, SparseSolve  # noqa: E402
 
-__all__ = ["Matrix", "Batch", "SparseSolve", "Assembly", "Ablation", "grad_values", "element_grad", "assemble", "SolveInfo", "GbcgError", "build", "selftest_wait_timeout", "FORMATS", "PRECISIONS"]
+__all__ = ["Matrix", "Batch", "SparseSolve", "Assembly", "Ablation", "grad_values", "element_grad", "assemble", "SolveInfo", "GbcgError", "build", "selftest_wait_timeout", "measure_fp64_fma_rate", "FORMATS", "PRECISIONS"]

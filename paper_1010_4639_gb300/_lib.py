@@ -24,7 +24,7 @@ EXPORTS = ["gbcg_create", "gbcg_destroy", "gbcg_spmv", "gbcg_spmv_f32", "gbcg_so
            "gbcg_batch_create", "gbcg_batch_destroy", "gbcg_batch_autotune", "gbcg_batch_set_tuning",
            "gbcg_batch_solve", "gbcg_batch_instance_times", "gbcg_batch_stats",
            "gbcg_batch_selftest_group_timeout", "gbcg_update_values", "gbcg_grad_values", "gbcg_element_grad",
-           "gbcg_assemble", "gbcg_ablation_spmv", "gbcg_ablation_solve"]
+           "gbcg_assemble", "gbcg_ablation_spmv", "gbcg_ablation_solve", "gbcg_measure_fp64_fma_rate"]
 STATIC_MAX_N = 680000
 
 
@@ -133,12 +133,13 @@ def load(path: str = LIB_PATH):
     lib.gbcg_assemble.argtypes = [i64, vp, vp, vp, vp, vp, vp]
     lib.gbcg_ablation_spmv.argtypes = [i32, i64, vp, vp, vp, vp, vp, vp]
     lib.gbcg_ablation_solve.argtypes = [i32, i64, vp, vp, vp, vp, vp, d, i32, ctypes.POINTER(Info), vp]
+    lib.gbcg_measure_fp64_fma_rate.argtypes = [ctypes.POINTER(d), vp]
     for name in ("gbcg_create", "gbcg_destroy", "gbcg_spmv", "gbcg_spmv_f32", "gbcg_solve", "gbcg_stats",
                  "gbcg_selftest_wait_timeout", "gbcg_solve_csr_static", "gbcg_batch_create", "gbcg_batch_destroy",
                  "gbcg_batch_autotune", "gbcg_batch_set_tuning", "gbcg_batch_solve", "gbcg_batch_instance_times",
                  "gbcg_batch_stats", "gbcg_batch_selftest_group_timeout", "gbcg_update_values",
                  "gbcg_grad_values", "gbcg_element_grad", "gbcg_assemble", "gbcg_ablation_spmv",
-                 "gbcg_ablation_solve"):
+                 "gbcg_ablation_solve", "gbcg_measure_fp64_fma_rate"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib

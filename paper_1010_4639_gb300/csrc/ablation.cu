@@ -167,6 +167,25 @@ int dot(int64_t n, const double* a, const double* b, Work& w, cudaStream_t s, in
   return 0;
 }
 
+// FP64 FMA throughput probe: every thread runs kFmaChains independent FMA
+// chains of kFmaSteps steps (enough independent work to fill the FP64 pipe
+// at full occupancy); the sum is tested against a value it never takes, so
+// the chains stay live without a store per thread.
+constexpr int kFmaChains = 8, kFmaSteps = 4096;
+__global__ void __launch_bounds__(kThreads) k_fp64_fma(double seed, double* out) {
+  double a[kFmaChains];
+  const double m = 1.0 - 1e-13 * (double)(threadIdx.x & 7), c = 1e-9 * (double)(blockIdx.x & 15);
+#pragma unroll
+  for (int k = 0; k < kFmaChains; ++k) a[k] = seed + k;
+  for (int i = 0; i < kFmaSteps; ++i)
+#pragma unroll
+    for (int k = 0; k < kFmaChains; ++k) a[k] = fma(a[k], m, c);
+  double t = 0.0;
+#pragma unroll
+  for (int k = 0; k < kFmaChains; ++k) t += a[k];
+  if (t == -1.0) out[0] = t;
+}
+
 int check_format(int32_t format) {
   if (format != GBCG_CSR && format != GBCG_SYM_CSR_UPPER)
     return fail(GBCG_ERR_INVALID, "ablation kernels take GBCG_CSR or GBCG_SYM_CSR_UPPER");
@@ -272,6 +291,41 @@ int gbcg_ablation_solve(int32_t format, int64_t n, const int32_t* ptr, const int
   info->launches = launches;
   info->ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   return status;
+}
+
+int gbcg_measure_fp64_fma_rate(double* fma_per_s, void* stream) {
+  if (!fma_per_s) return fail(GBCG_ERR_INVALID, "null output");
+  *fma_per_s = 0.0;
+  cudaStream_t s = (cudaStream_t)stream;
+  int dev = 0, sms = 0;
+  ACUDA(cudaGetDevice(&dev));
+  ACUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int blocks = sms * (2048 / kThreads);  // full occupancy on every SM
+  double* out = nullptr;
+  ACUDA(cudaMalloc(&out, sizeof(double)));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  float best = 0.f;
+  for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {  // the first launch warms up
+    e = cudaEventRecord(e0, s);
+    if (e == cudaSuccess) {
+      k_fp64_fma<<<blocks, kThreads, 0, s>>>(1.0 + rep, out);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e == cudaSuccess && rep > 0 && (best == 0.f || ms < best)) best = ms;
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(out);
+  ACUDA(e);
+  const double fmas = (double)blocks * kThreads * kFmaSteps * kFmaChains;
+  *fma_per_s = best > 0.f ? fmas / (best * 1e-3) : 0.0;
+  return GBCG_OK;
 }
 
 }  // extern "C"

@@ -45,3 +45,11 @@ def test_ablation_solve(torch, fmt):
     rel = np.linalg.norm(s.b - oracle.spmv("csr", s.ptr, s.idx, s.val, x.cpu().numpy())) / np.linalg.norm(s.b)
     assert rel <= 2e-10  # the recurrence residual reached 1e-10; no confirmation step
     assert info.launches >= 7 * info.iterations  # one launch per operation
+
+
+def test_fp64_fma_rate_probe(torch):
+    # the second roof of the double-precision products: GB300's FP64 FMA rate
+    # is a few hundred G FMA/s (1/64 of FP32); anything far outside means the
+    # probe did not run its chains
+    rate = gb.measure_fp64_fma_rate()
+    assert 5e10 < rate < 5e12, rate
