@@ -223,9 +223,19 @@ int main(int argc, char** argv) {
     }
   for (int64_t i = 0; i < n; ++i)
     if (std::fabs(y[i] - z[i]) > 1e-13 * scale[i]) return fail("product", i);
+  // balance of the CTA ranges under the tile cost the partition assumes:
+  // the tile's rounds plus six rounds' worth of fixed work, per tile
+  double cmax = 0.0, csum = 0.0;
+  for (int c = 0; c < ctas; ++c) {
+    double cost = 0.0;
+    for (int32_t t = T.cta_tile[c]; t < T.cta_tile[c + 1]; ++t) cost += 6.0 + T.tile_len[t];
+    cmax = std::max(cmax, cost);
+    csum += cost;
+  }
   printf("OK tiles=%d max_rounds=%lld max_slots=%lld stored=%lld pads=%lld directs=%lld partials=%lld carried=%lld "
-         "max_runs=%lld max_windows=%lld\n",
+         "max_runs=%lld max_windows=%lld balance=%.4f\n",
          NT, (long long)max_d, (long long)max_s, (long long)stored, (long long)pads, (long long)directs,
-         (long long)partials, (long long)carried, (long long)max_runs, (long long)max_wins);
+         (long long)partials, (long long)carried, (long long)max_runs, (long long)max_wins,
+         csum > 0 ? cmax / (csum / ctas) : 1.0);
   return 0;
 }

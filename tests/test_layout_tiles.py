@@ -54,6 +54,10 @@ def test_fem_tiles(checker, grid, ctas, caps):
     assert line.startswith("OK"), line
     stats = dict(kv.split("=") for kv in line.split()[1:])
     assert int(stats["max_rounds"]) <= 7  # a 15-point stencil: 7 strict-upper entries per row at most
+    if ctas == 7 and caps == "fp32" and grid == (31, 31, 32):
+        # the CTA ranges balance the modelled tile cost (rounds + a fixed six
+        # rounds per tile; 1.14 with a fixed part of three rounds)
+        assert float(stats["balance"]) <= 1.05, stats["balance"]
 
 
 def _random_upper(n, per_row, seed, long_rows=()):
