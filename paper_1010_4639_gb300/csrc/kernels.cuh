@@ -893,8 +893,9 @@ __device__ __forceinline__ void sym_tiles(const OpDev<V>& A, const SymDev<V>& T,
   }
 }
 
-// Adds the incoming window partial sums to y over the CTA's tiles (warp w
-// takes tiles t0 + w, t0 + w + 16, ...), runs in the layout's fixed order.
+// Adds the listed window partial sums (a row's second and later ones) to y
+// over the CTA's tiles (warp w takes tiles t0 + w, t0 + w + 16, ...), runs in
+// the layout's fixed order.
 template <typename V>
 __device__ __forceinline__ void sym_incoming(const SymDev<V>& T, V* y) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5, c = blockIdx.x;
@@ -1050,8 +1051,9 @@ constexpr size_t product_smem() {
 }
 
 // Computes A x into y for the CTA's rows: complete for kGather / kPlan; for
-// kTiles the CTA's own part, the ext partial sums going to T.part (to be
-// added by k_incoming after every CTA is done).
+// kTiles the CTA's own part, the window partial sums going to T.p1 (a row's
+// first) and T.part (further ones), added by sym_incoming and
+// add_first_partials after every CTA is done.
 template <typename V, int FMT, bool NC>
 __device__ __forceinline__ void product_rows(const OpDev<V>& A, const SymDev<V>& T, int64_t s0, int64_t s1,
                                              int64_t l0, int64_t l1, const V* x, V* y, unsigned char* smem,
